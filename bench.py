@@ -1,0 +1,459 @@
+#!/usr/bin/env python
+"""Throughput of the near-wall refinement hot path on GB300.
+
+One step = the whole path on one synthetic geometry: import (gather to SoA +
+face normals), binning (AABB count, scan, scatter), near-wall refinement of
+every level with child compaction, the finest level's adjacent-face lists and
+its D3Q19 wall links.  Headline value: near-wall cells identified per second
+(adjacent cells summed over all levels), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl reference]
+
+Multi-GPU: the path has no exchange step, so N ranks run N independent
+replicas of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "near-wall cells/s & faces binned/s; batched vs single; adjoint/forward"
+UNIT = "cells/s"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 512 << 20
+
+# Algorithmic work per unit (FP32-pipe operations counted from the kernel source):
+OPS_BLOCK_CANDIDATE = 120.0   # face setup up to the AABB cull (vertex offsets, edges, three box axes)
+OPS_BLOCK_SURVIVOR = 280.0    # the remaining ten axes of the block-level test for a survivor
+OPS_CELL_TEST = 80.0          # one cell against one survivor: 13 axes x (projection + interval test)
+OPS_LINK_FACE = 150.0         # per (adjacent cell, face): double-float offsets, plane offset, cross products
+OPS_LINK_DIR = 40.0           # per (adjacent cell, face, direction): den, three edge signs, t
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--workload", default="c2")
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return p.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append({"sm": float(parts[1]), "max": float(parts[2]), "power": float(parts[3]),
+                             "hw": parts[5], "hwth": parts[6], "swth": parts[7], "swpc": parts[8]})
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sms = sorted(r["sm"] for r in rows)
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwth", "hw_thermal_slowdown"), ("swth", "sw_thermal_slowdown"),
+                            ("swpc", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def near_wall_cells(res):
+    import torch
+
+    tot = 0
+    for lv in res["levels"]:
+        m = lv["mask"]
+        if m.numel() == 0:
+            continue
+        bits = torch.zeros_like(m)
+        x = m.clone()
+        # popcount of 64-bit masks
+        for s in range(64):
+            bits += (x >> s) & 1
+        tot += int(bits.sum().item())
+    return tot
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+    from synth import workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    verts = torch.from_numpy(w.verts).to(dev)
+    idx = torch.from_numpy(w.idx).to(dev)
+    g = AmrGeom(w.dim, (w.root,) * w.dim)
+    stream = g.stream
+
+    def step():
+        g.load(verts, idx)
+        g.bin(w.bins)
+        return g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True)
+
+    for _ in range(max(args.warmup, 1)):
+        res = step()
+    torch.cuda.synchronize()
+    cells = near_wall_cells(res)
+    n_links = int(res["link_q"].shape[0])
+    n_adj = int(res["adj_cell"].shape[0])
+    n_pairs = int(res["adj_ids"].shape[0])
+    n_cand, n_surv = res["n_candidates"], res["n_survivors"]
+    blocks = [int(lv["blocks"].shape[0]) for lv in res["levels"]]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # timed region: K steps, L2 flushed between steps (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = g.launch_count()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = g.launch_count() - launches0
+    barrier()
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = sum(ms) / len(ms)
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = cells * world / (ms_step * 1e-3)
+
+    # per-kernel timing pass (CUDA events around each launch, on the context stream)
+    g.timing(True)
+    g.timing_reset()
+    n_t = max(3, min(10, args.steps))
+    for k in range(n_t):
+        flush.fill_(k & 0xff)
+        step()
+    tk = g.timings()
+    g.timing(False)
+    kern = {name: {"ms_per_step": v[0] / n_t, "launches_per_step": v[1] / n_t} for name, v in tk.items()}
+    t_bin = sum(kern[k]["ms_per_step"] for k in ("bin_count", "bin_scan", "bin_scatter") if k in kern)
+    t_refine = kern.get("refine_level", {}).get("ms_per_step", float("nan"))
+    dom = max(kern.items(), key=lambda kv: kv[1]["ms_per_step"])
+    roof = roofline(dom[0], dom[1], w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {w.description}", "faces": w.n_faces, "levels": w.n_levels,
+                   "bins_per_axis": w.bins, "blocks_per_level": blocks, "near_wall_cells_per_step": cells,
+                   "adjacent_finest_cells": n_adj, "adjacent_pairs": n_pairs, "links": n_links,
+                   "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
+        "faces_binned_per_s": w.n_faces / (t_bin * 1e-3) if t_bin > 0 else None,
+        "cell_face_tests_per_s": (n_surv * (64 if w.dim == 3 else 16)) / (t_refine * 1e-3) if t_refine > 0 else None,
+        "kernels_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in kern.items()},
+        "wall_s": wall,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": roof,
+    }
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(g, w, args, dev)
+    g.close()
+    return line
+
+
+def roofline(name, k, w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks):
+    """Roofline entry for the dominant kernel: algorithmic work per launch / average launch time."""
+    hbm, src = measured_peaks()
+    launches = max(k["launches_per_step"], 1e-9)
+    t = k["ms_per_step"] / launches * 1e-3
+    NC = 64 if w.dim == 3 else 16
+    alu_peak = N_SM * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12  # FP32-pipe Tops/s at the max SM clock
+    if name == "refine_level":
+        ops = (n_cand * OPS_BLOCK_CANDIDATE + n_surv * OPS_BLOCK_SURVIVOR + n_surv * NC * OPS_CELL_TEST) / launches
+        a = ops / t / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s (FP32 pipe)",
+                "frac": a / alu_peak, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2070 MHz"}
+    if name in ("links", "adjacency"):
+        Q1 = 18 if w.dim == 3 else 8
+        if name == "links":
+            ops = n_pairs * (OPS_LINK_FACE + Q1 * OPS_LINK_DIR) / launches
+        else:
+            ops = (n_pairs * OPS_CELL_TEST * 0 + n_surv * NC * OPS_CELL_TEST) / launches
+        a = ops / t / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s (FP32 pipe)",
+                "frac": a / alu_peak, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2070 MHz"}
+    # HBM-bound kernels: algorithmic bytes
+    nb = w.bins ** w.dim
+    D = w.dim
+    byts = {"bin_count": w.n_faces * (4 * D * D + 4 * D) + 8.0 * nb,
+            "bin_scan": 8.0 * nb,
+            "bin_scatter": w.n_faces * (4 * D * D + 4 * D)}.get(name, 0.0) / launches
+    a = byts / t / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+            "traffic": None, "peak_source": src}
+
+
+def run_e2e(g, w, args, dev):
+    """Same metric through the public API with host buffers: H2D of the inputs and D2H of every output."""
+    import torch
+
+    hv = torch.from_numpy(w.verts).pin_memory()
+    hi = torch.from_numpy(w.idx).pin_memory()
+    bi = hv.numel() * 4 + hi.numel() * 4
+    out_bufs = {}
+
+    def step():
+        g.load(hv, hi)
+        g.bin(w.bins)
+        res = g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True)
+        nbytes = 0
+        tensors = []
+        for L, lv in enumerate(res["levels"]):
+            tensors += [lv["blocks"], lv["mask"]]
+        tensors += [res["adj_cell"], res["adj_off"], res["adj_ids"], res["link_cell"], res["link_dir"],
+                    res["link_q"], res["link_face"]]
+        for j, t in enumerate(tensors):
+            buf = out_bufs.get(j)
+            if buf is None or buf.numel() < t.numel() or buf.dtype != t.dtype:
+                buf = torch.empty(max(t.numel(), 1) * 2, dtype=t.dtype).pin_memory()
+                out_bufs[j] = buf
+            buf[:t.numel()].copy_(t.reshape(-1), non_blocking=True)
+            nbytes += t.numel() * t.element_size()
+        return res, nbytes
+
+    for _ in range(max(2, args.warmup)):
+        res, bo = step()
+    torch.cuda.synchronize()
+    cells = near_wall_cells(res)
+    K = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        res, bo = step()
+        torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / K
+    return {"value": cells / dt, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+            "ms_per_step": dt * 1e3, "note": "host wall clock around load(host)->bin->refine->D2H of all outputs"}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sampled_step(w, frac0, rng, max_blocks=400, max_cells=400):
+    """One oracle pass over a seeded subtree sample of the workload.
+
+    Level 0: a random fraction `frac0` of the roots.  Deeper levels: the
+    children of the sampled marked blocks, subsampled to at most `max_blocks`.
+    The finest level's adjacency and links run on at most `max_cells` sampled
+    adjacent cells.  Every time and count is scaled by the inverse inclusion
+    probability, giving an estimate for the whole workload.
+    Returns (estimated seconds, estimated near-wall cells, cpu seconds spent).
+    """
+    import numpy as np
+
+    from oracle.oracle import Domain, OracleGeometry, cells_of_mask, root_blocks
+
+    t_start = time.process_time()
+    geo = OracleGeometry(w.dim, w.verts, w.idx)
+    t0 = time.perf_counter()
+    geo.bin(Domain.unit(w.dim, w.root), w.bins)
+    est_t = time.perf_counter() - t0
+    blocks = root_blocks(w.dim, (w.root,) * w.dim)
+    sel = rng.random(blocks.shape[0]) < frac0
+    blocks = blocks[sel]
+    weight = 1.0 / frac0
+    est_cells = 0.0
+    for L in range(w.n_levels):
+        if blocks.shape[0] > max_blocks:
+            keep = rng.choice(blocks.shape[0], size=max_blocks, replace=False)
+            weight *= blocks.shape[0] / max_blocks
+            blocks = blocks[np.sort(keep)]
+        t0 = time.perf_counter()
+        mask, _, _, _ = geo.refine_blocks(L, blocks, w.d_abs, w.d_rel)
+        est_t += (time.perf_counter() - t0) * weight
+        est_cells += sum(bin(int(m)).count("1") for m in mask) * weight
+        if L + 1 < w.n_levels:
+            blocks, _ = geo.children(blocks, mask)
+    _, _, cells = cells_of_mask(w.dim, blocks, mask)
+    if cells.shape[0]:
+        cw = weight
+        if cells.shape[0] > max_cells:
+            cw *= cells.shape[0] / max_cells
+            cells = cells[rng.choice(cells.shape[0], size=max_cells, replace=False)]
+        t0 = time.perf_counter()
+        geo.cell_faces(w.n_levels - 1, cells, w.d_abs, w.d_rel)
+        geo.cell_links(w.n_levels - 1, w.lattice, cells)
+        est_t += (time.perf_counter() - t0) * cw
+    return est_t, est_cells, time.process_time() - t_start
+
+
+def run_cpu_baseline(w, seconds):
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(7)
+    # grow the sample until it costs a few seconds, then repeat to fill the budget
+    frac, spent, est_ts, est_cs = 1.0 / 256, 0.0, [], []
+    while spent < seconds:
+        et, ec, cpu = oracle_sampled_step(w, frac, rng)
+        spent += cpu
+        est_ts.append(et)
+        est_cs.append(ec)
+        if cpu < 1.0 and frac < 1.0 / 8:
+            frac *= 2
+    et, ec = float(np.mean(est_ts)), float(np.mean(est_cs))
+    return {"value": ec / et, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{len(est_ts)} seeded subtree samples of {w.name} (roots sampled at up to 1/8, <=400 "
+                       f"blocks per level, <=400 finest adjacent cells for faces+links), times and counts scaled "
+                       f"by inverse inclusion probability; {spent:.1f} s CPU"),
+            "est_full_seconds": et, "est_near_wall_cells": ec}
+
+
+def run_reference(args, rank, world):
+    import numpy as np
+
+    from synth import workload
+
+    if rank != 0:
+        return None
+    import oracle
+
+    oracle.build()
+    w = workload(args.workload)
+    rng = np.random.default_rng(11)
+    frac = 1.0 / 64
+    for _ in range(args.warmup):
+        oracle_sampled_step(w, frac, rng)
+    ts, cs, cpu = [], [], 0.0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        et, ec, c = oracle_sampled_step(w, frac, rng)
+        ts.append(et)
+        cs.append(ec)
+        cpu += c
+    wall = time.perf_counter() - t0
+    value = float(np.mean(cs)) / float(np.mean(ts))
+    sample = (f"each step: seeded subtree sample of {w.name} (1/64 of roots, <=400 blocks per level, <=400 finest "
+              f"adjacent cells), oracle times scaled to the full workload")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(ts)) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {w.description}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
+    import torch
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = run_ours(args, rank, world, local)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from synth import workload
+
+        line["cpu_baseline"] = run_cpu_baseline(workload(args.workload), args.cpu_seconds)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

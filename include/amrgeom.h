@@ -1,0 +1,191 @@
+/* amrgeom.h — C ABI of the GB300 geometry-to-AMR near-wall refinement library.
+ *
+ * The library implements the data-parallel hot path of the geometry module in
+ * Jaber, Essel & Sullivan, "Towards a GPU-native adaptive mesh refinement scheme
+ * for the Lattice Boltzmann Method in complex geometries" (2025), whose
+ * procedure has three steps (Abstract; Sec. "Methodology"):
+ *   1. import the faces (edges in 2D, triangles in 3D) as an index list or a
+ *      face-vertex coordinate list            -> amr_geom_load
+ *   2. spatially bin the faces into B^D bins   -> amr_bin_faces
+ *   3. near-wall refinement of a forest of octrees (blocks of 4^D cells): every
+ *      cell detects adjacency to the faces of the bins around it, marked blocks
+ *      are split, and the finest cells list their faces and form wall links
+ *      along the lattice directions         -> amr_refine_near_wall
+ * plus the vertex adjoint of the link fractions q (amr_q_backward).
+ *
+ * Conventions
+ *   - Domain box: origin[a] + [0, 4*root_blocks[a]*h0] per axis.  Level-L cell
+ *     size h_L = h0 * 2^-L.  Block (b0,b1,b2) of level L holds cells 4b..4b+3.
+ *   - Cell bit within a block: i + 4j (+ 16k), x fastest.  Level-0 blocks in
+ *     x-fastest lexicographic order; the children of the marked blocks of level
+ *     L follow in parent order, child slot s = bx + 2by (+ 4bz).
+ *   - Adjacency (Sec. "Face Detection", box form): a cell is adjacent to a face
+ *     when its box inflated by d_L = d_abs + d_rel*h_L meets the closed face.
+ *   - Bins (Sec. "Spatial Binning Algorithm"): a face is stored in every bin its
+ *     axis-aligned bounding box overlaps (bins half-open, outer bins unbounded).
+ *   - Lattice directions: D2Q9 1..8 = (1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),
+ *     (-1,-1),(1,-1); D3Q19 1..6 = +x,-x,+y,-y,+z,-z, 7..18 = xy, xz, yz plane
+ *     diagonals, each (+,+),(-,-),(+,-),(-,+).
+ *
+ * Ownership and threading
+ *   - The caller owns every input it passes; inputs are copied before the call
+ *     returns its status.  Pointers may be host or device memory (detected).
+ *   - Output views are BORROWED device pointers owned by the context, valid
+ *     until the next call of the same step or amr_destroy.
+ *   - All work is ordered on the context's stream.  A context is not
+ *     thread-safe; use one context per host thread.
+ *   - Every call returns a status and never aborts.  A failed device-side check
+ *     (bad index, non-finite coordinate, a bounded wait that ran out) is reported
+ *     by the call that synchronises after it.
+ */
+#ifndef AMRGEOM_H
+#define AMRGEOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMR_MAX_LEVELS 16
+
+#if defined(__GNUC__)
+#define AMR_API __attribute__((visibility("default")))
+#else
+#define AMR_API
+#endif
+
+typedef struct amr_ctx amr_ctx;
+
+typedef enum {
+  AMR_OK = 0,
+  AMR_EINVAL = 1,        /* invalid argument or input data */
+  AMR_ENOMEM = 2,        /* device or host allocation failed */
+  AMR_ECUDA = 3,         /* a CUDA runtime call failed (see amr_last_error) */
+  AMR_EOVERFLOW = 4,     /* a size exceeded its representable range (e.g. > 2^32 bin entries) */
+  AMR_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+  AMR_ESTATE = 6,        /* calls out of order (load -> bin -> refine -> backward) */
+  AMR_EDEVICE_CHECK = 7  /* a device-side input check failed */
+} amr_status;
+
+typedef struct {
+  int dim;               /* 2 or 3 */
+  int root_blocks[3];    /* root blocks per axis (entries beyond dim ignored), each >= 1 */
+  double origin[3];      /* domain origin */
+  double h0;             /* level-0 cell size, > 0 */
+  void* stream;          /* cudaStream_t to order all work on; NULL = a stream the context creates */
+} amr_domain;
+
+/* Create a context on the current CUDA device.  *out receives the handle.
+ * EINVAL: bad dim / root_blocks / h0.  ECUDA: no usable device. */
+AMR_API amr_status amr_create(const amr_domain* dom, amr_ctx** out);
+
+/* Free every device and host buffer of the context.  NULL is accepted. */
+AMR_API amr_status amr_destroy(amr_ctx* ctx);
+
+/* Static description of a status code. */
+AMR_API const char* amr_status_str(amr_status s);
+
+/* Detail text of the last error raised on this context ("" if none). */
+AMR_API const char* amr_last_error(const amr_ctx* ctx);
+
+/* Replace the stream all later work is ordered on (NULL = the context's own). */
+AMR_API amr_status amr_set_stream(amr_ctx* ctx, void* stream);
+
+/* Step 1 — import (Sec. "Representation of the Complex Boundary Geometry").
+ * idx == NULL: `coords` is a face-vertex list f32[n_faces][dim][dim].
+ * idx != NULL: `coords` = vertices f32[n_verts][dim], idx = i32[n_faces][dim].
+ * The faces are gathered into a resident structure-of-arrays copy on the device
+ * (the paper's geom_f_face_X) together with per-face double-float normals.
+ * 0 <= n_faces < 2^29.  EINVAL: bad sizes, null pointers; EDEVICE_CHECK: an index
+ * out of [0, n_verts) or a non-finite coordinate (detected on the device). */
+AMR_API amr_status amr_geom_load(amr_ctx* ctx, const float* coords, int64_t n_verts, const int32_t* idx,
+                         int64_t n_faces);
+
+/* Step 2 — binning (Sec. "Spatial Binning Algorithm": binned_face_ids_N,
+ * binned_face_ids).  B = bin_density bins per axis over the domain box, B >= 1
+ * (B = 1 is the paper's naive scheme), B^dim <= 2^30.  Bin b = bx + B*by (+ B^2*bz).
+ * offsets[b]..offsets[b+1] index the face ids of bin b in `ids`; the order
+ * within a bin is unspecified (atomic scatter).  EOVERFLOW: more than 2^32 - 1
+ * (face, bin) entries. */
+typedef struct {
+  int B;
+  int64_t n_bins;             /* B^dim */
+  int64_t nnz;                /* total (face, bin) entries */
+  const uint32_t* offsets;    /* device [n_bins + 1] */
+  const uint32_t* ids;        /* device [nnz] */
+} amr_bins_view;
+AMR_API amr_status amr_bin_faces(amr_ctx* ctx, int bin_density, amr_bins_view* out);
+
+/* Step 3 — near-wall refinement (Sec. "Cell-Face Identification Algorithms").
+ * n_levels total levels (n_levels - 1 refinement passes), 1 <= n_levels <= AMR_MAX_LEVELS.
+ * lattice: 0 (no links), 9 (D2Q9, dim 2) or 19 (D3Q19, dim 3).
+ * want_links requires want_adjacency and d_L >= h_L/2 on the finest level, so
+ * that every face a link crosses is in the cell's adjacency list. */
+typedef struct {
+  int n_levels;
+  double d_abs;               /* near-wall distance d_L = d_abs + d_rel * h_L, >= 0 */
+  double d_rel;
+  int lattice;
+  int want_adjacency;
+  int want_links;
+} amr_refine_params;
+
+/* Results.  Level arrays are per level 0..n_levels-1.
+ *   block_coords[L]  device i32 [N_L][dim]
+ *   block_parent[L]  device i32 [N_L], index of the parent in level L-1 (NULL for L = 0)
+ *   cell_mask[L]     device u64 [N_L], adjacency bit per cell (low 16 bits in 2D)
+ *   block_flag[L]    device u8  [N_L], 1 when the block is marked (mask != 0)
+ * Finest level (when want_adjacency):
+ *   adj_cell   device u32 [n_adj_cells]: block index * 4^dim + cell bit, ascending
+ *   adj_off    device u32 [n_adj_cells + 1]: CSR offsets into adj_ids
+ *   adj_ids    device u32 [n_adj_pairs]: adjacent face ids, ascending per cell
+ * Links (when want_links), sorted by (cell, direction):
+ *   link_cell  device u32 [n_links]: row of the adjacent cell in adj_cell
+ *   link_dir   device u8  [n_links]: lattice direction 1..Q-1
+ *   link_q     device f32 [n_links]: smallest t in [0,1] with centre + t*c_i*h on a face
+ *   link_face  device u32 [n_links]: the face hit at q (smallest id on ties)
+ * Diagnostics: n_fallback = close decisions re-evaluated in FP64; n_band = those
+ * whose FP64 margin was within 1e-6*h (adjacency) or 1e-6 (links) of the boundary. */
+typedef struct {
+  int n_levels;
+  int64_t n_blocks[AMR_MAX_LEVELS];
+  const int32_t* block_coords[AMR_MAX_LEVELS];
+  const int32_t* block_parent[AMR_MAX_LEVELS];
+  const uint64_t* cell_mask[AMR_MAX_LEVELS];
+  const uint8_t* block_flag[AMR_MAX_LEVELS];
+  int64_t n_adj_cells;
+  int64_t n_adj_pairs;
+  const uint32_t* adj_cell;
+  const uint32_t* adj_off;
+  const uint32_t* adj_ids;
+  int64_t n_links;
+  const uint32_t* link_cell;
+  const uint8_t* link_dir;
+  const float* link_q;
+  const uint32_t* link_face;
+  int64_t n_fallback;
+  int64_t n_band;
+  int64_t n_candidates;       /* (block, face) candidate pairs read from the bins, all levels */
+  int64_t n_survivors;        /* candidates that passed the block-level test */
+} amr_refine_result;
+AMR_API amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* params, amr_refine_result* out);
+
+/* Wait for all work of the context; report device-side check failures. */
+AMR_API amr_status amr_sync(amr_ctx* ctx);
+
+/* Per-kernel timing with CUDA events on the context stream (off by default).
+ * amr_timing_get fills up to `cap` entries in launch-table order and returns
+ * how many kernels have been timed; names are static strings. */
+AMR_API amr_status amr_timing_enable(amr_ctx* ctx, int on);
+AMR_API amr_status amr_timing_reset(amr_ctx* ctx);
+AMR_API int amr_timing_get(amr_ctx* ctx, const char** names, double* total_ms, int64_t* launches, int cap);
+
+/* Number of CUDA kernels this context has launched since its creation. */
+AMR_API int64_t amr_launch_count(const amr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,25 @@
+"""GB300-native near-wall refinement of a forest-of-octrees grid around a triangle (segment) mesh.
+
+Data-parallel hot path of Jaber, Essel & Sullivan (2025), "Towards a GPU-native
+adaptive mesh refinement scheme for the Lattice Boltzmann Method in complex
+geometries": import -> spatial binning -> near-wall refinement with adjacent-face
+lists and lattice wall links.  The compute runs in hand-written sm_103a CUDA
+kernels behind the C ABI of ``include/amrgeom.h``; this package is its binding.
+"""
+from .binding import (  # noqa: F401
+    EXPORTED,
+    AmrError,
+    AmrGeom,
+    amr_bin_faces,
+    amr_create,
+    amr_destroy,
+    amr_geom_load,
+    amr_launch_count,
+    amr_refine_near_wall,
+    amr_set_stream,
+    amr_sync,
+    amr_timing_enable,
+    amr_timing_get,
+    amr_timing_reset,
+    lib,
+)

@@ -1,0 +1,329 @@
+"""ctypes binding of ``libamrgeom.so`` (C ABI in ``include/amrgeom.h``).
+
+Argument marshalling only: every step of the refinement runs in the library's
+CUDA kernels.  The functions keep the C names (``amr_create``,
+``amr_geom_load``, ``amr_bin_faces``, ``amr_refine_near_wall`` ...).
+``AmrGeom`` wraps one context for PyTorch users: inputs may be torch tensors
+(CPU or CUDA) or numpy arrays, and outputs come back as zero-copy CUDA tensors
+that borrow the context's buffers (``.clone()`` them to keep them past the next
+call).  There is no CPU fallback: without the built library and a CUDA device
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libamrgeom.so")
+MAX_LEVELS = 16
+
+_lib = None
+_lock = threading.Lock()
+
+AMR_OK, AMR_EINVAL, AMR_ENOMEM, AMR_ECUDA, AMR_EOVERFLOW, AMR_ETIMEOUT, AMR_ESTATE, AMR_EDEVICE_CHECK = range(8)
+STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECUDA", 4: "AMR_EOVERFLOW",
+                5: "AMR_ETIMEOUT", 6: "AMR_ESTATE", 7: "AMR_EDEVICE_CHECK"}
+
+EXPORTED = ["amr_create", "amr_destroy", "amr_status_str", "amr_last_error", "amr_set_stream", "amr_geom_load",
+            "amr_bin_faces", "amr_refine_near_wall", "amr_sync", "amr_timing_enable", "amr_timing_reset",
+            "amr_timing_get", "amr_launch_count"]
+
+
+class AmrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class amr_domain(C.Structure):
+    _fields_ = [("dim", C.c_int), ("root_blocks", C.c_int * 3), ("origin", C.c_double * 3), ("h0", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class amr_bins_view(C.Structure):
+    _fields_ = [("B", C.c_int), ("n_bins", C.c_int64), ("nnz", C.c_int64), ("offsets", C.c_void_p),
+                ("ids", C.c_void_p)]
+
+
+class amr_refine_params(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("d_abs", C.c_double), ("d_rel", C.c_double), ("lattice", C.c_int),
+                ("want_adjacency", C.c_int), ("want_links", C.c_int)]
+
+
+class amr_refine_result(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("n_blocks", C.c_int64 * MAX_LEVELS),
+                ("block_coords", C.c_void_p * MAX_LEVELS), ("block_parent", C.c_void_p * MAX_LEVELS),
+                ("cell_mask", C.c_void_p * MAX_LEVELS), ("block_flag", C.c_void_p * MAX_LEVELS),
+                ("n_adj_cells", C.c_int64), ("n_adj_pairs", C.c_int64), ("adj_cell", C.c_void_p),
+                ("adj_off", C.c_void_p), ("adj_ids", C.c_void_p), ("n_links", C.c_int64),
+                ("link_cell", C.c_void_p), ("link_dir", C.c_void_p), ("link_q", C.c_void_p),
+                ("link_face", C.c_void_p), ("n_fallback", C.c_int64), ("n_band", C.c_int64),
+                ("n_candidates", C.c_int64), ("n_survivors", C.c_int64)]
+
+
+def lib(build_if_missing: bool = True):
+    """Load (building first when missing or stale and nvcc is available) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+
+        if build_if_missing:
+            try:
+                _build.build()
+            except Exception as e:  # no nvcc or a compile error: only an existing library may be used
+                if not os.path.exists(LIB_PATH):
+                    raise ImportError(f"libamrgeom.so is not built and cannot be built here: {e}") from e
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libamrgeom.so is not built; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P, i64 = C.c_void_p, C.c_int64
+        L.amr_create.restype = C.c_int
+        L.amr_create.argtypes = [C.POINTER(amr_domain), C.POINTER(P)]
+        L.amr_destroy.restype = C.c_int
+        L.amr_destroy.argtypes = [P]
+        L.amr_status_str.restype = C.c_char_p
+        L.amr_status_str.argtypes = [C.c_int]
+        L.amr_last_error.restype = C.c_char_p
+        L.amr_last_error.argtypes = [P]
+        L.amr_set_stream.restype = C.c_int
+        L.amr_set_stream.argtypes = [P, P]
+        L.amr_geom_load.restype = C.c_int
+        L.amr_geom_load.argtypes = [P, P, i64, P, i64]
+        L.amr_bin_faces.restype = C.c_int
+        L.amr_bin_faces.argtypes = [P, C.c_int, C.POINTER(amr_bins_view)]
+        L.amr_refine_near_wall.restype = C.c_int
+        L.amr_refine_near_wall.argtypes = [P, C.POINTER(amr_refine_params), C.POINTER(amr_refine_result)]
+        L.amr_sync.restype = C.c_int
+        L.amr_sync.argtypes = [P]
+        L.amr_timing_enable.restype = C.c_int
+        L.amr_timing_enable.argtypes = [P, C.c_int]
+        L.amr_timing_reset.restype = C.c_int
+        L.amr_timing_reset.argtypes = [P]
+        L.amr_timing_get.restype = C.c_int
+        L.amr_timing_get.argtypes = [P, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(i64), C.c_int]
+        L.amr_launch_count.restype = C.c_int64
+        L.amr_launch_count.argtypes = [P]
+        _lib = L
+        return L
+
+
+def _check(ctx, st: int):
+    if st != AMR_OK:
+        L = lib()
+        msg = L.amr_last_error(ctx).decode() if ctx else L.amr_status_str(st).decode()
+        raise AmrError(st, msg)
+
+
+# -- C-named entry points ------------------------------------------------------
+
+def amr_create(dim: int, root_blocks, origin=(0.0, 0.0, 0.0), h0: float | None = None, stream: int | None = None):
+    L = lib()
+    d = amr_domain()
+    d.dim = dim
+    rb = list(root_blocks) + [1] * (3 - len(root_blocks))
+    for a in range(3):
+        d.root_blocks[a] = int(rb[a])
+        d.origin[a] = float(origin[a]) if a < len(origin) else 0.0
+    d.h0 = float(h0 if h0 is not None else 1.0 / (4.0 * rb[0]))
+    d.stream = stream
+    h = C.c_void_p()
+    st = L.amr_create(C.byref(d), C.byref(h))
+    if st != AMR_OK:
+        raise AmrError(st, L.amr_status_str(st).decode())
+    return h
+
+
+def amr_destroy(ctx):
+    _check(None, lib().amr_destroy(ctx))
+
+
+def amr_set_stream(ctx, stream: int | None):
+    _check(ctx, lib().amr_set_stream(ctx, stream))
+
+
+def amr_geom_load(ctx, coords_ptr: int, n_verts: int, idx_ptr: int | None, n_faces: int):
+    _check(ctx, lib().amr_geom_load(ctx, coords_ptr, int(n_verts), idx_ptr, int(n_faces)))
+
+
+def amr_bin_faces(ctx, bin_density: int) -> amr_bins_view:
+    v = amr_bins_view()
+    _check(ctx, lib().amr_bin_faces(ctx, int(bin_density), C.byref(v)))
+    return v
+
+
+def amr_refine_near_wall(ctx, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True,
+                         want_links=True) -> amr_refine_result:
+    p = amr_refine_params()
+    p.n_levels, p.d_abs, p.d_rel, p.lattice = int(n_levels), float(d_abs), float(d_rel), int(lattice)
+    p.want_adjacency, p.want_links = int(bool(want_adjacency)), int(bool(want_links))
+    r = amr_refine_result()
+    _check(ctx, lib().amr_refine_near_wall(ctx, C.byref(p), C.byref(r)))
+    return r
+
+
+def amr_sync(ctx):
+    _check(ctx, lib().amr_sync(ctx))
+
+
+def amr_timing_enable(ctx, on: bool):
+    _check(ctx, lib().amr_timing_enable(ctx, int(bool(on))))
+
+
+def amr_timing_reset(ctx):
+    _check(ctx, lib().amr_timing_reset(ctx))
+
+
+def amr_timing_get(ctx) -> dict:
+    L = lib()
+    n = L.amr_timing_get(ctx, None, None, None, 0)
+    names = (C.c_char_p * max(n, 1))()
+    ms = (C.c_double * max(n, 1))()
+    cnt = (C.c_int64 * max(n, 1))()
+    n = L.amr_timing_get(ctx, names, ms, cnt, n)
+    return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(n)}
+
+
+def amr_launch_count(ctx) -> int:
+    return int(lib().amr_launch_count(ctx))
+
+
+# -- torch convenience layer ----------------------------------------------------
+
+class _DevArray:
+    """Minimal __cuda_array_interface__ holder for a borrowed device pointer."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3, "strides": None}
+
+
+def _view(ptr, shape, dtype):
+    import torch
+
+    n = int(np.prod(shape)) if len(shape) else 1
+    if n == 0 or not ptr:
+        return torch.empty(tuple(shape), dtype=dtype, device="cuda")
+    typestr = {torch.float32: "<f4", torch.int32: "<i4", torch.int64: "<i8", torch.uint8: "|u1"}[dtype]
+    t = torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
+    return t
+
+
+def _u32(ptr, n):
+    # torch has limited uint32 support: expose as int32 bits, then widen to int64 for convenience
+    import torch
+
+    return _view(ptr, (n,), torch.int32)
+
+
+class AmrGeom:
+    """One refinement context: ``load`` -> ``bin`` -> ``refine`` on the current CUDA device.
+
+    The context's work is ordered on the current torch CUDA stream at creation.
+    """
+
+    def __init__(self, dim: int, root_blocks, origin=(0.0, 0.0, 0.0), h0: float | None = None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("AmrGeom needs a CUDA device")
+        self.dim = dim
+        self.root = tuple(int(r) for r in (root_blocks if hasattr(root_blocks, "__len__") else [root_blocks] * dim))
+        self.stream = torch.cuda.current_stream()
+        # torch's default stream has handle 0; pass the legacy default stream (handle 1) so the
+        # context's work stays ordered with torch's own kernels and copies
+        handle = self.stream.cuda_stream or 1
+        self.ctx = amr_create(dim, self.root, origin, h0, handle)
+        self._keep = []
+        self.bins = None
+        self.result = None
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            amr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, verts, idx=None):
+        """Step 1: faces from vertices + index list (idx) or a face-vertex list (idx None)."""
+        import torch
+
+        v = torch.as_tensor(verts, dtype=torch.float32)
+        if not v.is_contiguous():
+            v = v.contiguous()
+        self._keep = [v]
+        if idx is None:
+            nf = v.shape[0]
+            amr_geom_load(self.ctx, v.data_ptr(), 0, None, nf)
+        else:
+            ix = torch.as_tensor(idx, dtype=torch.int32)
+            if not ix.is_contiguous():
+                ix = ix.contiguous()
+            self._keep.append(ix)
+            amr_geom_load(self.ctx, v.data_ptr(), v.shape[0], ix.data_ptr(), ix.shape[0])
+        return self
+
+    def bin(self, B: int):
+        """Step 2: CSR bins; returns dict(offsets, ids) as borrowed int32 CUDA tensors (uint32 bits)."""
+        v = amr_bin_faces(self.ctx, B)
+        self.bins = {"B": v.B, "n_bins": v.n_bins, "nnz": v.nnz,
+                     "offsets": _u32(v.offsets, v.n_bins + 1), "ids": _u32(v.ids, v.nnz)}
+        return self.bins
+
+    def refine(self, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=None):
+        """Step 3: near-wall refinement; returns per-level tensors, adjacency CSR and links (borrowed)."""
+        import torch
+
+        if want_links is None:
+            want_links = lattice != 0
+        r = amr_refine_near_wall(self.ctx, n_levels, d_abs, d_rel, lattice, want_adjacency, want_links)
+        D = self.dim
+        levels = []
+        for L in range(r.n_levels):
+            n = int(r.n_blocks[L])
+            levels.append({
+                "blocks": _view(r.block_coords[L], (n, D), torch.int32),
+                "parent": _view(r.block_parent[L], (n,), torch.int32) if L > 0 else None,
+                "mask": _view(r.cell_mask[L], (n,), torch.int64),
+                "flag": _view(r.block_flag[L], (n,), torch.uint8),
+            })
+        out = {"levels": levels, "n_fallback": int(r.n_fallback), "n_band": int(r.n_band),
+               "n_candidates": int(r.n_candidates), "n_survivors": int(r.n_survivors)}
+        if want_adjacency or want_links:
+            na, npairs = int(r.n_adj_cells), int(r.n_adj_pairs)
+            out["adj_cell"] = _u32(r.adj_cell, na)
+            out["adj_off"] = _u32(r.adj_off, na + 1)
+            out["adj_ids"] = _u32(r.adj_ids, npairs)
+        if want_links:
+            nl = int(r.n_links)
+            out["link_cell"] = _u32(r.link_cell, nl)
+            out["link_dir"] = _view(r.link_dir, (nl,), torch.uint8)
+            out["link_q"] = _view(r.link_q, (nl,), torch.float32)
+            out["link_face"] = _u32(r.link_face, nl)
+        self.result = out
+        return out
+
+    def sync(self):
+        amr_sync(self.ctx)
+
+    def timing(self, on: bool = True):
+        amr_timing_enable(self.ctx, on)
+
+    def timing_reset(self):
+        amr_timing_reset(self.ctx)
+
+    def timings(self) -> dict:
+        return amr_timing_get(self.ctx)
+
+    def launch_count(self) -> int:
+        return amr_launch_count(self.ctx)

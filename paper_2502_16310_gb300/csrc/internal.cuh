@@ -1,0 +1,212 @@
+// internal.cuh — device helpers and kernel launchers shared by the CUDA sources
+// of the near-wall refinement library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace amr {
+
+constexpr float kU32 = 5.9604644775390625e-8f;  // FP32 unit roundoff 2^-24
+constexpr double kBandRel = 1e-6;               // margin band of the adjacency (x h) and link tests
+constexpr int kMaxFaces = 1 << 29;              // face ids keep 3 flag bits in the bin payload
+constexpr uint32_t kIdMask = (1u << 29) - 1u;
+constexpr long long kSpinLimit = 1ll << 24;     // bounded waits: iterations before giving up
+
+// device error word bits
+enum : unsigned {
+  ERR_TIMEOUT = 1u,
+  ERR_OVERFLOW = 2u,
+  ERR_BADINDEX = 4u,
+  ERR_NONFINITE = 8u,
+};
+
+// diagnostic counters (device, u64 each)
+enum : int {
+  CNT_FALLBACK = 0,
+  CNT_BAND = 1,
+  CNT_CANDIDATES = 2,
+  CNT_SURVIVORS = 3,
+  CNT_LINK_FALLBACK = 4,
+  CNT_LINK_BAND = 5,
+  CNT_N = 8,
+};
+
+// Bin-grid parameters: bin of coordinate x along axis a is
+// clamp(floor((x - origin[a]) * scale[a]), 0, B - 1) evaluated in FP64.
+struct BinGrid {
+  int B;
+  double origin[3];
+  double scale[3];
+};
+
+// One bin entry with its face's coordinates, so that a bin's faces are one
+// contiguous run of memory (bulk-copyable).  `id` holds the face id in the low
+// 29 bits and, in bits 29..31, whether this bin is the first of the face's bin
+// range along x / y / z (used to visit each face once per query box).
+struct __align__(16) Entry3 {
+  float v[9];
+  uint32_t id;
+  uint32_t pad[2];
+};
+struct __align__(16) Entry2 {
+  float v[4];
+  uint32_t id;
+  uint32_t pad[3];
+};
+
+template <int D>
+struct EntryT;
+template <>
+struct EntryT<3> {
+  using type = Entry3;
+};
+template <>
+struct EntryT<2> {
+  using type = Entry2;
+};
+
+__device__ __forceinline__ int bin_coord(double x, double o, double s, int B) {
+  const double t = floor(__dmul_rn(__dsub_rn(x, o), s));
+  if (!(t >= 0.0)) return 0;
+  if (t > (double)(B - 1)) return B - 1;
+  return (int)t;
+}
+
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// Decoupled look-back over ticket-ordered tiles (single-pass prefix sums).
+// state[t] = flag(2 bits: 1 aggregate, 2 inclusive prefix) << 62 | value.
+// Called by thread 0 of the CTA with the tile's aggregate; returns the
+// exclusive prefix of the tile.  A wait that exceeds kSpinLimit polls sets
+// ERR_TIMEOUT and returns what it has (the caller's output is then invalid,
+// and the host reports AMR_ETIMEOUT).
+__device__ __forceinline__ uint64_t lookback_exclusive(uint64_t* state, long long tile, uint64_t aggregate,
+                                                       unsigned* err) {
+  constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kVal = (1ull << 62) - 1;
+  if (tile == 0) {
+    atomicExch(reinterpret_cast<unsigned long long*>(state), (unsigned long long)(kInc | (aggregate & kVal)));
+    return 0;
+  }
+  atomicExch(reinterpret_cast<unsigned long long*>(state + tile), (unsigned long long)(kAgg | (aggregate & kVal)));
+  uint64_t prefix = 0;
+  long long t = tile - 1;
+  long long spins = 0;
+  while (t >= 0) {
+    const uint64_t s = ld_volatile_u64(state + t);
+    const uint64_t f = s >> 62;
+    if (f == 0) {
+      if (++spins > kSpinLimit) {
+        atomicOr(err, ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(20);
+      continue;
+    }
+    prefix += s & kVal;
+    if (f == 2) break;
+    --t;
+  }
+  atomicExch(reinterpret_cast<unsigned long long*>(state + tile),
+             (unsigned long long)(kInc | ((prefix + aggregate) & kVal)));
+  return prefix;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T n = __shfl_up_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) >= o) v += n;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (host side).  All are asynchronous on `st`.
+// ---------------------------------------------------------------------------
+struct LaunchInfo {
+  int num_sms;
+};
+
+int launch_load_indexed(int dim, const float* verts, int64_t nv, const int32_t* idx, int64_t nf, float* X,
+                         unsigned* err, cudaStream_t st);
+int launch_load_facelist(int dim, const float* coords, int64_t nf, float* X, unsigned* err, cudaStream_t st);
+int launch_face_normals(const float* X, int64_t nf, float* nrm, cudaStream_t st);
+int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint32_t* frange, uint32_t* count,
+                      cudaStream_t st);
+// exclusive scan of n u32 values; out[n] = total (low 32 bits); total64 (device) = full total
+size_t scan_u32_scratch_bytes(int64_t n);
+int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* total64, void* scratch, unsigned* err,
+                     cudaStream_t st);
+size_t scan_u64_scratch_bytes(int64_t n);
+int launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* total, void* scratch, unsigned* err,
+                     cudaStream_t st);
+int launch_scatter(int dim, const float* X, int64_t nf, const uint32_t* frange, const uint32_t* offsets,
+                    uint32_t* count, uint32_t* ids, void* payload, int B, cudaStream_t st);
+
+struct RefineLevel {
+  int dim;
+  const int32_t* blocks;
+  int64_t n_blocks;
+  const uint32_t* offsets;
+  const void* payload;
+  const float* X;
+  const float* nrm;
+  int64_t nf;
+  BinGrid grid;
+  double origin[3];
+  double h;
+  double d;
+  uint64_t* mask;
+  uint8_t* flag;
+  uint16_t* cellcnt;   // per cell face count (finest level with adjacency) or null
+  uint64_t* blockcnt;  // per block (pairs | adjacent cells << 32) or null
+  unsigned long long* counters;
+  unsigned* work;      // dynamic work counter (zeroed before launch)
+  unsigned* err;       // device error word
+};
+int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st);
+
+struct EmitArgs {
+  RefineLevel lv;
+  const uint64_t* block_base;  // exclusive scan of blockcnt
+  uint32_t* adj_cell;
+  uint32_t* adj_off;
+  uint32_t* adj_ids;
+};
+int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st);
+
+size_t children_scratch_bytes(int64_t n);
+int launch_children(int dim, const int32_t* blocks, const uint64_t* mask, int64_t n, int32_t* child_blocks,
+                     int32_t* child_parent, uint64_t* total, void* scratch, unsigned* err, cudaStream_t st);
+int launch_root_blocks(int dim, const int* root, int32_t* blocks, int64_t n, cudaStream_t st);
+
+struct LinkArgs {
+  int dim;
+  int lattice;
+  const int32_t* blocks;       // finest-level blocks
+  const uint32_t* adj_cell;
+  const uint32_t* adj_off;
+  const uint32_t* adj_ids;
+  int64_t n_adj;
+  const float* X;
+  const float* nrm;
+  int64_t nf;
+  double origin[3];
+  double h;
+  uint32_t* link_cell;
+  uint8_t* link_dir;
+  float* link_q;
+  uint32_t* link_face;
+  int64_t link_cap;
+  uint64_t* n_links;           // device total
+  unsigned long long* counters;
+  unsigned* err;
+};
+size_t links_scratch_bytes(int64_t n_adj);
+int launch_links(const LinkArgs& a, void* scratch, cudaStream_t st);
+
+}  // namespace amr

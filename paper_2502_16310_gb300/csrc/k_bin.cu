@@ -1,0 +1,323 @@
+// k_bin.cu — import and spatial binning kernels.
+//
+// Import (Sec. "Representation of the Complex Boundary Geometry"): the index
+// list or the face-vertex list is gathered into one resident structure-of-arrays
+// copy X[k][c][f] (vertex k, coordinate c, face f), the paper's geom_f_face_X.
+//
+// Binning (Sec. "Spatial Binning Algorithm"): the paper fills a per-face bin
+// indicator array chunk by chunk (Cu_FillBins) and compacts it with Thrust.
+// Here the bins are exact and sized in one pass: a face-AABB kernel counts the
+// (face, bin) incidences with atomics, a single-pass decoupled look-back scan
+// turns counts into the CSR start indices (binned_face_ids_N), and a scatter
+// writes face ids plus a contiguous per-bin copy of the face coordinates.
+#include "internal.cuh"
+
+namespace amr {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+template <int D>
+__global__ void k_load_indexed(const float* __restrict__ verts, int64_t nv, const int32_t* __restrict__ idx,
+                               int64_t nf, float* __restrict__ X, unsigned* err) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      int64_t vi = idx[f * D + k];
+      const bool ok = vi >= 0 && vi < nv;
+      if (!ok) {
+        atomicOr(err, ERR_BADINDEX);
+        vi = 0;
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        float x = ok ? verts[vi * D + c] : 0.0f;
+        if (!isfinite(x)) {
+          atomicOr(err, ERR_NONFINITE);
+          x = 0.0f;
+        }
+        X[(int64_t)(k * D + c) * nf + f] = x;
+      }
+    }
+  }
+}
+
+template <int D>
+__global__ void k_load_facelist(const float* __restrict__ coords, int64_t nf, float* __restrict__ X, unsigned* err) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < D * D; ++j) {
+      float x = coords[f * D * D + j];
+      if (!isfinite(x)) {
+        atomicOr(err, ERR_NONFINITE);
+        x = 0.0f;
+      }
+      X[(int64_t)j * nf + f] = x;
+    }
+  }
+}
+
+// Face normal n = (v1 - v0) x (v2 - v0) evaluated in FP64 (the edge differences
+// and the products of FP32 inputs are exact there) and stored as an unevaluated
+// FP32 sum hi + lo, so that later FP32 kernels can form plane offsets with
+// double-float accuracy.  Layout nrm[6][nf] = hi.xyz, lo.xyz.
+__global__ void k_face_normals(const float* __restrict__ X, int64_t nf, float* __restrict__ nrm) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    double v[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[k][c] = (double)X[(int64_t)(k * 3 + c) * nf + f];
+    const double u0 = __dsub_rn(v[1][0], v[0][0]), u1 = __dsub_rn(v[1][1], v[0][1]), u2 = __dsub_rn(v[1][2], v[0][2]);
+    const double w0 = __dsub_rn(v[2][0], v[0][0]), w1 = __dsub_rn(v[2][1], v[0][1]), w2 = __dsub_rn(v[2][2], v[0][2]);
+    const double n[3] = {__dsub_rn(__dmul_rn(u1, w2), __dmul_rn(u2, w1)),
+                         __dsub_rn(__dmul_rn(u2, w0), __dmul_rn(u0, w2)),
+                         __dsub_rn(__dmul_rn(u0, w1), __dmul_rn(u1, w0))};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float hi = (float)n[c];
+      const float lo = (float)(n[c] - (double)hi);
+      nrm[(int64_t)c * nf + f] = hi;
+      nrm[(int64_t)(3 + c) * nf + f] = lo;
+    }
+  }
+}
+
+// Per face: bin range of its AABB along each axis (packed lo | hi << 16) and one
+// count per (face, bin) incidence.
+template <int D>
+__global__ void k_face_bins(const float* __restrict__ X, int64_t nf, BinGrid g, uint32_t* __restrict__ frange,
+                            uint32_t* __restrict__ count) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      float mn = X[(int64_t)a * nf + f], mx = mn;
+#pragma unroll
+      for (int k = 1; k < D; ++k) {
+        const float x = X[(int64_t)(k * D + a) * nf + f];
+        mn = fminf(mn, x);
+        mx = fmaxf(mx, x);
+      }
+      lo[a] = bin_coord((double)mn, g.origin[a], g.scale[a], g.B);
+      hi[a] = bin_coord((double)mx, g.origin[a], g.scale[a], g.B);
+      frange[(int64_t)a * nf + f] = (uint32_t)lo[a] | ((uint32_t)hi[a] << 16);
+    }
+    const int64_t B = g.B;
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&count[x + B * (y + B * (int64_t)z)], 1u);
+  }
+}
+
+// Scatter: every (face, bin) incidence claims a slot of the bin by decrementing
+// the bin's count (which leaves the counts zeroed for the next call) and writes
+// the face id and its coordinates there.
+template <int D>
+__global__ void k_scatter(const float* __restrict__ X, int64_t nf, const uint32_t* __restrict__ frange,
+                          const uint32_t* __restrict__ offsets, uint32_t* __restrict__ count,
+                          uint32_t* __restrict__ ids, typename EntryT<D>::type* __restrict__ payload, int Bi) {
+  using E = typename EntryT<D>::type;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const uint32_t r = frange[(int64_t)a * nf + f];
+      lo[a] = (int)(r & 0xffffu);
+      hi[a] = (int)(r >> 16);
+    }
+    E e;
+#pragma unroll
+    for (int j = 0; j < D * D; ++j) e.v[j] = X[(int64_t)j * nf + f];
+#pragma unroll
+    for (int j = 0; j < (int)(sizeof(e.pad) / sizeof(e.pad[0])); ++j) e.pad[j] = 0u;
+    const int64_t B = Bi;
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) {
+          const int64_t b = x + B * (y + B * (int64_t)z);
+          const uint32_t old = atomicSub(&count[b], 1u);
+          const int64_t pos = (int64_t)offsets[b] + old - 1;
+          ids[pos] = (uint32_t)f;
+          uint32_t flags = (x == lo[0] ? (1u << 29) : 0u) | (y == lo[1] ? (1u << 30) : 0u);
+          if (D == 3) flags |= (z == lo[2] ? (1u << 31) : 0u);
+          e.id = (uint32_t)f | flags;
+          const float4* src = reinterpret_cast<const float4*>(&e);
+          float4* dst = reinterpret_cast<float4*>(payload + pos);
+#pragma unroll
+          for (int q = 0; q < (int)(sizeof(E) / 16); ++q) dst[q] = src[q];
+        }
+  }
+}
+
+// Single-pass exclusive scan (decoupled look-back over ticket-ordered tiles).
+template <typename T, int ITEMS>
+__global__ void __launch_bounds__(kThreads) k_scan(const T* __restrict__ in, T* __restrict__ out, int64_t n,
+                                                    uint64_t* total, uint64_t* state, unsigned* ticket,
+                                                    unsigned* err) {
+  __shared__ unsigned s_tile;
+  __shared__ uint64_t s_warp[kThreads / 32];
+  __shared__ uint64_t s_prefix;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const long long tile = s_tile;
+  const int64_t base = tile * (int64_t)kThreads * ITEMS + (int64_t)threadIdx.x * ITEMS;
+  uint64_t v[ITEMS];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const int64_t j = base + i;
+    v[i] = j < n ? (uint64_t)in[j] : 0ull;
+    sum += v[i];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t incl = warp_inclusive_scan<unsigned long long>(sum);
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint64_t w = lane < kThreads / 32 ? s_warp[lane] : 0ull;
+    w = warp_inclusive_scan<unsigned long long>(w);
+    if (lane < kThreads / 32) s_warp[lane] = w;
+  }
+  __syncthreads();
+  const uint64_t warp_excl = wid > 0 ? s_warp[wid - 1] : 0ull;
+  if (threadIdx.x == 0) {
+    const uint64_t agg = s_warp[kThreads / 32 - 1];
+    const uint64_t pre = lookback_exclusive(state, tile, agg, err);
+    s_prefix = pre;
+    const int64_t ntiles = (n + (int64_t)kThreads * ITEMS - 1) / ((int64_t)kThreads * ITEMS);
+    if (tile == ntiles - 1 || ntiles == 0) *total = pre + agg;
+  }
+  __syncthreads();
+  uint64_t run = s_prefix + warp_excl + incl - sum;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const int64_t j = base + i;
+    if (j < n) out[j] = (T)run;
+    run += v[i];
+  }
+}
+
+__global__ void k_write_total_u32(const uint64_t* total, uint32_t* dst, unsigned* err) {
+  const uint64_t t = *total;
+  if (t > 0xffffffffull) atomicOr(err, ERR_OVERFLOW);
+  *dst = (uint32_t)t;
+}
+
+template <int D>
+__global__ void k_root_blocks(int r0, int r1, int r2, int32_t* __restrict__ blocks, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = i % r0;
+    const int64_t y = (i / r0) % r1;
+    blocks[i * D + 0] = (int32_t)x;
+    blocks[i * D + 1] = (int32_t)y;
+    if (D == 3) blocks[i * D + 2] = (int32_t)(i / ((int64_t)r0 * r1));
+  }
+}
+
+constexpr int kScanItemsU32 = 8;
+constexpr int kScanItemsU64 = 4;
+
+size_t scan_scratch(int64_t n, int items) {
+  const int64_t tiles = (n + (int64_t)kThreads * items - 1) / ((int64_t)kThreads * items);
+  return 16 + (size_t)(tiles > 0 ? tiles : 1) * 8;
+}
+
+}  // namespace
+
+int launch_load_indexed(int dim, const float* verts, int64_t nv, const int32_t* idx, int64_t nf, float* X,
+                         unsigned* err, cudaStream_t st) {
+  if (nf <= 0) return 0;
+  const int g = grid_for(nf, kThreads);
+  if (dim == 3)
+    k_load_indexed<3><<<g, kThreads, 0, st>>>(verts, nv, idx, nf, X, err);
+  else
+    k_load_indexed<2><<<g, kThreads, 0, st>>>(verts, nv, idx, nf, X, err);
+  return 1;
+}
+
+int launch_load_facelist(int dim, const float* coords, int64_t nf, float* X, unsigned* err, cudaStream_t st) {
+  if (nf <= 0) return 0;
+  const int g = grid_for(nf, kThreads);
+  if (dim == 3)
+    k_load_facelist<3><<<g, kThreads, 0, st>>>(coords, nf, X, err);
+  else
+    k_load_facelist<2><<<g, kThreads, 0, st>>>(coords, nf, X, err);
+  return 1;
+}
+
+int launch_face_normals(const float* X, int64_t nf, float* nrm, cudaStream_t st) {
+  if (nf <= 0) return 0;
+  k_face_normals<<<grid_for(nf, kThreads), kThreads, 0, st>>>(X, nf, nrm);
+  return 1;
+}
+
+int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint32_t* frange, uint32_t* count,
+                      cudaStream_t st) {
+  if (nf <= 0) return 0;
+  const int gr = grid_for(nf, kThreads);
+  if (dim == 3)
+    k_face_bins<3><<<gr, kThreads, 0, st>>>(X, nf, g, frange, count);
+  else
+    k_face_bins<2><<<gr, kThreads, 0, st>>>(X, nf, g, frange, count);
+  return 1;
+}
+
+size_t scan_u32_scratch_bytes(int64_t n) { return scan_scratch(n, kScanItemsU32); }
+size_t scan_u64_scratch_bytes(int64_t n) { return scan_scratch(n, kScanItemsU64); }
+
+int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* total64, void* scratch, unsigned* err,
+                     cudaStream_t st) {
+  const size_t sb = scan_u32_scratch_bytes(n);
+  cudaMemsetAsync(scratch, 0, sb, st);
+  const int64_t tiles = (n + (int64_t)kThreads * kScanItemsU32 - 1) / ((int64_t)kThreads * kScanItemsU32);
+  unsigned* ticket = reinterpret_cast<unsigned*>(scratch);
+  uint64_t* state = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 16);
+  k_scan<uint32_t, kScanItemsU32><<<(unsigned)(tiles > 0 ? tiles : 1), kThreads, 0, st>>>(in, out, n, total64, state,
+                                                                                        ticket, err);
+  k_write_total_u32<<<1, 1, 0, st>>>(total64, out + n, err);
+  return 2;
+}
+
+int launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* total, void* scratch, unsigned* err,
+                     cudaStream_t st) {
+  const size_t sb = scan_u64_scratch_bytes(n);
+  cudaMemsetAsync(scratch, 0, sb, st);
+  const int64_t tiles = (n + (int64_t)kThreads * kScanItemsU64 - 1) / ((int64_t)kThreads * kScanItemsU64);
+  unsigned* ticket = reinterpret_cast<unsigned*>(scratch);
+  uint64_t* state = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 16);
+  k_scan<uint64_t, kScanItemsU64><<<(unsigned)(tiles > 0 ? tiles : 1), kThreads, 0, st>>>(in, out, n, total, state,
+                                                                                        ticket, err);
+  return 1;
+}
+
+int launch_scatter(int dim, const float* X, int64_t nf, const uint32_t* frange, const uint32_t* offsets,
+                    uint32_t* count, uint32_t* ids, void* payload, int B, cudaStream_t st) {
+  if (nf <= 0) return 0;
+  const int g = grid_for(nf, kThreads);
+  if (dim == 3)
+    k_scatter<3><<<g, kThreads, 0, st>>>(X, nf, frange, offsets, count, ids, static_cast<Entry3*>(payload), B);
+  else
+    k_scatter<2><<<g, kThreads, 0, st>>>(X, nf, frange, offsets, count, ids, static_cast<Entry2*>(payload), B);
+  return 1;
+}
+
+int launch_root_blocks(int dim, const int* root, int32_t* blocks, int64_t n, cudaStream_t st) {
+  if (n <= 0) return 0;
+  const int g = grid_for(n, kThreads);
+  if (dim == 3)
+    k_root_blocks<3><<<g, kThreads, 0, st>>>(root[0], root[1], root[2], blocks, n);
+  else
+    k_root_blocks<2><<<g, kThreads, 0, st>>>(root[0], root[1], 1, blocks, n);
+  return 1;
+}
+
+}  // namespace amr

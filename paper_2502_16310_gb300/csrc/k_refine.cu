@@ -1,0 +1,630 @@
+// k_refine.cu — near-wall refinement of one grid level, child compaction and
+// the finest level's adjacent-face lists.
+//
+// Paper (Sec. "Identification of Cells Near the Boundary", "Face Detection",
+// "Spatial Binning Algorithm"): every cell of every block of the level checks
+// the faces stored in the bins around it; a block with an adjacent cell is
+// marked and M_RefineAndCoarsenBlocks subdivides it.  The paper maps one
+// thread to one cell (thread block = cell block) and tests the cell centre
+// against the face with Alg. 1.
+//
+// Here one warp owns one block of 4^D cells (two cells per lane in 3D).  The
+// warp walks the bins overlapped by the block's query box (block inflated by
+// d_L); each lane takes one bin entry, visits it only in its canonical bin
+// (so a face seen in several bins is tested once), and runs the separating-axis
+// test of the face against the whole inflated block.  Survivors leave their
+// per-axis projection intervals in shared memory and every lane tests its
+// cells against them.  The adjacency bits are combined with warp ballots.
+//
+// Decisions are exact: each FP32 axis test carries a forward error bound; a
+// (cell, face) pair whose sign is not certified on every axis is re-evaluated
+// in FP64 (and counted).  Block-level culls only use certified separations.
+#include "internal.cuh"
+
+namespace amr {
+
+namespace {
+
+constexpr int kWarps = 4;
+constexpr float kEpsK = 16.0f;  // safety factor over the forward error bound (see axis_bound)
+
+template <int D>
+struct Surv;
+
+// Per-survivor data in the block frame (origin = the block's lower corner).
+// Axis order (3D): 0..2 box axes, 3 face normal, 4 + 3k + i = e_i x edge_k.
+template <>
+struct Surv<3> {
+  float e[9];
+  float n[3];
+  float lo[13], hi[13], eps[13];
+  uint32_t face;
+};
+// 2D: 0..1 box axes, 2 segment normal (-e_y, e_x).
+template <>
+struct Surv<2> {
+  float e[2];
+  float lo[3], hi[3], eps[3];
+  uint32_t face;
+};
+
+__device__ __forceinline__ float3 axis3(int ai, const float* e, const float* n) {
+  if (ai < 3) return make_float3(ai == 0 ? 1.f : 0.f, ai == 1 ? 1.f : 0.f, ai == 2 ? 1.f : 0.f);
+  if (ai == 3) return make_float3(n[0], n[1], n[2]);
+  const int k = (ai - 4) / 3, i = (ai - 4) % 3;
+  const float ex = e[3 * k + 0], ey = e[3 * k + 1], ez = e[3 * k + 2];
+  if (i == 0) return make_float3(0.f, -ez, ey);
+  if (i == 1) return make_float3(ez, 0.f, -ex);
+  return make_float3(-ey, ex, 0.f);
+}
+
+// FP64 separating-axis margin of the box [x_c - r, x_c + r]^3 and the closed
+// triangle (vertices absolute FP32), normalised gap of the best axis.
+__device__ __noinline__ double margin_fp64_3(const float* V, const double* xc, double r) {
+  double p[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[k][c] = __dsub_rn((double)V[3 * k + c], xc[c]);
+  double m = -1e300;
+  auto axis = [&](double a0, double a1, double a2) {
+    const double l2 = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(a0, a0), __dmul_rn(a1, a1)), __dmul_rn(a2, a2)));
+    if (l2 == 0.0) return;
+    double lo = 1e300, hi = -1e300;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double s = __dadd_rn(__dadd_rn(__dmul_rn(p[k][0], a0), __dmul_rn(p[k][1], a1)), __dmul_rn(p[k][2], a2));
+      lo = fmin(lo, s);
+      hi = fmax(hi, s);
+    }
+    const double R = __dmul_rn(r, __dadd_rn(__dadd_rn(fabs(a0), fabs(a1)), fabs(a2)));
+    const double g = fmax(__dsub_rn(lo, R), __dsub_rn(-R, hi));
+    m = fmax(m, g / l2);
+  };
+  axis(1.0, 0.0, 0.0);
+  axis(0.0, 1.0, 0.0);
+  axis(0.0, 0.0, 1.0);
+  const double u0 = __dsub_rn(p[1][0], p[0][0]), u1 = __dsub_rn(p[1][1], p[0][1]), u2 = __dsub_rn(p[1][2], p[0][2]);
+  const double w0 = __dsub_rn(p[2][0], p[0][0]), w1 = __dsub_rn(p[2][1], p[0][1]), w2 = __dsub_rn(p[2][2], p[0][2]);
+  axis(__dsub_rn(__dmul_rn(u1, w2), __dmul_rn(u2, w1)), __dsub_rn(__dmul_rn(u2, w0), __dmul_rn(u0, w2)),
+       __dsub_rn(__dmul_rn(u0, w1), __dmul_rn(u1, w0)));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int k1 = (k + 1) % 3;
+    const double ex = __dsub_rn(p[k1][0], p[k][0]), ey = __dsub_rn(p[k1][1], p[k][1]),
+                 ez = __dsub_rn(p[k1][2], p[k][2]);
+    axis(0.0, -ez, ey);
+    axis(ez, 0.0, -ex);
+    axis(-ey, ex, 0.0);
+  }
+  return m;
+}
+
+__device__ __noinline__ double margin_fp64_2(const float* V, const double* xc, double r) {
+  double p[2][2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) p[k][c] = __dsub_rn((double)V[2 * k + c], xc[c]);
+  double m = -1e300;
+  auto axis = [&](double a0, double a1) {
+    const double l2 = sqrt(__dadd_rn(__dmul_rn(a0, a0), __dmul_rn(a1, a1)));
+    if (l2 == 0.0) return;
+    const double s0 = __dadd_rn(__dmul_rn(p[0][0], a0), __dmul_rn(p[0][1], a1));
+    const double s1 = __dadd_rn(__dmul_rn(p[1][0], a0), __dmul_rn(p[1][1], a1));
+    const double lo = fmin(s0, s1), hi = fmax(s0, s1);
+    const double R = __dmul_rn(r, __dadd_rn(fabs(a0), fabs(a1)));
+    m = fmax(m, fmax(__dsub_rn(lo, R), __dsub_rn(-R, hi)) / l2);
+  };
+  axis(1.0, 0.0);
+  axis(0.0, 1.0);
+  const double e0 = __dsub_rn(p[1][0], p[0][0]), e1 = __dsub_rn(p[1][1], p[0][1]);
+  axis(-e1, e0);
+  return m;
+}
+
+// Block-frame quantities shared by all lanes of the warp for one block.
+template <int D>
+struct BlockFrame {
+  double X64[3];   // block corner (FP64)
+  float Xb[3];     // block corner rounded to FP32 (the frame origin)
+  float cB[3];     // block centre in the frame
+  float h, r, rb;  // cell size, cell and block half-widths (inflated) in FP32
+  float O;         // bound on |cell centre offsets| and |block centre| in the frame
+};
+
+// Per-face setup (one lane): edges, projections of the face on every axis in
+// the block frame, the cell-level intervals [tmin - r|a|_1, tmax + r|a|_1] and
+// their error bounds.  Returns false when some axis certifiably separates the
+// face from the whole inflated block.
+//
+// Error bound per axis a: every computed projection, interval end and cell
+// coordinate differs from its exact value by at most a few unit roundoffs of
+// (P + O + r) |a|_1, where P bounds the vertex offsets in the frame (this also
+// covers the rounding of the frame origin, of the edges when they are not
+// exact and of the FP32 normal relative to the FP64 one).  eps = 16 u (P+O+r)|a|_1.
+template <int D>
+__device__ __forceinline__ bool setup_face(const float* V, const float* nh, const BlockFrame<D>& F, Surv<D>& S) {
+  float p[3][3];
+  float P = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      p[k][c] = V[D * k + c] - F.Xb[c];
+      P = fmaxf(P, fabsf(p[k][c]));
+    }
+  const float scale = kEpsK * kU32 * (P + F.O + F.r);
+  bool alive = true;
+  if constexpr (D == 3) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int k1 = (k + 1) % 3;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) S.e[3 * k + c] = V[3 * k1 + c] - V[3 * k + c];
+    }
+    S.n[0] = nh[0];
+    S.n[1] = nh[1];
+    S.n[2] = nh[2];
+#pragma unroll
+    for (int ai = 0; ai < 13; ++ai) {
+      const float3 a = axis3(ai, S.e, S.n);
+      const float A1 = fabsf(a.x) + fabsf(a.y) + fabsf(a.z);
+      if (A1 == 0.0f) {
+        S.lo[ai] = -INFINITY;
+        S.hi[ai] = INFINITY;
+        S.eps[ai] = 0.f;
+        continue;
+      }
+      float tmin = INFINITY, tmax = -INFINITY;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float s = fmaf(p[k][2], a.z, fmaf(p[k][1], a.y, p[k][0] * a.x));
+        tmin = fminf(tmin, s);
+        tmax = fmaxf(tmax, s);
+      }
+      const float eps = scale * A1;
+      const float xb = fmaf(F.cB[2], a.z, fmaf(F.cB[1], a.y, F.cB[0] * a.x));
+      const float RB = F.rb * A1;
+      // block interval [xb - RB, xb + RB] vs face interval [tmin, tmax]
+      if (xb - RB - tmax > eps || tmin - (xb + RB) > eps) alive = false;
+      const float R = F.r * A1;
+      S.lo[ai] = tmin - R;
+      S.hi[ai] = tmax + R;
+      S.eps[ai] = eps;
+      if (!alive) return false;  // box axes come first: the cheap AABB cull
+    }
+  } else {
+    S.e[0] = V[2] - V[0];
+    S.e[1] = V[3] - V[1];
+#pragma unroll
+    for (int ai = 0; ai < 3; ++ai) {
+      const float ax = ai == 0 ? 1.f : (ai == 1 ? 0.f : -S.e[1]);
+      const float ay = ai == 0 ? 0.f : (ai == 1 ? 1.f : S.e[0]);
+      const float A1 = fabsf(ax) + fabsf(ay);
+      if (A1 == 0.0f) {
+        S.lo[ai] = -INFINITY;
+        S.hi[ai] = INFINITY;
+        S.eps[ai] = 0.f;
+        continue;
+      }
+      const float s0 = fmaf(p[0][1], ay, p[0][0] * ax);
+      const float s1 = fmaf(p[1][1], ay, p[1][0] * ax);
+      const float tmin = fminf(s0, s1), tmax = fmaxf(s0, s1);
+      const float eps = scale * A1;
+      const float xb = fmaf(F.cB[1], ay, F.cB[0] * ax);
+      const float RB = F.rb * A1;
+      if (xb - RB - tmax > eps || tmin - (xb + RB) > eps) alive = false;
+      const float R = F.r * A1;
+      S.lo[ai] = tmin - R;
+      S.hi[ai] = tmax + R;
+      S.eps[ai] = eps;
+      if (!alive) return false;
+    }
+  }
+  return alive;
+}
+
+// Cell test against one survivor: 0 = separated, 1 = intersecting, 2 = not
+// certified (needs FP64).  `o` is the cell centre in the block frame.
+template <int D>
+__device__ __forceinline__ int cell_test(const Surv<D>& S, const float* o) {
+  bool unc = false;
+  if constexpr (D == 3) {
+#pragma unroll
+    for (int ai = 0; ai < 13; ++ai) {
+      float x;
+      if (ai < 3) {
+        x = o[ai];
+      } else if (ai == 3) {
+        x = fmaf(o[2], S.n[2], fmaf(o[1], S.n[1], o[0] * S.n[0]));
+      } else {
+        const int k = (ai - 4) / 3, i = (ai - 4) % 3;
+        const float ex = S.e[3 * k + 0], ey = S.e[3 * k + 1], ez = S.e[3 * k + 2];
+        if (i == 0)
+          x = fmaf(o[2], ey, -o[1] * ez);
+        else if (i == 1)
+          x = fmaf(o[0], ez, -o[2] * ex);
+        else
+          x = fmaf(o[1], ex, -o[0] * ey);
+      }
+      const float g = fmaxf(S.lo[ai] - x, x - S.hi[ai]);
+      if (g > S.eps[ai]) return 0;
+      unc |= g >= -S.eps[ai];
+    }
+  } else {
+#pragma unroll
+    for (int ai = 0; ai < 3; ++ai) {
+      const float x = ai < 2 ? o[ai] : fmaf(o[1], S.e[0], -o[0] * S.e[1]);
+      const float g = fmaxf(S.lo[ai] - x, x - S.hi[ai]);
+      if (g > S.eps[ai]) return 0;
+      unc |= g >= -S.eps[ai];
+    }
+  }
+  return unc ? 2 : 1;
+}
+
+struct WarpCounters {
+  unsigned long long fb = 0, band = 0, cand = 0, surv = 0;
+};
+
+template <int D>
+__device__ __forceinline__ bool resolve_fp64(const RefineLevel& a, uint32_t face, const int* b, int cell_local,
+                                             WarpCounters& wc) {
+  float V[D * D];
+#pragma unroll
+  for (int j = 0; j < D * D; ++j) V[j] = a.X[(int64_t)j * a.nf + face];
+  double xc[3];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const int li = (cell_local >> (2 * c)) & 3;
+    xc[c] = __dadd_rn(a.origin[c], __dmul_rn((double)(4 * b[c] + li) + 0.5, a.h));
+  }
+  const double r = __dadd_rn(0.5 * a.h, a.d);
+  const double m = D == 3 ? margin_fp64_3(V, xc, r) : margin_fp64_2(V, xc, r);
+  wc.fb++;
+  if (fabs(m) <= kBandRel * a.h) wc.band++;
+  return m <= 0.0;
+}
+
+// Shared walk of one block: bins of the query box, canonical-bin dedup,
+// block-level cull, cell tests.  `on_hit(cellslot, face)` is called for every
+// intersecting (cell, face) pair; cellslot 0 = cell `lane`, 1 = cell `lane + 32`.
+template <int D, typename OnHit>
+__device__ __forceinline__ void walk_block(const RefineLevel& a, const int* b, Surv<D>* s_surv, int lane,
+                                           WarpCounters& wc, OnHit on_hit) {
+  using E = typename EntryT<D>::type;
+  const float hf = (float)a.h;
+  BlockFrame<D> F;
+  int qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0};
+  const double slack = 1e-9 * a.h;
+  float O = 4.0f * hf;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    F.X64[c] = __dadd_rn(a.origin[c], __dmul_rn((double)(4 * b[c]), a.h));
+    F.Xb[c] = (float)F.X64[c];
+    const double shift = __dsub_rn(F.X64[c], (double)F.Xb[c]);
+    F.cB[c] = (float)__dadd_rn(2.0 * a.h, shift);
+    O = fmaxf(O, 4.0f * hf + 2.0f * (float)fabs(shift));
+    qlo[c] = bin_coord(F.X64[c] - a.d - slack, a.grid.origin[c], a.grid.scale[c], a.grid.B);
+    qhi[c] = bin_coord(F.X64[c] + 4.0 * a.h + a.d + slack, a.grid.origin[c], a.grid.scale[c], a.grid.B);
+  }
+  F.h = hf;
+  F.r = (float)(0.5 * a.h + a.d);
+  F.rb = (float)(2.0 * a.h + a.d);
+  F.O = O;
+  // cell centres of this lane in the frame (FP64 -> FP32 once)
+  float o0[3] = {0, 0, 0}, o1[3] = {0, 0, 0};
+  const bool lane_cell = D == 3 || lane < 16;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const int l0 = (lane >> (2 * c)) & 3;
+    const double xc0 = __dadd_rn(a.origin[c], __dmul_rn((double)(4 * b[c] + l0) + 0.5, a.h));
+    o0[c] = (float)__dsub_rn(xc0, (double)F.Xb[c]);
+    if (D == 3) {
+      const int l1 = ((lane + 32) >> (2 * c)) & 3;
+      const double xc1 = __dadd_rn(a.origin[c], __dmul_rn((double)(4 * b[c] + l1) + 0.5, a.h));
+      o1[c] = (float)__dsub_rn(xc1, (double)F.Xb[c]);
+    }
+  }
+  const int64_t B = a.grid.B;
+  const E* payload = static_cast<const E*>(a.payload);
+  for (int z = qlo[2]; z <= qhi[2]; ++z)
+    for (int y = qlo[1]; y <= qhi[1]; ++y)
+      for (int x = qlo[0]; x <= qhi[0]; ++x) {
+        const int64_t bin = x + B * (y + B * (int64_t)z);
+        const uint32_t s = a.offsets[bin], e = a.offsets[bin + 1];
+        for (uint32_t base = s; base < e; base += 32) {
+          const uint32_t j = base + lane;
+          bool surv = false;
+          if (j < e) {
+            const E ent = payload[j];
+            const uint32_t id = ent.id;
+            bool canon = ((id >> 29) & 1u) || x == qlo[0];
+            canon = canon && (((id >> 30) & 1u) || y == qlo[1]);
+            if (D == 3) canon = canon && (((id >> 31) & 1u) || z == qlo[2]);
+            if (canon) {
+              wc.cand++;
+              const uint32_t f = id & kIdMask;
+              float nh[3] = {0.f, 0.f, 0.f};
+              if (D == 3) {
+                nh[0] = a.nrm[f];
+                nh[1] = a.nrm[a.nf + f];
+                nh[2] = a.nrm[2 * a.nf + f];
+              }
+              surv = setup_face<D>(ent.v, nh, F, s_surv[lane]);
+              s_surv[lane].face = f;
+            }
+          }
+          unsigned m = __ballot_sync(0xffffffffu, surv);
+          __syncwarp();
+          wc.surv += __popc(m);
+          while (m) {
+            const int k = __ffs(m) - 1;
+            m &= m - 1;
+            const Surv<D>& S = s_surv[k];
+            if (lane_cell) {
+              int r0 = cell_test<D>(S, o0);
+              if (r0 == 2) r0 = resolve_fp64<D>(a, S.face, b, lane, wc) ? 1 : 0;
+              if (r0) on_hit(0, S.face);
+              if (D == 3) {
+                int r1 = cell_test<D>(S, o1);
+                if (r1 == 2) r1 = resolve_fp64<D>(a, S.face, b, lane + 32, wc) ? 1 : 0;
+                if (r1) on_hit(1, S.face);
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kWarps * 32) k_refine(RefineLevel a) {
+  __shared__ Surv<D> s_surv[kWarps][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpCounters wc;
+  for (;;) {
+    unsigned blk = 0;
+    if (lane == 0) blk = atomicAdd(a.work, 1u);
+    blk = __shfl_sync(0xffffffffu, blk, 0);
+    if (blk >= a.n_blocks) break;
+    int b[3] = {0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < D; ++c) b[c] = a.blocks[(int64_t)blk * D + c];
+    uint32_t cnt0 = 0, cnt1 = 0;
+    walk_block<D>(a, b, s_surv[wid], lane, wc, [&](int slot, uint32_t) {
+      if (slot == 0)
+        ++cnt0;
+      else
+        ++cnt1;
+    });
+    const uint64_t mask = (uint64_t)__ballot_sync(0xffffffffu, cnt0 > 0) |
+                          ((uint64_t)__ballot_sync(0xffffffffu, cnt1 > 0) << 32);
+    const uint64_t m = D == 3 ? mask : (mask & 0xffffull);
+    if (lane == 0) {
+      a.mask[blk] = m;
+      a.flag[blk] = m != 0 ? 1 : 0;
+    }
+    if (a.cellcnt) {
+      if (cnt0 > 0xffffu || cnt1 > 0xffffu) atomicOr(a.err, ERR_OVERFLOW);
+      constexpr int NC = D == 3 ? 64 : 16;
+      if (lane < NC) a.cellcnt[(int64_t)blk * NC + lane] = (uint16_t)min(cnt0, 0xffffu);
+      if (D == 3) a.cellcnt[(int64_t)blk * NC + 32 + lane] = (uint16_t)min(cnt1, 0xffffu);
+    }
+    if (a.blockcnt) {
+      uint32_t pairs = cnt0 + cnt1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+      if (lane == 0) a.blockcnt[blk] = (uint64_t)pairs | ((uint64_t)__popcll(m) << 32);
+    }
+  }
+  // flush warp counters
+  unsigned long long v[4] = {wc.fb, wc.band, wc.cand, wc.surv};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  }
+  if (lane == 0) {
+    if (v[0]) atomicAdd(&a.counters[CNT_FALLBACK], v[0]);
+    if (v[1]) atomicAdd(&a.counters[CNT_BAND], v[1]);
+    atomicAdd(&a.counters[CNT_CANDIDATES], v[2]);       // per-lane counts
+    atomicAdd(&a.counters[CNT_SURVIVORS], v[3] / 32);   // every lane counted the same survivors
+  }
+}
+
+// Emit the adjacent-face lists of the finest level: same walk as k_refine (so
+// the same decisions), each lane appends the faces of its cells at offsets
+// given by the block-level scan and the per-cell counts, then sorts each list.
+template <int D>
+__global__ void __launch_bounds__(kWarps * 32) k_adjacency(EmitArgs a) {
+  __shared__ Surv<D> s_surv[kWarps][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NC = D == 3 ? 64 : 16;
+  WarpCounters wc;
+  for (;;) {
+    unsigned blk = 0;
+    if (lane == 0) blk = atomicAdd(a.lv.work, 1u);
+    blk = __shfl_sync(0xffffffffu, blk, 0);
+    if (blk >= a.lv.n_blocks) break;
+    const uint64_t mask = a.lv.mask[blk];
+    if (mask == 0) continue;
+    int b[3] = {0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < D; ++c) b[c] = a.lv.blocks[(int64_t)blk * D + c];
+    const uint64_t base = a.block_base[blk];
+    const uint32_t pair_base = (uint32_t)(base & 0xffffffffull);
+    const uint32_t cell_base = (uint32_t)(base >> 32);
+    const uint32_t n0 = lane < NC ? a.lv.cellcnt[(int64_t)blk * NC + lane] : 0u;
+    const uint32_t n1 = D == 3 ? a.lv.cellcnt[(int64_t)blk * NC + 32 + lane] : 0u;
+    // exclusive prefixes over cells in bit order (cells 0..31 then 32..63)
+    const uint32_t i0 = warp_inclusive_scan<uint32_t>(n0);
+    const uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31);
+    const uint32_t i1 = warp_inclusive_scan<uint32_t>(n1);
+    const uint32_t off0 = pair_base + i0 - n0;
+    const uint32_t off1 = pair_base + tot0 + i1 - n1;
+    const uint32_t a0 = n0 > 0, a1 = n1 > 0;
+    const uint32_t j0 = warp_inclusive_scan<uint32_t>(a0);
+    const uint32_t atot0 = __shfl_sync(0xffffffffu, j0, 31);
+    const uint32_t j1 = warp_inclusive_scan<uint32_t>(a1);
+    if (a0) {
+      const uint32_t row = cell_base + j0 - 1;
+      a.adj_cell[row] = blk * (uint32_t)NC + lane;
+      a.adj_off[row] = off0;
+    }
+    if (a1) {
+      const uint32_t row = cell_base + atot0 + j1 - 1;
+      a.adj_cell[row] = blk * (uint32_t)NC + 32 + lane;
+      a.adj_off[row] = off1;
+    }
+    uint32_t c0 = 0, c1 = 0;
+    unsigned bad = 0;
+    walk_block<D>(a.lv, b, s_surv[wid], lane, wc, [&](int slot, uint32_t f) {
+      if (slot == 0) {
+        if (c0 < n0)
+          a.adj_ids[off0 + c0] = f;
+        else
+          bad = 1;
+        ++c0;
+      } else {
+        if (c1 < n1)
+          a.adj_ids[off1 + c1] = f;
+        else
+          bad = 1;
+        ++c1;
+      }
+    });
+    if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
+    // ascending face ids per cell (lists are short: insertion sort in place)
+    for (int s = 0; s < 2; ++s) {
+      const uint32_t n = s == 0 ? n0 : n1;
+      uint32_t* L = a.adj_ids + (s == 0 ? off0 : off1);
+      for (uint32_t i = 1; i < n; ++i) {
+        const uint32_t v = L[i];
+        uint32_t k = i;
+        while (k > 0 && L[k - 1] > v) {
+          L[k] = L[k - 1];
+          --k;
+        }
+        L[k] = v;
+      }
+    }
+  }
+}
+
+// Children of the marked blocks, canonical order, single pass with look-back.
+constexpr int kChThreads = 256;
+constexpr int kChItems = 4;
+
+template <int D>
+__global__ void __launch_bounds__(kChThreads) k_children(const int32_t* __restrict__ blocks,
+                                                         const uint64_t* __restrict__ mask, int64_t n,
+                                                         int32_t* __restrict__ cb, int32_t* __restrict__ cp,
+                                                         uint64_t* total, uint64_t* state, unsigned* ticket,
+                                                         unsigned* err) {
+  __shared__ unsigned s_tile;
+  __shared__ uint32_t s_warp[kChThreads / 32];
+  __shared__ uint64_t s_prefix;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const long long tile = s_tile;
+  const int64_t base = tile * (int64_t)kChThreads * kChItems + (int64_t)threadIdx.x * kChItems;
+  uint32_t fl[kChItems];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < kChItems; ++i) {
+    const int64_t j = base + i;
+    fl[i] = (j < n && mask[j] != 0) ? 1u : 0u;
+    sum += fl[i];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t incl = warp_inclusive_scan<uint32_t>(sum);
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < kChThreads / 32 ? s_warp[lane] : 0u;
+    w = warp_inclusive_scan<uint32_t>(w);
+    if (lane < kChThreads / 32) s_warp[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t wex = wid > 0 ? s_warp[wid - 1] : 0u;
+  if (threadIdx.x == 0) {
+    const uint64_t agg = s_warp[kChThreads / 32 - 1];
+    const uint64_t pre = lookback_exclusive(state, tile, agg, err);
+    s_prefix = pre;
+    const int64_t ntiles = (n + (int64_t)kChThreads * kChItems - 1) / ((int64_t)kChThreads * kChItems);
+    if (tile == ntiles - 1 || ntiles == 0) *total = (pre + agg) * (D == 3 ? 8 : 4);
+  }
+  __syncthreads();
+  uint64_t k = s_prefix + wex + incl - sum;
+  constexpr int NCH = D == 3 ? 8 : 4;
+#pragma unroll
+  for (int i = 0; i < kChItems; ++i) {
+    if (fl[i]) {
+      const int64_t p = base + i;
+      int bc[3] = {0, 0, 0};
+#pragma unroll
+      for (int c = 0; c < D; ++c) bc[c] = blocks[p * D + c];
+#pragma unroll
+      for (int s = 0; s < NCH; ++s) {
+        const int64_t o = (int64_t)k * NCH + s;
+        cb[o * D + 0] = 2 * bc[0] + (s & 1);
+        cb[o * D + 1] = 2 * bc[1] + ((s >> 1) & 1);
+        if (D == 3) cb[o * D + 2] = 2 * bc[2] + ((s >> 2) & 1);
+        cp[o] = (int32_t)p;
+      }
+      ++k;
+    }
+  }
+}
+
+int refine_grid(int num_sms, int64_t n) {
+  int64_t need = (n + kWarps - 1) / kWarps;
+  int64_t cap = (int64_t)num_sms * 8;
+  if (need < 1) need = 1;
+  return (int)(need < cap ? need : cap);
+}
+
+}  // namespace
+
+int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st) {
+  if (a.n_blocks <= 0) return 0;
+  const int g = refine_grid(num_sms, a.n_blocks);
+  if (a.dim == 3)
+    k_refine<3><<<g, kWarps * 32, 0, st>>>(a);
+  else
+    k_refine<2><<<g, kWarps * 32, 0, st>>>(a);
+  return 1;
+}
+
+int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st) {
+  if (a.lv.n_blocks <= 0) return 0;
+  const int g = refine_grid(num_sms, a.lv.n_blocks);
+  if (a.lv.dim == 3)
+    k_adjacency<3><<<g, kWarps * 32, 0, st>>>(a);
+  else
+    k_adjacency<2><<<g, kWarps * 32, 0, st>>>(a);
+  return 1;
+}
+
+size_t children_scratch_bytes(int64_t n) {
+  const int64_t tiles = (n + (int64_t)kChThreads * kChItems - 1) / ((int64_t)kChThreads * kChItems);
+  return 16 + (size_t)(tiles > 0 ? tiles : 1) * 8;
+}
+
+int launch_children(int dim, const int32_t* blocks, const uint64_t* mask, int64_t n, int32_t* cb, int32_t* cp,
+                     uint64_t* total, void* scratch, unsigned* err, cudaStream_t st) {
+  cudaMemsetAsync(scratch, 0, children_scratch_bytes(n), st);
+  const int64_t tiles = (n + (int64_t)kChThreads * kChItems - 1) / ((int64_t)kChThreads * kChItems);
+  unsigned* ticket = reinterpret_cast<unsigned*>(scratch);
+  uint64_t* state = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 16);
+  const unsigned g = (unsigned)(tiles > 0 ? tiles : 1);
+  if (dim == 3)
+    k_children<3><<<g, kChThreads, 0, st>>>(blocks, mask, n, cb, cp, total, state, ticket, err);
+  else
+    k_children<2><<<g, kChThreads, 0, st>>>(blocks, mask, n, cb, cp, total, state, ticket, err);
+  return 1;
+}
+
+}  // namespace amr
