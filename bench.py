@@ -130,19 +130,15 @@ def measured_peaks():
 # our arm
 # ---------------------------------------------------------------------------
 def near_wall_cells(res):
+    """Adjacent cells summed over all levels (popcount of every level's cell masks)."""
     import torch
 
+    lut = torch.tensor([bin(i).count("1") for i in range(256)], dtype=torch.int64, device="cuda")
     tot = 0
     for lv in res["levels"]:
         m = lv["mask"]
-        if m.numel() == 0:
-            continue
-        bits = torch.zeros_like(m)
-        x = m.clone()
-        # popcount of 64-bit masks
-        for s in range(64):
-            bits += (x >> s) & 1
-        tot += int(bits.sum().item())
+        if m.numel():
+            tot += int(lut[m.view(torch.uint8).long()].sum().item())
     return tot
 
 
