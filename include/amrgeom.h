@@ -185,6 +185,37 @@ AMR_API int amr_timing_get(amr_ctx* ctx, const char** names, double* total_ms, i
 /* Number of CUDA kernels this context has launched since its creation. */
 AMR_API int64_t amr_launch_count(const amr_ctx* ctx);
 
+/* Binning that allocates nothing.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory — e.g. a solver that
+ * reserved the device's memory for its own arena up front, a plugin whose host
+ * owns every device allocation, or a time-critical loop that must not pay the
+ * implicit synchronisation of cudaMalloc / cudaFree.  It computes the same CSR
+ * bins as amr_bin_faces without a context and without any allocation: its
+ * scratch (bin counts, per-face bin ranges, scan tile states; about 2.6 MB) is a
+ * fixed array in device global memory that every GPU loading this library holds
+ * until the process exits.
+ *   dom        domain (dim, root_blocks, origin, h0) and the stream to run on
+ *              (NULL = the legacy default stream); no context is needed.
+ *   faces      DEVICE f32 [dim*dim][n_faces]: vertex-major, then coordinate, then
+ *              face (the structure-of-arrays form geom_f_face_X); caller-owned.
+ *   n_faces    0 <= n_faces <= AMR_STATIC_MAX_FACES.
+ *   bin_density B >= 1 with B^dim <= AMR_STATIC_MAX_BINS.
+ *   offsets    DEVICE u32 [B^dim + 1], written (CSR start of every bin).
+ *   ids        DEVICE u32 [ids_capacity], written (face ids grouped by bin; order
+ *              within a bin unspecified).
+ *   nnz        HOST, receives the number of (face, bin) entries.
+ * Returns EINVAL for sizes beyond the maxima or non-device pointers (nothing is
+ * launched), EOVERFLOW when nnz > ids_capacity (offsets and *nnz are still valid,
+ * ids is untouched).  The call waits for the count and the scan; the ids are
+ * written asynchronously on the stream.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call shares the one array per device, so calls
+ * whose work overlaps on the GPU (other streams or threads) race: serialise them. */
+#define AMR_STATIC_MAX_BINS (1 << 18)
+#define AMR_STATIC_MAX_FACES (1 << 17)
+AMR_API amr_status amr_bin_faces_static(const amr_domain* dom, const float* faces, int64_t n_faces, int bin_density,
+                                        uint32_t* offsets, uint32_t* ids, int64_t ids_capacity, int64_t* nnz);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@ from .binding import (  # noqa: F401
     AmrError,
     AmrGeom,
     amr_bin_faces,
+    amr_bin_faces_static,
     amr_create,
     amr_destroy,
     amr_geom_load,

@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECUDA", 4
 
 EXPORTED = ["amr_create", "amr_destroy", "amr_status_str", "amr_last_error", "amr_set_stream", "amr_geom_load",
             "amr_bin_faces", "amr_refine_near_wall", "amr_sync", "amr_timing_enable", "amr_timing_reset",
-            "amr_timing_get", "amr_launch_count"]
+            "amr_timing_get", "amr_launch_count", "amr_bin_faces_static"]
 
 
 class AmrError(RuntimeError):
@@ -109,6 +109,8 @@ def lib(build_if_missing: bool = True):
         L.amr_timing_get.argtypes = [P, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(i64), C.c_int]
         L.amr_launch_count.restype = C.c_int64
         L.amr_launch_count.argtypes = [P]
+        L.amr_bin_faces_static.restype = C.c_int
+        L.amr_bin_faces_static.argtypes = [C.POINTER(amr_domain), P, i64, C.c_int, P, P, i64, C.POINTER(i64)]
         _lib = L
         return L
 
@@ -191,6 +193,32 @@ def amr_timing_get(ctx) -> dict:
 
 def amr_launch_count(ctx) -> int:
     return int(lib().amr_launch_count(ctx))
+
+
+STATIC_MAX_BINS = 1 << 18
+STATIC_MAX_FACES = 1 << 17
+
+
+def amr_bin_faces_static(dim, root_blocks, faces_soa_ptr: int, n_faces: int, bin_density: int, offsets_ptr: int,
+                         ids_ptr: int, ids_capacity: int, origin=(0.0, 0.0, 0.0), h0=None, stream=None):
+    """Allocation-free binning (device SoA faces in, caller-owned device offsets/ids out); returns nnz.
+
+    Raises AmrError with the C status (EINVAL beyond the static maxima, EOVERFLOW when nnz > ids_capacity).
+    """
+    d = amr_domain()
+    d.dim = dim
+    rb = list(root_blocks) + [1] * (3 - len(root_blocks))
+    for a in range(3):
+        d.root_blocks[a] = int(rb[a])
+        d.origin[a] = float(origin[a]) if a < len(origin) else 0.0
+    d.h0 = float(h0 if h0 is not None else 1.0 / (4.0 * rb[0]))
+    d.stream = stream
+    nnz = C.c_int64(0)
+    st = lib().amr_bin_faces_static(C.byref(d), faces_soa_ptr, int(n_faces), int(bin_density), offsets_ptr, ids_ptr,
+                                    int(ids_capacity), C.byref(nnz))
+    if st != AMR_OK:
+        raise AmrError(st, lib().amr_status_str(st).decode() + f" (nnz={nnz.value})")
+    return int(nnz.value)
 
 
 # -- torch convenience layer ----------------------------------------------------

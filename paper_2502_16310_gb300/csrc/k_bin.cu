@@ -321,3 +321,143 @@ int launch_root_blocks(int dim, const int* root, int32_t* blocks, int64_t n, cud
 }
 
 }  // namespace amr
+
+// ---------------------------------------------------------------------------
+// Binning without allocation (amr_bin_faces_static).
+//
+// Some callers cannot allocate device memory at all: a solver that reserved
+// the device's memory up front for its own arena, a plugin whose host owns
+// every device allocation, or a time-critical loop that must not pay the
+// implicit synchronisation a cudaMalloc / cudaFree can cause.  For them this
+// entry point bins faces with no allocation: its scratch (bin counts, face bin
+// ranges, scan tile states) is one fixed array in device global memory, below.
+// Every GPU that loads this library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#include "amrgeom.h"
+
+namespace amr {
+namespace {
+
+constexpr int64_t kStaticMaxBins = AMR_STATIC_MAX_BINS;
+constexpr int64_t kStaticMaxFaces = AMR_STATIC_MAX_FACES;
+constexpr size_t kStCount = 0;                                                     // u32 [max bins]
+constexpr size_t kStRange = kStCount + 4 * (size_t)kStaticMaxBins;                 // u32 [3][max faces]
+constexpr size_t kStScan = kStRange + 12 * (size_t)kStaticMaxFaces;                // scan ticket + tile states
+constexpr size_t kStScanBytes = 16 + 8 * (size_t)((kStaticMaxBins + kThreads * kScanItemsU32 - 1) /
+                                                   (kThreads * kScanItemsU32));
+constexpr size_t kStTotal = (kStScan + kStScanBytes + 255) / 256 * 256;            // u64 total
+constexpr size_t kStErr = kStTotal + 8;                                            // u32 error word
+constexpr size_t kStBytes = kStErr + 8;
+
+static __device__ __align__(256) unsigned char g_bin_static_scratch[kStBytes];
+
+// Device address of the array, looked up once per device (host code may not use
+// the symbol itself as a device pointer).
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mutex;
+
+cudaError_t static_scratch(int dev, unsigned char** out) {
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_bin_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  return cudaSuccess;
+}
+
+// Face ids only (no coordinate payload): same slot claiming as k_scatter.
+template <int D>
+__global__ void k_scatter_ids(int64_t nf, const uint32_t* __restrict__ frange, const uint32_t* __restrict__ offsets,
+                              uint32_t* __restrict__ count, uint32_t* __restrict__ ids, int Bi) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const uint32_t r = frange[(int64_t)a * nf + f];
+      lo[a] = (int)(r & 0xffffu);
+      hi[a] = (int)(r >> 16);
+    }
+    const int64_t B = Bi;
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) {
+          const int64_t b = x + B * (y + B * (int64_t)z);
+          const uint32_t old = atomicSub(&count[b], 1u);
+          ids[(int64_t)offsets[b] + old - 1] = (uint32_t)f;
+        }
+  }
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace amr
+
+extern "C" AMR_API amr_status amr_bin_faces_static(const amr_domain* dom, const float* faces, int64_t n_faces,
+                                                   int bin_density, uint32_t* offsets, uint32_t* ids,
+                                                   int64_t ids_capacity, int64_t* nnz) {
+  using namespace amr;
+  if (!dom || !offsets || !nnz || (dom->dim != 2 && dom->dim != 3) || !(dom->h0 > 0.0)) return AMR_EINVAL;
+  const int D = dom->dim;
+  const int B = bin_density;
+  if (B < 1 || B > 65535 || n_faces < 0 || n_faces > kStaticMaxFaces || ids_capacity < 0) return AMR_EINVAL;
+  int64_t nb = 1;
+  for (int a = 0; a < D; ++a) {
+    if (dom->root_blocks[a] < 1) return AMR_EINVAL;
+    nb *= B;
+    if (nb > kStaticMaxBins) return AMR_EINVAL;
+  }
+  if (n_faces > 0 && (!faces || !on_device(faces))) return AMR_EINVAL;
+  if (!on_device(offsets) || (ids_capacity > 0 && (!ids || !on_device(ids)))) return AMR_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AMR_ECUDA;
+  unsigned char* s = nullptr;
+  if (static_scratch(dev, &s) != cudaSuccess) return AMR_ECUDA;
+  cudaStream_t st = dom->stream ? static_cast<cudaStream_t>(dom->stream) : cudaStreamLegacy;
+  uint32_t* count = reinterpret_cast<uint32_t*>(s + kStCount);
+  uint32_t* frange = reinterpret_cast<uint32_t*>(s + kStRange);
+  uint64_t* total = reinterpret_cast<uint64_t*>(s + kStTotal);
+  unsigned* err = reinterpret_cast<unsigned*>(s + kStErr);
+  BinGrid g{};
+  g.B = B;
+  for (int a = 0; a < 3; ++a) {
+    g.origin[a] = dom->origin[a];
+    const double extent = (4.0 * (double)(a < D ? dom->root_blocks[a] : 1)) * dom->h0;
+    g.scale[a] = (double)B / extent;
+  }
+  // the array keeps the previous call's contents: zero the counts, the total and the error word
+  if (cudaMemsetAsync(count, 0, 4 * (size_t)nb, st) != cudaSuccess) return AMR_ECUDA;
+  if (cudaMemsetAsync(s + kStTotal, 0, 16, st) != cudaSuccess) return AMR_ECUDA;
+  launch_face_bins(D, faces, n_faces, g, frange, count, st);
+  launch_scan_u32(count, offsets, nb, total, s + kStScan, err, st);
+  uint64_t h_total = 0;
+  unsigned h_err = 0;
+  if (cudaMemcpyAsync(&h_total, total, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return AMR_ECUDA;
+  if (cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return AMR_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return AMR_ECUDA;
+  if (h_err & ERR_TIMEOUT) return AMR_ETIMEOUT;
+  if (h_err || h_total > 0xffffffffull) return AMR_EOVERFLOW;
+  *nnz = (int64_t)h_total;
+  if ((int64_t)h_total > ids_capacity) return AMR_EOVERFLOW;
+  if (n_faces > 0) {
+    const int gr = grid_for(n_faces, kThreads);
+    if (D == 3)
+      k_scatter_ids<3><<<gr, kThreads, 0, st>>>(n_faces, frange, offsets, count, ids, B);
+    else
+      k_scatter_ids<2><<<gr, kThreads, 0, st>>>(n_faces, frange, offsets, count, ids, B);
+  }
+  return cudaGetLastError() == cudaSuccess ? AMR_OK : AMR_ECUDA;
+}
