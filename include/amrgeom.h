@@ -172,6 +172,19 @@ typedef struct {
 } amr_refine_result;
 AMR_API amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* params, amr_refine_result* out);
 
+/* Vertex adjoint of the link fractions q (not part of the paper: it lets a
+ * training loop differentiate a loss of q with respect to the geometry).
+ * grad_q: DEVICE f32 [n_links] aligned with the link arrays of the last
+ * amr_refine_near_wall (which must have formed links).  grad_out: DEVICE f32,
+ * overwritten: [n_verts][dim] when the geometry was loaded as an index list,
+ * else [n_faces][dim][dim].  Gradients flow through q of the hit face only
+ * (dt/dv of the plane / line through that face); flags, masks and adjacency are
+ * not differentiated.  Deterministic: links are grouped by face with a stable
+ * radix sort and summed in ascending link order, face corners by vertex in
+ * ascending (face, corner) order, without float atomics, so repeated calls give
+ * bitwise identical results.  ESTATE without links; EINVAL for host pointers. */
+AMR_API amr_status amr_q_backward(amr_ctx* ctx, const float* grad_q, float* grad_out);
+
 /* Wait for all work of the context; report device-side check failures. */
 AMR_API amr_status amr_sync(amr_ctx* ctx);
 

@@ -16,6 +16,7 @@ from .binding import (  # noqa: F401
     amr_destroy,
     amr_geom_load,
     amr_launch_count,
+    amr_q_backward,
     amr_refine_near_wall,
     amr_set_stream,
     amr_sync,
@@ -23,4 +24,5 @@ from .binding import (  # noqa: F401
     amr_timing_get,
     amr_timing_reset,
     lib,
+    q_links,
 )

@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECUDA", 4
 
 EXPORTED = ["amr_create", "amr_destroy", "amr_status_str", "amr_last_error", "amr_set_stream", "amr_geom_load",
             "amr_bin_faces", "amr_refine_near_wall", "amr_sync", "amr_timing_enable", "amr_timing_reset",
-            "amr_timing_get", "amr_launch_count", "amr_bin_faces_static"]
+            "amr_timing_get", "amr_launch_count", "amr_bin_faces_static", "amr_q_backward"]
 
 
 class AmrError(RuntimeError):
@@ -109,6 +109,8 @@ def lib(build_if_missing: bool = True):
         L.amr_timing_get.argtypes = [P, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(i64), C.c_int]
         L.amr_launch_count.restype = C.c_int64
         L.amr_launch_count.argtypes = [P]
+        L.amr_q_backward.restype = C.c_int
+        L.amr_q_backward.argtypes = [P, P, P]
         L.amr_bin_faces_static.restype = C.c_int
         L.amr_bin_faces_static.argtypes = [C.POINTER(amr_domain), P, i64, C.c_int, P, P, i64, C.POINTER(i64)]
         _lib = L
@@ -167,6 +169,10 @@ def amr_refine_near_wall(ctx, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, wa
     r = amr_refine_result()
     _check(ctx, lib().amr_refine_near_wall(ctx, C.byref(p), C.byref(r)))
     return r
+
+
+def amr_q_backward(ctx, grad_q_ptr: int, grad_out_ptr: int):
+    _check(ctx, lib().amr_q_backward(ctx, grad_q_ptr, grad_out_ptr))
 
 
 def amr_sync(ctx):
@@ -290,6 +296,7 @@ class AmrGeom:
         if not v.is_contiguous():
             v = v.contiguous()
         self._keep = [v]
+        self.load_shape = tuple(v.shape)
         if idx is None:
             nf = v.shape[0]
             amr_geom_load(self.ctx, v.data_ptr(), 0, None, nf)
@@ -341,6 +348,15 @@ class AmrGeom:
         self.result = out
         return out
 
+    def q_backward(self, grad_q):
+        """d(loss)/d(load input) from d(loss)/d(link_q) of the last refine (shape of the load input)."""
+        import torch
+
+        g = torch.as_tensor(grad_q, dtype=torch.float32, device="cuda").contiguous()
+        out = torch.empty(self.load_shape, dtype=torch.float32, device="cuda")
+        amr_q_backward(self.ctx, g.data_ptr(), out.data_ptr())
+        return out
+
     def sync(self):
         amr_sync(self.ctx)
 
@@ -355,3 +371,43 @@ class AmrGeom:
 
     def launch_count(self) -> int:
         return amr_launch_count(self.ctx)
+
+
+def _make_qlinks():
+    import torch
+
+    class QLinks(torch.autograd.Function):
+        """q of the wall links as a differentiable function of the vertex coordinates.
+
+        Forward runs load -> bin -> refine (with links) on ``geom``; backward runs the
+        library's deterministic adjoint.  Only q is differentiated (flags, adjacency and
+        the choice of hit face are piecewise constant).  Call backward before the next
+        refine on the same ``geom``.
+        """
+
+        @staticmethod
+        def forward(ctx, verts, geom, idx, B, n_levels, d_abs, d_rel, lattice):
+            geom.load(verts.detach(), idx)
+            geom.bin(B)
+            res = geom.refine(n_levels, d_abs, d_rel, lattice, True, True)
+            ctx.geom = geom
+            q = res["link_q"].clone()
+            return q
+
+        @staticmethod
+        def backward(ctx, grad_q):
+            g = ctx.geom.q_backward(grad_q)
+            return g, None, None, None, None, None, None, None
+
+    return QLinks
+
+
+_QLINKS = None
+
+
+def q_links(geom, verts, idx, B, n_levels, d_abs=0.0, d_rel=1.0, lattice=19):
+    """Differentiable wall-link fractions q (see QLinks); returns a CUDA tensor [n_links]."""
+    global _QLINKS
+    if _QLINKS is None:
+        _QLINKS = _make_qlinks()
+    return _QLINKS.apply(verts, geom, idx, B, n_levels, d_abs, d_rel, lattice)

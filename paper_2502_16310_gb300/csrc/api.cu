@@ -57,6 +57,12 @@ struct amr_ctx {
   DevBuf cellcnt, blockcnt, block_base, adj_cell, adj_off, adj_ids;
   DevBuf link_cell, link_dir, link_q, link_face;
   int64_t link_cap = 0;
+  // adjoint: device copy of the index list, vertex -> corner and face -> link groupings
+  DevBuf idx, vert_off, vert_corners, face_off, face_links, sort_keys, grad_face, sort_scratch, group_cnt;
+  bool vert_groups = false, face_groups = false;
+  int64_t n_links = 0;
+  double finest_h = 0.0;
+  const int32_t* finest_blocks = nullptr;
   // misc layout: [0..CNT_N) u64 counters, then u32 err word, u32 work, u64 totals[4]
   unsigned long long* counters = nullptr;
   unsigned* d_err = nullptr;
@@ -300,6 +306,9 @@ amr_status amr_create(const amr_domain* dom, amr_ctx** out) {
 amr_status amr_destroy(amr_ctx* ctx) {
   if (!ctx) return AMR_OK;
   cudaStreamSynchronize(ctx->stream);
+  DevBuf* extra[] = {&ctx->idx, &ctx->vert_off, &ctx->vert_corners, &ctx->face_off, &ctx->face_links,
+                     &ctx->sort_keys, &ctx->grad_face, &ctx->sort_scratch, &ctx->group_cnt};
+  for (DevBuf* b : extra) release(ctx, *b);
   DevBuf* all[] = {&ctx->X,        &ctx->nrm,       &ctx->stage_a,    &ctx->stage_b,  &ctx->frange,
                    &ctx->count,    &ctx->offsets,   &ctx->ids,        &ctx->payload,  &ctx->scratch,
                    &ctx->misc,     &ctx->cellcnt,   &ctx->blockcnt,   &ctx->block_base, &ctx->adj_cell,
@@ -354,6 +363,7 @@ amr_status amr_geom_load(amr_ctx* ctx, const float* coords, int64_t n_verts, con
   if (n_faces > 0 && !coords) return fail(ctx, AMR_EINVAL, "null coordinates");
   if (idx && n_verts <= 0 && n_faces > 0) return fail(ctx, AMR_EINVAL, "indexed input needs n_verts > 0");
   ctx->loaded = ctx->binned = ctx->refined = false;
+  ctx->vert_groups = ctx->face_groups = false;
   ctx->nf = n_faces;
   ctx->nv = idx ? n_verts : 0;
   ctx->indexed = idx != nullptr;
@@ -365,6 +375,9 @@ amr_status amr_geom_load(amr_ctx* ctx, const float* coords, int64_t n_verts, con
       const void* di = nullptr;
       TRY(to_device(ctx, coords, sizeof(float) * D * (size_t)n_verts, ctx->stage_a, &dv));
       TRY(to_device(ctx, idx, sizeof(int32_t) * D * (size_t)n_faces, ctx->stage_b, &di));
+      TRY(ensure(ctx, ctx->idx, sizeof(int32_t) * D * (size_t)n_faces));
+      CK(cudaMemcpyAsync(ctx->idx.p, di, sizeof(int32_t) * D * (size_t)n_faces, cudaMemcpyDeviceToDevice,
+                         ctx->stream));
       timed(ctx, "load_gather", [&] {
         return launch_load_indexed(D, static_cast<const float*>(dv), n_verts, static_cast<const int32_t*>(di), n_faces,
                             static_cast<float*>(ctx->X.p), ctx->d_err, ctx->stream);
@@ -466,6 +479,8 @@ amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_
       return fail(ctx, AMR_EINVAL, "links need d_L >= h_L/2 on the finest level");
   }
   ctx->refined = false;
+  ctx->face_groups = false;
+  ctx->n_links = 0;
   amr_refine_result r{};
   r.n_levels = NL;
   CK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * CNT_N, ctx->stream));
@@ -633,9 +648,101 @@ amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_
   TRY(device_error(ctx, *reinterpret_cast<unsigned*>(h + 128)));
   ctx->refined = true;
   ctx->last = r;
+  ctx->n_links = links ? r.n_links : -1;
+  ctx->finest_h = ctx->dom.h0 * std::ldexp(1.0, -(NL - 1));
+  ctx->finest_blocks = r.block_coords[NL - 1];
   *out = r;
   return AMR_OK;
 }
+
+namespace {
+
+int key_bits(int64_t n) {
+  int b = 1;
+  while (b < 32 && ((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
+// Stable grouping of `n` keys in [0, n_keys): CSR offsets [n_keys + 1] and the
+// values (default 0..n-1) in ascending order within each key.
+amr_status group_by_key(amr_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n_keys, const uint32_t* vals,
+                        DevBuf& off, DevBuf& grouped, const char* name) {
+  TRY(ensure(ctx, off, sizeof(uint32_t) * (size_t)(n_keys + 1)));
+  TRY(ensure(ctx, grouped, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)));
+  TRY(ensure(ctx, ctx->sort_keys, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)));
+  TRY(ensure(ctx, ctx->sort_scratch, radix_sort_scratch_bytes(n)));
+  TRY(ensure(ctx, ctx->scratch, scan_u32_scratch_bytes(n_keys)));
+  TRY(ensure(ctx, ctx->group_cnt, sizeof(uint32_t) * (size_t)(n_keys > 0 ? n_keys : 1)));
+  CK(cudaMemsetAsync(ctx->group_cnt.p, 0, sizeof(uint32_t) * (size_t)(n_keys > 0 ? n_keys : 1), ctx->stream));
+  timed(ctx, name, [&] {
+    int k = launch_count_keys(keys, n, static_cast<uint32_t*>(ctx->group_cnt.p), ctx->stream);
+    k += launch_scan_u32(static_cast<const uint32_t*>(ctx->group_cnt.p), static_cast<uint32_t*>(off.p), n_keys,
+                         ctx->d_tot, ctx->scratch.p, ctx->d_err, ctx->stream);
+    k += launch_stable_sort(keys, n, key_bits(n_keys), static_cast<uint32_t*>(ctx->sort_keys.p),
+                            static_cast<uint32_t*>(grouped.p), vals, ctx->sort_scratch.p, ctx->d_tot, ctx->d_err,
+                            ctx->stream);
+    return k;
+  });
+  CK(cudaGetLastError());
+  return AMR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+amr_status amr_q_backward(amr_ctx* ctx, const float* grad_q, float* grad_out) {
+  if (!ctx) return AMR_EINVAL;
+  if (!ctx->refined || ctx->n_links < 0)
+    return fail(ctx, AMR_ESTATE, "amr_q_backward needs a preceding amr_refine_near_wall with links");
+  const int D = ctx->dom.dim;
+  const int64_t nl = ctx->n_links, nf = ctx->nf;
+  if (!grad_out || (nl > 0 && !grad_q)) return fail(ctx, AMR_EINVAL, "null gradient pointer");
+  if ((nl > 0 && !is_device_ptr(grad_q)) || !is_device_ptr(grad_out))
+    return fail(ctx, AMR_EINVAL, "gradients must be device pointers");
+  if (!ctx->face_groups) {
+    TRY(group_by_key(ctx, static_cast<const uint32_t*>(ctx->link_face.p), nl, nf, nullptr, ctx->face_off,
+                     ctx->face_links, "adjoint_group_links"));
+    ctx->face_groups = true;
+  }
+  const bool indexed = ctx->indexed;
+  if (indexed && !ctx->vert_groups) {
+    TRY(group_by_key(ctx, static_cast<const uint32_t*>(ctx->idx.p), nf * D, ctx->nv, nullptr, ctx->vert_off,
+                     ctx->vert_corners, "adjoint_group_corners"));
+    ctx->vert_groups = true;
+  }
+  float* gface = grad_out;
+  if (indexed) {
+    TRY(ensure(ctx, ctx->grad_face, sizeof(float) * D * D * (size_t)(nf > 0 ? nf : 1)));
+    gface = static_cast<float*>(ctx->grad_face.p);
+  }
+  AdjointArgs a{};
+  a.dim = D;
+  a.nf = nf;
+  a.X = static_cast<const float*>(ctx->X.p);
+  a.nrm = static_cast<const float*>(ctx->nrm.p);
+  a.face_off = static_cast<const uint32_t*>(ctx->face_off.p);
+  a.face_links = static_cast<const uint32_t*>(ctx->face_links.p);
+  a.grad_q = grad_q;
+  a.link_cell = static_cast<const uint32_t*>(ctx->link_cell.p);
+  a.link_dir = static_cast<const uint8_t*>(ctx->link_dir.p);
+  a.link_q = static_cast<const float*>(ctx->link_q.p);
+  a.adj_cell = static_cast<const uint32_t*>(ctx->adj_cell.p);
+  a.blocks = ctx->finest_blocks;
+  for (int c = 0; c < 3; ++c) a.origin[c] = ctx->dom.origin[c];
+  a.h = ctx->finest_h;
+  a.grad_face = gface;
+  timed(ctx, "adjoint_face", [&] { return launch_face_grad(a, ctx->stream); });
+  if (indexed)
+    timed(ctx, "adjoint_vertex", [&] {
+      return launch_vertex_grad(D, gface, static_cast<const uint32_t*>(ctx->vert_off.p),
+                                static_cast<const uint32_t*>(ctx->vert_corners.p), ctx->nv, grad_out, ctx->stream);
+    });
+  CK(cudaGetLastError());
+  return AMR_OK;
+}
+
+}  // extern "C"
 
 amr_status amr_timing_enable(amr_ctx* ctx, int on) {
   if (!ctx) return AMR_EINVAL;

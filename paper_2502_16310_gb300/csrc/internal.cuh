@@ -206,6 +206,32 @@ struct LinkArgs {
   unsigned long long* counters;
   unsigned* err;
 };
+struct AdjointArgs {
+  int dim;
+  int64_t nf;
+  const float* X;
+  const float* nrm;
+  const uint32_t* face_off;     // [nf + 1]
+  const uint32_t* face_links;   // link indices grouped by face, ascending within a face
+  const float* grad_q;
+  const uint32_t* link_cell;
+  const uint8_t* link_dir;
+  const float* link_q;
+  const uint32_t* adj_cell;
+  const int32_t* blocks;        // finest-level blocks
+  double origin[3];
+  double h;
+  float* grad_face;             // [nf][D][D]
+};
+size_t radix_sort_scratch_bytes(int64_t n);
+// Stable sort of n u32 keys (low key_bits significant); values default to 0..n-1.
+int launch_stable_sort(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys, uint32_t* sorted_vals,
+                       const uint32_t* vals_in, void* scratch, uint64_t* total, unsigned* err, cudaStream_t st);
+int launch_count_keys(const uint32_t* keys, int64_t n, uint32_t* cnt, cudaStream_t st);
+int launch_face_grad(const AdjointArgs& a, cudaStream_t st);
+int launch_vertex_grad(int dim, const float* grad_face, const uint32_t* vert_off, const uint32_t* vert_corners,
+                       int64_t nv, float* out, cudaStream_t st);
+
 size_t links_scratch_bytes(int64_t n_adj);
 int launch_links(const LinkArgs& a, void* scratch, cudaStream_t st);
 
