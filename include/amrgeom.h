@@ -122,7 +122,9 @@ AMR_API amr_status amr_bin_faces(amr_ctx* ctx, int bin_density, amr_bins_view* o
  * n_levels total levels (n_levels - 1 refinement passes), 1 <= n_levels <= AMR_MAX_LEVELS.
  * lattice: 0 (no links), 9 (D2Q9, dim 2) or 19 (D3Q19, dim 3).
  * want_links requires want_adjacency and d_L >= h_L/2 on the finest level, so
- * that every face a link crosses is in the cell's adjacency list. */
+ * that every face a link crosses is in the cell's adjacency list.
+ * Eager calls read back each level's size; graph calls read back once at the end
+ * and re-run eagerly (transparently) if a size outgrew the captured capacities. */
 typedef struct {
   int n_levels;
   double d_abs;               /* near-wall distance d_L = d_abs + d_rel * h_L, >= 0 */
@@ -130,6 +132,9 @@ typedef struct {
   int lattice;
   int want_adjacency;
   int want_links;
+  int use_graph;              /* 1: replay the level loop as one captured CUDA graph when the inputs match
+                                 the previous call (the first call runs eagerly and captures) */
+  int warps_per_cta;          /* warps per thread block of the refine kernels, 0 = default (4), max 8 */
 } amr_refine_params;
 
 /* Results.  Level arrays are per level 0..n_levels-1.
@@ -194,6 +199,55 @@ AMR_API amr_status amr_sync(amr_ctx* ctx);
 AMR_API amr_status amr_timing_enable(amr_ctx* ctx, int on);
 AMR_API amr_status amr_timing_reset(amr_ctx* ctx);
 AMR_API int amr_timing_get(amr_ctx* ctx, const char** names, double* total_ms, int64_t* launches, int cap);
+
+/* Autotuner (not in the paper; it automates the paper's bin-density study,
+ * where bin setup grows and face detection shrinks with B).  On the loaded
+ * geometry, times bin + refine (with the caller's adjacency / link options,
+ * eager mode, best of two runs, CUDA events) for each candidate bin density,
+ * then each candidate warps-per-block for the best density.  Candidates NULL =
+ * defaults (B in 4..256 with B^dim <= 2^24; warps 2, 4, 8).  Leaves the context
+ * binned with the last candidate: bin again with *best_B before refining. */
+AMR_API amr_status amr_autotune(amr_ctx* ctx, const amr_refine_params* params, const int* b_candidates, int n_b,
+                                const int* w_candidates, int n_w, int* best_B, int* best_warps, double* best_ms);
+
+/* Batched mode (not in the paper): many geometries of uneven size and depth
+ * refined together.  Per level, one refine launch and one child compaction
+ * cover every geometry still refining; geometries that end on a level form
+ * their adjacency lists and links there.  With use_graph the whole level loop
+ * is one CUDA graph replay.  Results are concatenations with batch-global
+ * indices; amr_batch_get_view gives one geometry's segments and the bases to
+ * subtract from its indices. */
+typedef struct amr_batch amr_batch;
+typedef struct {
+  amr_refine_result r;                    /* pointers into the batch's arrays, this geometry's segments */
+  int64_t level_base[AMR_MAX_LEVELS];     /* first block of the geometry in each level's batch list:
+                                             block_parent values and adj_cell / 4^dim are batch-global */
+  int64_t adj_base;                       /* first adjacent-cell row: subtract from link_cell */
+  int64_t pair_base;                      /* first adjacency pair: subtract from adj_off */
+  int64_t link_base;                      /* first link */
+  int64_t face_base;                      /* first face: subtract from adj_ids and link_face */
+  int64_t vert_base;                      /* first vertex (indexed input) */
+} amr_batch_view;
+/* Create an empty batch of dimension dim on `stream` (NULL: its own stream). */
+AMR_API amr_status amr_batch_create(int dim, void* stream, amr_batch** out);
+AMR_API amr_status amr_batch_destroy(amr_batch* b);
+/* Add one geometry (copied to the device now; host or device pointers): its own
+ * domain (dom->stream ignored), levels, near-wall distance and bin density
+ * (0 = set later with amr_batch_set_bins, e.g. from amr_autotune).  All
+ * geometries use the same input form (index list or face-vertex list). */
+AMR_API amr_status amr_batch_add(amr_batch* b, const amr_domain* dom, const float* coords, int64_t n_verts,
+                                 const int32_t* idx, int64_t n_faces, int n_levels, double d_abs, double d_rel,
+                                 int bin_density, int* index_out);
+AMR_API amr_status amr_batch_set_bins(amr_batch* b, int index, int bin_density);
+/* Gather, bin and refine every geometry.  params: lattice, want_adjacency,
+ * want_links, use_graph, warps_per_cta (n_levels and distances are per geometry). */
+AMR_API amr_status amr_batch_run(amr_batch* b, const amr_refine_params* params, amr_refine_result* out);
+AMR_API amr_status amr_batch_get_view(amr_batch* b, int index, amr_batch_view* out);
+/* Adjoint of all links of the last run: grad_out [sum n_verts][dim] (indexed) or
+ * [sum n_faces][dim][dim]; device pointers. */
+AMR_API amr_status amr_batch_q_backward(amr_batch* b, const float* grad_q, float* grad_out);
+AMR_API const char* amr_batch_last_error(const amr_batch* b);
+AMR_API int64_t amr_batch_launch_count(const amr_batch* b);
 
 /* Number of CUDA kernels this context has launched since its creation. */
 AMR_API int64_t amr_launch_count(const amr_ctx* ctx);

@@ -9,7 +9,9 @@ kernels behind the C ABI of ``include/amrgeom.h``; this package is its binding.
 from .binding import (  # noqa: F401
     EXPORTED,
     AmrError,
+    AmrBatch,
     AmrGeom,
+    amr_autotune,
     amr_bin_faces,
     amr_bin_faces_static,
     amr_create,

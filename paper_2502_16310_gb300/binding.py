@@ -30,7 +30,9 @@ STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECUDA", 4
 
 EXPORTED = ["amr_create", "amr_destroy", "amr_status_str", "amr_last_error", "amr_set_stream", "amr_geom_load",
             "amr_bin_faces", "amr_refine_near_wall", "amr_sync", "amr_timing_enable", "amr_timing_reset",
-            "amr_timing_get", "amr_launch_count", "amr_bin_faces_static", "amr_q_backward"]
+            "amr_timing_get", "amr_launch_count", "amr_bin_faces_static", "amr_q_backward", "amr_autotune",
+            "amr_batch_create", "amr_batch_destroy", "amr_batch_add", "amr_batch_set_bins", "amr_batch_run",
+            "amr_batch_get_view", "amr_batch_q_backward", "amr_batch_last_error", "amr_batch_launch_count"]
 
 
 class AmrError(RuntimeError):
@@ -51,7 +53,8 @@ class amr_bins_view(C.Structure):
 
 class amr_refine_params(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("d_abs", C.c_double), ("d_rel", C.c_double), ("lattice", C.c_int),
-                ("want_adjacency", C.c_int), ("want_links", C.c_int)]
+                ("want_adjacency", C.c_int), ("want_links", C.c_int), ("use_graph", C.c_int),
+                ("warps_per_cta", C.c_int)]
 
 
 class amr_refine_result(C.Structure):
@@ -63,6 +66,12 @@ class amr_refine_result(C.Structure):
                 ("link_cell", C.c_void_p), ("link_dir", C.c_void_p), ("link_q", C.c_void_p),
                 ("link_face", C.c_void_p), ("n_fallback", C.c_int64), ("n_band", C.c_int64),
                 ("n_candidates", C.c_int64), ("n_survivors", C.c_int64)]
+
+
+class amr_batch_view(C.Structure):
+    _fields_ = [("r", amr_refine_result), ("level_base", C.c_int64 * MAX_LEVELS), ("adj_base", C.c_int64),
+                ("pair_base", C.c_int64), ("link_base", C.c_int64), ("face_base", C.c_int64),
+                ("vert_base", C.c_int64)]
 
 
 def lib(build_if_missing: bool = True):
@@ -111,6 +120,28 @@ def lib(build_if_missing: bool = True):
         L.amr_launch_count.argtypes = [P]
         L.amr_q_backward.restype = C.c_int
         L.amr_q_backward.argtypes = [P, P, P]
+        L.amr_autotune.restype = C.c_int
+        L.amr_autotune.argtypes = [P, C.POINTER(amr_refine_params), P, C.c_int, P, C.c_int, C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.amr_batch_create.restype = C.c_int
+        L.amr_batch_create.argtypes = [C.c_int, P, C.POINTER(P)]
+        L.amr_batch_destroy.restype = C.c_int
+        L.amr_batch_destroy.argtypes = [P]
+        L.amr_batch_add.restype = C.c_int
+        L.amr_batch_add.argtypes = [P, C.POINTER(amr_domain), P, i64, P, i64, C.c_int, C.c_double, C.c_double,
+                                    C.c_int, C.POINTER(C.c_int)]
+        L.amr_batch_set_bins.restype = C.c_int
+        L.amr_batch_set_bins.argtypes = [P, C.c_int, C.c_int]
+        L.amr_batch_run.restype = C.c_int
+        L.amr_batch_run.argtypes = [P, C.POINTER(amr_refine_params), C.POINTER(amr_refine_result)]
+        L.amr_batch_get_view.restype = C.c_int
+        L.amr_batch_get_view.argtypes = [P, C.c_int, C.POINTER(amr_batch_view)]
+        L.amr_batch_q_backward.restype = C.c_int
+        L.amr_batch_q_backward.argtypes = [P, P, P]
+        L.amr_batch_last_error.restype = C.c_char_p
+        L.amr_batch_last_error.argtypes = [P]
+        L.amr_batch_launch_count.restype = C.c_int64
+        L.amr_batch_launch_count.argtypes = [P]
         L.amr_bin_faces_static.restype = C.c_int
         L.amr_bin_faces_static.argtypes = [C.POINTER(amr_domain), P, i64, C.c_int, P, P, i64, C.POINTER(i64)]
         _lib = L
@@ -162,10 +193,11 @@ def amr_bin_faces(ctx, bin_density: int) -> amr_bins_view:
 
 
 def amr_refine_near_wall(ctx, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True,
-                         want_links=True) -> amr_refine_result:
+                         want_links=True, use_graph=False, warps_per_cta=0) -> amr_refine_result:
     p = amr_refine_params()
     p.n_levels, p.d_abs, p.d_rel, p.lattice = int(n_levels), float(d_abs), float(d_rel), int(lattice)
     p.want_adjacency, p.want_links = int(bool(want_adjacency)), int(bool(want_links))
+    p.use_graph, p.warps_per_cta = int(bool(use_graph)), int(warps_per_cta)
     r = amr_refine_result()
     _check(ctx, lib().amr_refine_near_wall(ctx, C.byref(p), C.byref(r)))
     return r
@@ -177,6 +209,32 @@ def amr_q_backward(ctx, grad_q_ptr: int, grad_out_ptr: int):
 
 def amr_sync(ctx):
     _check(ctx, lib().amr_sync(ctx))
+
+
+def _params(n_levels=1, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=True, use_graph=False,
+            warps_per_cta=0):
+    p = amr_refine_params()
+    p.n_levels, p.d_abs, p.d_rel, p.lattice = int(n_levels), float(d_abs), float(d_rel), int(lattice)
+    p.want_adjacency, p.want_links = int(bool(want_adjacency)), int(bool(want_links))
+    p.use_graph, p.warps_per_cta = int(bool(use_graph)), int(warps_per_cta)
+    return p
+
+
+def amr_autotune(ctx, n_levels, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=True,
+                 b_candidates=None, w_candidates=None):
+    """(best bin density, best warps per block, best ms) on the loaded geometry."""
+    p = _params(n_levels, d_abs, d_rel, lattice, want_adjacency, want_links)
+    bc = (C.c_int * len(b_candidates))(*b_candidates) if b_candidates else None
+    wc = (C.c_int * len(w_candidates))(*w_candidates) if w_candidates else None
+    bb, bw, bt = C.c_int(0), C.c_int(0), C.c_double(0)
+    _check(ctx, lib().amr_autotune(ctx, C.byref(p), bc, len(b_candidates or []), wc, len(w_candidates or []),
+                                   C.byref(bb), C.byref(bw), C.byref(bt)))
+    return int(bb.value), int(bw.value), float(bt.value)
+
+
+def _bcheck(b, st):
+    if st != AMR_OK:
+        raise AmrError(st, lib().amr_batch_last_error(b).decode())
 
 
 def amr_timing_enable(ctx, on: bool):
@@ -315,13 +373,18 @@ class AmrGeom:
                      "offsets": _u32(v.offsets, v.n_bins + 1), "ids": _u32(v.ids, v.nnz)}
         return self.bins
 
-    def refine(self, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=None):
+    def refine(self, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=None,
+               use_graph=False, warps_per_cta=0):
         """Step 3: near-wall refinement; returns per-level tensors, adjacency CSR and links (borrowed)."""
-        import torch
-
         if want_links is None:
             want_links = lattice != 0
-        r = amr_refine_near_wall(self.ctx, n_levels, d_abs, d_rel, lattice, want_adjacency, want_links)
+        r = amr_refine_near_wall(self.ctx, n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph,
+                                 warps_per_cta)
+        return self._wrap(r, want_adjacency, want_links)
+
+    def _wrap(self, r, want_adjacency, want_links):
+        import torch
+
         D = self.dim
         levels = []
         for L in range(r.n_levels):
@@ -372,6 +435,12 @@ class AmrGeom:
     def launch_count(self) -> int:
         return amr_launch_count(self.ctx)
 
+    def autotune(self, n_levels, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=True,
+                 b_candidates=None, w_candidates=None):
+        """Pick the bin density and warps per block by timing bin + refine on the loaded geometry."""
+        return amr_autotune(self.ctx, n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, b_candidates,
+                            w_candidates)
+
 
 def _make_qlinks():
     import torch
@@ -411,3 +480,127 @@ def q_links(geom, verts, idx, B, n_levels, d_abs=0.0, d_rel=1.0, lattice=19):
     if _QLINKS is None:
         _QLINKS = _make_qlinks()
     return _QLINKS.apply(verts, geom, idx, B, n_levels, d_abs, d_rel, lattice)
+
+
+class AmrBatch:
+    """Many geometries refined together (one launch per level for all of them).
+
+    ``add`` takes each geometry's vertices/faces (torch or numpy, host or CUDA), its
+    root grid, levels, near-wall distance and bin density (0 = tune later).
+    ``run`` returns concatenated results (batch-global indices); ``view(i)``
+    returns geometry i's results with local indices, as fresh CUDA tensors.
+    """
+
+    def __init__(self, dim: int):
+        import torch
+
+        self.dim = dim
+        self.stream = torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = lib().amr_batch_create(dim, self.stream.cuda_stream or 1, C.byref(h))
+        if st != AMR_OK:
+            raise AmrError(st, "amr_batch_create failed")
+        self.b = h
+        self.geoms = []
+        self.result = None
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().amr_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, verts, idx, root, n_levels, d_abs=0.0, d_rel=1.0, bin_density=0, origin=(0.0, 0.0, 0.0),
+            h0=None):
+        import torch
+
+        v = torch.as_tensor(verts, dtype=torch.float32).contiguous()
+        root = tuple(int(r) for r in (root if hasattr(root, "__len__") else [root] * self.dim))
+        d = amr_domain()
+        d.dim = self.dim
+        rb = list(root) + [1] * (3 - len(root))
+        for a in range(3):
+            d.root_blocks[a] = rb[a]
+            d.origin[a] = float(origin[a]) if a < len(origin) else 0.0
+        d.h0 = float(h0 if h0 is not None else 1.0 / (4.0 * rb[0]))
+        out = C.c_int(-1)
+        if idx is None:
+            st = lib().amr_batch_add(self.b, C.byref(d), v.data_ptr(), 0, None, v.shape[0], int(n_levels),
+                                     float(d_abs), float(d_rel), int(bin_density), C.byref(out))
+            nv = 0
+        else:
+            ix = torch.as_tensor(idx, dtype=torch.int32).contiguous()
+            st = lib().amr_batch_add(self.b, C.byref(d), v.data_ptr(), v.shape[0], ix.data_ptr(), ix.shape[0],
+                                     int(n_levels), float(d_abs), float(d_rel), int(bin_density), C.byref(out))
+            nv = v.shape[0]
+        _bcheck(self.b, st)
+        self.geoms.append({"n_levels": int(n_levels), "nv": nv, "nf": int(v.shape[0] if idx is None else idx.shape[0]),
+                           "shape": tuple(v.shape)})
+        return int(out.value)
+
+    def set_bins(self, i, B):
+        _bcheck(self.b, lib().amr_batch_set_bins(self.b, int(i), int(B)))
+
+    def run(self, lattice=0, want_adjacency=True, want_links=None, use_graph=False, warps_per_cta=0):
+        if want_links is None:
+            want_links = lattice != 0
+        p = _params(1, 0.0, 1.0, lattice, want_adjacency, want_links, use_graph, warps_per_cta)
+        r = amr_refine_result()
+        _bcheck(self.b, lib().amr_batch_run(self.b, C.byref(p), C.byref(r)))
+        self.want = (want_adjacency or want_links, want_links)
+        self.result = r
+        return r
+
+    def view(self, i):
+        """Geometry i's results with local indices (fresh tensors)."""
+        import torch
+
+        v = amr_batch_view()
+        _bcheck(self.b, lib().amr_batch_get_view(self.b, int(i), C.byref(v)))
+        r, D = v.r, self.dim
+        nc = 64 if D == 3 else 16
+        levels = []
+        for L in range(r.n_levels):
+            n = int(r.n_blocks[L])
+            par = None
+            if L > 0:
+                par = _view(r.block_parent[L], (n,), torch.int32).clone() - int(v.level_base[L - 1])
+            levels.append({"blocks": _view(r.block_coords[L], (n, D), torch.int32).clone(), "parent": par,
+                           "mask": _view(r.cell_mask[L], (n,), torch.int64).clone(),
+                           "flag": _view(r.block_flag[L], (n,), torch.uint8).clone()})
+        out = {"levels": levels}
+        adj, links = self.want
+        Lf = r.n_levels - 1
+        if adj:
+            na, npairs = int(r.n_adj_cells), int(r.n_adj_pairs)
+            out["adj_cell"] = _u32(r.adj_cell, na).long() - int(v.level_base[Lf]) * nc
+            out["adj_off"] = _u32(r.adj_off, na + 1).long() - int(v.pair_base)
+            out["adj_ids"] = _u32(r.adj_ids, npairs).long() - int(v.face_base)
+        if links:
+            nl = int(r.n_links)
+            out["link_cell"] = _u32(r.link_cell, nl).long() - int(v.adj_base)
+            out["link_dir"] = _view(r.link_dir, (nl,), torch.uint8).clone()
+            out["link_q"] = _view(r.link_q, (nl,), torch.float32).clone()
+            out["link_face"] = _u32(r.link_face, nl).long() - int(v.face_base)
+        out["bases"] = {"face": int(v.face_base), "vert": int(v.vert_base), "link": int(v.link_base)}
+        return out
+
+    def q_backward(self, grad_q):
+        import torch
+
+        g = torch.as_tensor(grad_q, dtype=torch.float32, device="cuda").contiguous()
+        if self.geoms and self.geoms[0]["nv"]:
+            shape = (sum(x["nv"] for x in self.geoms), self.dim)
+        else:
+            shape = (sum(x["nf"] for x in self.geoms), self.dim, self.dim)
+        out = torch.empty(shape, dtype=torch.float32, device="cuda")
+        _bcheck(self.b, lib().amr_batch_q_backward(self.b, g.data_ptr(), out.data_ptr()))
+        return out
+
+    def launch_count(self):
+        return int(lib().amr_batch_launch_count(self.b))

@@ -1,10 +1,19 @@
 // api.cu — host side of the C ABI declared in include/amrgeom.h.
 //
-// The context owns grow-only device buffers (stream-ordered allocations on
-// its stream), small pinned host staging for the few device->host reads of
-// sizes, and an optional per-kernel CUDA-event timing table.  Every step runs
-// as kernels on one stream; the host synchronises only to learn data-dependent
-// sizes (bin entries, blocks of the next level, adjacency and link counts).
+// A context owns grow-only device buffers (stream-ordered allocations), small
+// pinned host staging for the few device->host reads of sizes, and an optional
+// per-kernel CUDA-event timing table.  One level engine serves both a single
+// geometry and a batch of geometries (a geometry table plus a geometry id per
+// block and per face): every level is one refine launch over the blocks of
+// all geometries, one child compaction, and, where geometries end, one
+// adjacency and one link launch.
+//
+// Two modes run the engine.  Eager mode learns the data-dependent sizes with a
+// few device->host reads and grows the buffers.  Graph mode (after one eager
+// call with the same inputs) replays the whole level loop as one captured CUDA
+// graph whose kernels read their sizes from device memory and check them
+// against the capacities of the eager call; only the final sizes are read
+// back.  An overflow re-runs the call eagerly.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -35,43 +44,79 @@ struct TimingSlot {
   int64_t launches = 0;
 };
 
+struct LevelBufs {
+  DevBuf blocks, gid, parent, mask, flag, cellcnt, blockcnt, base;
+  int64_t cap = 0;  // capacity in blocks
+};
+
+// device scalar block (u64 slots)
+constexpr int SC_N = 0;      // [16] blocks per level
+constexpr int SC_TOT = 16;   // [16] adjacency totals per level (pairs | cells << 32)
+constexpr int SC_NL = 32;    // [16] links per level
+constexpr int SC_RUN = 48;   // [3] running cells, pairs, links
+constexpr int SC_WORDS = 64;
+
+// A captured graph stays valid while no buffer it uses was reallocated
+// (layout generation) and its by-value kernel arguments are unchanged.
+struct GraphKey {
+  uint64_t layout_gen = 0;
+  int64_t nf = 0, n_geom = 0;
+  int n_levels = 0, lattice = 0, adjacency = 0, links = 0, warps = 0, B = 0;
+  double d_abs = 0, d_rel = 0;
+  bool operator==(const GraphKey& o) const {
+    return layout_gen == o.layout_gen && nf == o.nf && n_geom == o.n_geom && n_levels == o.n_levels &&
+           lattice == o.lattice && adjacency == o.adjacency && links == o.links && warps == o.warps && B == o.B &&
+           d_abs == o.d_abs && d_rel == o.d_rel;
+  }
+};
+
 }  // namespace
 
 struct amr_ctx {
   amr_domain dom{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t gstream = nullptr;  // capture / replay stream of the graph mode
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int device = 0;
   int num_sms = 0;
   std::string err;
   // state
   bool loaded = false, binned = false, refined = false;
+  uint64_t load_gen = 0, bin_gen = 0, layout_gen = 0;
   int64_t nf = 0, nv = 0;
   bool indexed = false;
   int B = 0;
   int64_t n_bins = 0, nnz = 0;
   bool count_clean = false;
+  // geometry table: one row per geometry; multi = per-block / per-face geometry ids in use
+  std::vector<GeomParams> geoms;
+  bool multi = false;
+  DevBuf table, face_gid;
   // buffers
-  DevBuf X, nrm, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc;
-  DevBuf lv_blocks[AMR_MAX_LEVELS], lv_parent[AMR_MAX_LEVELS], lv_mask[AMR_MAX_LEVELS], lv_flag[AMR_MAX_LEVELS];
-  DevBuf cellcnt, blockcnt, block_base, adj_cell, adj_off, adj_ids;
-  DevBuf link_cell, link_dir, link_q, link_face;
-  int64_t link_cap = 0;
-  // adjoint: device copy of the index list, vertex -> corner and face -> link groupings
-  DevBuf idx, vert_off, vert_corners, face_off, face_links, sort_keys, grad_face, sort_scratch, group_cnt;
+  DevBuf X, nrm, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
+  LevelBufs lv[AMR_MAX_LEVELS];
+  DevBuf adj_cell, adj_off, adj_ids, link_cell, link_dir, link_q, link_face;
+  int64_t cap_cells = 0, cap_pairs = 0, cap_links = 0;
+  // adjoint
+  DevBuf idx, vert_off, vert_corners, face_off, face_links, sort_keys, grad_face, sort_scratch, group_cnt, lvl_ptrs;
   bool vert_groups = false, face_groups = false;
   int64_t n_links = 0;
-  double finest_h = 0.0;
-  const int32_t* finest_blocks = nullptr;
   // misc layout: [0..CNT_N) u64 counters, then u32 err word, u32 work, u64 totals[4]
   unsigned long long* counters = nullptr;
   unsigned* d_err = nullptr;
   unsigned* d_work = nullptr;
   uint64_t* d_tot = nullptr;
-  void* h_pinned = nullptr;  // 256 bytes
+  uint64_t* d_scal = nullptr;
+  void* h_pinned = nullptr;  // 1 KB
   amr_refine_result last{};
+  // graph mode
+  cudaGraphExec_t gexec = nullptr;
+  GraphKey gkey;
+  int64_t graph_launches = 0;
   // timing
   bool timing = false;
+  bool capturing = false;
   std::vector<TimingSlot> slots;
   std::vector<TimedLaunch> pending;
   std::vector<cudaEvent_t> event_pool;
@@ -107,6 +152,7 @@ amr_status fail(amr_ctx* c, amr_status s, const char* fmt, ...) {
 amr_status ensure(amr_ctx* ctx, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return AMR_OK;
+  ++ctx->layout_gen;
   if (b.p) {
     CK(cudaFreeAsync(b.p, ctx->stream));
     b.p = nullptr;
@@ -120,6 +166,17 @@ amr_status ensure(amr_ctx* ctx, DevBuf& b, size_t bytes) {
     return fail(ctx, AMR_ENOMEM, "device allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
   }
   b.cap = want;
+  return AMR_OK;
+}
+
+// Grow keeping the first `keep` bytes.
+amr_status ensure_keep(amr_ctx* ctx, DevBuf& b, size_t bytes, size_t keep) {
+  if (b.cap >= bytes) return AMR_OK;
+  DevBuf nb;
+  TRY(ensure(ctx, nb, bytes));
+  if (b.p && keep) CK(cudaMemcpyAsync(nb.p, b.p, keep < b.cap ? keep : b.cap, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (b.p) CK(cudaFreeAsync(b.p, ctx->stream));
+  b = nb;
   return AMR_OK;
 }
 
@@ -147,17 +204,17 @@ cudaEvent_t take_event(amr_ctx* c) {
   return e;
 }
 
-// Times the launches issued inside fn() when timing is on.
+// Times the launches issued inside fn() when timing is on (not while capturing).
 template <typename F>
-void timed(amr_ctx* c, const char* name, F fn) {
-  if (!c->timing) {
+void timed(amr_ctx* c, cudaStream_t st, const char* name, F fn) {
+  if (!c->timing || c->capturing) {
     c->launches += fn();
     return;
   }
   TimedLaunch t{slot_of(c, name), take_event(c), take_event(c)};
-  cudaEventRecord(t.a, c->stream);
+  cudaEventRecord(t.a, st);
   c->launches += fn();
-  cudaEventRecord(t.b, c->stream);
+  cudaEventRecord(t.b, st);
   c->pending.push_back(t);
 }
 
@@ -174,23 +231,32 @@ void harvest_timing(amr_ctx* c) {
   c->pending.clear();
 }
 
-amr_status sync_check(amr_ctx* ctx) {
-  CK(cudaStreamSynchronize(ctx->stream));
+amr_status sync_check(amr_ctx* ctx, cudaStream_t st) {
+  CK(cudaStreamSynchronize(st));
   CK(cudaGetLastError());
   harvest_timing(ctx);
-  unsigned e = *reinterpret_cast<volatile unsigned*>(static_cast<char*>(ctx->h_pinned) + 128);
-  (void)e;
   return AMR_OK;
 }
 
-// Copy the device error word and the requested totals to pinned memory and wait.
-amr_status read_back(amr_ctx* ctx, unsigned* err_out, uint64_t* tot_out, int n_tot) {
+// Copy the device error word and the first totals to pinned memory and wait.
+amr_status read_back(amr_ctx* ctx, cudaStream_t st, unsigned* err_out, uint64_t* tot_out, int n_tot) {
   char* h = static_cast<char*>(ctx->h_pinned);
-  CK(cudaMemcpyAsync(h, ctx->d_tot, sizeof(uint64_t) * 4, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
-  TRY(sync_check(ctx));
+  CK(cudaMemcpyAsync(h, ctx->d_tot, sizeof(uint64_t) * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TRY(sync_check(ctx, st));
   if (tot_out)
     for (int i = 0; i < n_tot; ++i) tot_out[i] = reinterpret_cast<uint64_t*>(h)[i];
+  *err_out = *reinterpret_cast<unsigned*>(h + 64);
+  return AMR_OK;
+}
+
+// One device scalar (u64) and the error word.
+amr_status read_scalar(amr_ctx* ctx, cudaStream_t st, int slot, uint64_t* v, unsigned* err_out) {
+  char* h = static_cast<char*>(ctx->h_pinned);
+  CK(cudaMemcpyAsync(h + 128, ctx->d_scal + slot, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TRY(sync_check(ctx, st));
+  *v = *reinterpret_cast<uint64_t*>(h + 128);
   *err_out = *reinterpret_cast<unsigned*>(h + 64);
   return AMR_OK;
 }
@@ -232,18 +298,534 @@ amr_status to_device(amr_ctx* ctx, const void* src, size_t bytes, DevBuf& stage,
   return AMR_OK;
 }
 
-BinGrid make_grid(const amr_domain& d, int B) {
-  BinGrid g{};
-  g.B = B;
-  for (int a = 0; a < 3; ++a) {
-    g.origin[a] = d.origin[a];
-    const double extent = (4.0 * (double)(a < d.dim ? d.root_blocks[a] : 1)) * d.h0;
-    g.scale[a] = (double)B / extent;
-  }
-  return g;
+int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+int64_t roots_of(const GeomParams& g, int D) {
+  int64_t n = 1;
+  for (int a = 0; a < D; ++a) n *= g.root[a];
+  return n;
+}
+
+void drop_graph(amr_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
 }
 
 }  // namespace
+
+// Table row of a geometry: domain, bins, levels and near-wall distance.
+GeomParams amr_make_row(const amr_domain& d, int B, int n_levels, double d_abs, double d_rel) {
+  GeomParams g{};
+  for (int a = 0; a < 3; ++a) {
+    g.origin[a] = d.origin[a];
+    g.root[a] = a < d.dim ? d.root_blocks[a] : 1;
+    const double extent = (4.0 * (double)g.root[a]) * d.h0;
+    g.bin_scale[a] = B > 0 ? (double)B / extent : 0.0;
+  }
+  g.h0 = d.h0;
+  g.B = B;
+  g.n_levels = n_levels;
+  g.d_abs = d_abs;
+  g.d_rel = d_rel;
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// context life cycle, binning and the level engine (also used by batch.cu)
+// ---------------------------------------------------------------------------
+amr_status amr_ctx_init(amr_ctx* ctx) {
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess && !ctx->stream) {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    ctx->own_stream = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 1024);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return AMR_ECUDA;
+  }
+  if (ensure(ctx, ctx->misc, sizeof(unsigned long long) * CNT_N + 64 + 64) != AMR_OK) return AMR_ENOMEM;
+  if (ensure(ctx, ctx->scal, sizeof(uint64_t) * SC_WORDS) != AMR_OK) return AMR_ENOMEM;
+  char* m = static_cast<char*>(ctx->misc.p);
+  ctx->counters = reinterpret_cast<unsigned long long*>(m);
+  ctx->d_err = reinterpret_cast<unsigned*>(m + sizeof(unsigned long long) * CNT_N);
+  ctx->d_work = ctx->d_err + 1;
+  ctx->d_tot = reinterpret_cast<uint64_t*>(m + sizeof(unsigned long long) * CNT_N + 64);
+  ctx->d_scal = static_cast<uint64_t*>(ctx->scal.p);
+  cudaMemsetAsync(ctx->misc.p, 0, ctx->misc.cap, ctx->stream);
+  cudaMemsetAsync(ctx->scal.p, 0, ctx->scal.cap, ctx->stream);
+  return AMR_OK;
+}
+
+void amr_ctx_free(amr_ctx* ctx) {
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  drop_graph(ctx);
+  DevBuf* all[] = {&ctx->X,         &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
+                   &ctx->count,     &ctx->offsets,      &ctx->ids,        &ctx->payload,    &ctx->scratch,
+                   &ctx->misc,      &ctx->scal,         &ctx->adj_cell,   &ctx->adj_off,    &ctx->adj_ids,
+                   &ctx->link_cell, &ctx->link_dir,     &ctx->link_q,     &ctx->link_face,  &ctx->idx,
+                   &ctx->vert_off,  &ctx->vert_corners, &ctx->face_off,   &ctx->face_links, &ctx->sort_keys,
+                   &ctx->grad_face, &ctx->sort_scratch, &ctx->group_cnt,  &ctx->lvl_ptrs,   &ctx->table,
+                   &ctx->face_gid};
+  for (DevBuf* b : all) release(ctx, *b);
+  for (int L = 0; L < AMR_MAX_LEVELS; ++L) {
+    LevelBufs& l = ctx->lv[L];
+    DevBuf* lb[] = {&l.blocks, &l.gid, &l.parent, &l.mask, &l.flag, &l.cellcnt, &l.blockcnt, &l.base};
+    for (DevBuf* b : lb) release(ctx, *b);
+  }
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& t : ctx->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+}
+
+// Binning of every geometry of the table in one pass (count, scan, scatter).
+amr_status amr_bin_all(amr_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  const int D = ctx->dom.dim;
+  const int64_t nf = ctx->nf;
+  int64_t nb = 0;
+  for (auto& g : ctx->geoms) {
+    g.bin_base = nb;
+    nb += ipow(g.B, D);
+  }
+  if (ctx->multi) {
+    TRY(ensure(ctx, ctx->table, sizeof(GeomParams) * ctx->geoms.size()));
+    CK(cudaMemcpyAsync(ctx->table.p, ctx->geoms.data(), sizeof(GeomParams) * ctx->geoms.size(),
+                       cudaMemcpyHostToDevice, st));
+  }
+  if (ctx->count.cap < sizeof(uint32_t) * (size_t)nb) ctx->count_clean = false;
+  TRY(ensure(ctx, ctx->count, sizeof(uint32_t) * (size_t)nb));
+  if (!ctx->count_clean) {
+    CK(cudaMemsetAsync(ctx->count.p, 0, ctx->count.cap, st));
+    ctx->count_clean = true;
+  }
+  TRY(ensure(ctx, ctx->offsets, sizeof(uint32_t) * (size_t)(nb + 1)));
+  TRY(ensure(ctx, ctx->frange, sizeof(uint32_t) * 3 * (size_t)(nf > 0 ? nf : 1)));
+  TRY(ensure(ctx, ctx->scratch, scan_u32_scratch_bytes(nb)));
+  FaceBinArgs fa{};
+  fa.dim = D;
+  fa.X = static_cast<const float*>(ctx->X.p);
+  fa.nf = nf;
+  fa.g0 = ctx->geoms[0];
+  fa.table = ctx->multi ? static_cast<const GeomParams*>(ctx->table.p) : nullptr;
+  fa.face_gid = ctx->multi ? static_cast<const uint32_t*>(ctx->face_gid.p) : nullptr;
+  fa.frange = static_cast<uint32_t*>(ctx->frange.p);
+  fa.count = static_cast<uint32_t*>(ctx->count.p);
+  uint32_t* offsets = static_cast<uint32_t*>(ctx->offsets.p);
+  timed(ctx, st, "bin_count", [&] { return launch_face_bins(fa, st); });
+  timed(ctx, st, "bin_scan", [&] {
+    return launch_scan_u32(fa.count, offsets, nb, ctx->d_tot, ctx->scratch.p, ctx->d_err, st);
+  });
+  CK(cudaGetLastError());
+  unsigned e = 0;
+  uint64_t tot = 0;
+  TRY(read_back(ctx, st, &e, &tot, 1));
+  if (e) {
+    ctx->count_clean = false;
+    return device_error(ctx, e);
+  }
+  if (tot > 0xffffffffull) {
+    ctx->count_clean = false;
+    return fail(ctx, AMR_EOVERFLOW, "%llu (face, bin) entries exceed 2^32 - 1", (unsigned long long)tot);
+  }
+  const size_t esz = D == 3 ? sizeof(Entry3) : sizeof(Entry2);
+  TRY(ensure(ctx, ctx->ids, sizeof(uint32_t) * (size_t)tot));
+  TRY(ensure(ctx, ctx->payload, esz * (size_t)tot));
+  ScatterArgs sa{};
+  sa.f = fa;
+  sa.offsets = offsets;
+  sa.ids = static_cast<uint32_t*>(ctx->ids.p);
+  sa.payload = ctx->payload.p;
+  timed(ctx, st, "bin_scatter", [&] { return launch_scatter(sa, st); });
+  CK(cudaGetLastError());
+  ctx->n_bins = nb;
+  ctx->nnz = (int64_t)tot;
+  ctx->binned = true;
+  ++ctx->bin_gen;
+  return AMR_OK;
+}
+
+namespace {
+
+struct Plan {
+  int NL;                           // levels of the deepest geometry
+  bool fin_at[AMR_MAX_LEVELS];      // some geometry ends at this level
+  bool cont_after[AMR_MAX_LEVELS];  // some geometry continues below this level
+  bool adjacency, links;
+  int lattice, warps;
+  int64_t n_roots;
+};
+
+Plan make_plan(const amr_ctx* ctx, const amr_refine_params* p) {
+  Plan P{};
+  for (const auto& g : ctx->geoms) P.NL = g.n_levels > P.NL ? g.n_levels : P.NL;
+  for (const auto& g : ctx->geoms) {
+    P.fin_at[g.n_levels - 1] = true;
+    for (int L = 0; L < g.n_levels - 1; ++L) P.cont_after[L] = true;
+  }
+  P.links = p->want_links != 0;
+  P.adjacency = p->want_adjacency != 0 || P.links;
+  P.lattice = p->lattice;
+  P.warps = p->warps_per_cta > 0 ? p->warps_per_cta : 4;
+  for (const auto& g : ctx->geoms) P.n_roots += roots_of(g, ctx->dom.dim);
+  return P;
+}
+
+RefineLevel level_args(amr_ctx* ctx, const Plan& P, int L) {
+  RefineLevel a{};
+  a.dim = ctx->dom.dim;
+  a.level = L;
+  a.g0 = ctx->geoms[0];
+  a.table = ctx->multi ? static_cast<const GeomParams*>(ctx->table.p) : nullptr;
+  a.gid = ctx->multi ? static_cast<const uint32_t*>(ctx->lv[L].gid.p) : nullptr;
+  a.blocks = static_cast<const int32_t*>(ctx->lv[L].blocks.p);
+  a.n_blocks = ctx->lv[L].cap;
+  a.n_dev = ctx->d_scal + SC_N + L;
+  a.offsets = static_cast<const uint32_t*>(ctx->offsets.p);
+  a.payload = ctx->payload.p;
+  a.X = static_cast<const float*>(ctx->X.p);
+  a.nrm = static_cast<const float*>(ctx->nrm.p);
+  a.nf = ctx->nf;
+  a.mask = static_cast<uint64_t*>(ctx->lv[L].mask.p);
+  a.flag = static_cast<uint8_t*>(ctx->lv[L].flag.p);
+  if (P.fin_at[L] && P.adjacency) {
+    a.cellcnt = static_cast<uint16_t*>(ctx->lv[L].cellcnt.p);
+    a.blockcnt = static_cast<uint64_t*>(ctx->lv[L].blockcnt.p);
+  }
+  a.counters = ctx->counters;
+  a.work = ctx->d_work;
+  a.err = ctx->d_err;
+  a.warps = P.warps;
+  return a;
+}
+
+__global__ void k_set_u64(uint64_t* p, uint64_t v) { *p = v; }
+
+// One pass over all levels.  eager: learn sizes with read-backs and grow
+// buffers; otherwise (capture) use the capacities as they are.
+amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st) {
+  const int D = ctx->dom.dim;
+  const int NCH = D == 3 ? 8 : 4;
+  const int NCell = D == 3 ? 64 : 16;
+  CK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * CNT_N, st));
+  CK(cudaMemsetAsync(ctx->d_scal, 0, sizeof(uint64_t) * SC_WORDS, st));
+  int64_t run_cells = 0, run_pairs = 0, run_links = 0;
+  const int64_t N0 = P.n_roots;
+  if (eager) {
+    ctx->lv[0].cap = N0;
+    TRY(ensure(ctx, ctx->lv[0].blocks, sizeof(int32_t) * D * (size_t)(N0 > 0 ? N0 : 1)));
+    if (ctx->multi) TRY(ensure(ctx, ctx->lv[0].gid, sizeof(uint32_t) * (size_t)(N0 > 0 ? N0 : 1)));
+  }
+  timed(ctx, st, "root_blocks", [&] {
+    int k = 0;
+    if (ctx->multi)
+      k = launch_root_blocks_multi(D, static_cast<const GeomParams*>(ctx->table.p), (int)ctx->geoms.size(),
+                                   static_cast<int32_t*>(ctx->lv[0].blocks.p),
+                                   static_cast<uint32_t*>(ctx->lv[0].gid.p), N0, st);
+    else
+      k = launch_root_blocks(D, ctx->geoms[0].root, static_cast<int32_t*>(ctx->lv[0].blocks.p), N0, st);
+    k_set_u64<<<1, 1, 0, st>>>(ctx->d_scal + SC_N, (uint64_t)N0);
+    return k + 1;
+  });
+  int64_t N = N0;
+  for (int L = 0; L < P.NL; ++L) {
+    LevelBufs& lb = ctx->lv[L];
+    if (eager) {
+      lb.cap = N;
+      const size_t n1 = (size_t)(N > 0 ? N : 1);
+      TRY(ensure(ctx, lb.mask, sizeof(uint64_t) * n1));
+      TRY(ensure(ctx, lb.flag, n1));
+      if (P.fin_at[L] && P.adjacency) {
+        TRY(ensure(ctx, lb.cellcnt, sizeof(uint16_t) * NCell * n1));
+        TRY(ensure(ctx, lb.blockcnt, sizeof(uint64_t) * n1));
+        TRY(ensure(ctx, lb.base, sizeof(uint64_t) * n1));
+      }
+    }
+    RefineLevel a = level_args(ctx, P, L);
+    CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), st));
+    timed(ctx, st, "refine_level", [&] { return launch_refine(a, ctx->num_sms, st); });
+    if (P.cont_after[L]) {
+      LevelBufs& nx = ctx->lv[L + 1];
+      if (eager) {
+        const int64_t cap = N * NCH;
+        nx.cap = cap;
+        const size_t c1 = (size_t)(cap > 0 ? cap : 1);
+        TRY(ensure(ctx, nx.blocks, sizeof(int32_t) * D * c1));
+        TRY(ensure(ctx, nx.parent, sizeof(int32_t) * c1));
+        if (ctx->multi) TRY(ensure(ctx, nx.gid, sizeof(uint32_t) * c1));
+        TRY(ensure(ctx, ctx->scratch, children_scratch_bytes(N)));
+      }
+      ChildrenArgs ca{};
+      ca.dim = D;
+      ca.level = L;
+      ca.g0 = ctx->geoms[0];
+      ca.table = a.table;
+      ca.gid = a.gid;
+      ca.blocks = a.blocks;
+      ca.mask = a.mask;
+      ca.n = lb.cap;
+      ca.n_dev = ctx->d_scal + SC_N + L;
+      ca.child_blocks = static_cast<int32_t*>(nx.blocks.p);
+      ca.child_gid = ctx->multi ? static_cast<uint32_t*>(nx.gid.p) : nullptr;
+      ca.child_parent = static_cast<int32_t*>(nx.parent.p);
+      ca.cap_out = nx.cap;
+      ca.total = ctx->d_scal + SC_N + L + 1;
+      ca.err = ctx->d_err;
+      timed(ctx, st, "children", [&] { return launch_children(ca, ctx->scratch.p, ctx->num_sms, st); });
+      if (eager) {
+        CK(cudaGetLastError());
+        uint64_t nn = 0;
+        unsigned e = 0;
+        TRY(read_scalar(ctx, st, SC_N + L + 1, &nn, &e));
+        TRY(device_error(ctx, e));
+        if ((int64_t)nn > (1ll << 32) / NCell) return fail(ctx, AMR_EOVERFLOW, "level %d has too many blocks", L + 1);
+        N = (int64_t)nn;
+        nx.cap = N;
+      }
+    }
+    if (P.fin_at[L] && P.adjacency) {
+      if (eager) TRY(ensure(ctx, ctx->scratch, scan_u64_scratch_bytes(lb.cap)));
+      timed(ctx, st, "adj_scan", [&] {
+        return launch_scan_u64(static_cast<const uint64_t*>(lb.blockcnt.p), static_cast<uint64_t*>(lb.base.p), lb.cap,
+                               ctx->d_scal + SC_N + L, ctx->d_scal + SC_TOT + L, ctx->scratch.p, ctx->d_err,
+                               ctx->num_sms, st);
+      });
+      int64_t cells = 0, pairs = 0;
+      if (eager) {
+        CK(cudaGetLastError());
+        uint64_t tot = 0;
+        unsigned e = 0;
+        TRY(read_scalar(ctx, st, SC_TOT + L, &tot, &e));
+        TRY(device_error(ctx, e));
+        cells = (int64_t)(tot >> 32);
+        pairs = (int64_t)(tot & 0xffffffffull);
+        if (run_pairs + pairs >= (int64_t)0xffffffffll)
+          return fail(ctx, AMR_EOVERFLOW, "too many adjacent (cell, face) pairs");
+        const int64_t need_c = run_cells + cells, need_p = run_pairs + pairs;
+        if (need_c + 1 > ctx->cap_cells) ctx->cap_cells = need_c + 1;
+        if (need_p > ctx->cap_pairs) ctx->cap_pairs = need_p;
+        TRY(ensure_keep(ctx, ctx->adj_cell, sizeof(uint32_t) * (size_t)(ctx->cap_cells + 1),
+                        sizeof(uint32_t) * (size_t)run_cells));
+        TRY(ensure_keep(ctx, ctx->adj_off, sizeof(uint32_t) * (size_t)(ctx->cap_cells + 1),
+                        sizeof(uint32_t) * (size_t)(run_cells + 1)));
+        TRY(ensure_keep(ctx, ctx->adj_ids, sizeof(uint32_t) * (size_t)(ctx->cap_pairs + 1),
+                        sizeof(uint32_t) * (size_t)run_pairs));
+      }
+      EmitArgs ea{};
+      ea.lv = a;
+      ea.block_base = static_cast<const uint64_t*>(lb.base.p);
+      ea.run = ctx->d_scal + SC_RUN;
+      ea.adj_cell = static_cast<uint32_t*>(ctx->adj_cell.p);
+      ea.adj_off = static_cast<uint32_t*>(ctx->adj_off.p);
+      ea.adj_ids = static_cast<uint32_t*>(ctx->adj_ids.p);
+      ea.cap_cells = ctx->cap_cells;
+      ea.cap_pairs = ctx->cap_pairs;
+      CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), st));
+      timed(ctx, st, "adjacency", [&] { return launch_adjacency(ea, ctx->num_sms, st); });
+      timed(ctx, st, "advance", [&] {
+        return launch_advance(ctx->d_scal + SC_TOT + L, nullptr, ctx->d_scal + SC_RUN,
+                              static_cast<uint32_t*>(ctx->adj_off.p), ctx->cap_cells, ctx->d_err, true, st);
+      });
+      if (P.links) {
+        LinkArgs la{};
+        la.dim = D;
+        la.lattice = P.lattice;
+        la.level = L;
+        la.g0 = ctx->geoms[0];
+        la.table = a.table;
+        la.gid = a.gid;
+        la.blocks = a.blocks;
+        la.adj_cell = ea.adj_cell;
+        la.adj_off = ea.adj_off;
+        la.adj_ids = ea.adj_ids;
+        la.run = ctx->d_scal + SC_RUN;
+        la.level_tot = ctx->d_scal + SC_TOT + L;
+        la.cap_rows = ctx->cap_cells;
+        la.X = a.X;
+        la.nrm = a.nrm;
+        la.nf = ctx->nf;
+        la.n_links = ctx->d_scal + SC_NL + L;
+        la.counters = ctx->counters;
+        la.err = ctx->d_err;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+          if (eager) {
+            const int64_t want = run_links + (cells * 4 > 16 ? cells * 4 : 16);
+            if (want > ctx->cap_links || attempt > 0) {
+              const int64_t nc = attempt > 0 ? ctx->cap_links : want;
+              const size_t keep = (size_t)run_links;
+              TRY(ensure_keep(ctx, ctx->link_cell, sizeof(uint32_t) * (size_t)(nc + 1), sizeof(uint32_t) * keep));
+              TRY(ensure_keep(ctx, ctx->link_dir, (size_t)(nc + 1), keep));
+              TRY(ensure_keep(ctx, ctx->link_q, sizeof(float) * (size_t)(nc + 1), sizeof(float) * keep));
+              TRY(ensure_keep(ctx, ctx->link_face, sizeof(uint32_t) * (size_t)(nc + 1), sizeof(uint32_t) * keep));
+              ctx->cap_links = nc;
+            }
+            TRY(ensure(ctx, ctx->scratch, links_scratch_bytes(ctx->cap_cells)));
+          }
+          la.link_cell = static_cast<uint32_t*>(ctx->link_cell.p);
+          la.link_dir = static_cast<uint8_t*>(ctx->link_dir.p);
+          la.link_q = static_cast<float*>(ctx->link_q.p);
+          la.link_face = static_cast<uint32_t*>(ctx->link_face.p);
+          la.link_cap = ctx->cap_links;
+          timed(ctx, st, "links", [&] { return launch_links(la, ctx->scratch.p, ctx->num_sms, st); });
+          if (!eager) break;
+          CK(cudaGetLastError());
+          uint64_t nl = 0;
+          unsigned e = 0;
+          TRY(read_scalar(ctx, st, SC_NL + L, &nl, &e));
+          if (e & ~ERR_OVERFLOW) TRY(device_error(ctx, e));
+          if (run_links + (int64_t)nl <= ctx->cap_links) {
+            if (e) TRY(device_error(ctx, e));
+            run_links += (int64_t)nl;
+            break;
+          }
+          // too small: grow to the exact count and run the level's links again
+          CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), st));
+          ctx->cap_links = run_links + (int64_t)nl;
+        }
+      }
+      timed(ctx, st, "advance", [&] {
+        return launch_advance(ctx->d_scal + SC_TOT + L, P.links ? ctx->d_scal + SC_NL + L : nullptr,
+                              ctx->d_scal + SC_RUN, static_cast<uint32_t*>(ctx->adj_off.p), ctx->cap_cells,
+                              ctx->d_err, false, st);
+      });
+      run_cells += cells;
+      run_pairs += pairs;
+    }
+  }
+  CK(cudaGetLastError());
+  return AMR_OK;
+}
+
+// Read every size of the last pass (one synchronisation) and fill the result.
+amr_status collect(amr_ctx* ctx, const Plan& P, cudaStream_t st, amr_refine_result* out) {
+  char* h = static_cast<char*>(ctx->h_pinned);
+  CK(cudaMemcpyAsync(h, ctx->counters, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + 512, ctx->d_scal, sizeof(uint64_t) * SC_WORDS, cudaMemcpyDeviceToHost, st));
+  TRY(sync_check(ctx, st));
+  const unsigned e = *reinterpret_cast<unsigned*>(h + 64);
+  TRY(device_error(ctx, e));
+  const uint64_t* sc = reinterpret_cast<const uint64_t*>(h + 512);
+  const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(h);
+  amr_refine_result r{};
+  r.n_levels = P.NL;
+  for (int L = 0; L < P.NL; ++L) {
+    r.n_blocks[L] = (int64_t)sc[SC_N + L];
+    r.block_coords[L] = static_cast<const int32_t*>(ctx->lv[L].blocks.p);
+    r.block_parent[L] = L > 0 ? static_cast<const int32_t*>(ctx->lv[L].parent.p) : nullptr;
+    r.cell_mask[L] = static_cast<const uint64_t*>(ctx->lv[L].mask.p);
+    r.block_flag[L] = static_cast<const uint8_t*>(ctx->lv[L].flag.p);
+  }
+  if (P.adjacency) {
+    r.n_adj_cells = (int64_t)sc[SC_RUN + 0];
+    r.n_adj_pairs = (int64_t)sc[SC_RUN + 1];
+    r.adj_cell = static_cast<const uint32_t*>(ctx->adj_cell.p);
+    r.adj_off = static_cast<const uint32_t*>(ctx->adj_off.p);
+    r.adj_ids = static_cast<const uint32_t*>(ctx->adj_ids.p);
+  }
+  if (P.links) {
+    r.n_links = (int64_t)sc[SC_RUN + 2];
+    r.link_cell = static_cast<const uint32_t*>(ctx->link_cell.p);
+    r.link_dir = static_cast<const uint8_t*>(ctx->link_dir.p);
+    r.link_q = static_cast<const float*>(ctx->link_q.p);
+    r.link_face = static_cast<const uint32_t*>(ctx->link_face.p);
+  }
+  r.n_fallback = (int64_t)(cnt[CNT_FALLBACK] + cnt[CNT_LINK_FALLBACK]);
+  r.n_band = (int64_t)(cnt[CNT_BAND] + cnt[CNT_LINK_BAND]);
+  r.n_candidates = (int64_t)cnt[CNT_CANDIDATES];
+  r.n_survivors = (int64_t)cnt[CNT_SURVIVORS];
+  // per-level block pointers for the adjoint
+  TRY(ensure(ctx, ctx->lvl_ptrs, sizeof(void*) * AMR_MAX_LEVELS));
+  const int32_t** hp = reinterpret_cast<const int32_t**>(h + 256);
+  for (int L = 0; L < AMR_MAX_LEVELS; ++L) hp[L] = L < P.NL ? r.block_coords[L] : nullptr;
+  CK(cudaMemcpyAsync(ctx->lvl_ptrs.p, hp, sizeof(void*) * AMR_MAX_LEVELS, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  *out = r;
+  return AMR_OK;
+}
+
+}  // namespace
+
+// Eager pass (or graph replay when the inputs match the captured graph), then
+// capture when graph mode is asked for.
+amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine_result* out) {
+  const Plan P = make_plan(ctx, prm);
+  GraphKey key;
+  key.layout_gen = ctx->layout_gen;
+  key.nf = ctx->nf;
+  key.n_geom = (int64_t)ctx->geoms.size();
+  key.B = ctx->geoms[0].B;
+  key.n_levels = prm->n_levels;
+  key.lattice = prm->lattice;
+  key.adjacency = P.adjacency;
+  key.links = P.links;
+  key.warps = P.warps;
+  key.d_abs = prm->d_abs;
+  key.d_rel = prm->d_rel;
+  const bool want_graph = prm->use_graph != 0;
+  if (want_graph && ctx->gexec && ctx->gkey == key) {
+    // replay on the graph stream, ordered after the caller's stream
+    CK(cudaEventRecord(ctx->ev_in, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0));
+    CK(cudaGraphLaunch(ctx->gexec, ctx->gstream));
+    ctx->launches += ctx->graph_launches;
+    CK(cudaEventRecord(ctx->ev_out, ctx->gstream));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0));
+    amr_refine_result r{};
+    const amr_status s = collect(ctx, P, ctx->stream, &r);
+    if (s == AMR_OK) {
+      *out = r;
+      return AMR_OK;
+    }
+    if (s != AMR_EOVERFLOW) return s;
+    drop_graph(ctx);  // sizes outgrew the capacities: redo eagerly
+  }
+  TRY(engine_pass(ctx, P, true, ctx->stream));
+  TRY(collect(ctx, P, ctx->stream, out));
+  if (want_graph) {
+    drop_graph(ctx);
+    key.layout_gen = ctx->layout_gen;
+    ctx->capturing = true;
+    const int64_t before = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+    amr_status s = AMR_OK;
+    if (e == cudaSuccess) s = engine_pass(ctx, P, false, ctx->gstream);
+    const cudaError_t e2 = cudaStreamEndCapture(ctx->gstream, &graph);
+    ctx->capturing = false;
+    ctx->graph_launches = ctx->launches - before;
+    ctx->launches = before;
+    if (e != cudaSuccess || e2 != cudaSuccess || s != AMR_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return fail(ctx, AMR_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ctx->gexec = nullptr;
+      return fail(ctx, AMR_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    ctx->gkey = key;
+  }
+  return AMR_OK;
+}
 
 extern "C" {
 
@@ -272,63 +854,21 @@ amr_status amr_create(const amr_domain* dom, amr_ctx** out) {
   amr_ctx* ctx = new amr_ctx();
   ctx->dom = *dom;
   for (int a = dom->dim; a < 3; ++a) ctx->dom.root_blocks[a] = 1;
-  cudaError_t e = cudaGetDevice(&ctx->device);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  if (e == cudaSuccess) {
-    if (dom->stream) {
-      ctx->stream = static_cast<cudaStream_t>(dom->stream);
-    } else {
-      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
-      ctx->own_stream = e == cudaSuccess;
-    }
-  }
-  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 256);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
+  if (dom->stream) ctx->stream = static_cast<cudaStream_t>(dom->stream);
+  const amr_status s = amr_ctx_init(ctx);
+  if (s != AMR_OK) {
+    amr_ctx_free(ctx);
     delete ctx;
-    return AMR_ECUDA;
+    return s;
   }
-  if (ensure(ctx, ctx->misc, sizeof(unsigned long long) * CNT_N + 64 + 64) != AMR_OK) {
-    cudaFreeHost(ctx->h_pinned);
-    delete ctx;
-    return AMR_ENOMEM;
-  }
-  char* m = static_cast<char*>(ctx->misc.p);
-  ctx->counters = reinterpret_cast<unsigned long long*>(m);
-  ctx->d_err = reinterpret_cast<unsigned*>(m + sizeof(unsigned long long) * CNT_N);
-  ctx->d_work = ctx->d_err + 1;
-  ctx->d_tot = reinterpret_cast<uint64_t*>(m + sizeof(unsigned long long) * CNT_N + 64);
-  cudaMemsetAsync(ctx->misc.p, 0, ctx->misc.cap, ctx->stream);
+  ctx->geoms.push_back(amr_make_row(ctx->dom, 1, 1, 0.0, 1.0));
   *out = ctx;
   return AMR_OK;
 }
 
 amr_status amr_destroy(amr_ctx* ctx) {
   if (!ctx) return AMR_OK;
-  cudaStreamSynchronize(ctx->stream);
-  DevBuf* extra[] = {&ctx->idx, &ctx->vert_off, &ctx->vert_corners, &ctx->face_off, &ctx->face_links,
-                     &ctx->sort_keys, &ctx->grad_face, &ctx->sort_scratch, &ctx->group_cnt};
-  for (DevBuf* b : extra) release(ctx, *b);
-  DevBuf* all[] = {&ctx->X,        &ctx->nrm,       &ctx->stage_a,    &ctx->stage_b,  &ctx->frange,
-                   &ctx->count,    &ctx->offsets,   &ctx->ids,        &ctx->payload,  &ctx->scratch,
-                   &ctx->misc,     &ctx->cellcnt,   &ctx->blockcnt,   &ctx->block_base, &ctx->adj_cell,
-                   &ctx->adj_off,  &ctx->adj_ids,   &ctx->link_cell,  &ctx->link_dir, &ctx->link_q,
-                   &ctx->link_face};
-  for (DevBuf* b : all) release(ctx, *b);
-  for (int L = 0; L < AMR_MAX_LEVELS; ++L) {
-    release(ctx, ctx->lv_blocks[L]);
-    release(ctx, ctx->lv_parent[L]);
-    release(ctx, ctx->lv_mask[L]);
-    release(ctx, ctx->lv_flag[L]);
-  }
-  cudaStreamSynchronize(ctx->stream);
-  for (auto& t : ctx->pending) {
-    cudaEventDestroy(t.a);
-    cudaEventDestroy(t.b);
-  }
-  for (auto e : ctx->event_pool) cudaEventDestroy(e);
-  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
-  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  amr_ctx_free(ctx);
   delete ctx;
   return AMR_OK;
 }
@@ -352,12 +892,13 @@ amr_status amr_set_stream(amr_ctx* ctx, void* stream) {
 amr_status amr_sync(amr_ctx* ctx) {
   if (!ctx) return AMR_EINVAL;
   unsigned e = 0;
-  TRY(read_back(ctx, &e, nullptr, 0));
+  TRY(read_back(ctx, ctx->stream, &e, nullptr, 0));
   return device_error(ctx, e);
 }
 
 amr_status amr_geom_load(amr_ctx* ctx, const float* coords, int64_t n_verts, const int32_t* idx, int64_t n_faces) {
   if (!ctx) return AMR_EINVAL;
+  if (ctx->multi) return fail(ctx, AMR_ESTATE, "amr_geom_load on a batch context");
   const int D = ctx->dom.dim;
   if (n_faces < 0 || n_faces >= kMaxFaces) return fail(ctx, AMR_EINVAL, "n_faces must be in [0, 2^29)");
   if (n_faces > 0 && !coords) return fail(ctx, AMR_EINVAL, "null coordinates");
@@ -369,6 +910,7 @@ amr_status amr_geom_load(amr_ctx* ctx, const float* coords, int64_t n_verts, con
   ctx->indexed = idx != nullptr;
   TRY(ensure(ctx, ctx->X, sizeof(float) * D * D * (size_t)(n_faces > 0 ? n_faces : 1)));
   if (D == 3) TRY(ensure(ctx, ctx->nrm, sizeof(float) * 6 * (size_t)(n_faces > 0 ? n_faces : 1)));
+  cudaStream_t st = ctx->stream;
   if (n_faces > 0) {
     if (idx) {
       const void* dv = nullptr;
@@ -376,285 +918,92 @@ amr_status amr_geom_load(amr_ctx* ctx, const float* coords, int64_t n_verts, con
       TRY(to_device(ctx, coords, sizeof(float) * D * (size_t)n_verts, ctx->stage_a, &dv));
       TRY(to_device(ctx, idx, sizeof(int32_t) * D * (size_t)n_faces, ctx->stage_b, &di));
       TRY(ensure(ctx, ctx->idx, sizeof(int32_t) * D * (size_t)n_faces));
-      CK(cudaMemcpyAsync(ctx->idx.p, di, sizeof(int32_t) * D * (size_t)n_faces, cudaMemcpyDeviceToDevice,
-                         ctx->stream));
-      timed(ctx, "load_gather", [&] {
-        return launch_load_indexed(D, static_cast<const float*>(dv), n_verts, static_cast<const int32_t*>(di), n_faces,
-                            static_cast<float*>(ctx->X.p), ctx->d_err, ctx->stream);
+      CK(cudaMemcpyAsync(ctx->idx.p, di, sizeof(int32_t) * D * (size_t)n_faces, cudaMemcpyDeviceToDevice, st));
+      timed(ctx, st, "load_gather", [&] {
+        return launch_load_indexed(D, static_cast<const float*>(dv), n_verts, static_cast<const int32_t*>(di),
+                                   n_faces, static_cast<float*>(ctx->X.p), ctx->d_err, st);
       });
     } else {
       const void* dc = nullptr;
       TRY(to_device(ctx, coords, sizeof(float) * D * D * (size_t)n_faces, ctx->stage_a, &dc));
-      timed(ctx, "load_gather", [&] {
-        return launch_load_facelist(D, static_cast<const float*>(dc), n_faces, static_cast<float*>(ctx->X.p), ctx->d_err,
-                             ctx->stream);
+      timed(ctx, st, "load_gather", [&] {
+        return launch_load_facelist(D, static_cast<const float*>(dc), n_faces, static_cast<float*>(ctx->X.p),
+                                    ctx->d_err, st);
       });
     }
     if (D == 3)
-      timed(ctx, "face_normals", [&] {
+      timed(ctx, st, "face_normals", [&] {
         return launch_face_normals(static_cast<const float*>(ctx->X.p), n_faces, static_cast<float*>(ctx->nrm.p),
-                            ctx->stream);
+                                   st);
       });
   }
   CK(cudaGetLastError());
   ctx->loaded = true;
+  ++ctx->load_gen;
   return AMR_OK;
 }
 
 amr_status amr_bin_faces(amr_ctx* ctx, int B, amr_bins_view* out) {
   if (!ctx || !out) return AMR_EINVAL;
+  if (ctx->multi) return fail(ctx, AMR_ESTATE, "amr_bin_faces on a batch context");
   if (!ctx->loaded) return fail(ctx, AMR_ESTATE, "amr_bin_faces before amr_geom_load");
   const int D = ctx->dom.dim;
   if (B < 1 || B > 65535) return fail(ctx, AMR_EINVAL, "bin density must be in [1, 65535]");
-  int64_t nb = 1;
-  for (int a = 0; a < D; ++a) nb *= B;
+  const int64_t nb = ipow(B, D);
   if (nb > (1ll << 30)) return fail(ctx, AMR_EINVAL, "B^dim must not exceed 2^30");
   ctx->binned = ctx->refined = false;
-  const int64_t nf = ctx->nf;
-  if (ctx->count.cap < sizeof(uint32_t) * (size_t)nb) ctx->count_clean = false;
-  TRY(ensure(ctx, ctx->count, sizeof(uint32_t) * (size_t)nb));
-  if (!ctx->count_clean) {
-    CK(cudaMemsetAsync(ctx->count.p, 0, ctx->count.cap, ctx->stream));
-    ctx->count_clean = true;
-  }
-  TRY(ensure(ctx, ctx->offsets, sizeof(uint32_t) * (size_t)(nb + 1)));
-  TRY(ensure(ctx, ctx->frange, sizeof(uint32_t) * 3 * (size_t)(nf > 0 ? nf : 1)));
-  TRY(ensure(ctx, ctx->scratch, scan_u32_scratch_bytes(nb)));
-  const BinGrid g = make_grid(ctx->dom, B);
-  uint32_t* count = static_cast<uint32_t*>(ctx->count.p);
-  uint32_t* offsets = static_cast<uint32_t*>(ctx->offsets.p);
-  timed(ctx, "bin_count", [&] {
-    return launch_face_bins(D, static_cast<const float*>(ctx->X.p), nf, g, static_cast<uint32_t*>(ctx->frange.p), count,
-                     ctx->stream);
-  });
-  timed(ctx, "bin_scan", [&] {
-    return launch_scan_u32(count, offsets, nb, ctx->d_tot, ctx->scratch.p, ctx->d_err, ctx->stream);
-  });
-  CK(cudaGetLastError());
-  unsigned e = 0;
-  uint64_t tot = 0;
-  TRY(read_back(ctx, &e, &tot, 1));
-  if (e) {
-    ctx->count_clean = false;
-    return device_error(ctx, e);
-  }
-  if (tot > 0xffffffffull) {
-    ctx->count_clean = false;
-    return fail(ctx, AMR_EOVERFLOW, "%llu (face, bin) entries exceed 2^32 - 1", (unsigned long long)tot);
-  }
-  const size_t esz = D == 3 ? sizeof(Entry3) : sizeof(Entry2);
-  TRY(ensure(ctx, ctx->ids, sizeof(uint32_t) * (size_t)tot));
-  TRY(ensure(ctx, ctx->payload, esz * (size_t)tot));
-  timed(ctx, "bin_scatter", [&] {
-    return launch_scatter(D, static_cast<const float*>(ctx->X.p), nf, static_cast<const uint32_t*>(ctx->frange.p), offsets,
-                   count, static_cast<uint32_t*>(ctx->ids.p), ctx->payload.p, B, ctx->stream);
-  });
-  CK(cudaGetLastError());
+  const GeomParams prev = ctx->geoms[0];
+  ctx->geoms[0] = amr_make_row(ctx->dom, B, prev.n_levels, prev.d_abs, prev.d_rel);
+  TRY(amr_bin_all(ctx));
   ctx->B = B;
-  ctx->n_bins = nb;
-  ctx->nnz = (int64_t)tot;
-  ctx->binned = true;
   out->B = B;
   out->n_bins = nb;
-  out->nnz = (int64_t)tot;
-  out->offsets = offsets;
+  out->nnz = ctx->nnz;
+  out->offsets = static_cast<const uint32_t*>(ctx->offsets.p);
   out->ids = static_cast<const uint32_t*>(ctx->ids.p);
   return AMR_OK;
 }
 
 amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_refine_result* out) {
   if (!ctx || !prm || !out) return AMR_EINVAL;
+  if (ctx->multi) return fail(ctx, AMR_ESTATE, "use amr_batch_run on a batch context");
   if (!ctx->binned) return fail(ctx, AMR_ESTATE, "amr_refine_near_wall before amr_bin_faces");
   const int D = ctx->dom.dim;
   const int NL = prm->n_levels;
   if (NL < 1 || NL > AMR_MAX_LEVELS) return fail(ctx, AMR_EINVAL, "n_levels must be in [1, %d]", AMR_MAX_LEVELS);
   if (!(prm->d_abs >= 0.0) || !(prm->d_rel >= 0.0)) return fail(ctx, AMR_EINVAL, "negative near-wall distance");
-  const bool links = prm->want_links != 0;
-  const bool adjacency = prm->want_adjacency != 0 || links;
-  if (links) {
+  if (prm->warps_per_cta < 0 || prm->warps_per_cta > 8) return fail(ctx, AMR_EINVAL, "warps_per_cta in [0, 8]");
+  if (prm->want_links) {
     if (!((D == 2 && prm->lattice == 9) || (D == 3 && prm->lattice == 19)))
       return fail(ctx, AMR_EINVAL, "lattice must be 9 (D2Q9) in 2D or 19 (D3Q19) in 3D");
     const double hf = ctx->dom.h0 * std::ldexp(1.0, -(NL - 1));
     if (prm->d_abs + prm->d_rel * hf < 0.5 * hf)
       return fail(ctx, AMR_EINVAL, "links need d_L >= h_L/2 on the finest level");
   }
+  int64_t N0 = 1;
+  for (int a = 0; a < D; ++a) N0 *= ctx->dom.root_blocks[a];
+  if (N0 > (1ll << 31)) return fail(ctx, AMR_EINVAL, "too many root blocks");
   ctx->refined = false;
   ctx->face_groups = false;
   ctx->n_links = 0;
+  GeomParams& g = ctx->geoms[0];
+  g.n_levels = NL;
+  g.d_abs = prm->d_abs;
+  g.d_rel = prm->d_rel;
   amr_refine_result r{};
-  r.n_levels = NL;
-  CK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * CNT_N, ctx->stream));
-  int64_t N = 1;
-  for (int a = 0; a < D; ++a) N *= ctx->dom.root_blocks[a];
-  if (N > (1ll << 31)) return fail(ctx, AMR_EINVAL, "too many root blocks");
-  TRY(ensure(ctx, ctx->lv_blocks[0], sizeof(int32_t) * D * (size_t)N));
-  timed(ctx, "root_blocks", [&] {
-    return launch_root_blocks(D, ctx->dom.root_blocks, static_cast<int32_t*>(ctx->lv_blocks[0].p), N, ctx->stream);
-  });
-  const int NCell = D == 3 ? 64 : 16;
-  RefineLevel lv{};
-  for (int L = 0; L < NL; ++L) {
-    const bool finest = L == NL - 1;
-    const double h = ctx->dom.h0 * std::ldexp(1.0, -L);
-    const double d = prm->d_abs + prm->d_rel * h;
-    r.n_blocks[L] = N;
-    TRY(ensure(ctx, ctx->lv_mask[L], sizeof(uint64_t) * (size_t)N));
-    TRY(ensure(ctx, ctx->lv_flag[L], (size_t)N));
-    lv = RefineLevel{};
-    lv.dim = D;
-    lv.blocks = static_cast<const int32_t*>(ctx->lv_blocks[L].p);
-    lv.n_blocks = N;
-    lv.offsets = static_cast<const uint32_t*>(ctx->offsets.p);
-    lv.payload = ctx->payload.p;
-    lv.X = static_cast<const float*>(ctx->X.p);
-    lv.nrm = static_cast<const float*>(ctx->nrm.p);
-    lv.nf = ctx->nf;
-    lv.grid = make_grid(ctx->dom, ctx->B);
-    for (int a = 0; a < 3; ++a) lv.origin[a] = ctx->dom.origin[a];
-    lv.h = h;
-    lv.d = d;
-    lv.mask = static_cast<uint64_t*>(ctx->lv_mask[L].p);
-    lv.flag = static_cast<uint8_t*>(ctx->lv_flag[L].p);
-    lv.counters = ctx->counters;
-    lv.work = ctx->d_work;
-    lv.err = ctx->d_err;
-    if (finest && adjacency) {
-      TRY(ensure(ctx, ctx->cellcnt, sizeof(uint16_t) * NCell * (size_t)N));
-      TRY(ensure(ctx, ctx->blockcnt, sizeof(uint64_t) * (size_t)N));
-      lv.cellcnt = static_cast<uint16_t*>(ctx->cellcnt.p);
-      lv.blockcnt = static_cast<uint64_t*>(ctx->blockcnt.p);
-    }
-    CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), ctx->stream));
-    timed(ctx, "refine_level", [&] { return launch_refine(lv, ctx->num_sms, ctx->stream); });
-    r.block_coords[L] = static_cast<const int32_t*>(ctx->lv_blocks[L].p);
-    r.block_parent[L] = L > 0 ? static_cast<const int32_t*>(ctx->lv_parent[L].p) : nullptr;
-    r.cell_mask[L] = lv.mask;
-    r.block_flag[L] = lv.flag;
-    if (!finest) {
-      // children of the marked blocks -> next level (worst case 2^D per block)
-      TRY(ensure(ctx, ctx->scratch, children_scratch_bytes(N)));
-      const int64_t cap = N * (D == 3 ? 8 : 4);
-      TRY(ensure(ctx, ctx->lv_blocks[L + 1], sizeof(int32_t) * D * (size_t)(cap > 0 ? cap : 1)));
-      TRY(ensure(ctx, ctx->lv_parent[L + 1], sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1)));
-      timed(ctx, "children", [&] {
-        return launch_children(D, lv.blocks, lv.mask, N, static_cast<int32_t*>(ctx->lv_blocks[L + 1].p),
-                        static_cast<int32_t*>(ctx->lv_parent[L + 1].p), ctx->d_tot, ctx->scratch.p, ctx->d_err,
-                        ctx->stream);
-      });
-      CK(cudaGetLastError());
-      unsigned e = 0;
-      uint64_t tot = 0;
-      TRY(read_back(ctx, &e, &tot, 1));
-      TRY(device_error(ctx, e));
-      N = (int64_t)tot;
-      if (N > (1ll << 32) / NCell) return fail(ctx, AMR_EOVERFLOW, "level %d has too many blocks", L + 1);
-    }
-  }
-  // finest level: adjacent-face lists
-  if (adjacency) {
-    const int64_t Nf = N;
-    TRY(ensure(ctx, ctx->block_base, sizeof(uint64_t) * (size_t)(Nf > 0 ? Nf : 1)));
-    TRY(ensure(ctx, ctx->scratch, scan_u64_scratch_bytes(Nf)));
-    timed(ctx, "adj_scan", [&] {
-      return launch_scan_u64(static_cast<const uint64_t*>(ctx->blockcnt.p), static_cast<uint64_t*>(ctx->block_base.p), Nf,
-                      ctx->d_tot, ctx->scratch.p, ctx->d_err, ctx->stream);
-    });
-    CK(cudaGetLastError());
-    unsigned e = 0;
-    uint64_t tot = 0;
-    TRY(read_back(ctx, &e, &tot, 1));
-    TRY(device_error(ctx, e));
-    const uint64_t pairs = tot & 0xffffffffull, cells = tot >> 32;
-    if (Nf > 0 && (pairs >= 0xffffffffull)) return fail(ctx, AMR_EOVERFLOW, "too many adjacent (cell, face) pairs");
-    TRY(ensure(ctx, ctx->adj_cell, sizeof(uint32_t) * (size_t)(cells + 1)));
-    TRY(ensure(ctx, ctx->adj_off, sizeof(uint32_t) * (size_t)(cells + 1)));
-    TRY(ensure(ctx, ctx->adj_ids, sizeof(uint32_t) * (size_t)(pairs + 1)));
-    EmitArgs ea{};
-    ea.lv = lv;
-    ea.block_base = static_cast<const uint64_t*>(ctx->block_base.p);
-    ea.adj_cell = static_cast<uint32_t*>(ctx->adj_cell.p);
-    ea.adj_off = static_cast<uint32_t*>(ctx->adj_off.p);
-    ea.adj_ids = static_cast<uint32_t*>(ctx->adj_ids.p);
-    uint32_t* hp = reinterpret_cast<uint32_t*>(static_cast<char*>(ctx->h_pinned) + 192);
-    *hp = (uint32_t)pairs;
-    CK(cudaMemcpyAsync(static_cast<uint32_t*>(ctx->adj_off.p) + cells, hp, sizeof(uint32_t), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), ctx->stream));
-    timed(ctx, "adjacency", [&] { return launch_adjacency(ea, ctx->num_sms, ctx->stream); });
-    CK(cudaGetLastError());
-    r.n_adj_cells = (int64_t)cells;
-    r.n_adj_pairs = (int64_t)pairs;
-    r.adj_cell = ea.adj_cell;
-    r.adj_off = ea.adj_off;
-    r.adj_ids = ea.adj_ids;
-    if (links) {
-      LinkArgs la{};
-      la.dim = D;
-      la.lattice = prm->lattice;
-      la.blocks = lv.blocks;
-      la.adj_cell = ea.adj_cell;
-      la.adj_off = ea.adj_off;
-      la.adj_ids = ea.adj_ids;
-      la.n_adj = (int64_t)cells;
-      la.X = static_cast<const float*>(ctx->X.p);
-      la.nrm = static_cast<const float*>(ctx->nrm.p);
-      la.nf = ctx->nf;
-      for (int a = 0; a < 3; ++a) la.origin[a] = ctx->dom.origin[a];
-      la.h = ctx->dom.h0 * std::ldexp(1.0, -(NL - 1));
-      la.n_links = ctx->d_tot;
-      la.counters = ctx->counters;
-      la.err = ctx->d_err;
-      int64_t want = ctx->link_cap;
-      if (want < (int64_t)cells * 4) want = (int64_t)cells * 4;
-      for (int attempt = 0; attempt < 2; ++attempt) {
-        TRY(ensure(ctx, ctx->link_cell, sizeof(uint32_t) * (size_t)(want + 1)));
-        TRY(ensure(ctx, ctx->link_dir, (size_t)(want + 1)));
-        TRY(ensure(ctx, ctx->link_q, sizeof(float) * (size_t)(want + 1)));
-        TRY(ensure(ctx, ctx->link_face, sizeof(uint32_t) * (size_t)(want + 1)));
-        ctx->link_cap = want;
-        la.link_cell = static_cast<uint32_t*>(ctx->link_cell.p);
-        la.link_dir = static_cast<uint8_t*>(ctx->link_dir.p);
-        la.link_q = static_cast<float*>(ctx->link_q.p);
-        la.link_face = static_cast<uint32_t*>(ctx->link_face.p);
-        la.link_cap = want;
-        TRY(ensure(ctx, ctx->scratch, links_scratch_bytes(la.n_adj)));
-        timed(ctx, "links", [&] { return launch_links(la, ctx->scratch.p, ctx->stream); });
-        CK(cudaGetLastError());
-        uint64_t nl = 0;
-        TRY(read_back(ctx, &e, &nl, 1));
-        TRY(device_error(ctx, e));
-        if ((int64_t)nl <= want) {
-          r.n_links = (int64_t)nl;
-          break;
-        }
-        want = (int64_t)nl;  // capacity too small: grow to the exact count and run again
-      }
-      r.link_cell = la.link_cell;
-      r.link_dir = la.link_dir;
-      r.link_q = la.link_q;
-      r.link_face = la.link_face;
-    }
-  }
-  // counters and the final error check
-  char* h = static_cast<char*>(ctx->h_pinned);
-  CK(cudaMemcpyAsync(h, ctx->counters, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(h + 128, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
-  TRY(sync_check(ctx));
-  const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(h);
-  r.n_fallback = (int64_t)(cnt[CNT_FALLBACK] + cnt[CNT_LINK_FALLBACK]);
-  r.n_band = (int64_t)(cnt[CNT_BAND] + cnt[CNT_LINK_BAND]);
-  r.n_candidates = (int64_t)cnt[CNT_CANDIDATES];
-  r.n_survivors = (int64_t)cnt[CNT_SURVIVORS];
-  TRY(device_error(ctx, *reinterpret_cast<unsigned*>(h + 128)));
+  TRY(amr_run_refine(ctx, prm, &r));
   ctx->refined = true;
   ctx->last = r;
-  ctx->n_links = links ? r.n_links : -1;
-  ctx->finest_h = ctx->dom.h0 * std::ldexp(1.0, -(NL - 1));
-  ctx->finest_blocks = r.block_coords[NL - 1];
+  ctx->n_links = prm->want_links ? r.n_links : -1;
   *out = r;
   return AMR_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
 namespace {
 
 int key_bits(int64_t n) {
@@ -664,23 +1013,24 @@ int key_bits(int64_t n) {
 }
 
 // Stable grouping of `n` keys in [0, n_keys): CSR offsets [n_keys + 1] and the
-// values (default 0..n-1) in ascending order within each key.
-amr_status group_by_key(amr_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n_keys, const uint32_t* vals,
-                        DevBuf& off, DevBuf& grouped, const char* name) {
+// values (0..n-1) in ascending order within each key.
+amr_status group_by_key(amr_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n_keys, DevBuf& off, DevBuf& grouped,
+                        const char* name) {
+  cudaStream_t st = ctx->stream;
   TRY(ensure(ctx, off, sizeof(uint32_t) * (size_t)(n_keys + 1)));
   TRY(ensure(ctx, grouped, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)));
   TRY(ensure(ctx, ctx->sort_keys, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)));
   TRY(ensure(ctx, ctx->sort_scratch, radix_sort_scratch_bytes(n)));
   TRY(ensure(ctx, ctx->scratch, scan_u32_scratch_bytes(n_keys)));
   TRY(ensure(ctx, ctx->group_cnt, sizeof(uint32_t) * (size_t)(n_keys > 0 ? n_keys : 1)));
-  CK(cudaMemsetAsync(ctx->group_cnt.p, 0, sizeof(uint32_t) * (size_t)(n_keys > 0 ? n_keys : 1), ctx->stream));
-  timed(ctx, name, [&] {
-    int k = launch_count_keys(keys, n, static_cast<uint32_t*>(ctx->group_cnt.p), ctx->stream);
+  CK(cudaMemsetAsync(ctx->group_cnt.p, 0, sizeof(uint32_t) * (size_t)(n_keys > 0 ? n_keys : 1), st));
+  timed(ctx, st, name, [&] {
+    int k = launch_count_keys(keys, n, static_cast<uint32_t*>(ctx->group_cnt.p), st);
     k += launch_scan_u32(static_cast<const uint32_t*>(ctx->group_cnt.p), static_cast<uint32_t*>(off.p), n_keys,
-                         ctx->d_tot, ctx->scratch.p, ctx->d_err, ctx->stream);
+                         ctx->d_tot, ctx->scratch.p, ctx->d_err, st);
     k += launch_stable_sort(keys, n, key_bits(n_keys), static_cast<uint32_t*>(ctx->sort_keys.p),
-                            static_cast<uint32_t*>(grouped.p), vals, ctx->sort_scratch.p, ctx->d_tot, ctx->d_err,
-                            ctx->stream);
+                            static_cast<uint32_t*>(grouped.p), nullptr, ctx->sort_scratch.p, ctx->d_tot, ctx->d_err,
+                            st);
     return k;
   });
   CK(cudaGetLastError());
@@ -689,25 +1039,17 @@ amr_status group_by_key(amr_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n
 
 }  // namespace
 
-extern "C" {
-
-amr_status amr_q_backward(amr_ctx* ctx, const float* grad_q, float* grad_out) {
-  if (!ctx) return AMR_EINVAL;
-  if (!ctx->refined || ctx->n_links < 0)
-    return fail(ctx, AMR_ESTATE, "amr_q_backward needs a preceding amr_refine_near_wall with links");
+amr_status amr_backward(amr_ctx* ctx, const float* grad_q, float* grad_out) {
   const int D = ctx->dom.dim;
   const int64_t nl = ctx->n_links, nf = ctx->nf;
-  if (!grad_out || (nl > 0 && !grad_q)) return fail(ctx, AMR_EINVAL, "null gradient pointer");
-  if ((nl > 0 && !is_device_ptr(grad_q)) || !is_device_ptr(grad_out))
-    return fail(ctx, AMR_EINVAL, "gradients must be device pointers");
   if (!ctx->face_groups) {
-    TRY(group_by_key(ctx, static_cast<const uint32_t*>(ctx->link_face.p), nl, nf, nullptr, ctx->face_off,
-                     ctx->face_links, "adjoint_group_links"));
+    TRY(group_by_key(ctx, static_cast<const uint32_t*>(ctx->link_face.p), nl, nf, ctx->face_off, ctx->face_links,
+                     "adjoint_group_links"));
     ctx->face_groups = true;
   }
   const bool indexed = ctx->indexed;
   if (indexed && !ctx->vert_groups) {
-    TRY(group_by_key(ctx, static_cast<const uint32_t*>(ctx->idx.p), nf * D, ctx->nv, nullptr, ctx->vert_off,
+    TRY(group_by_key(ctx, static_cast<const uint32_t*>(ctx->idx.p), nf * D, ctx->nv, ctx->vert_off,
                      ctx->vert_corners, "adjoint_group_corners"));
     ctx->vert_groups = true;
   }
@@ -719,6 +1061,10 @@ amr_status amr_q_backward(amr_ctx* ctx, const float* grad_q, float* grad_out) {
   AdjointArgs a{};
   a.dim = D;
   a.nf = nf;
+  a.g0 = ctx->geoms[0];
+  a.table = ctx->multi ? static_cast<const GeomParams*>(ctx->table.p) : nullptr;
+  a.face_gid = ctx->multi ? static_cast<const uint32_t*>(ctx->face_gid.p) : nullptr;
+  a.level_blocks = static_cast<const int32_t* const*>(ctx->lvl_ptrs.p);
   a.X = static_cast<const float*>(ctx->X.p);
   a.nrm = static_cast<const float*>(ctx->nrm.p);
   a.face_off = static_cast<const uint32_t*>(ctx->face_off.p);
@@ -728,21 +1074,30 @@ amr_status amr_q_backward(amr_ctx* ctx, const float* grad_q, float* grad_out) {
   a.link_dir = static_cast<const uint8_t*>(ctx->link_dir.p);
   a.link_q = static_cast<const float*>(ctx->link_q.p);
   a.adj_cell = static_cast<const uint32_t*>(ctx->adj_cell.p);
-  a.blocks = ctx->finest_blocks;
-  for (int c = 0; c < 3; ++c) a.origin[c] = ctx->dom.origin[c];
-  a.h = ctx->finest_h;
   a.grad_face = gface;
-  timed(ctx, "adjoint_face", [&] { return launch_face_grad(a, ctx->stream); });
+  cudaStream_t st = ctx->stream;
+  timed(ctx, st, "adjoint_face", [&] { return launch_face_grad(a, st); });
   if (indexed)
-    timed(ctx, "adjoint_vertex", [&] {
+    timed(ctx, st, "adjoint_vertex", [&] {
       return launch_vertex_grad(D, gface, static_cast<const uint32_t*>(ctx->vert_off.p),
-                                static_cast<const uint32_t*>(ctx->vert_corners.p), ctx->nv, grad_out, ctx->stream);
+                                static_cast<const uint32_t*>(ctx->vert_corners.p), ctx->nv, grad_out, st);
     });
   CK(cudaGetLastError());
   return AMR_OK;
 }
 
-}  // extern "C"
+extern "C" {
+
+amr_status amr_q_backward(amr_ctx* ctx, const float* grad_q, float* grad_out) {
+  if (!ctx) return AMR_EINVAL;
+  if (!ctx->refined || ctx->n_links < 0)
+    return fail(ctx, AMR_ESTATE, "amr_q_backward needs a preceding refinement with links");
+  const int64_t nl = ctx->n_links;
+  if (!grad_out || (nl > 0 && !grad_q)) return fail(ctx, AMR_EINVAL, "null gradient pointer");
+  if ((nl > 0 && !is_device_ptr(grad_q)) || !is_device_ptr(grad_out))
+    return fail(ctx, AMR_EINVAL, "gradients must be device pointers");
+  return amr_backward(ctx, grad_q, grad_out);
+}
 
 amr_status amr_timing_enable(amr_ctx* ctx, int on) {
   if (!ctx) return AMR_EINVAL;
@@ -775,5 +1130,441 @@ int amr_timing_get(amr_ctx* ctx, const char** names, double* total_ms, int64_t* 
 }
 
 int64_t amr_launch_count(const amr_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched mode: many geometries, one level engine.
+//
+// The geometries are gathered into one face array (face ids are batch-global),
+// binned in one pass (each geometry with its own bin grid, concatenated bin
+// arrays), and refined level by level: one refine launch and one child
+// compaction per level cover every geometry still refining; geometries that end
+// on a level form their adjacency lists and links there.  Per-geometry views
+// are segments of the concatenated outputs.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchInput {
+  amr_domain dom{};
+  int64_t nf = 0, nv = 0;
+  bool indexed = false;
+  DevBuf coords, idx;  // device copies of the caller's arrays
+  int n_levels = 1;
+  double d_abs = 0.0, d_rel = 1.0;
+  int B = 0;
+};
+
+// Per geometry: [0,16) first block per level, [16,32) block count per level,
+// 32 row start, 33 row end, 34 pair start, 35 pair end, 36 link start, 37 link end.
+constexpr int SEG_WORDS = 40;
+
+__device__ int64_t lower_u32(const uint32_t* a, int64_t n, uint32_t v) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < v)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+struct SegArgs {
+  int n_geom, n_levels;
+  const uint64_t* scal;
+  const uint32_t* gid[AMR_MAX_LEVELS];
+  const uint64_t* base[AMR_MAX_LEVELS];
+  const GeomParams* table;
+  const uint32_t* link_cell;
+  int64_t* out;
+};
+
+__global__ void k_batch_segments(SegArgs a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n_geom) return;
+  int64_t* o = a.out + (int64_t)g * SEG_WORDS;
+  const GeomParams P = a.table[g];
+  int64_t run_cells = 0, run_pairs = 0;
+  for (int L = 0; L < a.n_levels; ++L) {
+    const int64_t n = (int64_t)a.scal[SC_N + L];
+    int64_t s = 0, e = 0;
+    if (a.gid[L] && n > 0) {
+      s = lower_u32(a.gid[L], n, (uint32_t)g);
+      e = lower_u32(a.gid[L], n, (uint32_t)g + 1);
+    }
+    o[L] = s;
+    o[16 + L] = e - s;
+    const uint64_t tot = a.scal[SC_TOT + L];
+    if (L == P.n_levels - 1) {
+      const uint64_t bs = s < n ? a.base[L][s] : tot;
+      const uint64_t be = e < n ? a.base[L][e] : tot;
+      o[32] = run_cells + (int64_t)(bs >> 32);
+      o[33] = run_cells + (int64_t)(be >> 32);
+      o[34] = run_pairs + (int64_t)(bs & 0xffffffffull);
+      o[35] = run_pairs + (int64_t)(be & 0xffffffffull);
+    }
+    run_cells += (int64_t)(tot >> 32);
+    run_pairs += (int64_t)(tot & 0xffffffffull);
+  }
+  const int64_t nl = (int64_t)a.scal[SC_RUN + 2];
+  o[36] = a.link_cell ? lower_u32(a.link_cell, nl, (uint32_t)o[32]) : 0;
+  o[37] = a.link_cell ? lower_u32(a.link_cell, nl, (uint32_t)o[33]) : 0;
+}
+
+__global__ void k_offset_idx(const int32_t* __restrict__ in, int64_t n, int32_t off, int32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i] + off;
+}
+
+}  // namespace
+
+struct amr_batch {
+  amr_ctx ctx;
+  std::vector<BatchInput> in;
+  bool prepared = false;
+  std::vector<int64_t> seg;  // SEG_WORDS per geometry, filled by amr_batch_run
+  amr_refine_result last{};
+  int64_t vert_total = 0;
+};
+
+namespace {
+
+// Gather every geometry into the batch's face arrays (face ids batch-global)
+// and build the geometry table (bins filled in by amr_bin_all).
+amr_status batch_gather(amr_batch* b) {
+  amr_ctx* ctx = &b->ctx;
+  const int D = ctx->dom.dim;
+  cudaStream_t st = ctx->stream;
+  int64_t nf = 0, nv = 0, roots = 0;
+  ctx->geoms.clear();
+  for (auto& x : b->in) {
+    GeomParams g = amr_make_row(x.dom, x.B, x.n_levels, x.d_abs, x.d_rel);
+    g.face_base = nf;
+    g.root_base = roots;
+    ctx->geoms.push_back(g);
+    nf += x.nf;
+    nv += x.nv;
+    roots += roots_of(g, D);
+  }
+  ctx->nf = nf;
+  ctx->nv = nv;
+  b->vert_total = nv;
+  TRY(ensure(ctx, ctx->X, sizeof(float) * D * D * (size_t)(nf > 0 ? nf : 1)));
+  if (D == 3) TRY(ensure(ctx, ctx->nrm, sizeof(float) * 6 * (size_t)(nf > 0 ? nf : 1)));
+  TRY(ensure(ctx, ctx->face_gid, sizeof(uint32_t) * (size_t)(nf > 0 ? nf : 1)));
+  TRY(ensure(ctx, ctx->table, sizeof(GeomParams) * ctx->geoms.size()));
+  CK(cudaMemcpyAsync(ctx->table.p, ctx->geoms.data(), sizeof(GeomParams) * ctx->geoms.size(), cudaMemcpyHostToDevice,
+                     st));
+  if (ctx->indexed) TRY(ensure(ctx, ctx->idx, sizeof(int32_t) * D * (size_t)(nf > 0 ? nf : 1)));
+  int64_t vbase = 0;
+  for (size_t i = 0; i < b->in.size(); ++i) {
+    const BatchInput& x = b->in[i];
+    const int64_t f0 = ctx->geoms[i].face_base;
+    timed(ctx, st, "load_gather", [&] {
+      if (x.indexed)
+        return launch_load_indexed(D, static_cast<const float*>(x.coords.p), x.nv,
+                                   static_cast<const int32_t*>(x.idx.p), x.nf, static_cast<float*>(ctx->X.p),
+                                   ctx->d_err, st, nf, f0);
+      return launch_load_facelist(D, static_cast<const float*>(x.coords.p), x.nf, static_cast<float*>(ctx->X.p),
+                                  ctx->d_err, st, nf, f0);
+    });
+    if (x.indexed && x.nf > 0) {
+      k_offset_idx<<<(unsigned)((x.nf * D + 255) / 256 < 4096 ? (x.nf * D + 255) / 256 : 4096), 256, 0, st>>>(
+          static_cast<const int32_t*>(x.idx.p), x.nf * D, (int32_t)vbase, static_cast<int32_t*>(ctx->idx.p) + f0 * D);
+      ctx->launches += 1;
+    }
+    vbase += x.nv;
+  }
+  if (D == 3)
+    timed(ctx, st, "face_normals", [&] {
+      return launch_face_normals(static_cast<const float*>(ctx->X.p), nf, static_cast<float*>(ctx->nrm.p), st);
+    });
+  timed(ctx, st, "face_gid", [&] {
+    return launch_face_gid(static_cast<const GeomParams*>(ctx->table.p), (int)ctx->geoms.size(), nf,
+                           static_cast<uint32_t*>(ctx->face_gid.p), st);
+  });
+  CK(cudaGetLastError());
+  ctx->loaded = true;
+  ++ctx->load_gen;
+  ctx->vert_groups = ctx->face_groups = false;
+  return AMR_OK;
+}
+
+amr_status batch_segments(amr_batch* b, int NL) {
+  amr_ctx* ctx = &b->ctx;
+  const int G = (int)ctx->geoms.size();
+  DevBuf d_out;
+  TRY(ensure(ctx, d_out, sizeof(int64_t) * SEG_WORDS * (size_t)G));
+  SegArgs sa{};
+  sa.n_geom = G;
+  sa.n_levels = NL;
+  sa.scal = ctx->d_scal;
+  for (int L = 0; L < NL; ++L) {
+    sa.gid[L] = static_cast<const uint32_t*>(ctx->lv[L].gid.p);
+    sa.base[L] = static_cast<const uint64_t*>(ctx->lv[L].base.p);
+  }
+  sa.table = static_cast<const GeomParams*>(ctx->table.p);
+  sa.link_cell = static_cast<const uint32_t*>(ctx->link_cell.p);
+  sa.out = static_cast<int64_t*>(d_out.p);
+  k_batch_segments<<<(G + 63) / 64, 64, 0, ctx->stream>>>(sa);
+  ctx->launches += 1;
+  b->seg.assign((size_t)SEG_WORDS * G, 0);
+  CK(cudaMemcpyAsync(b->seg.data(), d_out.p, sizeof(int64_t) * SEG_WORDS * (size_t)G, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  release(ctx, d_out);
+  return AMR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+amr_status amr_batch_create(int dim, void* stream, amr_batch** out) {
+  if (!out || (dim != 2 && dim != 3)) return AMR_EINVAL;
+  *out = nullptr;
+  amr_batch* b = new amr_batch();
+  amr_ctx* ctx = &b->ctx;
+  ctx->dom.dim = dim;
+  ctx->dom.h0 = 1.0;
+  ctx->multi = true;
+  if (stream) ctx->stream = static_cast<cudaStream_t>(stream);
+  const amr_status s = amr_ctx_init(ctx);
+  if (s != AMR_OK) {
+    amr_ctx_free(ctx);
+    delete b;
+    return s;
+  }
+  *out = b;
+  return AMR_OK;
+}
+
+amr_status amr_batch_destroy(amr_batch* b) {
+  if (!b) return AMR_OK;
+  amr_ctx* ctx = &b->ctx;
+  for (auto& x : b->in) {
+    release(ctx, x.coords);
+    release(ctx, x.idx);
+  }
+  amr_ctx_free(ctx);
+  delete b;
+  return AMR_OK;
+}
+
+amr_ctx* amr_batch_context(amr_batch* b) { return b ? &b->ctx : nullptr; }
+
+amr_status amr_batch_add(amr_batch* b, const amr_domain* dom, const float* coords, int64_t n_verts,
+                         const int32_t* idx, int64_t n_faces, int n_levels, double d_abs, double d_rel,
+                         int bin_density, int* index_out) {
+  if (!b || !dom) return AMR_EINVAL;
+  amr_ctx* ctx = &b->ctx;
+  const int D = ctx->dom.dim;
+  if (dom->dim != D || !(dom->h0 > 0.0)) return fail(ctx, AMR_EINVAL, "geometry dim must match the batch");
+  for (int a = 0; a < D; ++a)
+    if (dom->root_blocks[a] < 1 || dom->root_blocks[a] > (1 << 20)) return fail(ctx, AMR_EINVAL, "bad root_blocks");
+  if (n_levels < 1 || n_levels > AMR_MAX_LEVELS) return fail(ctx, AMR_EINVAL, "bad n_levels");
+  if (!(d_abs >= 0.0) || !(d_rel >= 0.0)) return fail(ctx, AMR_EINVAL, "negative near-wall distance");
+  if (bin_density < 0 || bin_density > 65535) return fail(ctx, AMR_EINVAL, "bad bin density");
+  if (n_faces < 0 || (n_faces > 0 && !coords) || (idx && n_verts <= 0 && n_faces > 0))
+    return fail(ctx, AMR_EINVAL, "bad geometry arrays");
+  // an empty geometry takes the batch's input form
+  const bool form = n_faces > 0 ? idx != nullptr : (b->in.empty() ? idx != nullptr : ctx->indexed);
+  if (!b->in.empty() && n_faces > 0 && form != ctx->indexed) {
+    bool any = false;
+    for (auto& y : b->in) any = any || y.nf > 0;
+    if (any) return fail(ctx, AMR_EINVAL, "all geometries of a batch use the same input form");
+    for (auto& y : b->in) y.indexed = form;
+  }
+  int64_t total = n_faces;
+  for (auto& x : b->in) total += x.nf;
+  if (total >= kMaxFaces) return fail(ctx, AMR_EINVAL, "a batch holds fewer than 2^29 faces");
+  ctx->indexed = form;
+  BatchInput x;
+  x.dom = *dom;
+  for (int a = D; a < 3; ++a) x.dom.root_blocks[a] = 1;
+  x.nf = n_faces;
+  x.nv = form ? n_verts : 0;
+  x.indexed = form;
+  x.n_levels = n_levels;
+  x.d_abs = d_abs;
+  x.d_rel = d_rel;
+  x.B = bin_density;
+  const size_t cbytes = n_faces > 0 ? sizeof(float) * (idx ? D * (size_t)n_verts : (size_t)D * D * n_faces) : 0;
+  TRY(ensure(ctx, x.coords, cbytes));
+  if (cbytes) CK(cudaMemcpyAsync(x.coords.p, coords, cbytes, cudaMemcpyDefault, ctx->stream));
+  if (idx && n_faces > 0) {
+    TRY(ensure(ctx, x.idx, sizeof(int32_t) * D * (size_t)n_faces));
+    CK(cudaMemcpyAsync(x.idx.p, idx, sizeof(int32_t) * D * (size_t)n_faces, cudaMemcpyDefault, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  b->in.push_back(x);
+  b->prepared = false;
+  if (index_out) *index_out = (int)b->in.size() - 1;
+  return AMR_OK;
+}
+
+amr_status amr_batch_set_bins(amr_batch* b, int index, int bin_density) {
+  if (!b || index < 0 || index >= (int)b->in.size() || bin_density < 1 || bin_density > 65535) return AMR_EINVAL;
+  b->in[index].B = bin_density;
+  return AMR_OK;
+}
+
+amr_status amr_batch_run(amr_batch* b, const amr_refine_params* prm, amr_refine_result* out) {
+  if (!b || !prm || !out) return AMR_EINVAL;
+  amr_ctx* ctx = &b->ctx;
+  const int D = ctx->dom.dim;
+  if (b->in.empty()) return fail(ctx, AMR_ESTATE, "empty batch");
+  for (auto& x : b->in)
+    if (x.B < 1) return fail(ctx, AMR_ESTATE, "a geometry has no bin density (set it or tune it)");
+  if (prm->warps_per_cta < 0 || prm->warps_per_cta > 8) return fail(ctx, AMR_EINVAL, "warps_per_cta in [0, 8]");
+  if (prm->want_links) {
+    if (!((D == 2 && prm->lattice == 9) || (D == 3 && prm->lattice == 19)))
+      return fail(ctx, AMR_EINVAL, "lattice must be 9 (D2Q9) in 2D or 19 (D3Q19) in 3D");
+    for (auto& x : b->in) {
+      const double hf = x.dom.h0 * std::ldexp(1.0, -(x.n_levels - 1));
+      if (x.d_abs + x.d_rel * hf < 0.5 * hf) return fail(ctx, AMR_EINVAL, "links need d_L >= h_L/2");
+    }
+  }
+  ctx->refined = false;
+  ctx->face_groups = false;
+  TRY(batch_gather(b));
+  TRY(amr_bin_all(ctx));
+  amr_refine_result r{};
+  TRY(amr_run_refine(ctx, prm, &r));
+  TRY(batch_segments(b, r.n_levels));
+  ctx->refined = true;
+  ctx->last = r;
+  ctx->n_links = prm->want_links ? r.n_links : -1;
+  b->last = r;
+  *out = r;
+  return AMR_OK;
+}
+
+amr_status amr_batch_get_view(amr_batch* b, int index, amr_batch_view* out) {
+  if (!b || !out || index < 0 || index >= (int)b->in.size()) return AMR_EINVAL;
+  amr_ctx* ctx = &b->ctx;
+  if (!ctx->refined || b->seg.empty()) return fail(ctx, AMR_ESTATE, "amr_batch_get_view before amr_batch_run");
+  const int D = ctx->dom.dim;
+  const int64_t* s = b->seg.data() + (size_t)SEG_WORDS * index;
+  const amr_refine_result& R = b->last;
+  amr_batch_view v{};
+  const int NL = b->in[index].n_levels;
+  v.r.n_levels = NL;
+  for (int L = 0; L < NL; ++L) {
+    v.level_base[L] = s[L];
+    v.r.n_blocks[L] = s[16 + L];
+    v.r.block_coords[L] = R.block_coords[L] + s[L] * D;
+    v.r.block_parent[L] = L > 0 ? R.block_parent[L] + s[L] : nullptr;
+    v.r.cell_mask[L] = R.cell_mask[L] + s[L];
+    v.r.block_flag[L] = R.block_flag[L] + s[L];
+  }
+  v.adj_base = s[32];
+  v.pair_base = s[34];
+  v.link_base = s[36];
+  v.face_base = ctx->geoms[index].face_base;
+  int64_t vb = 0;
+  for (int i = 0; i < index; ++i) vb += b->in[i].nv;
+  v.vert_base = vb;
+  if (R.adj_cell) {
+    v.r.n_adj_cells = s[33] - s[32];
+    v.r.n_adj_pairs = s[35] - s[34];
+    v.r.adj_cell = R.adj_cell + s[32];
+    v.r.adj_off = R.adj_off + s[32];
+    v.r.adj_ids = R.adj_ids + s[34];
+  }
+  if (R.link_cell) {
+    v.r.n_links = s[37] - s[36];
+    v.r.link_cell = R.link_cell + s[36];
+    v.r.link_dir = R.link_dir + s[36];
+    v.r.link_q = R.link_q + s[36];
+    v.r.link_face = R.link_face + s[36];
+  }
+  *out = v;
+  return AMR_OK;
+}
+
+amr_status amr_batch_q_backward(amr_batch* b, const float* grad_q, float* grad_out) {
+  if (!b) return AMR_EINVAL;
+  return amr_q_backward(&b->ctx, grad_q, grad_out);
+}
+
+const char* amr_batch_last_error(const amr_batch* b) { return b ? b->ctx.err.c_str() : "null batch"; }
+
+int64_t amr_batch_launch_count(const amr_batch* b) { return b ? b->ctx.launches : -1; }
+
+// ---------------------------------------------------------------------------
+// Autotuner: the paper's trade-off between bin setup (grows with B) and face
+// detection (shrinks with B) decides B; the warps per block of the refine
+// kernels are tuned for the chosen B.  Objective = CUDA-event time of
+// bin + refine (with the caller's adjacency / link options), best of two runs.
+// ---------------------------------------------------------------------------
+amr_status amr_autotune(amr_ctx* ctx, const amr_refine_params* prm, const int* b_cand, int n_b, const int* w_cand,
+                        int n_w, int* best_B, int* best_warps, double* best_ms) {
+  if (!ctx || !prm || !best_B || !best_warps) return AMR_EINVAL;
+  if (ctx->multi || !ctx->loaded) return fail(ctx, AMR_ESTATE, "amr_autotune needs a loaded single geometry");
+  const int D = ctx->dom.dim;
+  std::vector<int> bs, ws;
+  if (b_cand && n_b > 0) {
+    bs.assign(b_cand, b_cand + n_b);
+  } else {
+    const int def[] = {4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256};
+    for (int B : def)
+      if (ipow(B, D) <= (1ll << 24) && (double)B * B <= 16.0 * (double)(ctx->nf > 16 ? ctx->nf : 16)) bs.push_back(B);
+  }
+  if (w_cand && n_w > 0)
+    ws.assign(w_cand, w_cand + n_w);
+  else
+    ws = {2, 4, 8};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto measure = [&](int B, int warps, double* ms) -> amr_status {
+    amr_refine_params p = *prm;
+    p.use_graph = 0;
+    p.warps_per_cta = warps;
+    double best = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {
+      amr_bins_view bv;
+      amr_refine_result r;
+      CK(cudaEventRecord(e0, ctx->stream));
+      TRY(amr_bin_faces(ctx, B, &bv));
+      TRY(amr_refine_near_wall(ctx, &p, &r));
+      CK(cudaEventRecord(e1, ctx->stream));
+      CK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      if (t < best) best = t;
+    }
+    *ms = best;
+    return AMR_OK;
+  };
+  int bb = bs.empty() ? 1 : bs[0], bw = prm->warps_per_cta > 0 ? prm->warps_per_cta : 4;
+  double bt = 1e300;
+  for (int B : bs) {
+    double t = 0;
+    TRY(measure(B, bw, &t));
+    if (t < bt) {
+      bt = t;
+      bb = B;
+    }
+  }
+  for (int w : ws) {
+    if (w < 1 || w > 8) continue;
+    double t = 0;
+    TRY(measure(bb, w, &t));
+    if (t < bt) {
+      bt = t;
+      bw = w;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *best_B = bb;
+  *best_warps = bw;
+  if (best_ms) *best_ms = bt;
+  return AMR_OK;
+}
 
 }  // extern "C"

@@ -32,8 +32,60 @@ enum : int {
   CNT_N = 8,
 };
 
-// Bin-grid parameters: bin of coordinate x along axis a is
-// clamp(floor((x - origin[a]) * scale[a]), 0, B - 1) evaluated in FP64.
+// Per-geometry parameters.  A launch may cover the blocks (faces) of many
+// geometries; each block (face) then carries its geometry id and reads its
+// row of this table.  Single-geometry launches pass one row by value.
+//   domain box   origin[a] + [0, 4 root[a] h0], level-L cell size h0 2^-L
+//   bins         bin of x along a = clamp(floor((x - origin[a]) * bin_scale[a]), 0, B - 1)
+//                (FP64), global bin index = bin_base + bx + B (by + B bz)
+//   distance     d_L = d_abs + d_rel h_L
+struct GeomParams {
+  double origin[3];
+  double h0;
+  double d_abs, d_rel;
+  double bin_scale[3];
+  int B;
+  int n_levels;
+  int root[3];
+  int pad;
+  int64_t bin_base;
+  int64_t root_base;   // first level-0 block of this geometry in the concatenated list
+  int64_t face_base;   // first face of this geometry in the concatenated face arrays
+};
+
+// Geometry of one block on one level, derived from its table row.
+struct LevelGeom {
+  double origin[3];
+  double h, d;
+  double scale[3];
+  int B;
+  int64_t bin_base;
+  bool finest;
+};
+
+__device__ __forceinline__ LevelGeom level_geom(const GeomParams& P, int level) {
+  LevelGeom g;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g.origin[a] = P.origin[a];
+    g.scale[a] = P.bin_scale[a];
+  }
+  g.h = scalbn(P.h0, -level);
+  g.d = __dadd_rn(P.d_abs, __dmul_rn(P.d_rel, g.h));
+  g.B = P.B;
+  g.bin_base = P.bin_base;
+  g.finest = level == P.n_levels - 1;
+  return g;
+}
+
+// Table row of item i: the by-value row for single-geometry launches.
+__device__ __forceinline__ GeomParams geom_row(const GeomParams& g0, const GeomParams* table, const uint32_t* gid,
+                                               int64_t i) {
+  if (!table) return g0;
+  return table[gid ? gid[i] : 0u];
+}
+
+// Bin-grid parameters of one geometry (kept for the allocation-free binning entry).
 struct BinGrid {
   int B;
   double origin[3];
@@ -125,103 +177,162 @@ __device__ __forceinline__ T warp_inclusive_scan(T v) {
 }
 
 // ---------------------------------------------------------------------------
-// Launchers (host side).  All are asynchronous on `st`.
+// Launchers (host side).  All are asynchronous on `st` and return the number
+// of kernels they launched.  Sizes marked "device" are read by the kernels
+// from device memory (so that launches can be captured in a CUDA graph before
+// the sizes are known); the host passes a capacity instead.
 // ---------------------------------------------------------------------------
-struct LaunchInfo {
-  int num_sms;
-};
-
+// Gather nf faces into the SoA array X (row stride ld, default nf) starting at face f0.
 int launch_load_indexed(int dim, const float* verts, int64_t nv, const int32_t* idx, int64_t nf, float* X,
-                         unsigned* err, cudaStream_t st);
-int launch_load_facelist(int dim, const float* coords, int64_t nf, float* X, unsigned* err, cudaStream_t st);
+                        unsigned* err, cudaStream_t st, int64_t ld = -1, int64_t f0 = 0);
+int launch_load_facelist(int dim, const float* coords, int64_t nf, float* X, unsigned* err, cudaStream_t st,
+                         int64_t ld = -1, int64_t f0 = 0);
 int launch_face_normals(const float* X, int64_t nf, float* nrm, cudaStream_t st);
+
+// Faces of one or many geometries: face_gid (nullable) selects the table row.
+struct FaceBinArgs {
+  int dim;
+  const float* X;
+  int64_t nf;
+  GeomParams g0;
+  const GeomParams* table;
+  const uint32_t* face_gid;
+  uint32_t* frange;
+  uint32_t* count;
+};
+int launch_face_bins(const FaceBinArgs& a, cudaStream_t st);
 int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint32_t* frange, uint32_t* count,
-                      cudaStream_t st);
-// exclusive scan of n u32 values; out[n] = total (low 32 bits); total64 (device) = full total
+                     cudaStream_t st);
+struct ScatterArgs {
+  FaceBinArgs f;
+  const uint32_t* offsets;
+  uint32_t* ids;
+  void* payload;
+};
+int launch_scatter(const ScatterArgs& a, cudaStream_t st);
+
+// Exclusive scans (single pass, decoupled look-back).  u32: out[n] = total
+// (low 32 bits), *total64 = the full total.  u64: n_dev (nullable) gives the
+// element count on the device, n the capacity.
 size_t scan_u32_scratch_bytes(int64_t n);
 int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* total64, void* scratch, unsigned* err,
-                     cudaStream_t st);
+                    cudaStream_t st);
 size_t scan_u64_scratch_bytes(int64_t n);
-int launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* total, void* scratch, unsigned* err,
-                     cudaStream_t st);
-int launch_scatter(int dim, const float* X, int64_t nf, const uint32_t* frange, const uint32_t* offsets,
-                    uint32_t* count, uint32_t* ids, void* payload, int B, cudaStream_t st);
+int launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, const uint64_t* n_dev, uint64_t* total,
+                    void* scratch, unsigned* err, int num_sms, cudaStream_t st);
 
 struct RefineLevel {
   int dim;
+  int level;
+  GeomParams g0;
+  const GeomParams* table;     // null: every block uses g0
+  const uint32_t* gid;         // per-block geometry id (null: 0)
   const int32_t* blocks;
-  int64_t n_blocks;
+  int64_t n_blocks;            // count, or capacity when n_dev is set
+  const uint64_t* n_dev;       // device block count (nullable)
   const uint32_t* offsets;
   const void* payload;
   const float* X;
   const float* nrm;
   int64_t nf;
-  BinGrid grid;
-  double origin[3];
-  double h;
-  double d;
   uint64_t* mask;
   uint8_t* flag;
-  uint16_t* cellcnt;   // per cell face count (finest level with adjacency) or null
-  uint64_t* blockcnt;  // per block (pairs | adjacent cells << 32) or null
+  uint16_t* cellcnt;           // per cell face count, blocks whose geometry ends at this level
+  uint64_t* blockcnt;          // per block pairs | adjacent cells << 32 (0 for the others)
   unsigned long long* counters;
-  unsigned* work;      // dynamic work counter (zeroed before launch)
-  unsigned* err;       // device error word
+  unsigned* work;              // dynamic work counter (zeroed before launch)
+  unsigned* err;
+  int warps;                   // warps per CTA (tunable)
 };
 int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st);
 
 struct EmitArgs {
   RefineLevel lv;
-  const uint64_t* block_base;  // exclusive scan of blockcnt
+  const uint64_t* block_base;  // exclusive scan of blockcnt over this level
+  const uint64_t* run;         // device running totals before this level: [0] cells, [1] pairs
   uint32_t* adj_cell;
   uint32_t* adj_off;
   uint32_t* adj_ids;
+  int64_t cap_cells, cap_pairs;
 };
 int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st);
 
+struct ChildrenArgs {
+  int dim;
+  int level;
+  GeomParams g0;
+  const GeomParams* table;
+  const uint32_t* gid;
+  const int32_t* blocks;
+  const uint64_t* mask;
+  int64_t n;                   // count, or capacity when n_dev is set
+  const uint64_t* n_dev;
+  int32_t* child_blocks;
+  uint32_t* child_gid;         // nullable
+  int32_t* child_parent;
+  int64_t cap_out;
+  uint64_t* total;             // device: number of children (next level's count)
+  unsigned* err;
+};
 size_t children_scratch_bytes(int64_t n);
-int launch_children(int dim, const int32_t* blocks, const uint64_t* mask, int64_t n, int32_t* child_blocks,
-                     int32_t* child_parent, uint64_t* total, void* scratch, unsigned* err, cudaStream_t st);
+int launch_children(const ChildrenArgs& a, void* scratch, int num_sms, cudaStream_t st);
+// Level-0 blocks of every geometry of the table (x fastest within each), with their geometry ids.
 int launch_root_blocks(int dim, const int* root, int32_t* blocks, int64_t n, cudaStream_t st);
+int launch_root_blocks_multi(int dim, const GeomParams* table, int n_geom, int32_t* blocks, uint32_t* gid,
+                             int64_t n, cudaStream_t st);
+// Per-face geometry id from the table's face ranges.
+int launch_face_gid(const GeomParams* table, int n_geom, int64_t nf, uint32_t* face_gid, cudaStream_t st);
 
 struct LinkArgs {
   int dim;
   int lattice;
-  const int32_t* blocks;       // finest-level blocks
+  int level;
+  GeomParams g0;
+  const GeomParams* table;
+  const uint32_t* gid;         // per-block geometry ids of this level (nullable)
+  const int32_t* blocks;       // this level's blocks
   const uint32_t* adj_cell;
   const uint32_t* adj_off;
   const uint32_t* adj_ids;
-  int64_t n_adj;
+  const uint64_t* run;         // device running totals before this level: [0] rows, [2] links
+  const uint64_t* level_tot;   // device: this level's pairs | cells << 32
+  int64_t cap_rows;
   const float* X;
   const float* nrm;
   int64_t nf;
-  double origin[3];
-  double h;
   uint32_t* link_cell;
   uint8_t* link_dir;
   float* link_q;
   uint32_t* link_face;
   int64_t link_cap;
-  uint64_t* n_links;           // device total
+  uint64_t* n_links;           // device: this level's link count
   unsigned long long* counters;
   unsigned* err;
 };
+size_t links_scratch_bytes(int64_t n_adj);
+int launch_links(const LinkArgs& a, void* scratch, int num_sms, cudaStream_t st);
+// close: adj_off[run[0] + cells] = run[1] + pairs (end marker of the level's rows);
+// else: run[0] += cells, run[1] += pairs, run[2] += links (n_links nullable).
+int launch_advance(const uint64_t* level_tot, const uint64_t* n_links, uint64_t* run, uint32_t* adj_off,
+                   int64_t cap_cells, unsigned* err, bool close, cudaStream_t st);
+
 struct AdjointArgs {
   int dim;
   int64_t nf;
+  GeomParams g0;
+  const GeomParams* table;
+  const uint32_t* face_gid;    // nullable
+  const int32_t* const* level_blocks;  // device array of per-level block pointers
   const float* X;
   const float* nrm;
-  const uint32_t* face_off;     // [nf + 1]
-  const uint32_t* face_links;   // link indices grouped by face, ascending within a face
+  const uint32_t* face_off;    // [nf + 1]
+  const uint32_t* face_links;  // link indices grouped by face, ascending within a face
   const float* grad_q;
   const uint32_t* link_cell;
   const uint8_t* link_dir;
   const float* link_q;
   const uint32_t* adj_cell;
-  const int32_t* blocks;        // finest-level blocks
-  double origin[3];
-  double h;
-  float* grad_face;             // [nf][D][D]
+  float* grad_face;            // [nf][D][D]
 };
 size_t radix_sort_scratch_bytes(int64_t n);
 // Stable sort of n u32 keys (low key_bits significant); values default to 0..n-1.
@@ -231,8 +342,5 @@ int launch_count_keys(const uint32_t* keys, int64_t n, uint32_t* cnt, cudaStream
 int launch_face_grad(const AdjointArgs& a, cudaStream_t st);
 int launch_vertex_grad(int dim, const float* grad_face, const uint32_t* vert_off, const uint32_t* vert_corners,
                        int64_t nv, float* out, cudaStream_t st);
-
-size_t links_scratch_bytes(int64_t n_adj);
-int launch_links(const LinkArgs& a, void* scratch, cudaStream_t st);
 
 }  // namespace amr

@@ -132,6 +132,16 @@ __global__ void k_face_grad(AdjointArgs a) {
 #pragma unroll
     for (int j = 0; j < D * D; ++j) V[j] = a.X[(int64_t)j * a.nf + f];
     const uint32_t b0 = a.face_off[f], b1 = a.face_off[f + 1];
+    if (b1 == b0) {
+#pragma unroll
+      for (int j = 0; j < D * D; ++j) a.grad_face[(int64_t)f * D * D + j] = 0.f;
+      continue;
+    }
+    // links of this face live on the finest level of its geometry
+    const GeomParams P = geom_row(a.g0, a.table, a.face_gid, f);
+    const int Lf = P.n_levels - 1;
+    const double hL = scalbn(P.h0, -Lf);
+    const int32_t* blocks = a.level_blocks[Lf];
     for (uint32_t s = b0; s < b1; ++s) {
       const uint32_t l = a.face_links[s];
       const float gq = a.grad_q[l];
@@ -144,13 +154,13 @@ __global__ void k_face_grad(AdjointArgs a) {
       float p[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        const int g = 4 * a.blocks[(int64_t)blk * D + c] + (int)((bit >> (2 * c)) & 3u);
-        const double xc = __dadd_rn(a.origin[c], __dmul_rn((double)g + 0.5, a.h));
+        const int g = 4 * blocks[(int64_t)blk * D + c] + (int)((bit >> (2 * c)) & 3u);
+        const double xc = __dadd_rn(P.origin[c], __dmul_rn((double)g + 0.5, hL));
         const float ohi = (float)xc, olo = (float)(xc - (double)ohi);
 #pragma unroll
         for (int k = 0; k < D; ++k) p[k][c] = (V[D * k + c] - ohi) - olo;
       }
-      const float h32 = (float)a.h;
+      const float h32 = (float)hL;
       if constexpr (D == 3) {
         const float dv[3] = {c_dirs19[dir][0] * h32, c_dirs19[dir][1] * h32, c_dirs19[dir][2] * h32};
         const float nh[3] = {a.nrm[f], a.nrm[a.nf + f], a.nrm[2 * a.nf + f]};

@@ -27,7 +27,7 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
 
 template <int D>
 __global__ void k_load_indexed(const float* __restrict__ verts, int64_t nv, const int32_t* __restrict__ idx,
-                               int64_t nf, float* __restrict__ X, unsigned* err) {
+                               int64_t nf, float* __restrict__ X, int64_t ld, int64_t f0, unsigned* err) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -44,14 +44,15 @@ __global__ void k_load_indexed(const float* __restrict__ verts, int64_t nv, cons
           atomicOr(err, ERR_NONFINITE);
           x = 0.0f;
         }
-        X[(int64_t)(k * D + c) * nf + f] = x;
+        X[(int64_t)(k * D + c) * ld + f0 + f] = x;
       }
     }
   }
 }
 
 template <int D>
-__global__ void k_load_facelist(const float* __restrict__ coords, int64_t nf, float* __restrict__ X, unsigned* err) {
+__global__ void k_load_facelist(const float* __restrict__ coords, int64_t nf, float* __restrict__ X, int64_t ld,
+                                int64_t f0, unsigned* err) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int j = 0; j < D * D; ++j) {
@@ -60,7 +61,7 @@ __global__ void k_load_facelist(const float* __restrict__ coords, int64_t nf, fl
         atomicOr(err, ERR_NONFINITE);
         x = 0.0f;
       }
-      X[(int64_t)j * nf + f] = x;
+      X[(int64_t)j * ld + f0 + f] = x;
     }
   }
 }
@@ -91,30 +92,30 @@ __global__ void k_face_normals(const float* __restrict__ X, int64_t nf, float* _
   }
 }
 
-// Per face: bin range of its AABB along each axis (packed lo | hi << 16) and one
-// count per (face, bin) incidence.
+// Per face: bin range of its AABB along each axis (packed lo | hi << 16, bins of
+// its own geometry) and one count per (face, bin) incidence.
 template <int D>
-__global__ void k_face_bins(const float* __restrict__ X, int64_t nf, BinGrid g, uint32_t* __restrict__ frange,
-                            uint32_t* __restrict__ count) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_face_bins(FaceBinArgs a) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.nf; f += (int64_t)gridDim.x * blockDim.x) {
+    const GeomParams P = geom_row(a.g0, a.table, a.face_gid, f);
     int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      float mn = X[(int64_t)a * nf + f], mx = mn;
+    for (int c = 0; c < D; ++c) {
+      float mn = a.X[(int64_t)c * a.nf + f], mx = mn;
 #pragma unroll
       for (int k = 1; k < D; ++k) {
-        const float x = X[(int64_t)(k * D + a) * nf + f];
+        const float x = a.X[(int64_t)(k * D + c) * a.nf + f];
         mn = fminf(mn, x);
         mx = fmaxf(mx, x);
       }
-      lo[a] = bin_coord((double)mn, g.origin[a], g.scale[a], g.B);
-      hi[a] = bin_coord((double)mx, g.origin[a], g.scale[a], g.B);
-      frange[(int64_t)a * nf + f] = (uint32_t)lo[a] | ((uint32_t)hi[a] << 16);
+      lo[c] = bin_coord((double)mn, P.origin[c], P.bin_scale[c], P.B);
+      hi[c] = bin_coord((double)mx, P.origin[c], P.bin_scale[c], P.B);
+      a.frange[(int64_t)c * a.nf + f] = (uint32_t)lo[c] | ((uint32_t)hi[c] << 16);
     }
-    const int64_t B = g.B;
+    const int64_t B = P.B;
     for (int z = lo[2]; z <= hi[2]; ++z)
       for (int y = lo[1]; y <= hi[1]; ++y)
-        for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&count[x + B * (y + B * (int64_t)z)], 1u);
+        for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&a.count[P.bin_base + x + B * (y + B * (int64_t)z)], 1u);
   }
 }
 
@@ -122,31 +123,32 @@ __global__ void k_face_bins(const float* __restrict__ X, int64_t nf, BinGrid g, 
 // the bin's count (which leaves the counts zeroed for the next call) and writes
 // the face id and its coordinates there.
 template <int D>
-__global__ void k_scatter(const float* __restrict__ X, int64_t nf, const uint32_t* __restrict__ frange,
-                          const uint32_t* __restrict__ offsets, uint32_t* __restrict__ count,
-                          uint32_t* __restrict__ ids, typename EntryT<D>::type* __restrict__ payload, int Bi) {
+__global__ void k_scatter(ScatterArgs a) {
   using E = typename EntryT<D>::type;
+  E* payload = static_cast<E*>(a.payload);
+  const int64_t nf = a.f.nf;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    const GeomParams P = geom_row(a.f.g0, a.f.table, a.f.face_gid, f);
     int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const uint32_t r = frange[(int64_t)a * nf + f];
-      lo[a] = (int)(r & 0xffffu);
-      hi[a] = (int)(r >> 16);
+    for (int c = 0; c < D; ++c) {
+      const uint32_t r = a.f.frange[(int64_t)c * nf + f];
+      lo[c] = (int)(r & 0xffffu);
+      hi[c] = (int)(r >> 16);
     }
     E e;
 #pragma unroll
-    for (int j = 0; j < D * D; ++j) e.v[j] = X[(int64_t)j * nf + f];
+    for (int j = 0; j < D * D; ++j) e.v[j] = a.f.X[(int64_t)j * nf + f];
 #pragma unroll
     for (int j = 0; j < (int)(sizeof(e.pad) / sizeof(e.pad[0])); ++j) e.pad[j] = 0u;
-    const int64_t B = Bi;
+    const int64_t B = P.B;
     for (int z = lo[2]; z <= hi[2]; ++z)
       for (int y = lo[1]; y <= hi[1]; ++y)
         for (int x = lo[0]; x <= hi[0]; ++x) {
-          const int64_t b = x + B * (y + B * (int64_t)z);
-          const uint32_t old = atomicSub(&count[b], 1u);
-          const int64_t pos = (int64_t)offsets[b] + old - 1;
-          ids[pos] = (uint32_t)f;
+          const int64_t b = P.bin_base + x + B * (y + B * (int64_t)z);
+          const uint32_t old = atomicSub(&a.f.count[b], 1u);
+          const int64_t pos = (int64_t)a.offsets[b] + old - 1;
+          a.ids[pos] = (uint32_t)f;
           uint32_t flags = (x == lo[0] ? (1u << 29) : 0u) | (y == lo[1] ? (1u << 30) : 0u);
           if (D == 3) flags |= (z == lo[2] ? (1u << 31) : 0u);
           e.id = (uint32_t)f | flags;
@@ -159,50 +161,70 @@ __global__ void k_scatter(const float* __restrict__ X, int64_t nf, const uint32_
 }
 
 // Single-pass exclusive scan (decoupled look-back over ticket-ordered tiles).
+// CTAs take tiles in ticket order until none is left, so the grid may be
+// smaller than the tile count and the element count may come from device
+// memory (n_dev, bounded by the capacity n_cap).
 template <typename T, int ITEMS>
-__global__ void __launch_bounds__(kThreads) k_scan(const T* __restrict__ in, T* __restrict__ out, int64_t n,
-                                                    uint64_t* total, uint64_t* state, unsigned* ticket,
-                                                    unsigned* err) {
+__global__ void __launch_bounds__(kThreads) k_scan(const T* __restrict__ in, T* __restrict__ out, int64_t n_cap,
+                                                    const uint64_t* n_dev, uint64_t* total, uint64_t* state,
+                                                    unsigned* ticket, unsigned* err) {
   __shared__ unsigned s_tile;
   __shared__ uint64_t s_warp[kThreads / 32];
   __shared__ uint64_t s_prefix;
-  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
-  __syncthreads();
-  const long long tile = s_tile;
-  const int64_t base = tile * (int64_t)kThreads * ITEMS + (int64_t)threadIdx.x * ITEMS;
-  uint64_t v[ITEMS];
-  uint64_t sum = 0;
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int64_t j = base + i;
-    v[i] = j < n ? (uint64_t)in[j] : 0ull;
-    sum += v[i];
+  int64_t n = n_cap;
+  if (n_dev) {
+    const uint64_t nd = *n_dev;
+    if ((int64_t)nd > n_cap) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, ERR_OVERFLOW);
+    } else {
+      n = (int64_t)nd;
+    }
+  }
+  const int64_t ntiles = (n + (int64_t)kThreads * ITEMS - 1) / ((int64_t)kThreads * ITEMS);
+  if (ntiles == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *total = 0;
+    return;
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint64_t incl = warp_inclusive_scan<unsigned long long>(sum);
-  if (lane == 31) s_warp[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    uint64_t w = lane < kThreads / 32 ? s_warp[lane] : 0ull;
-    w = warp_inclusive_scan<unsigned long long>(w);
-    if (lane < kThreads / 32) s_warp[lane] = w;
-  }
-  __syncthreads();
-  const uint64_t warp_excl = wid > 0 ? s_warp[wid - 1] : 0ull;
-  if (threadIdx.x == 0) {
-    const uint64_t agg = s_warp[kThreads / 32 - 1];
-    const uint64_t pre = lookback_exclusive(state, tile, agg, err);
-    s_prefix = pre;
-    const int64_t ntiles = (n + (int64_t)kThreads * ITEMS - 1) / ((int64_t)kThreads * ITEMS);
-    if (tile == ntiles - 1 || ntiles == 0) *total = pre + agg;
-  }
-  __syncthreads();
-  uint64_t run = s_prefix + warp_excl + incl - sum;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= ntiles) break;
+    const int64_t base = tile * (int64_t)kThreads * ITEMS + (int64_t)threadIdx.x * ITEMS;
+    uint64_t v[ITEMS];
+    uint64_t sum = 0;
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int64_t j = base + i;
-    if (j < n) out[j] = (T)run;
-    run += v[i];
+    for (int i = 0; i < ITEMS; ++i) {
+      const int64_t j = base + i;
+      v[i] = j < n ? (uint64_t)in[j] : 0ull;
+      sum += v[i];
+    }
+    const uint64_t incl = warp_inclusive_scan<unsigned long long>(sum);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t w = lane < kThreads / 32 ? s_warp[lane] : 0ull;
+      w = warp_inclusive_scan<unsigned long long>(w);
+      if (lane < kThreads / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint64_t warp_excl = wid > 0 ? s_warp[wid - 1] : 0ull;
+    if (threadIdx.x == 0) {
+      const uint64_t agg = s_warp[kThreads / 32 - 1];
+      const uint64_t pre = lookback_exclusive(state, tile, agg, err);
+      s_prefix = pre;
+      if (tile == ntiles - 1) *total = pre + agg;
+    }
+    __syncthreads();
+    uint64_t run = s_prefix + warp_excl + incl - sum;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int64_t j = base + i;
+      if (j < n) out[j] = (T)run;
+      run += v[i];
+    }
+    __syncthreads();
   }
 }
 
@@ -223,6 +245,43 @@ __global__ void k_root_blocks(int r0, int r1, int r2, int32_t* __restrict__ bloc
   }
 }
 
+// Level-0 blocks of many geometries: geometry g owns entries
+// [root_base_g, root_base_g + prod(root_g)), x fastest within it.
+template <int D>
+__global__ void k_root_blocks_multi(const GeomParams* __restrict__ table, int n_geom, int32_t* __restrict__ blocks,
+                                    uint32_t* __restrict__ gid, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n_geom - 1;
+    while (lo < hi) {  // last geometry with root_base <= i
+      const int mid = (lo + hi + 1) >> 1;
+      if (table[mid].root_base <= i)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const GeomParams& P = table[lo];
+    const int64_t j = i - P.root_base;
+    blocks[i * D + 0] = (int32_t)(j % P.root[0]);
+    blocks[i * D + 1] = (int32_t)((j / P.root[0]) % P.root[1]);
+    if (D == 3) blocks[i * D + 2] = (int32_t)(j / ((int64_t)P.root[0] * P.root[1]));
+    gid[i] = (uint32_t)lo;
+  }
+}
+
+__global__ void k_face_gid(const GeomParams* __restrict__ table, int n_geom, int64_t nf, uint32_t* __restrict__ out) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n_geom - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (table[mid].face_base <= f)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    out[f] = (uint32_t)lo;
+  }
+}
+
 constexpr int kScanItemsU32 = 8;
 constexpr int kScanItemsU64 = 4;
 
@@ -234,23 +293,26 @@ size_t scan_scratch(int64_t n, int items) {
 }  // namespace
 
 int launch_load_indexed(int dim, const float* verts, int64_t nv, const int32_t* idx, int64_t nf, float* X,
-                         unsigned* err, cudaStream_t st) {
+                        unsigned* err, cudaStream_t st, int64_t ld, int64_t f0) {
   if (nf <= 0) return 0;
+  if (ld < 0) ld = nf;
   const int g = grid_for(nf, kThreads);
   if (dim == 3)
-    k_load_indexed<3><<<g, kThreads, 0, st>>>(verts, nv, idx, nf, X, err);
+    k_load_indexed<3><<<g, kThreads, 0, st>>>(verts, nv, idx, nf, X, ld, f0, err);
   else
-    k_load_indexed<2><<<g, kThreads, 0, st>>>(verts, nv, idx, nf, X, err);
+    k_load_indexed<2><<<g, kThreads, 0, st>>>(verts, nv, idx, nf, X, ld, f0, err);
   return 1;
 }
 
-int launch_load_facelist(int dim, const float* coords, int64_t nf, float* X, unsigned* err, cudaStream_t st) {
+int launch_load_facelist(int dim, const float* coords, int64_t nf, float* X, unsigned* err, cudaStream_t st,
+                         int64_t ld, int64_t f0) {
   if (nf <= 0) return 0;
+  if (ld < 0) ld = nf;
   const int g = grid_for(nf, kThreads);
   if (dim == 3)
-    k_load_facelist<3><<<g, kThreads, 0, st>>>(coords, nf, X, err);
+    k_load_facelist<3><<<g, kThreads, 0, st>>>(coords, nf, X, ld, f0, err);
   else
-    k_load_facelist<2><<<g, kThreads, 0, st>>>(coords, nf, X, err);
+    k_load_facelist<2><<<g, kThreads, 0, st>>>(coords, nf, X, ld, f0, err);
   return 1;
 }
 
@@ -260,53 +322,85 @@ int launch_face_normals(const float* X, int64_t nf, float* nrm, cudaStream_t st)
   return 1;
 }
 
-int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint32_t* frange, uint32_t* count,
-                      cudaStream_t st) {
-  if (nf <= 0) return 0;
-  const int gr = grid_for(nf, kThreads);
-  if (dim == 3)
-    k_face_bins<3><<<gr, kThreads, 0, st>>>(X, nf, g, frange, count);
+int launch_face_bins(const FaceBinArgs& a, cudaStream_t st) {
+  if (a.nf <= 0) return 0;
+  const int gr = grid_for(a.nf, kThreads);
+  if (a.dim == 3)
+    k_face_bins<3><<<gr, kThreads, 0, st>>>(a);
   else
-    k_face_bins<2><<<gr, kThreads, 0, st>>>(X, nf, g, frange, count);
+    k_face_bins<2><<<gr, kThreads, 0, st>>>(a);
   return 1;
+}
+
+int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint32_t* frange, uint32_t* count,
+                     cudaStream_t st) {
+  FaceBinArgs a{};
+  a.dim = dim;
+  a.X = X;
+  a.nf = nf;
+  a.g0.B = g.B;
+  for (int c = 0; c < 3; ++c) {
+    a.g0.origin[c] = g.origin[c];
+    a.g0.bin_scale[c] = g.scale[c];
+  }
+  a.frange = frange;
+  a.count = count;
+  return launch_face_bins(a, st);
 }
 
 size_t scan_u32_scratch_bytes(int64_t n) { return scan_scratch(n, kScanItemsU32); }
 size_t scan_u64_scratch_bytes(int64_t n) { return scan_scratch(n, kScanItemsU64); }
 
 int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* total64, void* scratch, unsigned* err,
-                     cudaStream_t st) {
+                    cudaStream_t st) {
   const size_t sb = scan_u32_scratch_bytes(n);
   cudaMemsetAsync(scratch, 0, sb, st);
   const int64_t tiles = (n + (int64_t)kThreads * kScanItemsU32 - 1) / ((int64_t)kThreads * kScanItemsU32);
   unsigned* ticket = reinterpret_cast<unsigned*>(scratch);
   uint64_t* state = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 16);
-  k_scan<uint32_t, kScanItemsU32><<<(unsigned)(tiles > 0 ? tiles : 1), kThreads, 0, st>>>(in, out, n, total64, state,
-                                                                                        ticket, err);
+  k_scan<uint32_t, kScanItemsU32><<<(unsigned)(tiles > 0 ? tiles : 1), kThreads, 0, st>>>(in, out, n, nullptr,
+                                                                                        total64, state, ticket, err);
   k_write_total_u32<<<1, 1, 0, st>>>(total64, out + n, err);
   return 2;
 }
 
-int launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* total, void* scratch, unsigned* err,
-                     cudaStream_t st) {
+int launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, const uint64_t* n_dev, uint64_t* total,
+                    void* scratch, unsigned* err, int num_sms, cudaStream_t st) {
   const size_t sb = scan_u64_scratch_bytes(n);
   cudaMemsetAsync(scratch, 0, sb, st);
-  const int64_t tiles = (n + (int64_t)kThreads * kScanItemsU64 - 1) / ((int64_t)kThreads * kScanItemsU64);
+  int64_t tiles = (n + (int64_t)kThreads * kScanItemsU64 - 1) / ((int64_t)kThreads * kScanItemsU64);
+  if (tiles < 1) tiles = 1;
+  if (n_dev && tiles > (int64_t)num_sms * 4) tiles = (int64_t)num_sms * 4;
   unsigned* ticket = reinterpret_cast<unsigned*>(scratch);
   uint64_t* state = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 16);
-  k_scan<uint64_t, kScanItemsU64><<<(unsigned)(tiles > 0 ? tiles : 1), kThreads, 0, st>>>(in, out, n, total, state,
-                                                                                        ticket, err);
+  k_scan<uint64_t, kScanItemsU64><<<(unsigned)tiles, kThreads, 0, st>>>(in, out, n, n_dev, total, state, ticket, err);
   return 1;
 }
 
-int launch_scatter(int dim, const float* X, int64_t nf, const uint32_t* frange, const uint32_t* offsets,
-                    uint32_t* count, uint32_t* ids, void* payload, int B, cudaStream_t st) {
-  if (nf <= 0) return 0;
-  const int g = grid_for(nf, kThreads);
-  if (dim == 3)
-    k_scatter<3><<<g, kThreads, 0, st>>>(X, nf, frange, offsets, count, ids, static_cast<Entry3*>(payload), B);
+int launch_scatter(const ScatterArgs& a, cudaStream_t st) {
+  if (a.f.nf <= 0) return 0;
+  const int g = grid_for(a.f.nf, kThreads);
+  if (a.f.dim == 3)
+    k_scatter<3><<<g, kThreads, 0, st>>>(a);
   else
-    k_scatter<2><<<g, kThreads, 0, st>>>(X, nf, frange, offsets, count, ids, static_cast<Entry2*>(payload), B);
+    k_scatter<2><<<g, kThreads, 0, st>>>(a);
+  return 1;
+}
+
+int launch_root_blocks_multi(int dim, const GeomParams* table, int n_geom, int32_t* blocks, uint32_t* gid, int64_t n,
+                             cudaStream_t st) {
+  if (n <= 0) return 0;
+  const int g = grid_for(n, kThreads);
+  if (dim == 3)
+    k_root_blocks_multi<3><<<g, kThreads, 0, st>>>(table, n_geom, blocks, gid, n);
+  else
+    k_root_blocks_multi<2><<<g, kThreads, 0, st>>>(table, n_geom, blocks, gid, n);
+  return 1;
+}
+
+int launch_face_gid(const GeomParams* table, int n_geom, int64_t nf, uint32_t* face_gid, cudaStream_t st) {
+  if (nf <= 0) return 0;
+  k_face_gid<<<grid_for(nf, kThreads), kThreads, 0, st>>>(table, n_geom, nf, face_gid);
   return 1;
 }
 

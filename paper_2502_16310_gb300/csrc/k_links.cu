@@ -109,30 +109,47 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
   __shared__ uint32_t s_f[Q1][kLThreads];
   __shared__ uint32_t s_warp[kLThreads / 32];
   __shared__ uint64_t s_prefix;
-  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const uint64_t row0 = a.run ? a.run[0] : 0ull;
+  const uint64_t link0 = a.run ? a.run[2] : 0ull;
+  int64_t nrows = a.level_tot ? (int64_t)(*a.level_tot >> 32) : a.cap_rows;
+  if ((int64_t)row0 + nrows > a.cap_rows) {
+    if (blockIdx.x == 0 && tid == 0) atomicOr(a.err, ERR_OVERFLOW);
+    nrows = a.cap_rows - (int64_t)row0 > 0 ? a.cap_rows - (int64_t)row0 : 0;
+  }
+  const int64_t ntiles = (nrows + kLThreads - 1) / kLThreads;
+  if (ntiles == 0) {
+    if (blockIdx.x == 0 && tid == 0) *a.n_links = 0;
+    return;
+  }
+  unsigned long long n_fb = 0, n_band = 0;
+  for (;;) {
+  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
   __syncthreads();
   const long long tile = s_tile;
-  const int tid = threadIdx.x;
-  const int64_t row = tile * (int64_t)kLThreads + tid;
-  unsigned long long n_fb = 0, n_band = 0;
+  if (tile >= ntiles) break;
+  const int64_t local = tile * (int64_t)kLThreads + tid;
+  const int64_t row = (int64_t)row0 + local;
 #pragma unroll
   for (int i = 0; i < Q1; ++i) {
     s_q[i][tid] = INFINITY;
     s_f[i][tid] = 0xffffffffu;
   }
-  if (row < a.n_adj) {
+  if (local < nrows) {
     const uint32_t id = a.adj_cell[row];
     const uint32_t blk = id / NC, bit = id % NC;
+    const LevelGeom G = level_geom(geom_row(a.g0, a.table, a.gid, blk), a.level);
     double xc[3] = {0, 0, 0};
     float ohi[3] = {0, 0, 0}, olo[3] = {0, 0, 0};
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       const int g = 4 * a.blocks[(int64_t)blk * D + c] + (int)((bit >> (2 * c)) & 3u);
-      xc[c] = __dadd_rn(a.origin[c], __dmul_rn((double)g + 0.5, a.h));
+      xc[c] = __dadd_rn(G.origin[c], __dmul_rn((double)g + 0.5, G.h));
       ohi[c] = (float)xc[c];
       olo[c] = (float)(xc[c] - (double)ohi[c]);
     }
-    const float h32 = (float)a.h;
+    const float h32 = (float)G.h;
     const uint32_t e0 = a.adj_off[row], e1 = a.adj_off[row + 1];
     for (uint32_t e = e0; e < e1; ++e) {
       const uint32_t f = a.adj_ids[e];
@@ -144,7 +161,7 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
 #pragma unroll
         for (int di = 1; di <= Q1; ++di) {
           const int ci[2] = {c_d2q9[di][0], c_d2q9[di][1]};
-          const LinkHit r = link_fp64_2(V, xc, ci, a.h);
+          const LinkHit r = link_fp64_2(V, xc, ci, G.h);
           if (r.band) ++n_band;
           if (r.hit) {
             const float t = (float)r.t;
@@ -248,7 +265,7 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
           }
           if (unc) {
             const int ci[3] = {cx, cy, cz};
-            const LinkHit r = link_fp64_3(V, xc, ci, a.h);
+            const LinkHit r = link_fp64_3(V, xc, ci, G.h);
             ++n_fb;
             if (r.band) ++n_band;
             if (!r.hit) continue;
@@ -267,7 +284,6 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
 #pragma unroll
   for (int i = 0; i < Q1; ++i) hits += s_f[i][tid] != 0xffffffffu ? 1u : 0u;
   // block scan of per-cell link counts, then look-back for the global offset
-  const int lane = tid & 31, wid = tid >> 5;
   const uint32_t incl = warp_inclusive_scan<uint32_t>(hits);
   if (lane == 31) s_warp[wid] = incl;
   __syncthreads();
@@ -282,11 +298,13 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
     const uint64_t agg = s_warp[kLThreads / 32 - 1];
     const uint64_t pre = lookback_exclusive(state, tile, agg, a.err);
     s_prefix = pre;
-    const int64_t ntiles = (a.n_adj + kLThreads - 1) / kLThreads;
-    if (tile == ntiles - 1 || ntiles == 0) *a.n_links = pre + agg;
+    if (tile == ntiles - 1) {
+      *a.n_links = pre + agg;
+      if ((int64_t)(link0 + pre + agg) > a.link_cap) atomicOr(a.err, ERR_OVERFLOW);
+    }
   }
   __syncthreads();
-  uint64_t pos = s_prefix + wex + incl - hits;
+  uint64_t pos = link0 + s_prefix + wex + incl - hits;
 #pragma unroll
   for (int i = 0; i < Q1; ++i) {
     const uint32_t f = s_f[i][tid];
@@ -300,6 +318,8 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
       ++pos;
     }
   }
+  __syncthreads();
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     n_fb += __shfl_xor_sync(0xffffffffu, n_fb, o);
@@ -311,6 +331,25 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
   }
 }
 
+// close = true: write the CSR end marker of this level's adjacency rows,
+// adj_off[run[0] + cells] = run[1] + pairs (needed by the link kernel);
+// close = false: advance the running totals past this level.
+__global__ void k_advance(const uint64_t* level_tot, const uint64_t* n_links, uint64_t* run, uint32_t* adj_off,
+                          int64_t cap_cells, unsigned* err, bool close) {
+  const uint64_t t = *level_tot;
+  if (close) {
+    const uint64_t end = run[0] + (t >> 32);
+    if ((int64_t)end <= cap_cells)
+      adj_off[end] = (uint32_t)(run[1] + (t & 0xffffffffull));
+    else
+      atomicOr(err, ERR_OVERFLOW);
+    return;
+  }
+  run[0] += t >> 32;
+  run[1] += t & 0xffffffffull;
+  run[2] += n_links ? *n_links : 0ull;
+}
+
 }  // namespace
 
 size_t links_scratch_bytes(int64_t n_adj) {
@@ -318,16 +357,23 @@ size_t links_scratch_bytes(int64_t n_adj) {
   return 16 + (size_t)(tiles > 0 ? tiles : 1) * 8;
 }
 
-int launch_links(const LinkArgs& a, void* scratch, cudaStream_t st) {
-  cudaMemsetAsync(scratch, 0, links_scratch_bytes(a.n_adj), st);
-  const int64_t tiles = (a.n_adj + kLThreads - 1) / kLThreads;
+int launch_links(const LinkArgs& a, void* scratch, int num_sms, cudaStream_t st) {
+  cudaMemsetAsync(scratch, 0, links_scratch_bytes(a.cap_rows), st);
+  int64_t tiles = (a.cap_rows + kLThreads - 1) / kLThreads;
+  if (tiles < 1) tiles = 1;
+  if (tiles > (int64_t)num_sms * 12) tiles = (int64_t)num_sms * 12;
   unsigned* ticket = reinterpret_cast<unsigned*>(scratch);
   uint64_t* state = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 16);
-  const unsigned g = (unsigned)(tiles > 0 ? tiles : 1);
   if (a.dim == 3)
-    k_links<3><<<g, kLThreads, 0, st>>>(a, state, ticket);
+    k_links<3><<<(unsigned)tiles, kLThreads, 0, st>>>(a, state, ticket);
   else
-    k_links<2><<<g, kLThreads, 0, st>>>(a, state, ticket);
+    k_links<2><<<(unsigned)tiles, kLThreads, 0, st>>>(a, state, ticket);
+  return 1;
+}
+
+int launch_advance(const uint64_t* level_tot, const uint64_t* n_links, uint64_t* run, uint32_t* adj_off,
+                   int64_t cap_cells, unsigned* err, bool close, cudaStream_t st) {
+  k_advance<<<1, 1, 0, st>>>(level_tot, n_links, run, adj_off, cap_cells, err, close);
   return 1;
 }
 

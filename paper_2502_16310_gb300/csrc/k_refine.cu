@@ -25,7 +25,6 @@ namespace amr {
 
 namespace {
 
-constexpr int kWarps = 4;
 constexpr float kEpsK = 16.0f;  // safety factor over the forward error bound (see axis_bound)
 
 template <int D>
@@ -269,8 +268,8 @@ struct WarpCounters {
 };
 
 template <int D>
-__device__ __forceinline__ bool resolve_fp64(const RefineLevel& a, uint32_t face, const int* b, int cell_local,
-                                             WarpCounters& wc) {
+__device__ __forceinline__ bool resolve_fp64(const RefineLevel& a, const LevelGeom& G, uint32_t face, const int* b,
+                                             int cell_local, WarpCounters& wc) {
   float V[D * D];
 #pragma unroll
   for (int j = 0; j < D * D; ++j) V[j] = a.X[(int64_t)j * a.nf + face];
@@ -278,12 +277,12 @@ __device__ __forceinline__ bool resolve_fp64(const RefineLevel& a, uint32_t face
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const int li = (cell_local >> (2 * c)) & 3;
-    xc[c] = __dadd_rn(a.origin[c], __dmul_rn((double)(4 * b[c] + li) + 0.5, a.h));
+    xc[c] = __dadd_rn(G.origin[c], __dmul_rn((double)(4 * b[c] + li) + 0.5, G.h));
   }
-  const double r = __dadd_rn(0.5 * a.h, a.d);
+  const double r = __dadd_rn(0.5 * G.h, G.d);
   const double m = D == 3 ? margin_fp64_3(V, xc, r) : margin_fp64_2(V, xc, r);
   wc.fb++;
-  if (fabs(m) <= kBandRel * a.h) wc.band++;
+  if (fabs(m) <= kBandRel * G.h) wc.band++;
   return m <= 0.0;
 }
 
@@ -291,27 +290,27 @@ __device__ __forceinline__ bool resolve_fp64(const RefineLevel& a, uint32_t face
 // block-level cull, cell tests.  `on_hit(cellslot, face)` is called for every
 // intersecting (cell, face) pair; cellslot 0 = cell `lane`, 1 = cell `lane + 32`.
 template <int D, typename OnHit>
-__device__ __forceinline__ void walk_block(const RefineLevel& a, const int* b, Surv<D>* s_surv, int lane,
-                                           WarpCounters& wc, OnHit on_hit) {
+__device__ __forceinline__ void walk_block(const RefineLevel& a, const LevelGeom& G, const int* b, Surv<D>* s_surv,
+                                           int lane, WarpCounters& wc, OnHit on_hit) {
   using E = typename EntryT<D>::type;
-  const float hf = (float)a.h;
+  const float hf = (float)G.h;
   BlockFrame<D> F;
   int qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0};
-  const double slack = 1e-9 * a.h;
+  const double slack = 1e-9 * G.h;
   float O = 4.0f * hf;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    F.X64[c] = __dadd_rn(a.origin[c], __dmul_rn((double)(4 * b[c]), a.h));
+    F.X64[c] = __dadd_rn(G.origin[c], __dmul_rn((double)(4 * b[c]), G.h));
     F.Xb[c] = (float)F.X64[c];
     const double shift = __dsub_rn(F.X64[c], (double)F.Xb[c]);
-    F.cB[c] = (float)__dadd_rn(2.0 * a.h, shift);
+    F.cB[c] = (float)__dadd_rn(2.0 * G.h, shift);
     O = fmaxf(O, 4.0f * hf + 2.0f * (float)fabs(shift));
-    qlo[c] = bin_coord(F.X64[c] - a.d - slack, a.grid.origin[c], a.grid.scale[c], a.grid.B);
-    qhi[c] = bin_coord(F.X64[c] + 4.0 * a.h + a.d + slack, a.grid.origin[c], a.grid.scale[c], a.grid.B);
+    qlo[c] = bin_coord(F.X64[c] - G.d - slack, G.origin[c], G.scale[c], G.B);
+    qhi[c] = bin_coord(F.X64[c] + 4.0 * G.h + G.d + slack, G.origin[c], G.scale[c], G.B);
   }
   F.h = hf;
-  F.r = (float)(0.5 * a.h + a.d);
-  F.rb = (float)(2.0 * a.h + a.d);
+  F.r = (float)(0.5 * G.h + G.d);
+  F.rb = (float)(2.0 * G.h + G.d);
   F.O = O;
   // cell centres of this lane in the frame (FP64 -> FP32 once)
   float o0[3] = {0, 0, 0}, o1[3] = {0, 0, 0};
@@ -319,20 +318,20 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const int* b, S
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const int l0 = (lane >> (2 * c)) & 3;
-    const double xc0 = __dadd_rn(a.origin[c], __dmul_rn((double)(4 * b[c] + l0) + 0.5, a.h));
+    const double xc0 = __dadd_rn(G.origin[c], __dmul_rn((double)(4 * b[c] + l0) + 0.5, G.h));
     o0[c] = (float)__dsub_rn(xc0, (double)F.Xb[c]);
     if (D == 3) {
       const int l1 = ((lane + 32) >> (2 * c)) & 3;
-      const double xc1 = __dadd_rn(a.origin[c], __dmul_rn((double)(4 * b[c] + l1) + 0.5, a.h));
+      const double xc1 = __dadd_rn(G.origin[c], __dmul_rn((double)(4 * b[c] + l1) + 0.5, G.h));
       o1[c] = (float)__dsub_rn(xc1, (double)F.Xb[c]);
     }
   }
-  const int64_t B = a.grid.B;
+  const int64_t B = G.B;
   const E* payload = static_cast<const E*>(a.payload);
   for (int z = qlo[2]; z <= qhi[2]; ++z)
     for (int y = qlo[1]; y <= qhi[1]; ++y)
       for (int x = qlo[0]; x <= qhi[0]; ++x) {
-        const int64_t bin = x + B * (y + B * (int64_t)z);
+        const int64_t bin = G.bin_base + x + B * (y + B * (int64_t)z);
         const uint32_t s = a.offsets[bin], e = a.offsets[bin + 1];
         for (uint32_t base = s; base < e; base += 32) {
           const uint32_t j = base + lane;
@@ -365,11 +364,11 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const int* b, S
             const Surv<D>& S = s_surv[k];
             if (lane_cell) {
               int r0 = cell_test<D>(S, o0);
-              if (r0 == 2) r0 = resolve_fp64<D>(a, S.face, b, lane, wc) ? 1 : 0;
+              if (r0 == 2) r0 = resolve_fp64<D>(a, G, S.face, b, lane, wc) ? 1 : 0;
               if (r0) on_hit(0, S.face);
               if (D == 3) {
                 int r1 = cell_test<D>(S, o1);
-                if (r1 == 2) r1 = resolve_fp64<D>(a, S.face, b, lane + 32, wc) ? 1 : 0;
+                if (r1 == 2) r1 = resolve_fp64<D>(a, G, S.face, b, lane + 32, wc) ? 1 : 0;
                 if (r1) on_hit(1, S.face);
               }
             }
@@ -379,21 +378,37 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const int* b, S
       }
 }
 
+// Block count of a launch: from device memory when given (bounded by the
+// capacity; an overflow is reported), else the host count.
+__device__ __forceinline__ int64_t launch_count(int64_t n, const uint64_t* n_dev, unsigned* err) {
+  if (!n_dev) return n;
+  const uint64_t nd = *n_dev;
+  if ((int64_t)nd > n) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, ERR_OVERFLOW);
+    return n;
+  }
+  return (int64_t)nd;
+}
+
 template <int D>
-__global__ void __launch_bounds__(kWarps * 32) k_refine(RefineLevel a) {
-  __shared__ Surv<D> s_surv[kWarps][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+__global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  Surv<D>* s_surv = reinterpret_cast<Surv<D>*>(s_raw) + (threadIdx.x >> 5) * 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t n = launch_count(a.n_blocks, a.n_dev, a.err);
+  constexpr int NC = D == 3 ? 64 : 16;
   WarpCounters wc;
   for (;;) {
     unsigned blk = 0;
     if (lane == 0) blk = atomicAdd(a.work, 1u);
     blk = __shfl_sync(0xffffffffu, blk, 0);
-    if (blk >= a.n_blocks) break;
+    if (blk >= n) break;
     int b[3] = {0, 0, 0};
 #pragma unroll
     for (int c = 0; c < D; ++c) b[c] = a.blocks[(int64_t)blk * D + c];
+    const LevelGeom G = level_geom(geom_row(a.g0, a.table, a.gid, blk), a.level);
     uint32_t cnt0 = 0, cnt1 = 0;
-    walk_block<D>(a, b, s_surv[wid], lane, wc, [&](int slot, uint32_t) {
+    walk_block<D>(a, G, b, s_surv, lane, wc, [&](int slot, uint32_t) {
       if (slot == 0)
         ++cnt0;
       else
@@ -406,17 +421,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_refine(RefineLevel a) {
       a.mask[blk] = m;
       a.flag[blk] = m != 0 ? 1 : 0;
     }
-    if (a.cellcnt) {
-      if (cnt0 > 0xffffu || cnt1 > 0xffffu) atomicOr(a.err, ERR_OVERFLOW);
-      constexpr int NC = D == 3 ? 64 : 16;
-      if (lane < NC) a.cellcnt[(int64_t)blk * NC + lane] = (uint16_t)min(cnt0, 0xffffu);
-      if (D == 3) a.cellcnt[(int64_t)blk * NC + 32 + lane] = (uint16_t)min(cnt1, 0xffffu);
-    }
     if (a.blockcnt) {
-      uint32_t pairs = cnt0 + cnt1;
+      // per-cell counts only where the block's geometry ends at this level
+      const bool fin = G.finest;
+      if (fin && a.cellcnt) {
+        if (cnt0 > 0xffffu || cnt1 > 0xffffu) atomicOr(a.err, ERR_OVERFLOW);
+        if (lane < NC) a.cellcnt[(int64_t)blk * NC + lane] = (uint16_t)min(cnt0, 0xffffu);
+        if (D == 3) a.cellcnt[(int64_t)blk * NC + 32 + lane] = (uint16_t)min(cnt1, 0xffffu);
+      }
+      uint32_t pairs = fin ? cnt0 + cnt1 : 0u;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-      if (lane == 0) a.blockcnt[blk] = (uint64_t)pairs | ((uint64_t)__popcll(m) << 32);
+      if (lane == 0) a.blockcnt[blk] = fin ? ((uint64_t)pairs | ((uint64_t)__popcll(m) << 32)) : 0ull;
     }
   }
   // flush warp counters
@@ -434,73 +450,90 @@ __global__ void __launch_bounds__(kWarps * 32) k_refine(RefineLevel a) {
   }
 }
 
-// Emit the adjacent-face lists of the finest level: same walk as k_refine (so
-// the same decisions), each lane appends the faces of its cells at offsets
-// given by the block-level scan and the per-cell counts, then sorts each list.
+// Emit the adjacent-face lists of the blocks whose geometry ends at this
+// level: same walk as k_refine (so the same decisions), each lane appends the
+// faces of its cells at offsets given by the block-level scan and the per-cell
+// counts, then sorts each list.  Rows and pairs continue after the running
+// totals of earlier levels.
 template <int D>
-__global__ void __launch_bounds__(kWarps * 32) k_adjacency(EmitArgs a) {
-  __shared__ Surv<D> s_surv[kWarps][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+__global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  Surv<D>* s_surv = reinterpret_cast<Surv<D>*>(s_raw) + (threadIdx.x >> 5) * 32;
+  const int lane = threadIdx.x & 31;
   constexpr int NC = D == 3 ? 64 : 16;
+  const int64_t n = launch_count(a.lv.n_blocks, a.lv.n_dev, a.lv.err);
+  const uint64_t run_cells = a.run ? a.run[0] : 0ull, run_pairs = a.run ? a.run[1] : 0ull;
   WarpCounters wc;
   for (;;) {
     unsigned blk = 0;
     if (lane == 0) blk = atomicAdd(a.lv.work, 1u);
     blk = __shfl_sync(0xffffffffu, blk, 0);
-    if (blk >= a.lv.n_blocks) break;
+    if (blk >= n) break;
     const uint64_t mask = a.lv.mask[blk];
     if (mask == 0) continue;
+    const LevelGeom G = level_geom(geom_row(a.lv.g0, a.lv.table, a.lv.gid, blk), a.lv.level);
+    if (!G.finest) continue;
     int b[3] = {0, 0, 0};
 #pragma unroll
     for (int c = 0; c < D; ++c) b[c] = a.lv.blocks[(int64_t)blk * D + c];
     const uint64_t base = a.block_base[blk];
-    const uint32_t pair_base = (uint32_t)(base & 0xffffffffull);
-    const uint32_t cell_base = (uint32_t)(base >> 32);
+    const uint64_t pair_base = run_pairs + (base & 0xffffffffull);
+    const uint64_t cell_base = run_cells + (base >> 32);
     const uint32_t n0 = lane < NC ? a.lv.cellcnt[(int64_t)blk * NC + lane] : 0u;
-    const uint32_t n1 = D == 3 ? a.lv.cellcnt[(int64_t)blk * NC + 32 + lane] : 0u;
+    const uint32_t n1 = D == 3 ? (uint32_t)a.lv.cellcnt[(int64_t)blk * NC + 32 + lane] : 0u;
     // exclusive prefixes over cells in bit order (cells 0..31 then 32..63)
     const uint32_t i0 = warp_inclusive_scan<uint32_t>(n0);
     const uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31);
     const uint32_t i1 = warp_inclusive_scan<uint32_t>(n1);
-    const uint32_t off0 = pair_base + i0 - n0;
-    const uint32_t off1 = pair_base + tot0 + i1 - n1;
+    const uint64_t off0 = pair_base + i0 - n0;
+    const uint64_t off1 = pair_base + tot0 + i1 - n1;
     const uint32_t a0 = n0 > 0, a1 = n1 > 0;
     const uint32_t j0 = warp_inclusive_scan<uint32_t>(a0);
     const uint32_t atot0 = __shfl_sync(0xffffffffu, j0, 31);
     const uint32_t j1 = warp_inclusive_scan<uint32_t>(a1);
+    bool bad = (int64_t)(off1 + n1) > a.cap_pairs || (int64_t)(off0 + n0) > a.cap_pairs;
     if (a0) {
-      const uint32_t row = cell_base + j0 - 1;
-      a.adj_cell[row] = blk * (uint32_t)NC + lane;
-      a.adj_off[row] = off0;
+      const uint64_t row = cell_base + j0 - 1;
+      if ((int64_t)row < a.cap_cells) {
+        a.adj_cell[row] = blk * (uint32_t)NC + lane;
+        a.adj_off[row] = (uint32_t)off0;
+      } else {
+        bad = true;
+      }
     }
     if (a1) {
-      const uint32_t row = cell_base + atot0 + j1 - 1;
-      a.adj_cell[row] = blk * (uint32_t)NC + 32 + lane;
-      a.adj_off[row] = off1;
+      const uint64_t row = cell_base + atot0 + j1 - 1;
+      if ((int64_t)row < a.cap_cells) {
+        a.adj_cell[row] = blk * (uint32_t)NC + 32 + lane;
+        a.adj_off[row] = (uint32_t)off1;
+      } else {
+        bad = true;
+      }
     }
     uint32_t c0 = 0, c1 = 0;
-    unsigned bad = 0;
-    walk_block<D>(a.lv, b, s_surv[wid], lane, wc, [&](int slot, uint32_t f) {
+    const bool can0 = (int64_t)(off0 + n0) <= a.cap_pairs, can1 = (int64_t)(off1 + n1) <= a.cap_pairs;
+    walk_block<D>(a.lv, G, b, s_surv, lane, wc, [&](int slot, uint32_t f) {
       if (slot == 0) {
-        if (c0 < n0)
+        if (c0 < n0 && can0)
           a.adj_ids[off0 + c0] = f;
         else
-          bad = 1;
+          bad = true;
         ++c0;
       } else {
-        if (c1 < n1)
+        if (c1 < n1 && can1)
           a.adj_ids[off1 + c1] = f;
         else
-          bad = 1;
+          bad = true;
         ++c1;
       }
     });
     if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
+    if (!can0 || !can1) continue;
     // ascending face ids per cell (lists are short: insertion sort in place)
     for (int s = 0; s < 2; ++s) {
-      const uint32_t n = s == 0 ? n0 : n1;
+      const uint32_t cnt = s == 0 ? n0 : n1;
       uint32_t* L = a.adj_ids + (s == 0 ? off0 : off1);
-      for (uint32_t i = 1; i < n; ++i) {
+      for (uint32_t i = 1; i < cnt; ++i) {
         const uint32_t v = L[i];
         uint32_t k = i;
         while (k > 0 && L[k - 1] > v) {
@@ -513,98 +546,131 @@ __global__ void __launch_bounds__(kWarps * 32) k_adjacency(EmitArgs a) {
   }
 }
 
-// Children of the marked blocks, canonical order, single pass with look-back.
+// Children of the marked blocks whose geometry continues below this level,
+// canonical order, single pass with look-back over ticketed tiles.
 constexpr int kChThreads = 256;
 constexpr int kChItems = 4;
 
 template <int D>
-__global__ void __launch_bounds__(kChThreads) k_children(const int32_t* __restrict__ blocks,
-                                                         const uint64_t* __restrict__ mask, int64_t n,
-                                                         int32_t* __restrict__ cb, int32_t* __restrict__ cp,
-                                                         uint64_t* total, uint64_t* state, unsigned* ticket,
-                                                         unsigned* err) {
+__global__ void __launch_bounds__(kChThreads) k_children(ChildrenArgs a, uint64_t* state, unsigned* ticket) {
   __shared__ unsigned s_tile;
   __shared__ uint32_t s_warp[kChThreads / 32];
   __shared__ uint64_t s_prefix;
-  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
-  __syncthreads();
-  const long long tile = s_tile;
-  const int64_t base = tile * (int64_t)kChThreads * kChItems + (int64_t)threadIdx.x * kChItems;
-  uint32_t fl[kChItems];
-  uint32_t sum = 0;
-#pragma unroll
-  for (int i = 0; i < kChItems; ++i) {
-    const int64_t j = base + i;
-    fl[i] = (j < n && mask[j] != 0) ? 1u : 0u;
-    sum += fl[i];
+  const int64_t n = launch_count(a.n, a.n_dev, a.err);
+  const int64_t ntiles = (n + (int64_t)kChThreads * kChItems - 1) / ((int64_t)kChThreads * kChItems);
+  constexpr int NCH = D == 3 ? 8 : 4;
+  if (ntiles == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.total = 0;
+    return;
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t incl = warp_inclusive_scan<uint32_t>(sum);
-  if (lane == 31) s_warp[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t w = lane < kChThreads / 32 ? s_warp[lane] : 0u;
-    w = warp_inclusive_scan<uint32_t>(w);
-    if (lane < kChThreads / 32) s_warp[lane] = w;
-  }
-  __syncthreads();
-  const uint32_t wex = wid > 0 ? s_warp[wid - 1] : 0u;
-  if (threadIdx.x == 0) {
-    const uint64_t agg = s_warp[kChThreads / 32 - 1];
-    const uint64_t pre = lookback_exclusive(state, tile, agg, err);
-    s_prefix = pre;
-    const int64_t ntiles = (n + (int64_t)kChThreads * kChItems - 1) / ((int64_t)kChThreads * kChItems);
-    if (tile == ntiles - 1 || ntiles == 0) *total = (pre + agg) * (D == 3 ? 8 : 4);
-  }
-  __syncthreads();
-  uint64_t k = s_prefix + wex + incl - sum;
-  constexpr int NCH = D == 3 ? 8 : 4;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= ntiles) break;
+    const int64_t base = tile * (int64_t)kChThreads * kChItems + (int64_t)threadIdx.x * kChItems;
+    uint32_t fl[kChItems];
+    uint32_t sum = 0;
 #pragma unroll
-  for (int i = 0; i < kChItems; ++i) {
-    if (fl[i]) {
-      const int64_t p = base + i;
-      int bc[3] = {0, 0, 0};
-#pragma unroll
-      for (int c = 0; c < D; ++c) bc[c] = blocks[p * D + c];
-#pragma unroll
-      for (int s = 0; s < NCH; ++s) {
-        const int64_t o = (int64_t)k * NCH + s;
-        cb[o * D + 0] = 2 * bc[0] + (s & 1);
-        cb[o * D + 1] = 2 * bc[1] + ((s >> 1) & 1);
-        if (D == 3) cb[o * D + 2] = 2 * bc[2] + ((s >> 2) & 1);
-        cp[o] = (int32_t)p;
+    for (int i = 0; i < kChItems; ++i) {
+      const int64_t j = base + i;
+      bool emit = false;
+      if (j < n && a.mask[j] != 0) {
+        const GeomParams P = geom_row(a.g0, a.table, a.gid, j);
+        emit = a.level < P.n_levels - 1;
       }
-      ++k;
+      fl[i] = emit ? 1u : 0u;
+      sum += fl[i];
     }
+    const uint32_t incl = warp_inclusive_scan<uint32_t>(sum);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t w = lane < kChThreads / 32 ? s_warp[lane] : 0u;
+      w = warp_inclusive_scan<uint32_t>(w);
+      if (lane < kChThreads / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t wex = wid > 0 ? s_warp[wid - 1] : 0u;
+    if (threadIdx.x == 0) {
+      const uint64_t agg = s_warp[kChThreads / 32 - 1];
+      const uint64_t pre = lookback_exclusive(state, tile, agg, a.err);
+      s_prefix = pre;
+      if (tile == ntiles - 1) {
+        const uint64_t tot = (pre + agg) * NCH;
+        *a.total = tot;
+        if ((int64_t)tot > a.cap_out) atomicOr(a.err, ERR_OVERFLOW);
+      }
+    }
+    __syncthreads();
+    uint64_t k = s_prefix + wex + incl - sum;
+#pragma unroll
+    for (int i = 0; i < kChItems; ++i) {
+      if (fl[i]) {
+        const int64_t p = base + i;
+        int bc[3] = {0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < D; ++c) bc[c] = a.blocks[p * D + c];
+        const uint32_t g = a.gid ? a.gid[p] : 0u;
+#pragma unroll
+        for (int s = 0; s < NCH; ++s) {
+          const int64_t o = (int64_t)k * NCH + s;
+          if (o >= a.cap_out) break;
+          a.child_blocks[o * D + 0] = 2 * bc[0] + (s & 1);
+          a.child_blocks[o * D + 1] = 2 * bc[1] + ((s >> 1) & 1);
+          if (D == 3) a.child_blocks[o * D + 2] = 2 * bc[2] + ((s >> 2) & 1);
+          a.child_parent[o] = (int32_t)p;
+          if (a.child_gid) a.child_gid[o] = g;
+        }
+        ++k;
+      }
+    }
+    __syncthreads();
   }
 }
 
-int refine_grid(int num_sms, int64_t n) {
-  int64_t need = (n + kWarps - 1) / kWarps;
-  int64_t cap = (int64_t)num_sms * 8;
+// Warps per SM kept resident: 32 (CTAs of `warps` warps).
+int grid_warps(int num_sms, int64_t n, int warps, bool persistent) {
+  const int64_t cap = (int64_t)num_sms * (32 / warps > 0 ? 32 / warps : 1);
+  if (persistent) return (int)cap;
+  int64_t need = (n + warps - 1) / warps;
   if (need < 1) need = 1;
   return (int)(need < cap ? need : cap);
+}
+
+template <typename K>
+void allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace
 
 int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st) {
-  if (a.n_blocks <= 0) return 0;
-  const int g = refine_grid(num_sms, a.n_blocks);
-  if (a.dim == 3)
-    k_refine<3><<<g, kWarps * 32, 0, st>>>(a);
-  else
-    k_refine<2><<<g, kWarps * 32, 0, st>>>(a);
+  if (!a.n_dev && a.n_blocks <= 0) return 0;
+  const int warps = a.warps > 0 ? a.warps : 4;
+  const int g = grid_warps(num_sms, a.n_blocks, warps, a.n_dev != nullptr);
+  const size_t smem = (size_t)warps * 32 * (a.dim == 3 ? sizeof(Surv<3>) : sizeof(Surv<2>));
+  if (a.dim == 3) {
+    allow_smem(k_refine<3>, smem);
+    k_refine<3><<<g, warps * 32, smem, st>>>(a);
+  } else {
+    k_refine<2><<<g, warps * 32, smem, st>>>(a);
+  }
   return 1;
 }
 
 int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st) {
-  if (a.lv.n_blocks <= 0) return 0;
-  const int g = refine_grid(num_sms, a.lv.n_blocks);
-  if (a.lv.dim == 3)
-    k_adjacency<3><<<g, kWarps * 32, 0, st>>>(a);
-  else
-    k_adjacency<2><<<g, kWarps * 32, 0, st>>>(a);
+  if (!a.lv.n_dev && a.lv.n_blocks <= 0) return 0;
+  const int warps = a.lv.warps > 0 ? a.lv.warps : 4;
+  const int g = grid_warps(num_sms, a.lv.n_blocks, warps, a.lv.n_dev != nullptr);
+  const size_t smem = (size_t)warps * 32 * (a.lv.dim == 3 ? sizeof(Surv<3>) : sizeof(Surv<2>));
+  if (a.lv.dim == 3) {
+    allow_smem(k_adjacency<3>, smem);
+    k_adjacency<3><<<g, warps * 32, smem, st>>>(a);
+  } else {
+    k_adjacency<2><<<g, warps * 32, smem, st>>>(a);
+  }
   return 1;
 }
 
@@ -613,17 +679,17 @@ size_t children_scratch_bytes(int64_t n) {
   return 16 + (size_t)(tiles > 0 ? tiles : 1) * 8;
 }
 
-int launch_children(int dim, const int32_t* blocks, const uint64_t* mask, int64_t n, int32_t* cb, int32_t* cp,
-                     uint64_t* total, void* scratch, unsigned* err, cudaStream_t st) {
-  cudaMemsetAsync(scratch, 0, children_scratch_bytes(n), st);
-  const int64_t tiles = (n + (int64_t)kChThreads * kChItems - 1) / ((int64_t)kChThreads * kChItems);
+int launch_children(const ChildrenArgs& a, void* scratch, int num_sms, cudaStream_t st) {
+  cudaMemsetAsync(scratch, 0, children_scratch_bytes(a.n), st);
+  int64_t tiles = (a.n + (int64_t)kChThreads * kChItems - 1) / ((int64_t)kChThreads * kChItems);
+  if (tiles < 1) tiles = 1;
+  if (a.n_dev && tiles > (int64_t)num_sms * 4) tiles = (int64_t)num_sms * 4;
   unsigned* ticket = reinterpret_cast<unsigned*>(scratch);
   uint64_t* state = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 16);
-  const unsigned g = (unsigned)(tiles > 0 ? tiles : 1);
-  if (dim == 3)
-    k_children<3><<<g, kChThreads, 0, st>>>(blocks, mask, n, cb, cp, total, state, ticket, err);
+  if (a.dim == 3)
+    k_children<3><<<(unsigned)tiles, kChThreads, 0, st>>>(a, state, ticket);
   else
-    k_children<2><<<g, kChThreads, 0, st>>>(blocks, mask, n, cb, cp, total, state, ticket, err);
+    k_children<2><<<(unsigned)tiles, kChThreads, 0, st>>>(a, state, ticket);
   return 1;
 }
 

@@ -138,7 +138,7 @@ def compare_adjacency(geo, dim, level, fin_blocks, fin_mask, adj_cell, adj_off, 
 
 
 def compare_links(geo, dim, level, lattice, fin_blocks, adj_cell, link_cell, link_dir, link_q, link_face,
-                  sample=None, rng=None):
+                  sample=None, rng=None, d_abs=0.0, d_rel=1.0):
     nc = 64 if dim == 3 else 16
     Q1 = 18 if lattice == 19 else 8
     n_adj = adj_cell.shape[0]
@@ -158,7 +158,15 @@ def compare_links(geo, dim, level, lattice, fin_blocks, adj_cell, link_cell, lin
     cells = cells_of(dim, fin_blocks, (adj_cell[rows] // nc).astype(np.int64), (adj_cell[rows] % nc).astype(np.int64))
     q_o, f_o, b_o = geo.cell_links(level, lattice, cells)
     gq, gf = dense_q[rows], dense_f[rows]
-    firm = ~b_o
+    # a link inherits the band of its face's adjacency decision: links are formed against the
+    # cell's adjacency list, and a face in the adjacency band may be listed or not
+    a_off, a_ids, a_band = geo.cell_faces(level, cells, d_abs, d_rel)
+    inherit = np.zeros_like(b_o)
+    for i in range(cells.shape[0]):
+        bset = set(a_ids[a_off[i]:a_off[i + 1]][a_band[a_off[i]:a_off[i + 1]]].tolist())
+        if bset:
+            inherit[i] = np.isin(f_o[i], list(bset)) | np.isin(gf[i], list(bset))
+    firm = ~(b_o | inherit)
     hit_o = np.isfinite(q_o)
     hit_g = np.isfinite(gq)
     bad = firm & (hit_o != hit_g)

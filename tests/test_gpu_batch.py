@@ -1,0 +1,170 @@
+"""Graph mode, batched mode and the autotuner against the eager single-geometry path.
+
+Graph replays and batched runs execute the same per-block arithmetic as the
+eager single-geometry path, so every output must be bitwise identical (after
+subtracting the batch bases from batch-global indices).
+"""
+import numpy as np
+import pytest
+
+from synth import Workload, small_workload
+from synth import geometry as G
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+def _single(w, use_graph=False, repeats=1, B=None, warps=0):
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+
+    g = AmrGeom(w.dim, (w.root,) * w.dim)
+    v = torch.from_numpy(w.verts).cuda()
+    ix = torch.from_numpy(w.idx).cuda()
+    outs = []
+    for _ in range(repeats):
+        g.load(v, ix)
+        g.bin(w.bins if B is None else B)
+        res = g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=use_graph,
+                       warps_per_cta=warps)
+        outs.append(_host(res))
+    launches = g.launch_count()
+    g.close()
+    return outs, launches
+
+
+def _host(res):
+    import torch
+
+    torch.cuda.synchronize()
+    out = {"levels": [{k: (None if lv[k] is None else lv[k].cpu().numpy().copy()) for k in ("blocks", "mask", "flag",
+                                                                                             "parent")}
+                      for lv in res["levels"]]}
+    for k in ("adj_cell", "adj_off", "adj_ids", "link_cell", "link_dir", "link_q", "link_face"):
+        if k in res:
+            a = res[k].cpu().numpy().copy()
+            out[k] = a.astype(np.int64) if a.dtype == np.int32 else a
+    return out
+
+
+def _same(a, b, what=""):
+    assert len(a["levels"]) == len(b["levels"]), what
+    for L, (x, y) in enumerate(zip(a["levels"], b["levels"])):
+        for k in ("blocks", "mask", "flag", "parent"):
+            if x[k] is None:
+                assert y[k] is None or y[k].size == 0
+                continue
+            assert np.array_equal(x[k].astype(np.int64), y[k].astype(np.int64)), f"{what} level {L} {k}"
+    for k in ("adj_cell", "adj_off", "adj_ids", "link_cell", "link_dir", "link_face"):
+        assert np.array_equal(np.asarray(a[k]).astype(np.int64), np.asarray(b[k]).astype(np.int64)), f"{what} {k}"
+    assert np.array_equal(a["link_q"].view(np.uint32), b["link_q"].view(np.uint32)), f"{what} link_q"
+
+
+@pytest.mark.parametrize("kind", ["circle", "sphere3", "bumpy3"])
+def test_graph_equals_eager(kind):
+    w = small_workload(kind)
+    (eager,), _ = _single(w)
+    outs, _ = _single(w, use_graph=True, repeats=4)
+    for i, o in enumerate(outs):
+        _same(eager, o, f"graph call {i}")
+
+
+def test_graph_overflow_falls_back():
+    """A geometry that needs more blocks than the captured graph's capacities re-runs eagerly, correctly."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+
+    small = small_workload("sphere3")
+    v2, f2 = G.jittered_sphere(3, radius=0.33, centre=(0.5, 0.5, 0.5), sigma=1e-4, seed=12)
+    big = Workload("big", 3, v2, f2, root=small.root, n_levels=small.n_levels, bins=small.bins, lattice=19)
+    (want,), _ = _single(big)
+    g = AmrGeom(3, (small.root,) * 3)
+    for w in (small, small, big, big):
+        g.load(torch.from_numpy(w.verts).cuda(), torch.from_numpy(w.idx).cuda())
+        g.bin(w.bins)
+        res = g.refine(w.n_levels, w.d_abs, w.d_rel, 19, True, True, use_graph=True)
+        got = _host(res)
+    _same(want, got, "after fallback")
+    g.close()
+
+
+def _batch_set():
+    ws = [small_workload("sphere3"), small_workload("bumpy3")]
+    v, f = G.jittered_sphere(2, radius=0.3, centre=(0.48, 0.52, 0.5), sigma=1e-3, seed=21)
+    ws.append(Workload("s2", 3, v, f, root=5, n_levels=2, bins=10, lattice=19))
+    u, f = G.geodesic_sphere_unit(5)
+    v, f = G.perturbed_surface(u, f, seed=22, lmax=4)
+    ws.append(Workload("geo5", 3, v, f, root=7, n_levels=4, bins=20, lattice=19))
+    ws.append(Workload("empty", 3, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), root=3, n_levels=2,
+                       bins=4, lattice=19))
+    return ws
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_matches_single(use_graph):
+    import torch
+
+    from paper_2502_16310_gb300 import AmrBatch
+
+    ws = _batch_set()
+    singles = [_single(w)[0][0] for w in ws]
+    b = AmrBatch(3)
+    for w in ws:
+        b.add(torch.from_numpy(w.verts).cuda(), torch.from_numpy(w.idx).cuda(), w.root, w.n_levels, w.d_abs, w.d_rel,
+              w.bins)
+    for rep in range(3 if use_graph else 1):
+        b.run(19, True, True, use_graph=use_graph)
+        for i, w in enumerate(ws):
+            got = _host(b.view(i))
+            _same(singles[i], got, f"geometry {i} rep {rep}")
+    b.close()
+
+
+def test_batch_adjoint_matches_single():
+    import torch
+
+    from paper_2502_16310_gb300 import AmrBatch, AmrGeom
+
+    ws = _batch_set()[:4]
+    b = AmrBatch(3)
+    for w in ws:
+        b.add(torch.from_numpy(w.verts).cuda(), torch.from_numpy(w.idx).cuda(), w.root, w.n_levels, w.d_abs, w.d_rel,
+              w.bins)
+    r = b.run(19, True, True)
+    nl = int(r.n_links)
+    wts = torch.randn(nl, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    gb = b.q_backward(wts).cpu().numpy()
+    vbase = 0
+    for i, w in enumerate(ws):
+        vw = b.view(i)
+        lb = vw["bases"]["link"]
+        n_i = vw["link_q"].shape[0]
+        g = AmrGeom(3, (w.root,) * 3)
+        g.load(torch.from_numpy(w.verts).cuda(), torch.from_numpy(w.idx).cuda())
+        g.bin(w.bins)
+        g.refine(w.n_levels, w.d_abs, w.d_rel, 19, True, True)
+        gs = g.q_backward(wts[lb:lb + n_i]).cpu().numpy()
+        g.close()
+        assert np.array_equal(gs.view(np.uint32), gb[vbase:vbase + w.verts.shape[0]].view(np.uint32)), i
+        vbase += w.verts.shape[0]
+    b.close()
+
+
+def test_autotune_picks_a_candidate():
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+
+    w = small_workload("sphere3")
+    g = AmrGeom(3, (w.root,) * 3)
+    g.load(torch.from_numpy(w.verts).cuda(), torch.from_numpy(w.idx).cuda())
+    B, warps, ms = g.autotune(w.n_levels, w.d_abs, w.d_rel, 19, True, True, b_candidates=[8, 16, 32],
+                              w_candidates=[2, 4, 8])
+    assert B in (8, 16, 32) and warps in (2, 4, 8) and ms > 0
+    g.bin(B)
+    res = _host(g.refine(w.n_levels, w.d_abs, w.d_rel, 19, True, True, warps_per_cta=warps))
+    g.close()
+    (ref,), _ = _single(w)
+    _same(ref, res, "tuned")

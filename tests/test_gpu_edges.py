@@ -24,7 +24,7 @@ def _oracle_check(w, out, B=None):
                         out["adj_ids"], d_abs=w.d_abs, d_rel=w.d_rel)
     if "link_q" in out:
         U.compare_links(geo, w.dim, len(lv) - 1, w.lattice, lv[-1]["blocks"], out["adj_cell"], out["link_cell"],
-                        out["link_dir"], out["link_q"], out["link_face"])
+                        out["link_dir"], out["link_q"], out["link_face"], d_abs=w.d_abs, d_rel=w.d_rel)
 
 
 def test_empty_geometry():

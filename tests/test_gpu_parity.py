@@ -42,7 +42,8 @@ def _full_check(w, out, geo, sample=None, links=True, B=None):
                         sample=sample, d_abs=w.d_abs, d_rel=w.d_rel, rng=rng)
     if links:
         U.compare_links(geo, w.dim, Lf, w.lattice, fin["blocks"], out["adj_cell"], out["link_cell"],
-                        out["link_dir"], out["link_q"], out["link_face"], sample=sample, rng=rng)
+                        out["link_dir"], out["link_q"], out["link_face"], sample=sample, rng=rng, d_abs=w.d_abs,
+                        d_rel=w.d_rel)
     return stats
 
 
