@@ -52,6 +52,9 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    p.add_argument("--no-graph", action="store_true", help="time the eager path instead of graph replays")
+    p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
+    p.add_argument("--batch-geoms", type=int, default=48)
     return p.parse_args(argv)
 
 
@@ -157,10 +160,12 @@ def run_ours(args, rank, world, local):
     g = AmrGeom(w.dim, (w.root,) * w.dim)
     stream = g.stream
 
+    use_graph = not args.no_graph
+
     def step():
         g.load(verts, idx)
         g.bin(w.bins)
-        return g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True)
+        return g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=use_graph)
 
     for _ in range(max(args.warmup, 1)):
         res = step()
@@ -170,6 +175,7 @@ def run_ours(args, rank, world, local):
     n_adj = int(res["adj_cell"].shape[0])
     n_pairs = int(res["adj_ids"].shape[0])
     n_cand, n_surv = res["n_candidates"], res["n_survivors"]
+    n_fb, n_band = res["n_fallback"], res["n_band"]
     blocks = [int(lv["blocks"].shape[0]) for lv in res["levels"]]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -210,7 +216,9 @@ def run_ours(args, rank, world, local):
     n_t = max(3, min(10, args.steps))
     for k in range(n_t):
         flush.fill_(k & 0xff)
-        step()
+        g.load(verts, idx)
+        g.bin(w.bins)
+        g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=False)
     tk = g.timings()
     g.timing(False)
     kern = {name: {"ms_per_step": v[0] / n_t, "launches_per_step": v[1] / n_t} for name, v in tk.items()}
@@ -226,7 +234,9 @@ def run_ours(args, rank, world, local):
         "config": {"workload": f"{args.workload}: {w.description}", "faces": w.n_faces, "levels": w.n_levels,
                    "bins_per_axis": w.bins, "blocks_per_level": blocks, "near_wall_cells_per_step": cells,
                    "adjacent_finest_cells": n_adj, "adjacent_pairs": n_pairs, "links": n_links,
-                   "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)"},
+                   "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)",
+                   "level_loop": "CUDA graph replay" if use_graph else "eager",
+                   "fp64_fallbacks_per_step": n_fb, "band_cases_per_step": n_band},
         "faces_binned_per_s": w.n_faces / (t_bin * 1e-3) if t_bin > 0 else None,
         "cell_face_tests_per_s": (n_surv * (64 if w.dim == 3 else 16)) / (t_refine * 1e-3) if t_refine > 0 else None,
         "kernels_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in kern.items()},
@@ -238,7 +248,128 @@ def run_ours(args, rank, world, local):
     if not args.no_e2e:
         line["e2e"] = run_e2e(g, w, args, dev)
     g.close()
+    if not args.no_extras and world == 1:
+        line["adjoint"] = run_adjoint(args, dev, flush)
+        line["batched"] = run_batched(args, dev, flush)
     return line
+
+
+def _timed_steps(fn, n, flush, stream):
+    """CUDA-event time (ms) of n calls of fn, L2 flushed before each (outside the events)."""
+    import torch
+
+    total = 0.0
+    for k in range(n):
+        flush.fill_(k & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+    return total / n
+
+
+def run_adjoint(args, dev, flush):
+    """Adjoint vs forward on the workload with q adjoint (c3): forward = load + bin + refine with links;
+    backward = amr_q_backward for random upstream weights (includes regrouping the links by face)."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+    from synth import workload
+
+    w = workload("c3")
+    g = AmrGeom(3, (w.root,) * 3)
+    v = torch.from_numpy(w.verts).to(dev)
+    ix = torch.from_numpy(w.idx).to(dev)
+    st = g.stream
+
+    def fwd():
+        g.load(v, ix)
+        g.bin(w.bins)
+        return g.refine(w.n_levels, w.d_abs, w.d_rel, 19, True, True, use_graph=True)
+
+    for _ in range(3):
+        res = fwd()
+    nl = int(res["link_q"].shape[0])
+    wts = torch.randn(nl, device=dev, generator=torch.Generator(dev).manual_seed(0))
+
+    def both():
+        fwd()
+        g.q_backward(wts)
+
+    t_f = _timed_steps(fwd, 10, flush, st)
+    t_fb = _timed_steps(both, 10, flush, st)
+    g.close()
+    t_b = t_fb - t_f
+    return {"workload": "c3: " + w.description, "links": nl, "forward_ms": t_f, "backward_ms": t_b,
+            "adjoint_over_forward": t_b / t_f}
+
+
+def run_batched(args, dev, flush):
+    """The 48-geometry workload: one batched launch per level (graph replay) vs one geometry at a time
+    (each with its own context and graph), bin densities and warps per block from the autotuner."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrBatch, AmrGeom
+    from synth import batched_workloads
+
+    t0 = time.perf_counter()
+    ws = batched_workloads(args.batch_geoms)
+    gen_s = time.perf_counter() - t0
+    st = torch.cuda.current_stream()
+    data = [(torch.from_numpy(w.verts).to(dev), torch.from_numpy(w.idx).to(dev)) for w in ws]
+    # autotune the bin density of every geometry (one-time setup, not timed)
+    t0 = time.perf_counter()
+    ctxs = []
+    for w, (v, ix) in zip(ws, data):
+        g = AmrGeom(3, (w.root,) * 3)
+        g.load(v, ix)
+        B, warps, _ = g.autotune(w.n_levels, w.d_abs, w.d_rel, 19, True, True,
+                                 b_candidates=[8, 16, 24, 32, 48, 64, 96, 128], w_candidates=[4])
+        w.bins = B
+        ctxs.append(g)
+    tune_s = time.perf_counter() - t0
+
+    def single():
+        cells = 0
+        for w, (v, ix), g in zip(ws, data, ctxs):
+            g.load(v, ix)
+            g.bin(w.bins)
+            g.refine(w.n_levels, w.d_abs, w.d_rel, 19, True, True, use_graph=True)
+        return cells
+
+    b = AmrBatch(3)
+    for w, (v, ix) in zip(ws, data):
+        b.add(v, ix, w.root, w.n_levels, w.d_abs, w.d_rel, w.bins)
+
+    def batched():
+        b.run(19, True, True, use_graph=True)
+
+    for _ in range(3):
+        single()
+        batched()
+    # near-wall cells of the whole set (from the batch's masks)
+    r = b.result
+    cells = 0
+    lut = torch.tensor([bin(i).count("1") for i in range(256)], dtype=torch.int64, device=dev)
+    from paper_2502_16310_gb300.binding import _view
+    for L in range(r.n_levels):
+        n = int(r.n_blocks[L])
+        if n:
+            m = _view(r.cell_mask[L], (n,), torch.int64)
+            cells += int(lut[m.view(torch.uint8).long()].sum().item())
+    t_single = _timed_steps(single, 5, flush, st)
+    t_batch = _timed_steps(batched, 5, flush, st)
+    launches_batch = b.launch_count()
+    for g in ctxs:
+        g.close()
+    b.close()
+    return {"workload": f"{len(ws)} SH-perturbed geodesic spheres, {sum(w.n_faces for w in ws)} triangles, "
+                        f"roots 16^3..48^3, 2..6 levels, bin density tuned per geometry",
+            "near_wall_cells": cells, "single_ms": t_single, "batched_ms": t_batch,
+            "single_cells_per_s": cells / (t_single * 1e-3), "batched_cells_per_s": cells / (t_batch * 1e-3),
+            "batched_over_single": t_single / t_batch, "generate_s": gen_s, "tune_s": tune_s}
 
 
 def roofline(name, k, w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks):

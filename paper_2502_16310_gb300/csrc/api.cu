@@ -317,6 +317,19 @@ void drop_graph(amr_ctx* ctx) {
 
 }  // namespace
 
+// FP32 forms of a row's FP64 fields (hi + lo pairs for h0 and the origin).
+void amr_finish_row(GeomParams& g) {
+  g.h0_hi = (float)g.h0;
+  g.h0_lo = (float)(g.h0 - (double)g.h0_hi);
+  for (int a = 0; a < 3; ++a) {
+    g.org_hi[a] = (float)g.origin[a];
+    g.org_lo[a] = (float)(g.origin[a] - (double)g.org_hi[a]);
+    g.scale32[a] = (float)g.bin_scale[a];
+  }
+  g.d_abs32 = (float)g.d_abs;
+  g.d_rel32 = (float)g.d_rel;
+}
+
 // Table row of a geometry: domain, bins, levels and near-wall distance.
 GeomParams amr_make_row(const amr_domain& d, int B, int n_levels, double d_abs, double d_rel) {
   GeomParams g{};
@@ -331,6 +344,7 @@ GeomParams amr_make_row(const amr_domain& d, int B, int n_levels, double d_abs, 
   g.n_levels = n_levels;
   g.d_abs = d_abs;
   g.d_rel = d_rel;
+  amr_finish_row(g);
   return g;
 }
 
@@ -449,6 +463,7 @@ amr_status amr_bin_all(amr_ctx* ctx) {
   TRY(ensure(ctx, ctx->payload, esz * (size_t)tot));
   ScatterArgs sa{};
   sa.f = fa;
+  sa.nrm = static_cast<const float*>(ctx->nrm.p);
   sa.offsets = offsets;
   sa.ids = static_cast<uint32_t*>(ctx->ids.p);
   sa.payload = ctx->payload.p;
@@ -990,6 +1005,7 @@ amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_
   g.n_levels = NL;
   g.d_abs = prm->d_abs;
   g.d_rel = prm->d_rel;
+  amr_finish_row(g);
   amr_refine_result r{};
   TRY(amr_run_refine(ctx, prm, &r));
   ctx->refined = true;

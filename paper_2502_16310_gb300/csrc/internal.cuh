@@ -51,7 +51,50 @@ struct GeomParams {
   int64_t bin_base;
   int64_t root_base;   // first level-0 block of this geometry in the concatenated list
   int64_t face_base;   // first face of this geometry in the concatenated face arrays
+  // FP32 forms for the hot loops: h0 and origin as unevaluated pairs hi + lo,
+  // the bin scale and the distance coefficients rounded once
+  float h0_hi, h0_lo;
+  float org_hi[3], org_lo[3];
+  float scale32[3];
+  float d_abs32, d_rel32;
 };
+
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void df_two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// origin + k * h as an unevaluated FP32 pair hi + lo (k an integer below 2^24,
+// h = h_hi + h_lo): relative error about 2^-46, so the hi part is the
+// position rounded to FP32 and lo its rounding error.
+__device__ __forceinline__ void df_position(float org_hi, float org_lo, float k, float h_hi, float h_lo, float& hi,
+                                            float& lo) {
+  float p, e, s, t;
+  df_two_prod(k, h_hi, p, e);
+  df_two_sum(org_hi, p, s, t);
+  const float rest = t + e + fmaf(k, h_lo, org_lo);
+  df_two_sum(s, rest, hi, lo);
+}
+
+// Level-L quantities of a geometry in FP32: h_L = 2^-L h0 (exact scaling of
+// both parts) and d_L = d_abs + d_rel h_L (a few ulps).
+struct FastGeom {
+  float h_hi, h_lo, d;
+};
+
+__device__ __forceinline__ FastGeom fast_geom(const GeomParams& P, int level) {
+  FastGeom g;
+  g.h_hi = ldexpf(P.h0_hi, -level);
+  g.h_lo = ldexpf(P.h0_lo, -level);
+  g.d = fmaf(P.d_rel32, g.h_hi, P.d_abs32);
+  return g;
+}
 
 // Geometry of one block on one level, derived from its table row.
 struct LevelGeom {
@@ -92,14 +135,16 @@ struct BinGrid {
   double scale[3];
 };
 
-// One bin entry with its face's coordinates, so that a bin's faces are one
-// contiguous run of memory (bulk-copyable).  `id` holds the face id in the low
-// 29 bits and, in bits 29..31, whether this bin is the first of the face's bin
+// One bin entry with its face's coordinates (and, in 3D, the FP32 face
+// normal), so that a bin's faces are one contiguous run of memory that TMA
+// bulk copies stage in shared memory.  `id` holds the face id in the low 29
+// bits and, in bits 29..31, whether this bin is the first of the face's bin
 // range along x / y / z (used to visit each face once per query box).
 struct __align__(16) Entry3 {
   float v[9];
+  float n[3];
   uint32_t id;
-  uint32_t pad[2];
+  uint32_t pad[3];
 };
 struct __align__(16) Entry2 {
   float v[4];
@@ -166,6 +211,63 @@ __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t* state, long lon
   return prefix;
 }
 
+// --- shared-memory barriers and TMA bulk copies (inline PTX, sm_90+) -------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+// completing on `bar` with its byte count.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for a barrier phase.  On timeout: flag ERR_TIMEOUT, then wait
+// once more (bounded) so that a copy still in flight lands before the caller
+// moves on; returns false after a timeout (the caller's results are invalid
+// and the host reports AMR_ETIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* err) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 32) __nanosleep(32);
+  }
+  atomicOr(err, ERR_TIMEOUT);
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) break;
+    __nanosleep(64);
+  }
+  return false;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_inclusive_scan(T v) {
 #pragma unroll
@@ -205,6 +307,7 @@ int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint
                      cudaStream_t st);
 struct ScatterArgs {
   FaceBinArgs f;
+  const float* nrm;   // 3D face normals (hi parts are copied into the entries)
   const uint32_t* offsets;
   uint32_t* ids;
   void* payload;

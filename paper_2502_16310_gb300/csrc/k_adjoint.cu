@@ -138,9 +138,9 @@ __global__ void k_face_grad(AdjointArgs a) {
       continue;
     }
     // links of this face live on the finest level of its geometry
-    const GeomParams P = geom_row(a.g0, a.table, a.face_gid, f);
+    const GeomParams& P = a.table ? a.table[a.face_gid ? a.face_gid[f] : 0u] : a.g0;
     const int Lf = P.n_levels - 1;
-    const double hL = scalbn(P.h0, -Lf);
+    const FastGeom fg = fast_geom(P, Lf);
     const int32_t* blocks = a.level_blocks[Lf];
     for (uint32_t s = b0; s < b1; ++s) {
       const uint32_t l = a.face_links[s];
@@ -155,12 +155,12 @@ __global__ void k_face_grad(AdjointArgs a) {
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         const int g = 4 * blocks[(int64_t)blk * D + c] + (int)((bit >> (2 * c)) & 3u);
-        const double xc = __dadd_rn(P.origin[c], __dmul_rn((double)g + 0.5, hL));
-        const float ohi = (float)xc, olo = (float)(xc - (double)ohi);
+        float ohi, olo;
+        df_position(P.org_hi[c], P.org_lo[c], (float)(2 * g + 1), 0.5f * fg.h_hi, 0.5f * fg.h_lo, ohi, olo);
 #pragma unroll
         for (int k = 0; k < D; ++k) p[k][c] = (V[D * k + c] - ohi) - olo;
       }
-      const float h32 = (float)hL;
+      const float h32 = fg.h_hi;
       if constexpr (D == 3) {
         const float dv[3] = {c_dirs19[dir][0] * h32, c_dirs19[dir][1] * h32, c_dirs19[dir][2] * h32};
         const float nh[3] = {a.nrm[f], a.nrm[a.nf + f], a.nrm[2 * a.nf + f]};

@@ -141,6 +141,10 @@ __global__ void k_scatter(ScatterArgs a) {
     for (int j = 0; j < D * D; ++j) e.v[j] = a.f.X[(int64_t)j * nf + f];
 #pragma unroll
     for (int j = 0; j < (int)(sizeof(e.pad) / sizeof(e.pad[0])); ++j) e.pad[j] = 0u;
+    if constexpr (D == 3) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) e.n[c] = a.nrm[(int64_t)c * nf + f];
+    }
     const int64_t B = P.B;
     for (int z = lo[2]; z <= hi[2]; ++z)
       for (int y = lo[1]; y <= hi[1]; ++y)

@@ -31,6 +31,80 @@ __constant__ int c_d3q19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0},  {0, 1, 
                                    {0, 1, 1},  {0, -1, -1}, {0, 1, -1},  {0, -1, 1}};
 __constant__ int c_d2q9[9][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}, {1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
 
+// D3Q19 direction i (1..18), component a, as a compile-time constant when i and
+// a are: 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = xy, xz, yz plane diagonals, each
+// (+,+),(-,-),(+,-),(-,+).
+__host__ __device__ constexpr int d3q19_c(int i, int a) {
+  return i <= 6 ? (((i - 1) >> 1) == a ? ((i & 1) ? 1 : -1) : 0)
+                : ((((i - 7) >> 2) == 0 ? (a == 0 ? 1 : (a == 1 ? 2 : 0))
+                                        : (((i - 7) >> 2) == 1 ? (a == 0 ? 1 : (a == 2 ? 2 : 0))
+                                                               : (a == 1 ? 1 : (a == 2 ? 2 : 0)))) == 1
+                       ? ((((i - 7) & 3) == 0 || ((i - 7) & 3) == 2) ? 1 : -1)
+                       : ((((i - 7) >> 2) == 0 ? (a == 0 ? 1 : (a == 1 ? 2 : 0))
+                                               : (((i - 7) >> 2) == 1 ? (a == 0 ? 1 : (a == 2 ? 2 : 0))
+                                                                      : (a == 1 ? 1 : (a == 2 ? 2 : 0)))) == 2
+                              ? ((((i - 7) & 3) == 0 || ((i - 7) & 3) == 3) ? 1 : -1)
+                              : 0));
+}
+static_assert(d3q19_c(1, 0) == 1 && d3q19_c(2, 0) == -1 && d3q19_c(5, 2) == 1 && d3q19_c(6, 2) == -1, "axes");
+static_assert(d3q19_c(7, 0) == 1 && d3q19_c(7, 1) == 1 && d3q19_c(8, 0) == -1 && d3q19_c(8, 1) == -1, "xy");
+static_assert(d3q19_c(9, 0) == 1 && d3q19_c(9, 1) == -1 && d3q19_c(10, 0) == -1 && d3q19_c(10, 1) == 1, "xy");
+static_assert(d3q19_c(13, 0) == 1 && d3q19_c(13, 2) == -1 && d3q19_c(13, 1) == 0, "xz");
+static_assert(d3q19_c(18, 1) == -1 && d3q19_c(18, 2) == 1 && d3q19_c(18, 0) == 0, "yz");
+
+__device__ __forceinline__ void d3q19_dir(int i, int& cx, int& cy, int& cz) {
+  cx = cy = cz = 0;
+  if (i <= 6) {
+    const int s = (i & 1) ? 1 : -1;
+    const int ax = (i - 1) >> 1;
+    if (ax == 0) cx = s;
+    else if (ax == 1) cy = s;
+    else cz = s;
+    return;
+  }
+  const int p = (i - 7) >> 2, j = (i - 7) & 3;
+  const int s1 = (j == 0 || j == 2) ? 1 : -1;
+  const int s2 = (j == 0 || j == 3) ? 1 : -1;
+  if (p == 0) {
+    cx = s1;
+    cy = s2;
+  } else if (p == 1) {
+    cx = s1;
+    cz = s2;
+  } else {
+    cy = s1;
+    cz = s2;
+  }
+}
+
+// Directions whose link segment box [0, c h] can meet the face's box (the hit
+// point lies in both): per axis the face must straddle 0 (c_a = 0), reach
+// [0, h] (c_a = +1) or [-h, 0] (c_a = -1), with a tolerance for the rounding
+// of the local coordinates.  Bit i-1 set = direction i may hit.
+__device__ __forceinline__ uint32_t d3q19_candidates(const float (*p)[3], float h) {
+  bool z[3], pos[3], neg[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float mn = fminf(fminf(p[0][a], p[1][a]), p[2][a]);
+    const float mx = fmaxf(fmaxf(p[0][a], p[1][a]), p[2][a]);
+    const float tol = 8.0f * kU32 * (fmaxf(fabsf(mn), fabsf(mx)) + h);
+    z[a] = mn <= tol && mx >= -tol;
+    pos[a] = mx >= -tol && mn <= h + tol;
+    neg[a] = mn <= tol && mx >= -h - tol;
+  }
+  uint32_t m = 0;
+#pragma unroll
+  for (int i = 1; i <= 18; ++i) {
+    int c[3];
+    d3q19_dir(i, c[0], c[1], c[2]);
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ok = ok && (c[a] == 0 ? z[a] : (c[a] > 0 ? pos[a] : neg[a]));
+    m |= ok ? (1u << (i - 1)) : 0u;
+  }
+  return m;
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   const float bb = s - a;
@@ -47,6 +121,22 @@ struct LinkHit {
   bool band;
   double t;
 };
+
+__device__ __noinline__ LinkHit link_fp64_3(const float* V, const double* xc, const int* ci, double h);
+
+// FP64 evaluation of direction di for the cell (block coordinates blk3, cell bit),
+// with the cell centre formed in FP64 (the slow path of undecided signs).
+__device__ __noinline__ LinkHit link_fallback_3(const float* V, const int* blk3, uint32_t bit, const double* origin,
+                                                double h, int di) {
+  int ci[3];
+  d3q19_dir(di, ci[0], ci[1], ci[2]);
+  double xc[3];
+  for (int c = 0; c < 3; ++c) {
+    const int gc = 4 * blk3[c] + (int)((bit >> (2 * c)) & 3u);
+    xc[c] = __dadd_rn(origin[c], __dmul_rn((double)gc + 0.5, h));
+  }
+  return link_fp64_3(V, xc, ci, h);
+}
 
 // FP64 evaluation of one (link, face) pair, same definition as the FP32 path.
 __device__ __noinline__ LinkHit link_fp64_3(const float* V, const double* xc, const int* ci, double h) {
@@ -139,17 +229,22 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
   if (local < nrows) {
     const uint32_t id = a.adj_cell[row];
     const uint32_t blk = id / NC, bit = id % NC;
-    const LevelGeom G = level_geom(geom_row(a.g0, a.table, a.gid, blk), a.level);
+    const GeomParams& P = a.table ? a.table[a.gid ? a.gid[blk] : 0u] : a.g0;
+    const FastGeom g = fast_geom(P, a.level);
+    // cell centre origin + (2 c + 1) (h/2) as hi + lo; the FP64 centre only for fallbacks
     double xc[3] = {0, 0, 0};
     float ohi[3] = {0, 0, 0}, olo[3] = {0, 0, 0};
+    const double hL = scalbn(P.h0, -a.level);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      const int g = 4 * a.blocks[(int64_t)blk * D + c] + (int)((bit >> (2 * c)) & 3u);
-      xc[c] = __dadd_rn(G.origin[c], __dmul_rn((double)g + 0.5, G.h));
-      ohi[c] = (float)xc[c];
-      olo[c] = (float)(xc[c] - (double)ohi[c]);
+      const int gc = 4 * a.blocks[(int64_t)blk * D + c] + (int)((bit >> (2 * c)) & 3u);
+      df_position(P.org_hi[c], P.org_lo[c], (float)(2 * gc + 1), 0.5f * g.h_hi, 0.5f * g.h_lo, ohi[c], olo[c]);
+      xc[c] = D == 3 ? 0.0 : __dadd_rn(P.origin[c], __dmul_rn((double)gc + 0.5, hL));
     }
-    const float h32 = (float)G.h;
+    const float h32 = g.h_hi;
+    struct GeomView {
+      double h;
+    } G{hL};
     const uint32_t e0 = a.adj_off[row], e1 = a.adj_off[row + 1];
     for (uint32_t e = e0; e < e1; ++e) {
       const uint32_t f = a.adj_ids[e];
@@ -186,6 +281,8 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
             p[k][c] = s + pl[k][c];
             pmax = fmaxf(pmax, fabsf(p[k][c]));
           }
+        uint32_t cand = d3q19_candidates(p, h32);
+        if (!cand) continue;
         const float nh[3] = {a.nrm[f], a.nrm[a.nf + f], a.nrm[2 * a.nf + f]};
         const float nl[3] = {a.nrm[3 * a.nf + f], a.nrm[4 * a.nf + f], a.nrm[5 * a.nf + f]};
         // num = n . (v0 - x) in double-float
@@ -206,7 +303,8 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
         const float xmax = fmaxf(fmaxf(fabsf(ohi[0]), fabsf(ohi[1])), fabsf(ohi[2]));
         const float eps_num = 16.0f * kU32 * kU32 * n1 * (xmax + pmax) + 4.0f * kU32 * fabsf(ne);
         // edge cross products C_k = p_a x p_b, (a,b) = (1,2),(2,0),(0,1), and their magnitudes
-        float C[3][3], M[3][3];
+        // and the largest component magnitude bound Mk = max_c (|A_a B_b| + |A_b B_a|)
+        float C[3][3], M[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const float* A = p[(k + 1) % 3];
@@ -214,36 +312,36 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
           C[k][0] = fmaf(A[1], B[2], -A[2] * B[1]);
           C[k][1] = fmaf(A[2], B[0], -A[0] * B[2]);
           C[k][2] = fmaf(A[0], B[1], -A[1] * B[0]);
-          M[k][0] = fabsf(A[1] * B[2]) + fabsf(A[2] * B[1]);
-          M[k][1] = fabsf(A[2] * B[0]) + fabsf(A[0] * B[2]);
-          M[k][2] = fabsf(A[0] * B[1]) + fabsf(A[1] * B[0]);
+          M[k] = fmaxf(fmaxf(fabsf(A[1] * B[2]) + fabsf(A[2] * B[1]), fabsf(A[2] * B[0]) + fabsf(A[0] * B[2])),
+                       fabsf(A[0] * B[1]) + fabsf(A[1] * B[0]));
         }
         const float nn2 = sqrtf(nh[0] * nh[0] + nh[1] * nh[1] + nh[2] * nh[2]);
-#pragma unroll 2
+#pragma unroll
         for (int di = 1; di <= 18; ++di) {
-          const int cx = c_d3q19[di][0], cy = c_d3q19[di][1], cz = c_d3q19[di][2];
-          // den_n = c . n in double-float (c has at most two non-zero unit entries)
-          float dh = 0.f, dl = 0.f;
-          {
-            float s, t;
-            two_sum(cx * nh[0], cy * nh[1], s, t);
-            float s2, t2;
-            two_sum(s, cz * nh[2], s2, t2);
-            dh = s2;
-            dl = t + t2 + (cx * nl[0] + cy * nl[1] + cz * nl[2]);
+          const int cx = d3q19_c(di, 0), cy = d3q19_c(di, 1), cz = d3q19_c(di, 2);
+          if (!((cand >> (di - 1)) & 1u)) continue;
+          // den_n = c . n in double-float: exact for an axis direction, one TwoSum for a diagonal
+          const float t0 = cx * nh[0], t1 = cy * nh[1], t2 = cz * nh[2];
+          const int cl_i = (cx != 0) + (cy != 0) + (cz != 0);
+          float dh, dl;
+          if (cl_i == 1) {
+            dh = t0 + t1 + t2;
+            dl = cx * nl[0] + cy * nl[1] + cz * nl[2];
+          } else {
+            float e2;
+            two_sum(cx != 0 ? t0 : t1, cz != 0 ? t2 : t1, dh, e2);
+            dl = e2 + (cx * nl[0] + cy * nl[1] + cz * nl[2]);
           }
           const float den = dh + dl;
-          const float cl = (float)(abs(cx) + abs(cy) + abs(cz));
           if (den == 0.0f && dh == 0.0f) continue;  // c_i parallel to the face plane: no hit
           const float sg = den > 0.f ? 1.f : -1.f;
           // inside test: sg * (c . C_k) >= 0 for k = 0..2
-          bool out = false, unc = fabsf(den) <= 1e-5f * sqrtf(cl) * nn2;
+          bool out = false, unc = fabsf(den) <= (cl_i == 1 ? 1e-5f : 1.41421356e-5f) * nn2;
           bool all_in = true;
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
             const float u = sg * (cx * C[k][0] + cy * C[k][1] + cz * C[k][2]);
-            const float eu = 8.0f * kU32 * (fabsf((float)cx) * M[k][0] + fabsf((float)cy) * M[k][1] +
-                                            fabsf((float)cz) * M[k][2]);
+            const float eu = 8.0f * kU32 * (float)cl_i * M[k];
             if (u < -eu) out = true;
             if (!(u > eu)) all_in = false;
           }
@@ -264,8 +362,7 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
             unc = true;
           }
           if (unc) {
-            const int ci[3] = {cx, cy, cz};
-            const LinkHit r = link_fp64_3(V, xc, ci, G.h);
+            const LinkHit r = link_fallback_3(V, a.blocks + (int64_t)blk * 3, bit, P.origin, G.h, di);
             ++n_fb;
             if (r.band) ++n_band;
             if (!r.hit) continue;

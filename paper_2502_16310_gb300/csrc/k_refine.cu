@@ -125,7 +125,6 @@ __device__ __noinline__ double margin_fp64_2(const float* V, const double* xc, d
 // Block-frame quantities shared by all lanes of the warp for one block.
 template <int D>
 struct BlockFrame {
-  double X64[3];   // block corner (FP64)
   float Xb[3];     // block corner rounded to FP32 (the frame origin)
   float cB[3];     // block centre in the frame
   float h, r, rb;  // cell size, cell and block half-widths (inflated) in FP32
@@ -268,8 +267,9 @@ struct WarpCounters {
 };
 
 template <int D>
-__device__ __forceinline__ bool resolve_fp64(const RefineLevel& a, const LevelGeom& G, uint32_t face, const int* b,
-                                             int cell_local, WarpCounters& wc) {
+__device__ __noinline__ bool resolve_fp64(const RefineLevel& a, uint32_t gid, uint32_t face, const int* b,
+                                          int cell_local, unsigned long long* fb, unsigned long long* band) {
+  const LevelGeom G = level_geom(a.table ? a.table[gid] : a.g0, a.level);
   float V[D * D];
 #pragma unroll
   for (int j = 0; j < D * D; ++j) V[j] = a.X[(int64_t)j * a.nf + face];
@@ -281,101 +281,210 @@ __device__ __forceinline__ bool resolve_fp64(const RefineLevel& a, const LevelGe
   }
   const double r = __dadd_rn(0.5 * G.h, G.d);
   const double m = D == 3 ? margin_fp64_3(V, xc, r) : margin_fp64_2(V, xc, r);
-  wc.fb++;
-  if (fabs(m) <= kBandRel * G.h) wc.band++;
+  ++*fb;
+  if (fabs(m) <= kBandRel * G.h) ++*band;
   return m <= 0.0;
 }
 
 // Shared walk of one block: bins of the query box, canonical-bin dedup,
 // block-level cull, cell tests.  `on_hit(cellslot, face)` is called for every
 // intersecting (cell, face) pair; cellslot 0 = cell `lane`, 1 = cell `lane + 32`.
+//
+// The block frame is built in FP32 from the geometry row's double-float h0 and
+// origin: the block corner origin + 4 b h is formed as hi + lo (hi = the frame
+// origin, lo = its rounding error, carried into the cell and block centres),
+// so no FP64 instruction runs per block.  The bin query range is widened by
+// a margin that covers the FP32 error of the bin coordinate (a superset of
+// bins only adds candidates the block test rejects).
+// Per-warp shared memory of the walk: survivor records, a double buffer of
+// bin entries filled by TMA bulk copies, and one mbarrier per buffer.
+template <int D>
+struct WarpSmem {
+  Surv<D> surv[32];
+  typename EntryT<D>::type buf[2][32];
+  uint64_t bar[2];
+};
+
+template <int D>
+__device__ __forceinline__ void warp_smem_init(WarpSmem<D>& sm, int lane) {
+  if (lane == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+}
+
+// A run of at most 32 consecutive entries of one bin.
+struct Chunk {
+  int x, y, z;
+  uint32_t j0, n;
+};
+
+// Walks the bins of the query box in z, y, x order, handing out chunks.
+struct ChunkCursor {
+  int qlo[3], qhi[3];
+  int x, y, z;
+  uint32_t s, e;
+  bool started;
+};
+
+__device__ __forceinline__ bool next_chunk(ChunkCursor& c, const uint32_t* offsets, int64_t bin_base, int64_t B,
+                                           Chunk& out) {
+  while (true) {
+    if (c.started && c.s < c.e) {
+      out.x = c.x;
+      out.y = c.y;
+      out.z = c.z;
+      out.j0 = c.s;
+      out.n = c.e - c.s < 32u ? c.e - c.s : 32u;
+      c.s += out.n;
+      return true;
+    }
+    // move to the next bin
+    if (!c.started) {
+      c.started = true;
+      c.x = c.qlo[0];
+      c.y = c.qlo[1];
+      c.z = c.qlo[2];
+    } else if (++c.x > c.qhi[0]) {
+      c.x = c.qlo[0];
+      if (++c.y > c.qhi[1]) {
+        c.y = c.qlo[1];
+        if (++c.z > c.qhi[2]) return false;
+      }
+    }
+    const int64_t bin = bin_base + c.x + B * (c.y + B * (int64_t)c.z);
+    c.s = offsets[bin];
+    c.e = offsets[bin + 1];
+  }
+}
+
+// Shared walk of one block: bins of the query box, canonical-bin dedup,
+// block-level cull, cell tests.  `on_hit(cellslot, face)` is called for every
+// intersecting (cell, face) pair; cellslot 0 = cell `lane`, 1 = cell `lane + 32`.
+//
+// The block frame is built in FP32 from the geometry row's double-float h0 and
+// origin: the block corner origin + 4 b h is formed as hi + lo (hi = the frame
+// origin, lo = its rounding error, carried into the cell and block centres),
+// so no FP64 instruction runs per block.  The bin query range is widened by
+// a margin that covers the FP32 error of the bin coordinate (a superset of
+// bins only adds candidates the block test rejects).
+//
+// Bin entries arrive in shared memory by TMA bulk copies, chunk by chunk
+// (<= 32 entries of one bin), double-buffered: lane 0 issues the copy of the
+// next chunk before the warp tests the current one.
 template <int D, typename OnHit>
-__device__ __forceinline__ void walk_block(const RefineLevel& a, const LevelGeom& G, const int* b, Surv<D>* s_surv,
-                                           int lane, WarpCounters& wc, OnHit on_hit) {
+__device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParams& P, uint32_t gid, const int* b,
+                                           WarpSmem<D>& sm, uint32_t& phase, int lane, WarpCounters& wc,
+                                           OnHit on_hit) {
   using E = typename EntryT<D>::type;
-  const float hf = (float)G.h;
+  const FastGeom g = fast_geom(P, a.level);
+  const float hf = g.h_hi;
   BlockFrame<D> F;
-  int qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0};
-  const double slack = 1e-9 * G.h;
+  ChunkCursor cur{};
+  cur.qlo[1] = cur.qlo[2] = cur.qhi[1] = cur.qhi[2] = 0;
   float O = 4.0f * hf;
+  float shift[3] = {0.f, 0.f, 0.f};
+  const int Bn = P.B;
+  const float margin = 1e-6f * (float)Bn + 1e-3f;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    F.X64[c] = __dadd_rn(G.origin[c], __dmul_rn((double)(4 * b[c]), G.h));
-    F.Xb[c] = (float)F.X64[c];
-    const double shift = __dsub_rn(F.X64[c], (double)F.Xb[c]);
-    F.cB[c] = (float)__dadd_rn(2.0 * G.h, shift);
-    O = fmaxf(O, 4.0f * hf + 2.0f * (float)fabs(shift));
-    qlo[c] = bin_coord(F.X64[c] - G.d - slack, G.origin[c], G.scale[c], G.B);
-    qhi[c] = bin_coord(F.X64[c] + 4.0 * G.h + G.d + slack, G.origin[c], G.scale[c], G.B);
+    float lo;
+    df_position(P.org_hi[c], P.org_lo[c], (float)(4 * b[c]), g.h_hi, g.h_lo, F.Xb[c], lo);
+    shift[c] = lo;
+    F.cB[c] = fmaf(2.0f, g.h_hi, lo);
+    O = fmaxf(O, 4.0f * hf + 2.0f * fabsf(lo));
+    // bin coordinates of the inflated block's ends relative to the domain origin
+    const float k0 = (float)(4 * b[c]);
+    const float xlo = fmaf(k0, g.h_hi, fmaf(k0, g.h_lo, -g.d));
+    const float xhi = fmaf(k0 + 4.0f, g.h_hi, fmaf(k0 + 4.0f, g.h_lo, g.d));
+    const float tlo = floorf(xlo * P.scale32[c] - margin);
+    const float thi = floorf(xhi * P.scale32[c] + margin);
+    cur.qlo[c] = tlo < 0.f ? 0 : (tlo > (float)(Bn - 1) ? Bn - 1 : (int)tlo);
+    cur.qhi[c] = thi < 0.f ? 0 : (thi > (float)(Bn - 1) ? Bn - 1 : (int)thi);
   }
   F.h = hf;
-  F.r = (float)(0.5 * G.h + G.d);
-  F.rb = (float)(2.0 * G.h + G.d);
+  F.r = fmaf(0.5f, hf, g.d);
+  F.rb = fmaf(2.0f, hf, g.d);
   F.O = O;
-  // cell centres of this lane in the frame (FP64 -> FP32 once)
+  // cell centres of this lane in the frame: lo + (l + 1/2) h
   float o0[3] = {0, 0, 0}, o1[3] = {0, 0, 0};
   const bool lane_cell = D == 3 || lane < 16;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const int l0 = (lane >> (2 * c)) & 3;
-    const double xc0 = __dadd_rn(G.origin[c], __dmul_rn((double)(4 * b[c] + l0) + 0.5, G.h));
-    o0[c] = (float)__dsub_rn(xc0, (double)F.Xb[c]);
+    const float l0 = (float)((lane >> (2 * c)) & 3) + 0.5f;
+    o0[c] = fmaf(l0, g.h_hi, fmaf(l0, g.h_lo, shift[c]));
     if (D == 3) {
-      const int l1 = ((lane + 32) >> (2 * c)) & 3;
-      const double xc1 = __dadd_rn(G.origin[c], __dmul_rn((double)(4 * b[c] + l1) + 0.5, G.h));
-      o1[c] = (float)__dsub_rn(xc1, (double)F.Xb[c]);
+      const float l1 = (float)(((lane + 32) >> (2 * c)) & 3) + 0.5f;
+      o1[c] = fmaf(l1, g.h_hi, fmaf(l1, g.h_lo, shift[c]));
     }
   }
-  const int64_t B = G.B;
+  const int64_t B = Bn;
   const E* payload = static_cast<const E*>(a.payload);
-  for (int z = qlo[2]; z <= qhi[2]; ++z)
-    for (int y = qlo[1]; y <= qhi[1]; ++y)
-      for (int x = qlo[0]; x <= qhi[0]; ++x) {
-        const int64_t bin = G.bin_base + x + B * (y + B * (int64_t)z);
-        const uint32_t s = a.offsets[bin], e = a.offsets[bin + 1];
-        for (uint32_t base = s; base < e; base += 32) {
-          const uint32_t j = base + lane;
-          bool surv = false;
-          if (j < e) {
-            const E ent = payload[j];
-            const uint32_t id = ent.id;
-            bool canon = ((id >> 29) & 1u) || x == qlo[0];
-            canon = canon && (((id >> 30) & 1u) || y == qlo[1]);
-            if (D == 3) canon = canon && (((id >> 31) & 1u) || z == qlo[2]);
-            if (canon) {
-              wc.cand++;
-              const uint32_t f = id & kIdMask;
-              float nh[3] = {0.f, 0.f, 0.f};
-              if (D == 3) {
-                nh[0] = a.nrm[f];
-                nh[1] = a.nrm[a.nf + f];
-                nh[2] = a.nrm[2 * a.nf + f];
-              }
-              surv = setup_face<D>(ent.v, nh, F, s_surv[lane]);
-              s_surv[lane].face = f;
-            }
-          }
-          unsigned m = __ballot_sync(0xffffffffu, surv);
-          __syncwarp();
-          wc.surv += __popc(m);
-          while (m) {
-            const int k = __ffs(m) - 1;
-            m &= m - 1;
-            const Surv<D>& S = s_surv[k];
-            if (lane_cell) {
-              int r0 = cell_test<D>(S, o0);
-              if (r0 == 2) r0 = resolve_fp64<D>(a, G, S.face, b, lane, wc) ? 1 : 0;
-              if (r0) on_hit(0, S.face);
-              if (D == 3) {
-                int r1 = cell_test<D>(S, o1);
-                if (r1 == 2) r1 = resolve_fp64<D>(a, G, S.face, b, lane + 32, wc) ? 1 : 0;
-                if (r1) on_hit(1, S.face);
-              }
-            }
-          }
-          __syncwarp();
+  Chunk ck[2];
+  bool have = next_chunk(cur, a.offsets, P.bin_base, B, ck[0]);
+  if (have && lane == 0) {
+    mbar_arrive_expect_tx(&sm.bar[0], ck[0].n * (uint32_t)sizeof(E));
+    bulk_copy_g2s(sm.buf[0], payload + ck[0].j0, ck[0].n * (uint32_t)sizeof(E), &sm.bar[0]);
+  }
+  int k = 0;
+  while (have) {
+    const int cb = k & 1, nb = cb ^ 1;
+    const bool more = next_chunk(cur, a.offsets, P.bin_base, B, ck[nb]);
+    if (more && lane == 0) {
+      fence_proxy_async_smem();  // the warp's reads of this buffer (previous chunk) come first
+      mbar_arrive_expect_tx(&sm.bar[nb], ck[nb].n * (uint32_t)sizeof(E));
+      bulk_copy_g2s(sm.buf[nb], payload + ck[nb].j0, ck[nb].n * (uint32_t)sizeof(E), &sm.bar[nb]);
+    }
+    mbar_wait_bounded(&sm.bar[cb], (phase >> cb) & 1u, a.err);
+    phase ^= 1u << cb;
+    const Chunk& C = ck[cb];
+    bool surv = false;
+    if ((uint32_t)lane < C.n) {
+      const E& ent = sm.buf[cb][lane];
+      const uint32_t id = ent.id;
+      bool canon = ((id >> 29) & 1u) || C.x == cur.qlo[0];
+      canon = canon && (((id >> 30) & 1u) || C.y == cur.qlo[1]);
+      if (D == 3) canon = canon && (((id >> 31) & 1u) || C.z == cur.qlo[2]);
+      if (canon) {
+        wc.cand++;
+        const uint32_t f = id & kIdMask;
+        float nh[3] = {0.f, 0.f, 0.f};
+        if constexpr (D == 3) {
+          nh[0] = ent.n[0];
+          nh[1] = ent.n[1];
+          nh[2] = ent.n[2];
+        }
+        float V[D * D];
+#pragma unroll
+        for (int j = 0; j < D * D; ++j) V[j] = ent.v[j];
+        surv = setup_face<D>(V, nh, F, sm.surv[lane]);
+        sm.surv[lane].face = f;
+      }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, surv);
+    __syncwarp();
+    wc.surv += __popc(m);
+    while (m) {
+      const int s = __ffs(m) - 1;
+      m &= m - 1;
+      const Surv<D>& S = sm.surv[s];
+      if (lane_cell) {
+        int r0 = cell_test<D>(S, o0);
+        if (r0 == 2) r0 = resolve_fp64<D>(a, gid, S.face, b, lane, &wc.fb, &wc.band) ? 1 : 0;
+        if (r0) on_hit(0, S.face);
+        if (D == 3) {
+          int r1 = cell_test<D>(S, o1);
+          if (r1 == 2) r1 = resolve_fp64<D>(a, gid, S.face, b, lane + 32, &wc.fb, &wc.band) ? 1 : 0;
+          if (r1) on_hit(1, S.face);
         }
       }
+    }
+    __syncwarp();
+    have = more;
+    ++k;
+  }
 }
 
 // Block count of a launch: from device memory when given (bounded by the
@@ -393,8 +502,10 @@ __device__ __forceinline__ int64_t launch_count(int64_t n, const uint64_t* n_dev
 template <int D>
 __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
   extern __shared__ __align__(16) unsigned char s_raw[];
-  Surv<D>* s_surv = reinterpret_cast<Surv<D>*>(s_raw) + (threadIdx.x >> 5) * 32;
+  WarpSmem<D>& sm = reinterpret_cast<WarpSmem<D>*>(s_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
+  warp_smem_init<D>(sm, lane);
+  uint32_t phase = 0;
   const int64_t n = launch_count(a.n_blocks, a.n_dev, a.err);
   constexpr int NC = D == 3 ? 64 : 16;
   WarpCounters wc;
@@ -406,9 +517,10 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
     int b[3] = {0, 0, 0};
 #pragma unroll
     for (int c = 0; c < D; ++c) b[c] = a.blocks[(int64_t)blk * D + c];
-    const LevelGeom G = level_geom(geom_row(a.g0, a.table, a.gid, blk), a.level);
+    const uint32_t gid = a.gid ? a.gid[blk] : 0u;
+    const GeomParams& P = a.table ? a.table[gid] : a.g0;
     uint32_t cnt0 = 0, cnt1 = 0;
-    walk_block<D>(a, G, b, s_surv, lane, wc, [&](int slot, uint32_t) {
+    walk_block<D>(a, P, gid, b, sm, phase, lane, wc, [&](int slot, uint32_t) {
       if (slot == 0)
         ++cnt0;
       else
@@ -423,7 +535,7 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
     }
     if (a.blockcnt) {
       // per-cell counts only where the block's geometry ends at this level
-      const bool fin = G.finest;
+      const bool fin = a.level == P.n_levels - 1;
       if (fin && a.cellcnt) {
         if (cnt0 > 0xffffu || cnt1 > 0xffffu) atomicOr(a.err, ERR_OVERFLOW);
         if (lane < NC) a.cellcnt[(int64_t)blk * NC + lane] = (uint16_t)min(cnt0, 0xffffu);
@@ -458,8 +570,10 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
 template <int D>
 __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
   extern __shared__ __align__(16) unsigned char s_raw[];
-  Surv<D>* s_surv = reinterpret_cast<Surv<D>*>(s_raw) + (threadIdx.x >> 5) * 32;
+  WarpSmem<D>& sm = reinterpret_cast<WarpSmem<D>*>(s_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
+  warp_smem_init<D>(sm, lane);
+  uint32_t phase = 0;
   constexpr int NC = D == 3 ? 64 : 16;
   const int64_t n = launch_count(a.lv.n_blocks, a.lv.n_dev, a.lv.err);
   const uint64_t run_cells = a.run ? a.run[0] : 0ull, run_pairs = a.run ? a.run[1] : 0ull;
@@ -471,8 +585,9 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
     if (blk >= n) break;
     const uint64_t mask = a.lv.mask[blk];
     if (mask == 0) continue;
-    const LevelGeom G = level_geom(geom_row(a.lv.g0, a.lv.table, a.lv.gid, blk), a.lv.level);
-    if (!G.finest) continue;
+    const uint32_t gid = a.lv.gid ? a.lv.gid[blk] : 0u;
+    const GeomParams& P = a.lv.table ? a.lv.table[gid] : a.lv.g0;
+    if (a.lv.level != P.n_levels - 1) continue;
     int b[3] = {0, 0, 0};
 #pragma unroll
     for (int c = 0; c < D; ++c) b[c] = a.lv.blocks[(int64_t)blk * D + c];
@@ -512,7 +627,7 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
     }
     uint32_t c0 = 0, c1 = 0;
     const bool can0 = (int64_t)(off0 + n0) <= a.cap_pairs, can1 = (int64_t)(off1 + n1) <= a.cap_pairs;
-    walk_block<D>(a.lv, G, b, s_surv, lane, wc, [&](int slot, uint32_t f) {
+    walk_block<D>(a.lv, P, gid, b, sm, phase, lane, wc, [&](int slot, uint32_t f) {
       if (slot == 0) {
         if (c0 < n0 && can0)
           a.adj_ids[off0 + c0] = f;
@@ -650,11 +765,12 @@ int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st) {
   if (!a.n_dev && a.n_blocks <= 0) return 0;
   const int warps = a.warps > 0 ? a.warps : 4;
   const int g = grid_warps(num_sms, a.n_blocks, warps, a.n_dev != nullptr);
-  const size_t smem = (size_t)warps * 32 * (a.dim == 3 ? sizeof(Surv<3>) : sizeof(Surv<2>));
+  const size_t smem = (size_t)warps * (a.dim == 3 ? sizeof(WarpSmem<3>) : sizeof(WarpSmem<2>));
   if (a.dim == 3) {
     allow_smem(k_refine<3>, smem);
     k_refine<3><<<g, warps * 32, smem, st>>>(a);
   } else {
+    allow_smem(k_refine<2>, smem);
     k_refine<2><<<g, warps * 32, smem, st>>>(a);
   }
   return 1;
@@ -664,11 +780,12 @@ int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st) {
   if (!a.lv.n_dev && a.lv.n_blocks <= 0) return 0;
   const int warps = a.lv.warps > 0 ? a.lv.warps : 4;
   const int g = grid_warps(num_sms, a.lv.n_blocks, warps, a.lv.n_dev != nullptr);
-  const size_t smem = (size_t)warps * 32 * (a.lv.dim == 3 ? sizeof(Surv<3>) : sizeof(Surv<2>));
+  const size_t smem = (size_t)warps * (a.lv.dim == 3 ? sizeof(WarpSmem<3>) : sizeof(WarpSmem<2>));
   if (a.lv.dim == 3) {
     allow_smem(k_adjacency<3>, smem);
     k_adjacency<3><<<g, warps * 32, smem, st>>>(a);
   } else {
+    allow_smem(k_adjacency<2>, smem);
     k_adjacency<2><<<g, warps * 32, smem, st>>>(a);
   }
   return 1;
