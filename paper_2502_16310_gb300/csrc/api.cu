@@ -94,7 +94,7 @@ struct amr_ctx {
   bool multi = false;
   DevBuf table, face_gid;
   // buffers
-  DevBuf X, nrm, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
+  DevBuf X, nrm, frec, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
   LevelBufs lv[AMR_MAX_LEVELS];
   DevBuf adj_cell, adj_off, adj_ids, link_cell, link_dir, link_q, link_face;
   int64_t cap_cells = 0, cap_pairs = 0, cap_links = 0;
@@ -382,7 +382,7 @@ amr_status amr_ctx_init(amr_ctx* ctx) {
 void amr_ctx_free(amr_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   drop_graph(ctx);
-  DevBuf* all[] = {&ctx->X,         &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
+  DevBuf* all[] = {&ctx->X, &ctx->frec, &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
                    &ctx->count,     &ctx->offsets,      &ctx->ids,        &ctx->payload,    &ctx->scratch,
                    &ctx->misc,      &ctx->scal,         &ctx->adj_cell,   &ctx->adj_off,    &ctx->adj_ids,
                    &ctx->link_cell, &ctx->link_dir,     &ctx->link_q,     &ctx->link_face,  &ctx->idx,
@@ -672,8 +672,9 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st)
         la.run = ctx->d_scal + SC_RUN;
         la.level_tot = ctx->d_scal + SC_TOT + L;
         la.cap_rows = ctx->cap_cells;
+        la.cap_pairs = ctx->cap_pairs;
         la.X = a.X;
-        la.nrm = a.nrm;
+        la.rec = static_cast<const FaceRec3*>(ctx->frec.p);
         la.nf = ctx->nf;
         la.n_links = ctx->d_scal + SC_NL + L;
         la.counters = ctx->counters;
@@ -925,6 +926,7 @@ amr_status amr_geom_load(amr_ctx* ctx, const float* coords, int64_t n_verts, con
   ctx->indexed = idx != nullptr;
   TRY(ensure(ctx, ctx->X, sizeof(float) * D * D * (size_t)(n_faces > 0 ? n_faces : 1)));
   if (D == 3) TRY(ensure(ctx, ctx->nrm, sizeof(float) * 6 * (size_t)(n_faces > 0 ? n_faces : 1)));
+  if (D == 3) TRY(ensure(ctx, ctx->frec, sizeof(FaceRec3) * (size_t)(n_faces > 0 ? n_faces : 1)));
   cudaStream_t st = ctx->stream;
   if (n_faces > 0) {
     if (idx) {
@@ -949,7 +951,7 @@ amr_status amr_geom_load(amr_ctx* ctx, const float* coords, int64_t n_verts, con
     if (D == 3)
       timed(ctx, st, "face_normals", [&] {
         return launch_face_normals(static_cast<const float*>(ctx->X.p), n_faces, static_cast<float*>(ctx->nrm.p),
-                                   st);
+                                   static_cast<FaceRec3*>(ctx->frec.p), st);
       });
   }
   CK(cudaGetLastError());
@@ -1269,6 +1271,7 @@ amr_status batch_gather(amr_batch* b) {
   b->vert_total = nv;
   TRY(ensure(ctx, ctx->X, sizeof(float) * D * D * (size_t)(nf > 0 ? nf : 1)));
   if (D == 3) TRY(ensure(ctx, ctx->nrm, sizeof(float) * 6 * (size_t)(nf > 0 ? nf : 1)));
+  if (D == 3) TRY(ensure(ctx, ctx->frec, sizeof(FaceRec3) * (size_t)(nf > 0 ? nf : 1)));
   TRY(ensure(ctx, ctx->face_gid, sizeof(uint32_t) * (size_t)(nf > 0 ? nf : 1)));
   TRY(ensure(ctx, ctx->table, sizeof(GeomParams) * ctx->geoms.size()));
   CK(cudaMemcpyAsync(ctx->table.p, ctx->geoms.data(), sizeof(GeomParams) * ctx->geoms.size(), cudaMemcpyHostToDevice,
@@ -1295,7 +1298,8 @@ amr_status batch_gather(amr_batch* b) {
   }
   if (D == 3)
     timed(ctx, st, "face_normals", [&] {
-      return launch_face_normals(static_cast<const float*>(ctx->X.p), nf, static_cast<float*>(ctx->nrm.p), st);
+      return launch_face_normals(static_cast<const float*>(ctx->X.p), nf, static_cast<float*>(ctx->nrm.p),
+                                 static_cast<FaceRec3*>(ctx->frec.p), st);
     });
   timed(ctx, st, "face_gid", [&] {
     return launch_face_gid(static_cast<const GeomParams*>(ctx->table.p), (int)ctx->geoms.size(), nf,

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace amr {
 
 constexpr float kU32 = 5.9604644775390625e-8f;  // FP32 unit roundoff 2^-24
@@ -289,7 +291,18 @@ int launch_load_indexed(int dim, const float* verts, int64_t nv, const int32_t* 
                         unsigned* err, cudaStream_t st, int64_t ld = -1, int64_t f0 = 0);
 int launch_load_facelist(int dim, const float* coords, int64_t nf, float* X, unsigned* err, cudaStream_t st,
                          int64_t ld = -1, int64_t f0 = 0);
-int launch_face_normals(const float* X, int64_t nf, float* nrm, cudaStream_t st);
+// Packed 3D face record for the link kernel: vertices, then the double-float
+// normal (hi, lo); 64 bytes, read as four 16-byte loads.
+struct __align__(16) FaceRec3 {
+  float v[9];
+  float nh[3];
+  float nl[3];
+  float pad;
+};
+static_assert(sizeof(FaceRec3) == 64, "face record is 64 bytes");
+
+// nrm[6][nf] (hi.xyz, lo.xyz) and the packed records rec[nf] (nullable).
+int launch_face_normals(const float* X, int64_t nf, float* nrm, FaceRec3* rec, cudaStream_t st);
 
 // Faces of one or many geometries: face_gid (nullable) selects the table row.
 struct FaceBinArgs {
@@ -400,8 +413,9 @@ struct LinkArgs {
   const uint64_t* run;         // device running totals before this level: [0] rows, [2] links
   const uint64_t* level_tot;   // device: this level's pairs | cells << 32
   int64_t cap_rows;
-  const float* X;
-  const float* nrm;
+  int64_t cap_pairs;           // capacity of adj_ids
+  const float* X;               // 2D faces (SoA)
+  const FaceRec3* rec;         // 3D face records
   int64_t nf;
   uint32_t* link_cell;
   uint8_t* link_dir;

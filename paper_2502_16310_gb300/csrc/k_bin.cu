@@ -69,8 +69,10 @@ __global__ void k_load_facelist(const float* __restrict__ coords, int64_t nf, fl
 // Face normal n = (v1 - v0) x (v2 - v0) evaluated in FP64 (the edge differences
 // and the products of FP32 inputs are exact there) and stored as an unevaluated
 // FP32 sum hi + lo, so that later FP32 kernels can form plane offsets with
-// double-float accuracy.  Layout nrm[6][nf] = hi.xyz, lo.xyz.
-__global__ void k_face_normals(const float* __restrict__ X, int64_t nf, float* __restrict__ nrm) {
+// double-float accuracy.  Layout nrm[6][nf] = hi.xyz, lo.xyz; rec (when given)
+// gets the packed record (vertices, hi, lo) the link kernel reads.
+__global__ void k_face_normals(const float* __restrict__ X, int64_t nf, float* __restrict__ nrm,
+                               FaceRec3* __restrict__ rec) {
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
     double v[3][3];
 #pragma unroll
@@ -88,6 +90,19 @@ __global__ void k_face_normals(const float* __restrict__ X, int64_t nf, float* _
       const float lo = (float)(n[c] - (double)hi);
       nrm[(int64_t)c * nf + f] = hi;
       nrm[(int64_t)(3 + c) * nf + f] = lo;
+    }
+    if (rec) {
+      float4* R = reinterpret_cast<float4*>(rec + f);
+      float h[3], l[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        h[c] = (float)n[c];
+        l[c] = (float)(n[c] - (double)h[c]);
+      }
+      R[0] = make_float4((float)v[0][0], (float)v[0][1], (float)v[0][2], (float)v[1][0]);
+      R[1] = make_float4((float)v[1][1], (float)v[1][2], (float)v[2][0], (float)v[2][1]);
+      R[2] = make_float4((float)v[2][2], h[0], h[1], h[2]);
+      R[3] = make_float4(l[0], l[1], l[2], 0.0f);
     }
   }
 }
@@ -320,9 +335,9 @@ int launch_load_facelist(int dim, const float* coords, int64_t nf, float* X, uns
   return 1;
 }
 
-int launch_face_normals(const float* X, int64_t nf, float* nrm, cudaStream_t st) {
+int launch_face_normals(const float* X, int64_t nf, float* nrm, FaceRec3* rec, cudaStream_t st) {
   if (nf <= 0) return 0;
-  k_face_normals<<<grid_for(nf, kThreads), kThreads, 0, st>>>(X, nf, nrm);
+  k_face_normals<<<grid_for(nf, kThreads), kThreads, 0, st>>>(X, nf, nrm, rec);
   return 1;
 }
 

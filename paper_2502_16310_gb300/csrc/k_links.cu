@@ -23,28 +23,22 @@ namespace amr {
 
 namespace {
 
-constexpr int kLThreads = 128;
+constexpr int kLThreads = 256;  // threads per block
+constexpr int kLRows = 256;     // adjacent cells per tile (one per thread in phases 0 and 2)
+static_assert(kLThreads == kLRows, "phase 0 and 2 map thread i to row i");
 
-__constant__ int c_d3q19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},
-                                   {0, 0, 1},  {0, 0, -1},  {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},
-                                   {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
-                                   {0, 1, 1},  {0, -1, -1}, {0, 1, -1},  {0, -1, 1}};
 __constant__ int c_d2q9[9][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}, {1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
 
-// D3Q19 direction i (1..18), component a, as a compile-time constant when i and
-// a are: 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = xy, xz, yz plane diagonals, each
-// (+,+),(-,-),(+,-),(-,+).
+// D3Q19 direction i (1..18), component a: 1..6 = +x,-x,+y,-y,+z,-z; 7..18 =
+// the xy, xz and yz plane diagonals, each as (+,+), (-,-), (+,-), (-,+).
 __host__ __device__ constexpr int d3q19_c(int i, int a) {
-  return i <= 6 ? (((i - 1) >> 1) == a ? ((i & 1) ? 1 : -1) : 0)
-                : ((((i - 7) >> 2) == 0 ? (a == 0 ? 1 : (a == 1 ? 2 : 0))
-                                        : (((i - 7) >> 2) == 1 ? (a == 0 ? 1 : (a == 2 ? 2 : 0))
-                                                               : (a == 1 ? 1 : (a == 2 ? 2 : 0)))) == 1
-                       ? ((((i - 7) & 3) == 0 || ((i - 7) & 3) == 2) ? 1 : -1)
-                       : ((((i - 7) >> 2) == 0 ? (a == 0 ? 1 : (a == 1 ? 2 : 0))
-                                               : (((i - 7) >> 2) == 1 ? (a == 0 ? 1 : (a == 2 ? 2 : 0))
-                                                                      : (a == 1 ? 1 : (a == 2 ? 2 : 0)))) == 2
-                              ? ((((i - 7) & 3) == 0 || ((i - 7) & 3) == 3) ? 1 : -1)
-                              : 0));
+  if (i <= 6) return ((i - 1) >> 1) == a ? ((i & 1) ? 1 : -1) : 0;
+  const int p = (i - 7) >> 2, j = (i - 7) & 3;
+  const int a1 = p == 2 ? 1 : 0;  // first axis of the plane
+  const int a2 = p == 0 ? 1 : 2;  // second axis
+  if (a == a1) return (j == 0 || j == 2) ? 1 : -1;
+  if (a == a2) return (j == 0 || j == 3) ? 1 : -1;
+  return 0;
 }
 static_assert(d3q19_c(1, 0) == 1 && d3q19_c(2, 0) == -1 && d3q19_c(5, 2) == 1 && d3q19_c(6, 2) == -1, "axes");
 static_assert(d3q19_c(7, 0) == 1 && d3q19_c(7, 1) == 1 && d3q19_c(8, 0) == -1 && d3q19_c(8, 1) == -1, "xy");
@@ -53,56 +47,9 @@ static_assert(d3q19_c(13, 0) == 1 && d3q19_c(13, 2) == -1 && d3q19_c(13, 1) == 0
 static_assert(d3q19_c(18, 1) == -1 && d3q19_c(18, 2) == 1 && d3q19_c(18, 0) == 0, "yz");
 
 __device__ __forceinline__ void d3q19_dir(int i, int& cx, int& cy, int& cz) {
-  cx = cy = cz = 0;
-  if (i <= 6) {
-    const int s = (i & 1) ? 1 : -1;
-    const int ax = (i - 1) >> 1;
-    if (ax == 0) cx = s;
-    else if (ax == 1) cy = s;
-    else cz = s;
-    return;
-  }
-  const int p = (i - 7) >> 2, j = (i - 7) & 3;
-  const int s1 = (j == 0 || j == 2) ? 1 : -1;
-  const int s2 = (j == 0 || j == 3) ? 1 : -1;
-  if (p == 0) {
-    cx = s1;
-    cy = s2;
-  } else if (p == 1) {
-    cx = s1;
-    cz = s2;
-  } else {
-    cy = s1;
-    cz = s2;
-  }
-}
-
-// Directions whose link segment box [0, c h] can meet the face's box (the hit
-// point lies in both): per axis the face must straddle 0 (c_a = 0), reach
-// [0, h] (c_a = +1) or [-h, 0] (c_a = -1), with a tolerance for the rounding
-// of the local coordinates.  Bit i-1 set = direction i may hit.
-__device__ __forceinline__ uint32_t d3q19_candidates(const float (*p)[3], float h) {
-  bool z[3], pos[3], neg[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float mn = fminf(fminf(p[0][a], p[1][a]), p[2][a]);
-    const float mx = fmaxf(fmaxf(p[0][a], p[1][a]), p[2][a]);
-    const float tol = 8.0f * kU32 * (fmaxf(fabsf(mn), fabsf(mx)) + h);
-    z[a] = mn <= tol && mx >= -tol;
-    pos[a] = mx >= -tol && mn <= h + tol;
-    neg[a] = mn <= tol && mx >= -h - tol;
-  }
-  uint32_t m = 0;
-#pragma unroll
-  for (int i = 1; i <= 18; ++i) {
-    int c[3];
-    d3q19_dir(i, c[0], c[1], c[2]);
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ok = ok && (c[a] == 0 ? z[a] : (c[a] > 0 ? pos[a] : neg[a]));
-    m |= ok ? (1u << (i - 1)) : 0u;
-  }
-  return m;
+  cx = d3q19_c(i, 0);
+  cy = d3q19_c(i, 1);
+  cz = d3q19_c(i, 2);
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -190,15 +137,83 @@ __device__ __noinline__ LinkHit link_fp64_2(const float* V, const double* xc, co
   return r;
 }
 
+// Sort key of a hit: the FP32 bits of t >= 0 order like t, the face id breaks ties.
+__device__ __forceinline__ unsigned long long hit_key(float t, uint32_t f) {
+  if (!(t > 0.0f)) t = 0.0f;  // also maps -0 to +0
+  return ((unsigned long long)__float_as_uint(t) << 32) | f;
+}
+
+// The D3Q19 tests of one (cell, face) pair.  p = vertex offsets from the cell
+// centre (rounded double-float differences), num = n.(v0 - x) with error
+// bound eps_num, C_k = p_{k+1} x p_{k+2} with magnitude bounds M_k.  Per
+// direction: den = c.n (exact for an axis, one TwoSum for a diagonal), then the
+// certified range test 0 < t < 1 (t = num / (h den)) without a division, then
+// the three edge signs sg c.C_k.  Hits go to the shared minimum; undecided
+// directions come back as bits of the returned mask.
+template <int DI>
+__device__ __forceinline__ void link_dir3(const float (&nh)[3], const float (&nl)[3], float num, float eps_num,
+                                          const float (&C)[3][3], const float (&M)[3], float nn2, float h32,
+                                          uint32_t f, unsigned long long* key, uint32_t& fb) {
+  constexpr int cx = d3q19_c(DI, 0), cy = d3q19_c(DI, 1), cz = d3q19_c(DI, 2);
+  constexpr int cl = (cx != 0) + (cy != 0) + (cz != 0);
+  float dh, dl;
+  if constexpr (cl == 1) {
+    dh = cx * nh[0] + cy * nh[1] + cz * nh[2];
+    dl = cx * nl[0] + cy * nl[1] + cz * nl[2];
+  } else {
+    float e2;
+    two_sum(cx != 0 ? cx * nh[0] : cy * nh[1], cz != 0 ? cz * nh[2] : cy * nh[1], dh, e2);
+    dl = e2 + (cx * nl[0] + cy * nl[1] + cz * nl[2]);
+  }
+  const float den = dh + dl;
+  if (den == 0.0f && dh == 0.0f) return;  // c_i parallel to the face plane: no hit
+  const float ad = fabsf(den);
+  const float sg = den > 0.f ? 1.f : -1.f;
+  const bool unc = ad <= (cl == 1 ? 1e-5f : 1.41421356e-5f) * nn2;
+  const float sn = sg * num, hd = h32 * ad;
+  // certified t < 0 or t > 1 (h32 * |den| is within 8u of h |den| when den is not tiny)
+  if (!unc && (sn < -eps_num || sn - eps_num > hd * (1.0f + 8.0f * kU32))) return;
+  bool out = false, all_in = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float u = sg * (cx * C[k][0] + cy * C[k][1] + cz * C[k][2]);
+    const float eu = 8.0f * kU32 * (float)cl * M[k];
+    if (u < -eu) out = true;
+    if (!(u > eu)) all_in = false;
+  }
+  if (out && !unc) return;
+  if (!unc && all_in && sn > eps_num && sn + eps_num < hd * (1.0f - 8.0f * kU32)) {
+    atomicMin(key + (DI - 1) * kLRows, hit_key(num / (h32 * den), f));
+  } else {
+    fb |= 1u << (DI - 1);
+  }
+}
+
+template <int... DI>
+__device__ __forceinline__ void link_dirs3(std::integer_sequence<int, DI...>, const float (&nh)[3],
+                                           const float (&nl)[3], float num, float eps_num, const float (&C)[3][3],
+                                           const float (&M)[3], float nn2, float h32, uint32_t f,
+                                           unsigned long long* key, uint32_t& fb) {
+  (link_dir3<DI + 1>(nh, nl, num, eps_num, C, M, nn2, h32, f, key, fb), ...);
+}
+
+// Links of one tile of kLRows adjacent cells.  Phase 0: per row, the cell
+// centre (double-float) and the row's slice of the pair list.  Phase 1: one
+// thread per (cell, face) pair evaluates every lattice direction and keeps, per
+// (cell, direction), the minimum of (t, face) in shared memory.  Phase 2: one
+// thread per row counts its links; a block scan plus the ticketed look-back
+// give the output position, in (cell, direction) order.
 template <int D>
-__global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state, unsigned* ticket) {
+__global__ void __launch_bounds__(kLThreads, 2) k_links(LinkArgs a, uint64_t* state, unsigned* ticket) {
   constexpr int Q1 = D == 3 ? 18 : 8;
   constexpr int NC = D == 3 ? 64 : 16;
-  __shared__ unsigned s_tile;
-  __shared__ float s_q[Q1][kLThreads];
-  __shared__ uint32_t s_f[Q1][kLThreads];
+  __shared__ unsigned long long s_key[Q1][kLRows];
+  __shared__ uint32_t s_off[kLRows + 1];
+  __shared__ float s_o[2 * D][kLRows];
+  __shared__ float s_h[kLRows];
   __shared__ uint32_t s_warp[kLThreads / 32];
   __shared__ uint64_t s_prefix;
+  __shared__ unsigned s_tile;
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const uint64_t row0 = a.run ? a.run[0] : 0ull;
@@ -208,102 +223,124 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
     if (blockIdx.x == 0 && tid == 0) atomicOr(a.err, ERR_OVERFLOW);
     nrows = a.cap_rows - (int64_t)row0 > 0 ? a.cap_rows - (int64_t)row0 : 0;
   }
-  const int64_t ntiles = (nrows + kLThreads - 1) / kLThreads;
+  const int64_t ntiles = (nrows + kLRows - 1) / kLRows;
   if (ntiles == 0) {
     if (blockIdx.x == 0 && tid == 0) *a.n_links = 0;
     return;
   }
   unsigned long long n_fb = 0, n_band = 0;
   for (;;) {
-  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
-  __syncthreads();
-  const long long tile = s_tile;
-  if (tile >= ntiles) break;
-  const int64_t local = tile * (int64_t)kLThreads + tid;
-  const int64_t row = (int64_t)row0 + local;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= ntiles) break;
+    const int64_t first = (int64_t)row0 + tile * (int64_t)kLRows;
+    const int nr = (int)(nrows - tile * (int64_t)kLRows < kLRows ? nrows - tile * (int64_t)kLRows : kLRows);
+    // phase 0 (kLThreads == kLRows: thread i owns row i)
+    {
+      const int i = tid;
+      s_off[i] = a.adj_off[first + (i < nr ? i : nr)];
+      if (i == 0) s_off[kLRows] = a.adj_off[first + nr];
 #pragma unroll
-  for (int i = 0; i < Q1; ++i) {
-    s_q[i][tid] = INFINITY;
-    s_f[i][tid] = 0xffffffffu;
-  }
-  if (local < nrows) {
-    const uint32_t id = a.adj_cell[row];
-    const uint32_t blk = id / NC, bit = id % NC;
-    const GeomParams& P = a.table ? a.table[a.gid ? a.gid[blk] : 0u] : a.g0;
-    const FastGeom g = fast_geom(P, a.level);
-    // cell centre origin + (2 c + 1) (h/2) as hi + lo; the FP64 centre only for fallbacks
-    double xc[3] = {0, 0, 0};
-    float ohi[3] = {0, 0, 0}, olo[3] = {0, 0, 0};
-    const double hL = scalbn(P.h0, -a.level);
+      for (int q = 0; q < Q1; ++q) s_key[q][i] = ~0ull;
+      if (i < nr) {
+        const uint32_t id = a.adj_cell[first + i];
+        const uint32_t blk = id / NC, bit = id % NC;
+        const GeomParams& P = a.table ? a.table[a.gid ? a.gid[blk] : 0u] : a.g0;
+        const FastGeom g = fast_geom(P, a.level);
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const int gc = 4 * a.blocks[(int64_t)blk * D + c] + (int)((bit >> (2 * c)) & 3u);
-      df_position(P.org_hi[c], P.org_lo[c], (float)(2 * gc + 1), 0.5f * g.h_hi, 0.5f * g.h_lo, ohi[c], olo[c]);
-      xc[c] = D == 3 ? 0.0 : __dadd_rn(P.origin[c], __dmul_rn((double)gc + 0.5, hL));
+        for (int c = 0; c < D; ++c) {
+          const int gc = 4 * a.blocks[(int64_t)blk * D + c] + (int)((bit >> (2 * c)) & 3u);
+          df_position(P.org_hi[c], P.org_lo[c], (float)(2 * gc + 1), 0.5f * g.h_hi, 0.5f * g.h_lo, s_o[c][i],
+                      s_o[D + c][i]);
+        }
+        s_h[i] = g.h_hi;
+      }
     }
-    const float h32 = g.h_hi;
-    struct GeomView {
-      double h;
-    } G{hL};
-    const uint32_t e0 = a.adj_off[row], e1 = a.adj_off[row + 1];
-    for (uint32_t e = e0; e < e1; ++e) {
+    __syncthreads();
+    // phase 1: one thread per (cell, face) pair
+    // (the clamp only matters after an overflow, which the host reports)
+    const uint32_t p0 = s_off[0];
+    const uint32_t p1 = (int64_t)s_off[nr] <= a.cap_pairs ? s_off[nr] : (uint32_t)a.cap_pairs;
+    for (uint32_t e = p0 + (uint32_t)tid; e < p1; e += kLThreads) {
+      int lo = 0, hi = nr;  // s_off[lo] <= e < s_off[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= e)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      const int r = lo;
       const uint32_t f = a.adj_ids[e];
-      float V[D * D];
-#pragma unroll
-      for (int j = 0; j < D * D; ++j) V[j] = a.X[(int64_t)j * a.nf + f];
+      if ((int64_t)f >= a.nf) continue;
       if constexpr (D == 2) {
-        // 2D workloads are small: evaluate every link in FP64
+        // 2D workloads are small: every link in FP64
+        const uint32_t id = a.adj_cell[first + r];
+        const uint32_t blk = id / NC, bit = id % NC;
+        const GeomParams& P = a.table ? a.table[a.gid ? a.gid[blk] : 0u] : a.g0;
+        const double hL = scalbn(P.h0, -a.level);
+        double xc[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int gc = 4 * a.blocks[(int64_t)blk * 2 + c] + (int)((bit >> (2 * c)) & 3u);
+          xc[c] = __dadd_rn(P.origin[c], __dmul_rn((double)gc + 0.5, hL));
+        }
+        float V[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) V[j] = a.X[(int64_t)j * a.nf + f];
 #pragma unroll
         for (int di = 1; di <= Q1; ++di) {
           const int ci[2] = {c_d2q9[di][0], c_d2q9[di][1]};
-          const LinkHit r = link_fp64_2(V, xc, ci, G.h);
-          if (r.band) ++n_band;
-          if (r.hit) {
-            const float t = (float)r.t;
-            if (t < s_q[di - 1][tid]) {
-              s_q[di - 1][tid] = t;
-              s_f[di - 1][tid] = f;
-            }
-          }
+          const LinkHit h = link_fp64_2(V, xc, ci, hL);
+          if (h.band) ++n_band;
+          if (h.hit) atomicMin(&s_key[di - 1][r], hit_key((float)h.t, f));
         }
       } else {
+        const float4* R = reinterpret_cast<const float4*>(a.rec + f);
+        const float4 r0 = __ldg(R), r1 = __ldg(R + 1), r2 = __ldg(R + 2), r3 = __ldg(R + 3);
+        const float V[9] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x};
+        const float nh[3] = {r2.y, r2.z, r2.w};
+        const float nl[3] = {r3.x, r3.y, r3.z};
+        const float ohi[3] = {s_o[0][r], s_o[1][r], s_o[2][r]};
+        const float olo[3] = {s_o[3][r], s_o[4][r], s_o[5][r]};
+        const float h32 = s_h[r];
         // vertex offsets from the cell centre: p = (V - ohi) - olo as hi + lo
-        float ph[3][3], pl[3][3], p[3][3];
+        float ph0[3], pl0[3], p[3][3];
         float pmax = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            float s, err;
-            two_sum(V[3 * k + c], -ohi[c], s, err);
-            ph[k][c] = s;
-            pl[k][c] = err - olo[c];
-            p[k][c] = s + pl[k][c];
+            float sm, err;
+            two_sum(V[3 * k + c], -ohi[c], sm, err);
+            const float l = err - olo[c];
+            if (k == 0) {
+              ph0[c] = sm;
+              pl0[c] = l;
+            }
+            p[k][c] = sm + l;
             pmax = fmaxf(pmax, fabsf(p[k][c]));
           }
-        uint32_t cand = d3q19_candidates(p, h32);
-        if (!cand) continue;
-        const float nh[3] = {a.nrm[f], a.nrm[a.nf + f], a.nrm[2 * a.nf + f]};
-        const float nl[3] = {a.nrm[3 * a.nf + f], a.nrm[4 * a.nf + f], a.nrm[5 * a.nf + f]};
         // num = n . (v0 - x) in double-float
         float ns, ne;
-        two_prod(nh[0], ph[0][0], ns, ne);
+        two_prod(nh[0], ph0[0], ns, ne);
 #pragma unroll
         for (int c = 1; c < 3; ++c) {
-          float pp, pe, s, t;
-          two_prod(nh[c], ph[0][c], pp, pe);
-          two_sum(ns, pp, s, t);
-          ns = s;
+          float pp, pe, sm, t;
+          two_prod(nh[c], ph0[c], pp, pe);
+          two_sum(ns, pp, sm, t);
+          ns = sm;
           ne += t + pe;
         }
-        float n1 = fabsf(nh[0]) + fabsf(nh[1]) + fabsf(nh[2]);
+        const float n1 = fabsf(nh[0]) + fabsf(nh[1]) + fabsf(nh[2]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ne = fmaf(nh[c], pl[0][c], fmaf(nl[c], ph[0][c], ne));
+        for (int c = 0; c < 3; ++c) ne = fmaf(nh[c], pl0[c], fmaf(nl[c], ph0[c], ne));
         const float num = ns + ne;
         const float xmax = fmaxf(fmaxf(fabsf(ohi[0]), fabsf(ohi[1])), fabsf(ohi[2]));
         const float eps_num = 16.0f * kU32 * kU32 * n1 * (xmax + pmax) + 4.0f * kU32 * fabsf(ne);
-        // edge cross products C_k = p_a x p_b, (a,b) = (1,2),(2,0),(0,1), and their magnitudes
-        // and the largest component magnitude bound Mk = max_c (|A_a B_b| + |A_b B_a|)
+        // edge cross products C_k = p_a x p_b, (a,b) = (1,2),(2,0),(0,1), and the
+        // largest component magnitude bound M_k = max_c (|A_a B_b| + |A_b B_a|)
         float C[3][3], M[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -316,106 +353,70 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
                        fabsf(A[0] * B[1]) + fabsf(A[1] * B[0]));
         }
         const float nn2 = sqrtf(nh[0] * nh[0] + nh[1] * nh[1] + nh[2] * nh[2]);
-#pragma unroll
-        for (int di = 1; di <= 18; ++di) {
-          const int cx = d3q19_c(di, 0), cy = d3q19_c(di, 1), cz = d3q19_c(di, 2);
-          if (!((cand >> (di - 1)) & 1u)) continue;
-          // den_n = c . n in double-float: exact for an axis direction, one TwoSum for a diagonal
-          const float t0 = cx * nh[0], t1 = cy * nh[1], t2 = cz * nh[2];
-          const int cl_i = (cx != 0) + (cy != 0) + (cz != 0);
-          float dh, dl;
-          if (cl_i == 1) {
-            dh = t0 + t1 + t2;
-            dl = cx * nl[0] + cy * nl[1] + cz * nl[2];
-          } else {
-            float e2;
-            two_sum(cx != 0 ? t0 : t1, cz != 0 ? t2 : t1, dh, e2);
-            dl = e2 + (cx * nl[0] + cy * nl[1] + cz * nl[2]);
-          }
-          const float den = dh + dl;
-          if (den == 0.0f && dh == 0.0f) continue;  // c_i parallel to the face plane: no hit
-          const float sg = den > 0.f ? 1.f : -1.f;
-          // inside test: sg * (c . C_k) >= 0 for k = 0..2
-          bool out = false, unc = fabsf(den) <= (cl_i == 1 ? 1e-5f : 1.41421356e-5f) * nn2;
-          bool all_in = true;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const float u = sg * (cx * C[k][0] + cy * C[k][1] + cz * C[k][2]);
-            const float eu = 8.0f * kU32 * (float)cl_i * M[k];
-            if (u < -eu) out = true;
-            if (!(u > eu)) all_in = false;
-          }
-          if (out && !unc) continue;
-          float t = 0.f;
-          bool hit = false;
-          if (!unc && all_in) {
-            // t = num / (h den): range [0,1] with certified ends
-            const float sn = sg * num;
-            t = num / (h32 * den);
-            if (sn < -eps_num || t > 1.0f + 8.0f * kU32) continue;
-            if (sn > eps_num && t < 1.0f - 8.0f * kU32) {
-              hit = true;
-            } else {
-              unc = true;
-            }
-          } else {
-            unc = true;
-          }
-          if (unc) {
-            const LinkHit r = link_fallback_3(V, a.blocks + (int64_t)blk * 3, bit, P.origin, G.h, di);
+        uint32_t fb = 0;
+        link_dirs3(std::make_integer_sequence<int, 18>{}, nh, nl, num, eps_num, C, M, nn2, h32, f, &s_key[0][r],
+                   fb);
+        // undecided signs: FP64 evaluation from the FP64 cell centre
+        if (fb) {
+          const uint32_t id = a.adj_cell[first + r];
+          const uint32_t blk = id / NC, bit = id % NC;
+          const GeomParams& P = a.table ? a.table[a.gid ? a.gid[blk] : 0u] : a.g0;
+          const double o3[3] = {P.origin[0], P.origin[1], P.origin[2]};
+          const double hL = scalbn(P.h0, -a.level);
+          for (; fb; fb &= fb - 1) {
+            const int di = __ffs(fb);
+            const LinkHit h = link_fallback_3(V, a.blocks + (int64_t)blk * 3, bit, o3, hL, di);
             ++n_fb;
-            if (r.band) ++n_band;
-            if (!r.hit) continue;
-            hit = true;
-            t = (float)r.t;
-          }
-          if (hit && t < s_q[di - 1][tid]) {
-            s_q[di - 1][tid] = t;
-            s_f[di - 1][tid] = f;
+            if (h.band) ++n_band;
+            if (h.hit) atomicMin(&s_key[di - 1][r], hit_key((float)h.t, f));
           }
         }
       }
     }
-  }
-  uint32_t hits = 0;
+    __syncthreads();
+    // phase 2: compaction in (cell, direction) order
+    uint32_t hits = 0;
+    if (tid < nr) {
 #pragma unroll
-  for (int i = 0; i < Q1; ++i) hits += s_f[i][tid] != 0xffffffffu ? 1u : 0u;
-  // block scan of per-cell link counts, then look-back for the global offset
-  const uint32_t incl = warp_inclusive_scan<uint32_t>(hits);
-  if (lane == 31) s_warp[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t w = lane < kLThreads / 32 ? s_warp[lane] : 0u;
-    w = warp_inclusive_scan<uint32_t>(w);
-    if (lane < kLThreads / 32) s_warp[lane] = w;
-  }
-  __syncthreads();
-  const uint32_t wex = wid > 0 ? s_warp[wid - 1] : 0u;
-  if (tid == 0) {
-    const uint64_t agg = s_warp[kLThreads / 32 - 1];
-    const uint64_t pre = lookback_exclusive(state, tile, agg, a.err);
-    s_prefix = pre;
-    if (tile == ntiles - 1) {
-      *a.n_links = pre + agg;
-      if ((int64_t)(link0 + pre + agg) > a.link_cap) atomicOr(a.err, ERR_OVERFLOW);
+      for (int q = 0; q < Q1; ++q) hits += s_key[q][tid] != ~0ull ? 1u : 0u;
     }
-  }
-  __syncthreads();
-  uint64_t pos = link0 + s_prefix + wex + incl - hits;
-#pragma unroll
-  for (int i = 0; i < Q1; ++i) {
-    const uint32_t f = s_f[i][tid];
-    if (f != 0xffffffffu) {
-      if ((int64_t)pos < a.link_cap) {
-        a.link_cell[pos] = (uint32_t)row;
-        a.link_dir[pos] = (uint8_t)(i + 1);
-        a.link_q[pos] = s_q[i][tid];
-        a.link_face[pos] = f;
+    const uint32_t incl = warp_inclusive_scan<uint32_t>(hits);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t w = lane < kLThreads / 32 ? s_warp[lane] : 0u;
+      w = warp_inclusive_scan<uint32_t>(w);
+      if (lane < kLThreads / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t wex = wid > 0 ? s_warp[wid - 1] : 0u;
+    if (tid == 0) {
+      const uint64_t agg = s_warp[kLThreads / 32 - 1];
+      const uint64_t pre = lookback_exclusive(state, tile, agg, a.err);
+      s_prefix = pre;
+      if (tile == ntiles - 1) {
+        *a.n_links = pre + agg;
+        if ((int64_t)(link0 + pre + agg) > a.link_cap) atomicOr(a.err, ERR_OVERFLOW);
       }
-      ++pos;
     }
-  }
-  __syncthreads();
+    __syncthreads();
+    uint64_t pos = link0 + s_prefix + wex + incl - hits;
+    if (hits) {
+#pragma unroll
+      for (int q = 0; q < Q1; ++q) {
+        const unsigned long long k = s_key[q][tid];
+        if (k != ~0ull) {
+          if ((int64_t)pos < a.link_cap) {
+            a.link_cell[pos] = (uint32_t)(first + tid);
+            a.link_dir[pos] = (uint8_t)(q + 1);
+            a.link_q[pos] = __uint_as_float((uint32_t)(k >> 32));
+            a.link_face[pos] = (uint32_t)k;
+          }
+          ++pos;
+        }
+      }
+    }
+    __syncthreads();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -450,15 +451,25 @@ __global__ void k_advance(const uint64_t* level_tot, const uint64_t* n_links, ui
 }  // namespace
 
 size_t links_scratch_bytes(int64_t n_adj) {
-  const int64_t tiles = (n_adj + kLThreads - 1) / kLThreads;
+  const int64_t tiles = (n_adj + kLRows - 1) / kLRows;
   return 16 + (size_t)(tiles > 0 ? tiles : 1) * 8;
 }
 
 int launch_links(const LinkArgs& a, void* scratch, int num_sms, cudaStream_t st) {
   cudaMemsetAsync(scratch, 0, links_scratch_bytes(a.cap_rows), st);
-  int64_t tiles = (a.cap_rows + kLThreads - 1) / kLThreads;
+  // persistent: as many blocks as fit on the GPU at once, tiles handed out by ticket
+  static int occ[2] = {0, 0};
+  int& o = occ[a.dim == 3 ? 1 : 0];
+  if (o == 0) {
+    if (a.dim == 3)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_links<3>, kLThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_links<2>, kLThreads, 0);
+    if (o < 1) o = 1;
+  }
+  int64_t tiles = (a.cap_rows + kLRows - 1) / kLRows;
   if (tiles < 1) tiles = 1;
-  if (tiles > (int64_t)num_sms * 12) tiles = (int64_t)num_sms * 12;
+  if (tiles > (int64_t)num_sms * o) tiles = (int64_t)num_sms * o;
   unsigned* ticket = reinterpret_cast<unsigned*>(scratch);
   uint64_t* state = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 16);
   if (a.dim == 3)
