@@ -45,7 +45,7 @@ struct TimingSlot {
 };
 
 struct LevelBufs {
-  DevBuf blocks, gid, parent, mask, flag, cellcnt, blockcnt, base;
+  DevBuf blocks, gid, parent, mask, flag, cellcnt, blockcnt, base, desc;
   int64_t cap = 0;  // capacity in blocks
 };
 
@@ -54,7 +54,8 @@ constexpr int SC_N = 0;      // [16] blocks per level
 constexpr int SC_TOT = 16;   // [16] adjacency totals per level (pairs | cells << 32)
 constexpr int SC_NL = 32;    // [16] links per level
 constexpr int SC_RUN = 48;   // [3] running cells, pairs, links
-constexpr int SC_WORDS = 64;
+constexpr int SC_REC = 52;   // [16] survivor records handed out per level
+constexpr int SC_WORDS = 72;
 
 // A captured graph stays valid while no buffer it uses was reallocated
 // (layout generation) and its by-value kernel arguments are unchanged.
@@ -94,10 +95,11 @@ struct amr_ctx {
   bool multi = false;
   DevBuf table, face_gid;
   // buffers
-  DevBuf X, nrm, frec, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
+  DevBuf X, nrm, frec, recs, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
   LevelBufs lv[AMR_MAX_LEVELS];
   DevBuf adj_cell, adj_off, adj_ids, link_cell, link_dir, link_q, link_face;
   int64_t cap_cells = 0, cap_pairs = 0, cap_links = 0;
+  int64_t cap_recs = 0, want_recs = 0;  // survivor record staging (entries)
   // adjoint
   DevBuf idx, vert_off, vert_corners, face_off, face_links, sort_keys, grad_face, sort_scratch, group_cnt, lvl_ptrs;
   bool vert_groups = false, face_groups = false;
@@ -108,7 +110,7 @@ struct amr_ctx {
   unsigned* d_work = nullptr;
   uint64_t* d_tot = nullptr;
   uint64_t* d_scal = nullptr;
-  void* h_pinned = nullptr;  // 1 KB
+  void* h_pinned = nullptr;  // 2 KB
   amr_refine_result last{};
   // graph mode
   cudaGraphExec_t gexec = nullptr;
@@ -361,7 +363,7 @@ amr_status amr_ctx_init(amr_ctx* ctx) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 1024);
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 2048);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return AMR_ECUDA;
@@ -382,7 +384,7 @@ amr_status amr_ctx_init(amr_ctx* ctx) {
 void amr_ctx_free(amr_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   drop_graph(ctx);
-  DevBuf* all[] = {&ctx->X, &ctx->frec, &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
+  DevBuf* all[] = {&ctx->X, &ctx->frec, &ctx->recs, &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
                    &ctx->count,     &ctx->offsets,      &ctx->ids,        &ctx->payload,    &ctx->scratch,
                    &ctx->misc,      &ctx->scal,         &ctx->adj_cell,   &ctx->adj_off,    &ctx->adj_ids,
                    &ctx->link_cell, &ctx->link_dir,     &ctx->link_q,     &ctx->link_face,  &ctx->idx,
@@ -522,6 +524,10 @@ RefineLevel level_args(amr_ctx* ctx, const Plan& P, int L) {
   if (P.fin_at[L] && P.adjacency) {
     a.cellcnt = static_cast<uint16_t*>(ctx->lv[L].cellcnt.p);
     a.blockcnt = static_cast<uint64_t*>(ctx->lv[L].blockcnt.p);
+    a.recs = static_cast<SurvRec*>(ctx->recs.p);
+    a.cap_recs = ctx->cap_recs;
+    a.rec_count = ctx->d_scal + SC_REC + L;
+    a.rec_desc = static_cast<uint64_t*>(ctx->lv[L].desc.p);
   }
   a.counters = ctx->counters;
   a.work = ctx->d_work;
@@ -570,6 +576,13 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st)
         TRY(ensure(ctx, lb.cellcnt, sizeof(uint16_t) * NCell * n1));
         TRY(ensure(ctx, lb.blockcnt, sizeof(uint64_t) * n1));
         TRY(ensure(ctx, lb.base, sizeof(uint64_t) * n1));
+        TRY(ensure(ctx, lb.desc, sizeof(uint64_t) * n1));
+        // record staging: what the last pass needed, at least a few per block
+        int64_t want = ctx->want_recs > 4 * N + 1024 ? ctx->want_recs : 4 * N + 1024;
+        if (want > ctx->cap_recs) {
+          TRY(ensure(ctx, ctx->recs, sizeof(SurvRec) * (size_t)want));
+          ctx->cap_recs = want;
+        }
       }
     }
     RefineLevel a = level_args(ctx, P, L);
@@ -742,6 +755,10 @@ amr_status collect(amr_ctx* ctx, const Plan& P, cudaStream_t st, amr_refine_resu
   amr_refine_result r{};
   r.n_levels = P.NL;
   for (int L = 0; L < P.NL; ++L) {
+    // record staging that overflowed (those blocks were re-walked): grow it on the next eager pass
+    const int64_t nrec = (int64_t)sc[SC_REC + L];
+    if (P.adjacency && P.fin_at[L] && nrec > ctx->cap_recs && nrec + nrec / 4 + 1024 > ctx->want_recs)
+      ctx->want_recs = nrec + nrec / 4 + 1024;
     r.n_blocks[L] = (int64_t)sc[SC_N + L];
     r.block_coords[L] = static_cast<const int32_t*>(ctx->lv[L].blocks.p);
     r.block_parent[L] = L > 0 ? static_cast<const int32_t*>(ctx->lv[L].parent.p) : nullptr;
@@ -807,6 +824,7 @@ amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine
     const amr_status s = collect(ctx, P, ctx->stream, &r);
     if (s == AMR_OK) {
       *out = r;
+      if (ctx->want_recs > ctx->cap_recs) drop_graph(ctx);  // next call: eager pass with more staging
       return AMR_OK;
     }
     if (s != AMR_EOVERFLOW) return s;

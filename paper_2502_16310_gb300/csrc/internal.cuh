@@ -337,6 +337,15 @@ size_t scan_u64_scratch_bytes(int64_t n);
 int launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, const uint64_t* n_dev, uint64_t* total,
                     void* scratch, unsigned* err, int num_sms, cudaStream_t st);
 
+// Survivor record of a block whose geometry ends at its level: a face that
+// meets some cell of the block and the mask of those cells (bit i = cell i).
+struct __align__(16) SurvRec {
+  uint32_t face;
+  uint32_t pad;
+  uint64_t cells;
+};
+constexpr int kRecCap = 64;  // records kept per block; more send the block to a full re-walk
+
 struct RefineLevel {
   int dim;
   int level;
@@ -355,6 +364,10 @@ struct RefineLevel {
   uint8_t* flag;
   uint16_t* cellcnt;           // per cell face count, blocks whose geometry ends at this level
   uint64_t* blockcnt;          // per block pairs | adjacent cells << 32 (0 for the others)
+  SurvRec* recs;               // survivor records (nullable), capacity cap_recs
+  int64_t cap_recs;
+  uint64_t* rec_count;         // device: records handed out on this level
+  uint64_t* rec_desc;          // per block: offset << 8 | count, or ~0 (records incomplete)
   unsigned long long* counters;
   unsigned* work;              // dynamic work counter (zeroed before launch)
   unsigned* err;

@@ -287,8 +287,11 @@ __device__ __noinline__ bool resolve_fp64(const RefineLevel& a, uint32_t gid, ui
 }
 
 // Shared walk of one block: bins of the query box, canonical-bin dedup,
-// block-level cull, cell tests.  `on_hit(cellslot, face)` is called for every
-// intersecting (cell, face) pair; cellslot 0 = cell `lane`, 1 = cell `lane + 32`.
+// block-level cull, cell tests.  For every surviving face the whole warp calls
+// `on_surv(face, r0, r1)`, r0 / r1 = whether the face meets the lane's cell
+// `lane` / `lane + 32`; h0 / h1 accumulate them.  kMarkOnly: only the mask is
+// wanted, so marked cells skip further tests and the walk ends as soon as every
+// cell of the block is marked.
 //
 // The block frame is built in FP32 from the geometry row's double-float h0 and
 // origin: the block corner origin + 4 b h is formed as hi + lo (hi = the frame
@@ -303,6 +306,8 @@ struct WarpSmem {
   Surv<D> surv[32];
   typename EntryT<D>::type buf[2][32];
   uint64_t bar[2];
+  uint64_t rm[kRecCap];  // survivor records of the block: cell-hit masks ...
+  uint32_t rf[kRecCap];  // ... and face ids
 };
 
 template <int D>
@@ -361,8 +366,11 @@ __device__ __forceinline__ bool next_chunk(ChunkCursor& c, const uint32_t* offse
 }
 
 // Shared walk of one block: bins of the query box, canonical-bin dedup,
-// block-level cull, cell tests.  `on_hit(cellslot, face)` is called for every
-// intersecting (cell, face) pair; cellslot 0 = cell `lane`, 1 = cell `lane + 32`.
+// block-level cull, cell tests.  For every surviving face the whole warp calls
+// `on_surv(face, r0, r1)`, r0 / r1 = whether the face meets the lane's cell
+// `lane` / `lane + 32`; h0 / h1 accumulate them.  kMarkOnly: only the mask is
+// wanted, so marked cells skip further tests and the walk ends as soon as every
+// cell of the block is marked.
 //
 // The block frame is built in FP32 from the geometry row's double-float h0 and
 // origin: the block corner origin + 4 b h is formed as hi + lo (hi = the frame
@@ -374,10 +382,10 @@ __device__ __forceinline__ bool next_chunk(ChunkCursor& c, const uint32_t* offse
 // Bin entries arrive in shared memory by TMA bulk copies, chunk by chunk
 // (<= 32 entries of one bin), double-buffered: lane 0 issues the copy of the
 // next chunk before the warp tests the current one.
-template <int D, typename OnHit>
+template <int D, bool kMarkOnly, typename OnSurv>
 __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParams& P, uint32_t gid, const int* b,
-                                           WarpSmem<D>& sm, uint32_t& phase, int lane, WarpCounters& wc,
-                                           OnHit on_hit) {
+                                           WarpSmem<D>& sm, uint32_t& phase, int lane, WarpCounters& wc, bool& h0,
+                                           bool& h1, OnSurv on_surv) {
   using E = typename EntryT<D>::type;
   const FastGeom g = fast_geom(P, a.level);
   const float hf = g.h_hi;
@@ -470,20 +478,31 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
       const int s = __ffs(m) - 1;
       m &= m - 1;
       const Surv<D>& S = sm.surv[s];
-      if (lane_cell) {
-        int r0 = cell_test<D>(S, o0);
-        if (r0 == 2) r0 = resolve_fp64<D>(a, gid, S.face, b, lane, &wc.fb, &wc.band) ? 1 : 0;
-        if (r0) on_hit(0, S.face);
-        if (D == 3) {
-          int r1 = cell_test<D>(S, o1);
-          if (r1 == 2) r1 = resolve_fp64<D>(a, gid, S.face, b, lane + 32, &wc.fb, &wc.band) ? 1 : 0;
-          if (r1) on_hit(1, S.face);
-        }
+      bool r0 = false, r1 = false;
+      if (lane_cell && !(kMarkOnly && h0)) {
+        int t = cell_test<D>(S, o0);
+        if (t == 2) t = resolve_fp64<D>(a, gid, S.face, b, lane, &wc.fb, &wc.band) ? 1 : 0;
+        r0 = t != 0;
       }
+      if (D == 3 && !(kMarkOnly && h1)) {
+        int t = cell_test<D>(S, o1);
+        if (t == 2) t = resolve_fp64<D>(a, gid, S.face, b, lane + 32, &wc.fb, &wc.band) ? 1 : 0;
+        r1 = t != 0;
+      }
+      h0 |= r0;
+      h1 |= r1;
+      on_surv(S.face, r0, r1);
     }
     __syncwarp();
     have = more;
     ++k;
+    // marking only: once every cell of the block is marked, the rest of the walk cannot change the mask
+    if (kMarkOnly && have && __all_sync(0xffffffffu, (h0 || !lane_cell) && (D == 2 || h1))) {
+      mbar_wait_bounded(&sm.bar[nb], (phase >> nb) & 1u, a.err);  // the copy already in flight
+      phase ^= 1u << nb;
+      __syncwarp();
+      break;
+    }
   }
 }
 
@@ -519,13 +538,52 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
     for (int c = 0; c < D; ++c) b[c] = a.blocks[(int64_t)blk * D + c];
     const uint32_t gid = a.gid ? a.gid[blk] : 0u;
     const GeomParams& P = a.table ? a.table[gid] : a.g0;
+    // per-cell face counts and survivor records only where the block's geometry ends here
+    const bool fin = a.blockcnt && a.level == P.n_levels - 1;
     uint32_t cnt0 = 0, cnt1 = 0;
-    walk_block<D>(a, P, gid, b, sm, phase, lane, wc, [&](int slot, uint32_t) {
-      if (slot == 0)
-        ++cnt0;
-      else
-        ++cnt1;
-    });
+    bool h0 = false, h1 = false;
+    if (fin) {
+      uint32_t K = 0;  // records of this block (warp-uniform)
+      walk_block<D, false>(a, P, gid, b, sm, phase, lane, wc, h0, h1, [&](uint32_t f, bool r0, bool r1) {
+        cnt0 += r0 ? 1u : 0u;
+        cnt1 += r1 ? 1u : 0u;
+        if (a.recs) {
+          const uint64_t cm = (uint64_t)__ballot_sync(0xffffffffu, r0) |
+                              ((uint64_t)__ballot_sync(0xffffffffu, r1) << 32);
+          if (cm) {
+            if (K < (uint32_t)kRecCap && lane == 0) {
+              sm.rf[K] = f;
+              sm.rm[K] = cm;
+            }
+            ++K;
+          }
+        }
+      });
+      if (a.recs) {
+        __syncwarp();
+        uint64_t base = ~0ull;
+        if (K > 0 && K <= (uint32_t)kRecCap) {
+          if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(a.rec_count), (unsigned long long)K);
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if ((int64_t)(base + K) > a.cap_recs) base = ~0ull;
+        }
+        if (base != ~0ull) {
+          for (uint32_t i = lane; i < K; i += 32) {
+            SurvRec r;
+            r.face = sm.rf[i];
+            r.pad = 0u;
+            r.cells = sm.rm[i];
+            a.recs[base + i] = r;
+          }
+        }
+        if (lane == 0) a.rec_desc[blk] = K == 0 ? 0ull : (base == ~0ull ? ~0ull : (base << 8) | K);
+        __syncwarp();
+      }
+    } else {
+      walk_block<D, true>(a, P, gid, b, sm, phase, lane, wc, h0, h1, [](uint32_t, bool, bool) {});
+      cnt0 = h0 ? 1u : 0u;
+      cnt1 = h1 ? 1u : 0u;
+    }
     const uint64_t mask = (uint64_t)__ballot_sync(0xffffffffu, cnt0 > 0) |
                           ((uint64_t)__ballot_sync(0xffffffffu, cnt1 > 0) << 32);
     const uint64_t m = D == 3 ? mask : (mask & 0xffffull);
@@ -534,8 +592,6 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
       a.flag[blk] = m != 0 ? 1 : 0;
     }
     if (a.blockcnt) {
-      // per-cell counts only where the block's geometry ends at this level
-      const bool fin = a.level == P.n_levels - 1;
       if (fin && a.cellcnt) {
         if (cnt0 > 0xffffu || cnt1 > 0xffffu) atomicOr(a.err, ERR_OVERFLOW);
         if (lane < NC) a.cellcnt[(int64_t)blk * NC + lane] = (uint16_t)min(cnt0, 0xffffu);
@@ -627,21 +683,68 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
     }
     uint32_t c0 = 0, c1 = 0;
     const bool can0 = (int64_t)(off0 + n0) <= a.cap_pairs, can1 = (int64_t)(off1 + n1) <= a.cap_pairs;
-    walk_block<D>(a.lv, P, gid, b, sm, phase, lane, wc, [&](int slot, uint32_t f) {
-      if (slot == 0) {
+    auto put = [&](bool r0, bool r1, uint32_t f) {
+      if (r0) {
         if (c0 < n0 && can0)
           a.adj_ids[off0 + c0] = f;
         else
           bad = true;
         ++c0;
-      } else {
+      }
+      if (r1) {
         if (c1 < n1 && can1)
           a.adj_ids[off1 + c1] = f;
         else
           bad = true;
         ++c1;
       }
-    });
+    };
+    const uint64_t desc = a.lv.recs ? a.lv.rec_desc[blk] : ~0ull;
+    if (desc != ~0ull) {
+      // the refine pass left this block's surviving faces with their cell masks:
+      // rank them by face id, then every lane lists its cells' faces in that order
+      const uint32_t K = (uint32_t)(desc & 0xffu);
+      const uint64_t r0 = desc >> 8;
+      uint32_t f[2] = {0xffffffffu, 0xffffffffu};
+      uint64_t cm[2] = {0ull, 0ull};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t i = (uint32_t)lane + 32u * h;
+        if (i < K) {
+          const SurvRec r = a.lv.recs[r0 + i];
+          f[h] = r.face;
+          cm[h] = r.cells;
+        }
+      }
+      uint32_t rank[2] = {0u, 0u};
+      for (uint32_t j = 0; j < K; ++j) {
+        const uint32_t fj = __shfl_sync(0xffffffffu, j < 32 ? f[0] : f[1], (int)(j & 31u));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t i = (uint32_t)lane + 32u * h;
+          rank[h] += (fj < f[h] || (fj == f[h] && j < i)) ? 1u : 0u;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t i = (uint32_t)lane + 32u * h;
+        if (i < K) {
+          sm.rf[rank[h]] = f[h];
+          sm.rm[rank[h]] = cm[h];
+        }
+      }
+      __syncwarp();
+      for (uint32_t j = 0; j < K; ++j) {
+        const uint64_t mj = sm.rm[j];
+        put(lane < NC && ((mj >> lane) & 1ull), D == 3 && ((mj >> (lane + 32)) & 1ull), sm.rf[j]);
+      }
+      __syncwarp();
+      if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
+      continue;
+    }
+    bool h0 = false, h1 = false;
+    walk_block<D, false>(a.lv, P, gid, b, sm, phase, lane, wc, h0, h1,
+                         [&](uint32_t fc, bool r0, bool r1) { put(r0, r1, fc); });
     if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
     if (!can0 || !can1) continue;
     // ascending face ids per cell (lists are short: insertion sort in place)
