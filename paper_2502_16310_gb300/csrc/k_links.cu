@@ -23,8 +23,8 @@ namespace amr {
 
 namespace {
 
-constexpr int kLThreads = 256;  // threads per block
-constexpr int kLRows = 256;     // adjacent cells per tile (one per thread in phases 0 and 2)
+constexpr int kLThreads = 128;  // threads per block
+constexpr int kLRows = 128;     // adjacent cells per tile (one per thread in phases 0 and 2)
 static_assert(kLThreads == kLRows, "phase 0 and 2 map thread i to row i");
 
 __constant__ int c_d2q9[9][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}, {1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
@@ -143,77 +143,73 @@ __device__ __forceinline__ unsigned long long hit_key(float t, uint32_t f) {
   return ((unsigned long long)__float_as_uint(t) << 32) | f;
 }
 
-// The D3Q19 tests of one (cell, face) pair.  p = vertex offsets from the cell
-// centre (rounded double-float differences), num = n.(v0 - x) with error
-// bound eps_num, C_k = p_{k+1} x p_{k+2} with magnitude bounds M_k.  Per
-// direction: den = c.n (exact for an axis, one TwoSum for a diagonal), then the
-// certified range test 0 < t < 1 (t = num / (h den)) without a division, then
-// the three edge signs sg c.C_k.  Hits go to the shared minimum; undecided
-// directions come back as bits of the returned mask.
-template <int DI>
-__device__ __forceinline__ void link_dir3(const float (&nh)[3], const float (&nl)[3], float num, float eps_num,
-                                          const float (&C)[3][3], const float (&M)[3], float nn2, float h32,
-                                          uint32_t f, unsigned long long* key, uint32_t& fb) {
-  constexpr int cx = d3q19_c(DI, 0), cy = d3q19_c(DI, 1), cz = d3q19_c(DI, 2);
-  constexpr int cl = (cx != 0) + (cy != 0) + (cz != 0);
-  float dh, dl;
-  if constexpr (cl == 1) {
-    dh = cx * nh[0] + cy * nh[1] + cz * nh[2];
-    dl = cx * nl[0] + cy * nl[1] + cz * nl[2];
-  } else {
-    float e2;
-    two_sum(cx != 0 ? cx * nh[0] : cy * nh[1], cz != 0 ? cz * nh[2] : cy * nh[1], dh, e2);
-    dl = e2 + (cx * nl[0] + cy * nl[1] + cz * nl[2]);
-  }
-  const float den = dh + dl;
-  if (den == 0.0f && dh == 0.0f) return;  // c_i parallel to the face plane: no hit
-  const float ad = fabsf(den);
-  const float sg = den > 0.f ? 1.f : -1.f;
-  const bool unc = ad <= (cl == 1 ? 1e-5f : 1.41421356e-5f) * nn2;
-  const float sn = sg * num, hd = h32 * ad;
-  // certified t < 0 or t > 1 (h32 * |den| is within 8u of h |den| when den is not tiny)
-  if (!unc && (sn < -eps_num || sn - eps_num > hd * (1.0f + 8.0f * kU32))) return;
-  bool out = false, all_in = true;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float u = sg * (cx * C[k][0] + cy * C[k][1] + cz * C[k][2]);
-    const float eu = 8.0f * kU32 * (float)cl * M[k];
-    if (u < -eu) out = true;
-    if (!(u > eu)) all_in = false;
-  }
-  if (out && !unc) return;
-  if (!unc && all_in && sn > eps_num && sn + eps_num < hd * (1.0f - 8.0f * kU32)) {
-    atomicMin(key + (DI - 1) * kLRows, hit_key(num / (h32 * den), f));
-  } else {
-    fb |= 1u << (DI - 1);
-  }
+// D3Q19 components packed two bits per direction (value + 1), for lanes that
+// each hold a different direction.
+__host__ __device__ constexpr uint64_t pack_dir_axis(int a) {
+  uint64_t k = 0;
+  for (int i = 1; i <= 18; ++i) k |= (uint64_t)(d3q19_c(i, a) + 1) << (2 * i);
+  return k;
 }
+constexpr uint64_t kDirX = pack_dir_axis(0), kDirY = pack_dir_axis(1), kDirZ = pack_dir_axis(2);
+__device__ __forceinline__ float dir_comp(uint64_t k, int i) { return (float)((int)((k >> (2 * i)) & 3ull) - 1); }
 
-template <int... DI>
-__device__ __forceinline__ void link_dirs3(std::integer_sequence<int, DI...>, const float (&nh)[3],
-                                           const float (&nl)[3], float num, float eps_num, const float (&C)[3][3],
-                                           const float (&M)[3], float nn2, float h32, uint32_t f,
-                                           unsigned long long* key, uint32_t& fb) {
-  (link_dir3<DI + 1>(nh, nl, num, eps_num, C, M, nn2, h32, f, key, fb), ...);
+// Per-pair quantities the direction tests share (one record per lane, 7 x 16 B
+// so that lanes reading different records hit different banks).
+struct PairRec {
+  float4 q[7];
+};
+
+// The lattice splits into 9 lines (an axis or a plane diagonal, both senses):
+// direction 2l+1 = +d_l and 2l+2 = -d_l, with d_l = x, y, z, x+y, x-y, x+z,
+// x-z, y+z, y-z.  A direction can hit the face plane within the link only if
+// t = num / (h c.n) lies in [0, 1]: this keeps every direction for which that
+// is possible under the error bounds of num (eps_num) and of D = d_l.n in FP32
+// (eD), a superset of the hits that the exact per-direction test then decides.
+__device__ __forceinline__ uint32_t line_candidates(const float (&nh)[3], float num, float eps_num, float h32) {
+  const float lim = fabsf(num) - eps_num;  // lower bound of |num|
+  const bool pos = num >= -eps_num, neg = num <= eps_num;
+  const float a0 = fabsf(nh[0]), a1 = fabsf(nh[1]), a2 = fabsf(nh[2]);
+  const float Dl[9] = {nh[0], nh[1], nh[2], nh[0] + nh[1], nh[0] - nh[1], nh[0] + nh[2], nh[0] - nh[2],
+                       nh[1] + nh[2], nh[1] - nh[2]};
+  const float El[9] = {a0, a1, a2, a0 + a1, a0 + a1, a0 + a2, a0 + a2, a1 + a2, a1 + a2};
+  uint32_t cand = 0;
+#pragma unroll
+  for (int l = 0; l < 9; ++l) {
+    const float eD = 4.0f * kU32 * El[l];
+    const float reach = h32 * (fabsf(Dl[l]) + eD) * (1.0f + 16.0f * kU32);
+    if (lim > reach) continue;
+    const bool dp = Dl[l] >= -eD, dn = Dl[l] <= eD;
+    if ((pos && dp) || (neg && dn)) cand |= 1u << (2 * l);
+    if ((pos && dn) || (neg && dp)) cand |= 2u << (2 * l);
+  }
+  return cand;
 }
 
 // Links of one tile of kLRows adjacent cells.  Phase 0: per row, the cell
-// centre (double-float) and the row's slice of the pair list.  Phase 1: one
-// thread per (cell, face) pair evaluates every lattice direction and keeps, per
-// (cell, direction), the minimum of (t, face) in shared memory.  Phase 2: one
+// centre (double-float) and the row's slice of the pair list.  Phase 1: warps
+// take chunks of 32 (cell, face) pairs.  Stage 1 (lane = pair): vertex offsets,
+// plane offset num, edge cross products and the candidate directions of the
+// 9 lattice lines.  Stage 2 (lane = candidate): the candidates of the chunk,
+// queued in shared memory, are tested densely, each by the certified
+// per-direction test (FP64 when a sign is not certified); hits keep the
+// per-(cell, direction) minimum of (t, face) in shared memory.  Phase 2: one
 // thread per row counts its links; a block scan plus the ticketed look-back
 // give the output position, in (cell, direction) order.
 template <int D>
-__global__ void __launch_bounds__(kLThreads, 2) k_links(LinkArgs a, uint64_t* state, unsigned* ticket) {
+__global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state, unsigned* ticket) {
   constexpr int Q1 = D == 3 ? 18 : 8;
   constexpr int NC = D == 3 ? 64 : 16;
+  constexpr int NW = kLThreads / 32;
+  constexpr int NPR = D == 3 ? 32 : 1;
   __shared__ unsigned long long s_key[Q1][kLRows];
   __shared__ uint32_t s_off[kLRows + 1];
   __shared__ float s_o[2 * D][kLRows];
   __shared__ float s_h[kLRows];
-  __shared__ uint32_t s_warp[kLThreads / 32];
+  __shared__ PairRec s_pr[NW][NPR];
+  __shared__ uint16_t s_q[NW][D == 3 ? 32 * 18 : 1];
+  __shared__ uint32_t s_warp[NW];
   __shared__ uint64_t s_prefix;
-  __shared__ unsigned s_tile;
+  __shared__ unsigned s_tile, s_chunk;
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const uint64_t row0 = a.run ? a.run[0] : 0ull;
@@ -230,7 +226,10 @@ __global__ void __launch_bounds__(kLThreads, 2) k_links(LinkArgs a, uint64_t* st
   }
   unsigned long long n_fb = 0, n_band = 0;
   for (;;) {
-    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    if (tid == 0) {
+      s_tile = atomicAdd(ticket, 1u);
+      s_chunk = 0u;
+    }
     __syncthreads();
     const long long tile = s_tile;
     if (tile >= ntiles) break;
@@ -258,119 +257,194 @@ __global__ void __launch_bounds__(kLThreads, 2) k_links(LinkArgs a, uint64_t* st
       }
     }
     __syncthreads();
-    // phase 1: one thread per (cell, face) pair
-    // (the clamp only matters after an overflow, which the host reports)
+    // phase 1 (the clamp only matters after an overflow, which the host reports)
     const uint32_t p0 = s_off[0];
     const uint32_t p1 = (int64_t)s_off[nr] <= a.cap_pairs ? s_off[nr] : (uint32_t)a.cap_pairs;
-    for (uint32_t e = p0 + (uint32_t)tid; e < p1; e += kLThreads) {
-      int lo = 0, hi = nr;  // s_off[lo] <= e < s_off[hi]
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (s_off[mid] <= e)
-          lo = mid;
-        else
-          hi = mid;
+    const uint32_t nchunks = p1 > p0 ? (p1 - p0 + 31u) / 32u : 0u;
+    for (;;) {
+      uint32_t ch = 0;
+      if (lane == 0) ch = atomicAdd(&s_chunk, 1u);
+      ch = __shfl_sync(0xffffffffu, ch, 0);
+      if (ch >= nchunks) break;
+      const uint32_t e = p0 + ch * 32u + (uint32_t)lane;
+      uint32_t cand = 0;
+      int r = 0;
+      uint32_t f = 0xffffffffu;
+      if (e < p1) {
+        int lo = 0, hi = nr;  // s_off[lo] <= e < s_off[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_off[mid] <= e)
+            lo = mid;
+          else
+            hi = mid;
+        }
+        r = lo;
+        f = a.adj_ids[e];
+        if ((int64_t)f >= a.nf) f = 0xffffffffu;
       }
-      const int r = lo;
-      const uint32_t f = a.adj_ids[e];
-      if ((int64_t)f >= a.nf) continue;
-      if constexpr (D == 2) {
-        // 2D workloads are small: every link in FP64
-        const uint32_t id = a.adj_cell[first + r];
-        const uint32_t blk = id / NC, bit = id % NC;
-        const GeomParams& P = a.table ? a.table[a.gid ? a.gid[blk] : 0u] : a.g0;
-        const double hL = scalbn(P.h0, -a.level);
-        double xc[2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int gc = 4 * a.blocks[(int64_t)blk * 2 + c] + (int)((bit >> (2 * c)) & 3u);
-          xc[c] = __dadd_rn(P.origin[c], __dmul_rn((double)gc + 0.5, hL));
-        }
-        float V[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) V[j] = a.X[(int64_t)j * a.nf + f];
-#pragma unroll
-        for (int di = 1; di <= Q1; ++di) {
-          const int ci[2] = {c_d2q9[di][0], c_d2q9[di][1]};
-          const LinkHit h = link_fp64_2(V, xc, ci, hL);
-          if (h.band) ++n_band;
-          if (h.hit) atomicMin(&s_key[di - 1][r], hit_key((float)h.t, f));
-        }
-      } else {
-        const float4* R = reinterpret_cast<const float4*>(a.rec + f);
-        const float4 r0 = __ldg(R), r1 = __ldg(R + 1), r2 = __ldg(R + 2), r3 = __ldg(R + 3);
-        const float V[9] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x};
-        const float nh[3] = {r2.y, r2.z, r2.w};
-        const float nl[3] = {r3.x, r3.y, r3.z};
-        const float ohi[3] = {s_o[0][r], s_o[1][r], s_o[2][r]};
-        const float olo[3] = {s_o[3][r], s_o[4][r], s_o[5][r]};
-        const float h32 = s_h[r];
-        // vertex offsets from the cell centre: p = (V - ohi) - olo as hi + lo
-        float ph0[3], pl0[3], p[3][3];
-        float pmax = 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float sm, err;
-            two_sum(V[3 * k + c], -ohi[c], sm, err);
-            const float l = err - olo[c];
-            if (k == 0) {
-              ph0[c] = sm;
-              pl0[c] = l;
-            }
-            p[k][c] = sm + l;
-            pmax = fmaxf(pmax, fabsf(p[k][c]));
-          }
-        // num = n . (v0 - x) in double-float
-        float ns, ne;
-        two_prod(nh[0], ph0[0], ns, ne);
-#pragma unroll
-        for (int c = 1; c < 3; ++c) {
-          float pp, pe, sm, t;
-          two_prod(nh[c], ph0[c], pp, pe);
-          two_sum(ns, pp, sm, t);
-          ns = sm;
-          ne += t + pe;
-        }
-        const float n1 = fabsf(nh[0]) + fabsf(nh[1]) + fabsf(nh[2]);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) ne = fmaf(nh[c], pl0[c], fmaf(nl[c], ph0[c], ne));
-        const float num = ns + ne;
-        const float xmax = fmaxf(fmaxf(fabsf(ohi[0]), fabsf(ohi[1])), fabsf(ohi[2]));
-        const float eps_num = 16.0f * kU32 * kU32 * n1 * (xmax + pmax) + 4.0f * kU32 * fabsf(ne);
-        // edge cross products C_k = p_a x p_b, (a,b) = (1,2),(2,0),(0,1), and the
-        // largest component magnitude bound M_k = max_c (|A_a B_b| + |A_b B_a|)
-        float C[3][3], M[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float* A = p[(k + 1) % 3];
-          const float* B = p[(k + 2) % 3];
-          C[k][0] = fmaf(A[1], B[2], -A[2] * B[1]);
-          C[k][1] = fmaf(A[2], B[0], -A[0] * B[2]);
-          C[k][2] = fmaf(A[0], B[1], -A[1] * B[0]);
-          M[k] = fmaxf(fmaxf(fabsf(A[1] * B[2]) + fabsf(A[2] * B[1]), fabsf(A[2] * B[0]) + fabsf(A[0] * B[2])),
-                       fabsf(A[0] * B[1]) + fabsf(A[1] * B[0]));
-        }
-        const float nn2 = sqrtf(nh[0] * nh[0] + nh[1] * nh[1] + nh[2] * nh[2]);
-        uint32_t fb = 0;
-        link_dirs3(std::make_integer_sequence<int, 18>{}, nh, nl, num, eps_num, C, M, nn2, h32, f, &s_key[0][r],
-                   fb);
-        // undecided signs: FP64 evaluation from the FP64 cell centre
-        if (fb) {
+      if (f != 0xffffffffu) {
+        if constexpr (D == 2) {
+          // 2D workloads are small: every link in FP64
           const uint32_t id = a.adj_cell[first + r];
           const uint32_t blk = id / NC, bit = id % NC;
           const GeomParams& P = a.table ? a.table[a.gid ? a.gid[blk] : 0u] : a.g0;
-          const double o3[3] = {P.origin[0], P.origin[1], P.origin[2]};
           const double hL = scalbn(P.h0, -a.level);
-          for (; fb; fb &= fb - 1) {
-            const int di = __ffs(fb);
-            const LinkHit h = link_fallback_3(V, a.blocks + (int64_t)blk * 3, bit, o3, hL, di);
-            ++n_fb;
+          double xc[2];
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int gc = 4 * a.blocks[(int64_t)blk * 2 + c] + (int)((bit >> (2 * c)) & 3u);
+            xc[c] = __dadd_rn(P.origin[c], __dmul_rn((double)gc + 0.5, hL));
+          }
+          float V[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) V[j] = a.X[(int64_t)j * a.nf + f];
+#pragma unroll
+          for (int di = 1; di <= Q1; ++di) {
+            const int ci[2] = {c_d2q9[di][0], c_d2q9[di][1]};
+            const LinkHit h = link_fp64_2(V, xc, ci, hL);
             if (h.band) ++n_band;
             if (h.hit) atomicMin(&s_key[di - 1][r], hit_key((float)h.t, f));
           }
+        } else {
+          // stage 1
+          const float4* R = reinterpret_cast<const float4*>(a.rec + f);
+          const float4 r0 = __ldg(R), r1 = __ldg(R + 1), r2 = __ldg(R + 2), r3 = __ldg(R + 3);
+          const float V[9] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x};
+          const float nh[3] = {r2.y, r2.z, r2.w};
+          const float nl[3] = {r3.x, r3.y, r3.z};
+          const float ohi[3] = {s_o[0][r], s_o[1][r], s_o[2][r]};
+          const float olo[3] = {s_o[3][r], s_o[4][r], s_o[5][r]};
+          const float h32 = s_h[r];
+          // vertex offsets from the cell centre: p = (V - ohi) - olo as hi + lo
+          float ph0[3], pl0[3], p[3][3];
+          float pmax = 0.f;
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              float sm, err;
+              two_sum(V[3 * k + c], -ohi[c], sm, err);
+              const float l = err - olo[c];
+              if (k == 0) {
+                ph0[c] = sm;
+                pl0[c] = l;
+              }
+              p[k][c] = sm + l;
+              pmax = fmaxf(pmax, fabsf(p[k][c]));
+            }
+          // num = n . (v0 - x) in double-float
+          float ns, ne;
+          two_prod(nh[0], ph0[0], ns, ne);
+#pragma unroll
+          for (int c = 1; c < 3; ++c) {
+            float pp, pe, sm, t;
+            two_prod(nh[c], ph0[c], pp, pe);
+            two_sum(ns, pp, sm, t);
+            ns = sm;
+            ne += t + pe;
+          }
+          const float n1 = fabsf(nh[0]) + fabsf(nh[1]) + fabsf(nh[2]);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) ne = fmaf(nh[c], pl0[c], fmaf(nl[c], ph0[c], ne));
+          const float num = ns + ne;
+          const float xmax = fmaxf(fmaxf(fabsf(ohi[0]), fabsf(ohi[1])), fabsf(ohi[2]));
+          const float eps_num = 16.0f * kU32 * kU32 * n1 * (xmax + pmax) + 4.0f * kU32 * fabsf(ne);
+          cand = line_candidates(nh, num, eps_num, h32);
+          if (cand) {
+            // edge cross products C_k = p_a x p_b, (a,b) = (1,2),(2,0),(0,1), and the
+            // largest component magnitude bound M_k = max_c (|A_a B_b| + |A_b B_a|)
+            float C[3][3], M[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const float* A = p[(k + 1) % 3];
+              const float* B = p[(k + 2) % 3];
+              C[k][0] = fmaf(A[1], B[2], -A[2] * B[1]);
+              C[k][1] = fmaf(A[2], B[0], -A[0] * B[2]);
+              C[k][2] = fmaf(A[0], B[1], -A[1] * B[0]);
+              M[k] = fmaxf(fmaxf(fabsf(A[1] * B[2]) + fabsf(A[2] * B[1]), fabsf(A[2] * B[0]) + fabsf(A[0] * B[2])),
+                           fabsf(A[0] * B[1]) + fabsf(A[1] * B[0]));
+            }
+            const float nn2 = sqrtf(nh[0] * nh[0] + nh[1] * nh[1] + nh[2] * nh[2]);
+            float4* W = s_pr[wid][lane].q;
+            W[0] = make_float4(C[0][0], C[0][1], C[0][2], C[1][0]);
+            W[1] = make_float4(C[1][1], C[1][2], C[2][0], C[2][1]);
+            W[2] = make_float4(C[2][2], M[0], M[1], M[2]);
+            W[3] = make_float4(num, eps_num, h32, nn2);
+            W[4] = make_float4(nh[0], nh[1], nh[2], __uint_as_float(f));
+            W[5] = make_float4(nl[0], nl[1], nl[2], __int_as_float(r));
+          }
         }
+      }
+      if constexpr (D == 3) {
+        // queue the chunk's candidates (lane-major), then test them 32 at a time
+        const uint32_t nc = __popc(cand);
+        const uint32_t incl = warp_inclusive_scan<uint32_t>(nc);
+        const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t pos = incl - nc;
+        for (uint32_t m = cand; m; m &= m - 1) s_q[wid][pos++] = (uint16_t)(lane | (__ffs(m) << 5));
+        __syncwarp();
+        for (uint32_t base = 0; base < T; base += 32) {
+          const uint32_t q = base + (uint32_t)lane;
+          if (q < T) {
+            const uint32_t qe = s_q[wid][q];
+            const int src = (int)(qe & 31u), di = (int)(qe >> 5);
+            const float4* Q = s_pr[wid][src].q;
+            const float4 w0 = Q[0], w1 = Q[1], w2 = Q[2], w3 = Q[3], w4 = Q[4], w5 = Q[5];
+            const float Cx[3][3] = {{w0.x, w0.y, w0.z}, {w0.w, w1.x, w1.y}, {w1.z, w1.w, w2.x}};
+            const float Mk[3] = {w2.y, w2.z, w2.w};
+            const float num = w3.x, eps_num = w3.y, h32 = w3.z, nn2 = w3.w;
+            const float nh[3] = {w4.x, w4.y, w4.z};
+            const float nl[3] = {w5.x, w5.y, w5.z};
+            const uint32_t fq = __float_as_uint(w4.w);
+            const int rq = __float_as_int(w5.w);
+            const float cx = dir_comp(kDirX, di), cy = dir_comp(kDirY, di), cz = dir_comp(kDirZ, di);
+            const float cl = fabsf(cx) + fabsf(cy) + fabsf(cz);
+            // den = c . n in double-float (c has at most two non-zero unit entries)
+            float s1, e1, dh, e2;
+            two_sum(cx * nh[0], cy * nh[1], s1, e1);
+            two_sum(s1, cz * nh[2], dh, e2);
+            const float dl = (e1 + e2) + (cx * nl[0] + cy * nl[1] + cz * nl[2]);
+            const float den = dh + dl;
+            bool test = !(den == 0.0f && dh == 0.0f);  // else c_i parallel to the face plane: no hit
+            const float ad = fabsf(den);
+            const float sg = den > 0.f ? 1.f : -1.f;
+            const bool unc = ad <= (cl == 1.0f ? 1e-5f : 1.41421356e-5f) * nn2;
+            const float sn = sg * num, hd = h32 * ad;
+            // certified t < 0 or t > 1 (h32 |den| is within 8u of h |den| when den is not tiny)
+            if (!unc && (sn < -eps_num || sn - eps_num > hd * (1.0f + 8.0f * kU32))) test = false;
+            if (test) {
+              bool out = false, all_in = true;
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                const float u = sg * (cx * Cx[k][0] + cy * Cx[k][1] + cz * Cx[k][2]);
+                const float eu = 8.0f * kU32 * cl * Mk[k];
+                if (u < -eu) out = true;
+                if (!(u > eu)) all_in = false;
+              }
+              if (!(out && !unc)) {
+                if (!unc && all_in && sn > eps_num && sn + eps_num < hd * (1.0f - 8.0f * kU32)) {
+                  atomicMin(&s_key[di - 1][rq], hit_key(num / (h32 * den), fq));
+                } else {
+                  // undecided signs: FP64 evaluation from the FP64 cell centre
+                  const uint32_t id = a.adj_cell[first + rq];
+                  const uint32_t blk = id / NC, bit = id % NC;
+                  const GeomParams& P = a.table ? a.table[a.gid ? a.gid[blk] : 0u] : a.g0;
+                  const double o3[3] = {P.origin[0], P.origin[1], P.origin[2]};
+                  const double hL = scalbn(P.h0, -a.level);
+                  const float4* R = reinterpret_cast<const float4*>(a.rec + fq);
+                  const float4 v0 = __ldg(R), v1 = __ldg(R + 1), v2 = __ldg(R + 2);
+                  const float V[9] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x};
+                  const LinkHit h = link_fallback_3(V, a.blocks + (int64_t)blk * 3, bit, o3, hL, di);
+                  ++n_fb;
+                  if (h.band) ++n_band;
+                  if (h.hit) atomicMin(&s_key[di - 1][rq], hit_key((float)h.t, fq));
+                }
+              }
+            }
+          }
+        }
+        __syncwarp();  // the next chunk reuses the records and the queue
       }
     }
     __syncthreads();
@@ -384,14 +458,14 @@ __global__ void __launch_bounds__(kLThreads, 2) k_links(LinkArgs a, uint64_t* st
     if (lane == 31) s_warp[wid] = incl;
     __syncthreads();
     if (wid == 0) {
-      uint32_t w = lane < kLThreads / 32 ? s_warp[lane] : 0u;
+      uint32_t w = lane < NW ? s_warp[lane] : 0u;
       w = warp_inclusive_scan<uint32_t>(w);
-      if (lane < kLThreads / 32) s_warp[lane] = w;
+      if (lane < NW) s_warp[lane] = w;
     }
     __syncthreads();
     const uint32_t wex = wid > 0 ? s_warp[wid - 1] : 0u;
     if (tid == 0) {
-      const uint64_t agg = s_warp[kLThreads / 32 - 1];
+      const uint64_t agg = s_warp[NW - 1];
       const uint64_t pre = lookback_exclusive(state, tile, agg, a.err);
       s_prefix = pre;
       if (tile == ntiles - 1) {
