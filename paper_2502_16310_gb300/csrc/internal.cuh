@@ -141,17 +141,18 @@ struct BinGrid {
 // normal), so that a bin's faces are one contiguous run of memory that TMA
 // bulk copies stage in shared memory.  `id` holds the face id in the low 29
 // bits and, in bits 29..31, whether this bin is the first of the face's bin
-// range along x / y / z (used to visit each face once per query box).
+// range along x / y / z; with the entry's own bin coordinates that lets a
+// query box visit each face once (in the first of its bins inside the box).
 struct __align__(16) Entry3 {
   float v[9];
   float n[3];
   uint32_t id;
-  uint32_t pad[3];
+  uint32_t bin[3];  // this entry's bin coordinates (within its geometry's grid)
 };
 struct __align__(16) Entry2 {
   float v[4];
   uint32_t id;
-  uint32_t pad[3];
+  uint32_t bin[3];  // bin x, y; bin[2] = 0
 };
 
 template <int D>

@@ -154,8 +154,6 @@ __global__ void k_scatter(ScatterArgs a) {
     E e;
 #pragma unroll
     for (int j = 0; j < D * D; ++j) e.v[j] = a.f.X[(int64_t)j * nf + f];
-#pragma unroll
-    for (int j = 0; j < (int)(sizeof(e.pad) / sizeof(e.pad[0])); ++j) e.pad[j] = 0u;
     if constexpr (D == 3) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) e.n[c] = a.nrm[(int64_t)c * nf + f];
@@ -171,6 +169,9 @@ __global__ void k_scatter(ScatterArgs a) {
           uint32_t flags = (x == lo[0] ? (1u << 29) : 0u) | (y == lo[1] ? (1u << 30) : 0u);
           if (D == 3) flags |= (z == lo[2] ? (1u << 31) : 0u);
           e.id = (uint32_t)f | flags;
+          e.bin[0] = (uint32_t)x;
+          e.bin[1] = (uint32_t)y;
+          e.bin[2] = (uint32_t)z;
           const float4* src = reinterpret_cast<const float4*>(&e);
           float4* dst = reinterpret_cast<float4*>(payload + pos);
 #pragma unroll

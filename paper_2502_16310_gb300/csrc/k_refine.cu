@@ -32,30 +32,25 @@ struct Surv;
 
 // Per-survivor data in the block frame (origin = the block's lower corner).
 // Axis order (3D): 0..2 box axes, 3 face normal, 4 + 3k + i = e_i x edge_k.
+// Per axis the cell-centre projection x is tested against four thresholds
+// t = (lo - eps, hi + eps, lo + eps, hi - eps), [lo, hi] being the face's
+// projection widened by the cell's: x < t.x or x > t.y certifies separation,
+// t.z < x < t.w certifies overlap, anything else is not certified.
 template <>
 struct Surv<3> {
-  float e[9];
-  float n[3];
-  float lo[13], hi[13], eps[13];
+  float4 en[3];  // e0.xyz e1.x | e1.yz e2.xy | e2.z n.xyz
+  float4 t[13];
   uint32_t face;
+  uint32_t pad[3];
 };
 // 2D: 0..1 box axes, 2 segment normal (-e_y, e_x).
 template <>
 struct Surv<2> {
+  float4 t[3];
   float e[2];
-  float lo[3], hi[3], eps[3];
   uint32_t face;
+  uint32_t pad;
 };
-
-__device__ __forceinline__ float3 axis3(int ai, const float* e, const float* n) {
-  if (ai < 3) return make_float3(ai == 0 ? 1.f : 0.f, ai == 1 ? 1.f : 0.f, ai == 2 ? 1.f : 0.f);
-  if (ai == 3) return make_float3(n[0], n[1], n[2]);
-  const int k = (ai - 4) / 3, i = (ai - 4) % 3;
-  const float ex = e[3 * k + 0], ey = e[3 * k + 1], ez = e[3 * k + 2];
-  if (i == 0) return make_float3(0.f, -ez, ey);
-  if (i == 1) return make_float3(ez, 0.f, -ex);
-  return make_float3(-ey, ex, 0.f);
-}
 
 // FP64 separating-axis margin of the box [x_c - r, x_c + r]^3 and the closed
 // triangle (vertices absolute FP32), normalised gap of the best axis.
@@ -153,113 +148,105 @@ __device__ __forceinline__ bool setup_face(const float* V, const float* nh, cons
       P = fmaxf(P, fabsf(p[k][c]));
     }
   const float scale = kEpsK * kU32 * (P + F.O + F.r);
-  bool alive = true;
+  // one axis: false when it certifiably separates the face from the whole inflated block
+  auto axis = [&](int ai, float ax, float ay, float az) -> bool {
+    const float A1 = fabsf(ax) + fabsf(ay) + fabsf(az);
+    if (A1 == 0.0f) {
+      S.t[ai] = make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
+      return true;
+    }
+    float tmin = INFINITY, tmax = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float s = D == 3 ? fmaf(p[k][2], az, fmaf(p[k][1], ay, p[k][0] * ax)) : fmaf(p[k][1], ay, p[k][0] * ax);
+      tmin = fminf(tmin, s);
+      tmax = fmaxf(tmax, s);
+    }
+    const float eps = scale * A1;
+    const float xb = D == 3 ? fmaf(F.cB[2], az, fmaf(F.cB[1], ay, F.cB[0] * ax)) : fmaf(F.cB[1], ay, F.cB[0] * ax);
+    const float RB = F.rb * A1;
+    // block interval [xb - RB, xb + RB] vs face interval [tmin, tmax]
+    if (xb - RB - tmax > eps || tmin - (xb + RB) > eps) return false;
+    const float R = F.r * A1;
+    const float lo = tmin - R, hi = tmax + R;
+    S.t[ai] = make_float4(lo - eps, hi + eps, lo + eps, hi - eps);
+    return true;
+  };
   if constexpr (D == 3) {
+    float e[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int k1 = (k + 1) % 3;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) S.e[3 * k + c] = V[3 * k1 + c] - V[3 * k + c];
+      for (int c = 0; c < 3; ++c) e[k][c] = V[3 * k1 + c] - V[3 * k + c];
     }
-    S.n[0] = nh[0];
-    S.n[1] = nh[1];
-    S.n[2] = nh[2];
+    // box axes first: the cheap AABB cull
+    if (!axis(0, 1.f, 0.f, 0.f) || !axis(1, 0.f, 1.f, 0.f) || !axis(2, 0.f, 0.f, 1.f)) return false;
+    if (!axis(3, nh[0], nh[1], nh[2])) return false;
 #pragma unroll
-    for (int ai = 0; ai < 13; ++ai) {
-      const float3 a = axis3(ai, S.e, S.n);
-      const float A1 = fabsf(a.x) + fabsf(a.y) + fabsf(a.z);
-      if (A1 == 0.0f) {
-        S.lo[ai] = -INFINITY;
-        S.hi[ai] = INFINITY;
-        S.eps[ai] = 0.f;
-        continue;
-      }
-      float tmin = INFINITY, tmax = -INFINITY;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float s = fmaf(p[k][2], a.z, fmaf(p[k][1], a.y, p[k][0] * a.x));
-        tmin = fminf(tmin, s);
-        tmax = fmaxf(tmax, s);
-      }
-      const float eps = scale * A1;
-      const float xb = fmaf(F.cB[2], a.z, fmaf(F.cB[1], a.y, F.cB[0] * a.x));
-      const float RB = F.rb * A1;
-      // block interval [xb - RB, xb + RB] vs face interval [tmin, tmax]
-      if (xb - RB - tmax > eps || tmin - (xb + RB) > eps) alive = false;
-      const float R = F.r * A1;
-      S.lo[ai] = tmin - R;
-      S.hi[ai] = tmax + R;
-      S.eps[ai] = eps;
-      if (!alive) return false;  // box axes come first: the cheap AABB cull
+    for (int k = 0; k < 3; ++k) {
+      const float ex = e[k][0], ey = e[k][1], ez = e[k][2];
+      if (!axis(4 + 3 * k, 0.f, -ez, ey)) return false;
+      if (!axis(5 + 3 * k, ez, 0.f, -ex)) return false;
+      if (!axis(6 + 3 * k, -ey, ex, 0.f)) return false;
     }
+    S.en[0] = make_float4(e[0][0], e[0][1], e[0][2], e[1][0]);
+    S.en[1] = make_float4(e[1][1], e[1][2], e[2][0], e[2][1]);
+    S.en[2] = make_float4(e[2][2], nh[0], nh[1], nh[2]);
   } else {
-    S.e[0] = V[2] - V[0];
-    S.e[1] = V[3] - V[1];
-#pragma unroll
-    for (int ai = 0; ai < 3; ++ai) {
-      const float ax = ai == 0 ? 1.f : (ai == 1 ? 0.f : -S.e[1]);
-      const float ay = ai == 0 ? 0.f : (ai == 1 ? 1.f : S.e[0]);
-      const float A1 = fabsf(ax) + fabsf(ay);
-      if (A1 == 0.0f) {
-        S.lo[ai] = -INFINITY;
-        S.hi[ai] = INFINITY;
-        S.eps[ai] = 0.f;
-        continue;
-      }
-      const float s0 = fmaf(p[0][1], ay, p[0][0] * ax);
-      const float s1 = fmaf(p[1][1], ay, p[1][0] * ax);
-      const float tmin = fminf(s0, s1), tmax = fmaxf(s0, s1);
-      const float eps = scale * A1;
-      const float xb = fmaf(F.cB[1], ay, F.cB[0] * ax);
-      const float RB = F.rb * A1;
-      if (xb - RB - tmax > eps || tmin - (xb + RB) > eps) alive = false;
-      const float R = F.r * A1;
-      S.lo[ai] = tmin - R;
-      S.hi[ai] = tmax + R;
-      S.eps[ai] = eps;
-      if (!alive) return false;
-    }
+    const float e0 = V[2] - V[0], e1 = V[3] - V[1];
+    if (!axis(0, 1.f, 0.f, 0.f) || !axis(1, 0.f, 1.f, 0.f)) return false;
+    if (!axis(2, -e1, e0, 0.f)) return false;
+    S.e[0] = e0;
+    S.e[1] = e1;
   }
-  return alive;
+  return true;
 }
 
-// Cell test against one survivor: 0 = separated, 1 = intersecting, 2 = not
-// certified (needs FP64).  `o` is the cell centre in the block frame.
+// Cell tests of the lane's two cells against one survivor: 0 = separated,
+// 1 = intersecting, 2 = not certified (needs FP64).  o0 / o1 are the cell
+// centres in the block frame.  All axes are evaluated (the warp runs the
+// longest lane anyway); the thresholds come as one 16-byte load per axis.
 template <int D>
-__device__ __forceinline__ int cell_test(const Surv<D>& S, const float* o) {
-  bool unc = false;
+__device__ __forceinline__ void cell_test2(const Surv<D>& S, const float* o0, const float* o1, int& r0, int& r1) {
+  bool sep0 = false, in0 = true, sep1 = false, in1 = true;
+  auto upd = [](float x, const float4& t, bool& sep, bool& in) {
+    sep |= (x < t.x) | (x > t.y);
+    in &= (x > t.z) & (x < t.w);
+  };
   if constexpr (D == 3) {
 #pragma unroll
-    for (int ai = 0; ai < 13; ++ai) {
-      float x;
-      if (ai < 3) {
-        x = o[ai];
-      } else if (ai == 3) {
-        x = fmaf(o[2], S.n[2], fmaf(o[1], S.n[1], o[0] * S.n[0]));
-      } else {
-        const int k = (ai - 4) / 3, i = (ai - 4) % 3;
-        const float ex = S.e[3 * k + 0], ey = S.e[3 * k + 1], ez = S.e[3 * k + 2];
-        if (i == 0)
-          x = fmaf(o[2], ey, -o[1] * ez);
-        else if (i == 1)
-          x = fmaf(o[0], ez, -o[2] * ex);
-        else
-          x = fmaf(o[1], ex, -o[0] * ey);
-      }
-      const float g = fmaxf(S.lo[ai] - x, x - S.hi[ai]);
-      if (g > S.eps[ai]) return 0;
-      unc |= g >= -S.eps[ai];
+    for (int ai = 0; ai < 3; ++ai) {
+      const float4 t = S.t[ai];
+      upd(o0[ai], t, sep0, in0);
+      upd(o1[ai], t, sep1, in1);
+    }
+    const float4 q0 = S.en[0], q1 = S.en[1], q2 = S.en[2];
+    const float e[3][3] = {{q0.x, q0.y, q0.z}, {q0.w, q1.x, q1.y}, {q1.z, q1.w, q2.x}};
+    {
+      const float4 t = S.t[3];
+      upd(fmaf(o0[2], q2.w, fmaf(o0[1], q2.z, o0[0] * q2.y)), t, sep0, in0);
+      upd(fmaf(o1[2], q2.w, fmaf(o1[1], q2.z, o1[0] * q2.y)), t, sep1, in1);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float ex = e[k][0], ey = e[k][1], ez = e[k][2];
+      const float4 ta = S.t[4 + 3 * k], tb = S.t[5 + 3 * k], tc = S.t[6 + 3 * k];
+      upd(fmaf(o0[2], ey, -o0[1] * ez), ta, sep0, in0);
+      upd(fmaf(o1[2], ey, -o1[1] * ez), ta, sep1, in1);
+      upd(fmaf(o0[0], ez, -o0[2] * ex), tb, sep0, in0);
+      upd(fmaf(o1[0], ez, -o1[2] * ex), tb, sep1, in1);
+      upd(fmaf(o0[1], ex, -o0[0] * ey), tc, sep0, in0);
+      upd(fmaf(o1[1], ex, -o1[0] * ey), tc, sep1, in1);
     }
   } else {
 #pragma unroll
-    for (int ai = 0; ai < 3; ++ai) {
-      const float x = ai < 2 ? o[ai] : fmaf(o[1], S.e[0], -o[0] * S.e[1]);
-      const float g = fmaxf(S.lo[ai] - x, x - S.hi[ai]);
-      if (g > S.eps[ai]) return 0;
-      unc |= g >= -S.eps[ai];
-    }
+    for (int ai = 0; ai < 2; ++ai) upd(o0[ai], S.t[ai], sep0, in0);
+    upd(fmaf(o0[1], S.e[0], -o0[0] * S.e[1]), S.t[2], sep0, in0);
+    sep1 = true;
   }
-  return unc ? 2 : 1;
+  r0 = sep0 ? 0 : (in0 ? 1 : 2);
+  r1 = sep1 ? 0 : (in1 ? 1 : 2);
 }
 
 struct WarpCounters {
@@ -299,8 +286,9 @@ __device__ __noinline__ bool resolve_fp64(const RefineLevel& a, uint32_t gid, ui
 // so no FP64 instruction runs per block.  The bin query range is widened by
 // a margin that covers the FP32 error of the bin coordinate (a superset of
 // bins only adds candidates the block test rejects).
-// Per-warp shared memory of the walk: survivor records, a double buffer of
-// bin entries filled by TMA bulk copies, and one mbarrier per buffer.
+// Per-warp shared memory of the walk: survivor data, a double buffer of bin
+// entries filled by TMA bulk copies with one mbarrier per buffer, and the
+// block's survivor records.
 template <int D>
 struct WarpSmem {
   Surv<D> surv[32];
@@ -320,48 +308,22 @@ __device__ __forceinline__ void warp_smem_init(WarpSmem<D>& sm, int lane) {
   __syncwarp();
 }
 
-// A run of at most 32 consecutive entries of one bin.
-struct Chunk {
-  int x, y, z;
-  uint32_t j0, n;
-};
-
-// Walks the bins of the query box in z, y, x order, handing out chunks.
-struct ChunkCursor {
-  int qlo[3], qhi[3];
-  int x, y, z;
-  uint32_t s, e;
-  bool started;
-};
-
-__device__ __forceinline__ bool next_chunk(ChunkCursor& c, const uint32_t* offsets, int64_t bin_base, int64_t B,
-                                           Chunk& out) {
-  while (true) {
-    if (c.started && c.s < c.e) {
-      out.x = c.x;
-      out.y = c.y;
-      out.z = c.z;
-      out.j0 = c.s;
-      out.n = c.e - c.s < 32u ? c.e - c.s : 32u;
-      c.s += out.n;
-      return true;
-    }
-    // move to the next bin
-    if (!c.started) {
-      c.started = true;
-      c.x = c.qlo[0];
-      c.y = c.qlo[1];
-      c.z = c.qlo[2];
-    } else if (++c.x > c.qhi[0]) {
-      c.x = c.qlo[0];
-      if (++c.y > c.qhi[1]) {
-        c.y = c.qlo[1];
-        if (++c.z > c.qhi[2]) return false;
-      }
-    }
-    const int64_t bin = bin_base + c.x + B * (c.y + B * (int64_t)c.z);
-    c.s = offsets[bin];
-    c.e = offsets[bin + 1];
+// The entries of the query box's x-rows (y, z fixed, x in [qlo_x, qhi_x]) are
+// contiguous in the bin payload.  Lane i holds row i of the current group of
+// (up to) 32 rows: its first entry `s`, its length `n` and the row's start
+// `v` in the group's concatenated entry list.  Chunk c = entries [32c, 32c+32)
+// of that list; every lane copies its row's part of the chunk into the buffer
+// (lane 0 first announces the chunk's bytes on the buffer's mbarrier).
+template <typename E>
+__device__ __forceinline__ void issue_chunk(const E* payload, uint32_t s, uint32_t n, uint32_t v, uint32_t c,
+                                            uint32_t T, E* buf, uint64_t* bar, int lane) {
+  const uint32_t c0 = 32u * c, c1 = c0 + 32u < T ? c0 + 32u : T;
+  if (lane == 0) mbar_arrive_expect_tx(bar, (c1 - c0) * (uint32_t)sizeof(E));
+  __syncwarp();
+  const uint32_t a0 = v > c0 ? v : c0, a1 = v + n < c1 ? v + n : c1;
+  if (a0 < a1) {
+    fence_proxy_async_smem();  // this warp's earlier reads of the buffer come first
+    bulk_copy_g2s(buf + (a0 - c0), payload + s + (a0 - v), (a1 - a0) * (uint32_t)sizeof(E), bar);
   }
 }
 
@@ -379,9 +341,10 @@ __device__ __forceinline__ bool next_chunk(ChunkCursor& c, const uint32_t* offse
 // a margin that covers the FP32 error of the bin coordinate (a superset of
 // bins only adds candidates the block test rejects).
 //
-// Bin entries arrive in shared memory by TMA bulk copies, chunk by chunk
-// (<= 32 entries of one bin), double-buffered: lane 0 issues the copy of the
-// next chunk before the warp tests the current one.
+// The bin ranges of all x-rows of the box are read in parallel (one lane per
+// row); entries then arrive in shared memory by TMA bulk copies in chunks of
+// 32, double-buffered: the next chunk is requested before the warp tests the
+// current one.
 template <int D, bool kMarkOnly, typename OnSurv>
 __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParams& P, uint32_t gid, const int* b,
                                            WarpSmem<D>& sm, uint32_t& phase, int lane, WarpCounters& wc, bool& h0,
@@ -390,8 +353,7 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
   const FastGeom g = fast_geom(P, a.level);
   const float hf = g.h_hi;
   BlockFrame<D> F;
-  ChunkCursor cur{};
-  cur.qlo[1] = cur.qlo[2] = cur.qhi[1] = cur.qhi[2] = 0;
+  int qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0};
   float O = 4.0f * hf;
   float shift[3] = {0.f, 0.f, 0.f};
   const int Bn = P.B;
@@ -409,8 +371,8 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
     const float xhi = fmaf(k0 + 4.0f, g.h_hi, fmaf(k0 + 4.0f, g.h_lo, g.d));
     const float tlo = floorf(xlo * P.scale32[c] - margin);
     const float thi = floorf(xhi * P.scale32[c] + margin);
-    cur.qlo[c] = tlo < 0.f ? 0 : (tlo > (float)(Bn - 1) ? Bn - 1 : (int)tlo);
-    cur.qhi[c] = thi < 0.f ? 0 : (thi > (float)(Bn - 1) ? Bn - 1 : (int)thi);
+    qlo[c] = tlo < 0.f ? 0 : (tlo > (float)(Bn - 1) ? Bn - 1 : (int)tlo);
+    qhi[c] = thi < 0.f ? 0 : (thi > (float)(Bn - 1) ? Bn - 1 : (int)thi);
   }
   F.h = hf;
   F.r = fmaf(0.5f, hf, g.d);
@@ -430,78 +392,89 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
   }
   const int64_t B = Bn;
   const E* payload = static_cast<const E*>(a.payload);
-  Chunk ck[2];
-  bool have = next_chunk(cur, a.offsets, P.bin_base, B, ck[0]);
-  if (have && lane == 0) {
-    mbar_arrive_expect_tx(&sm.bar[0], ck[0].n * (uint32_t)sizeof(E));
-    bulk_copy_g2s(sm.buf[0], payload + ck[0].j0, ck[0].n * (uint32_t)sizeof(E), &sm.bar[0]);
-  }
-  int k = 0;
-  while (have) {
-    const int cb = k & 1, nb = cb ^ 1;
-    const bool more = next_chunk(cur, a.offsets, P.bin_base, B, ck[nb]);
-    if (more && lane == 0) {
-      fence_proxy_async_smem();  // the warp's reads of this buffer (previous chunk) come first
-      mbar_arrive_expect_tx(&sm.bar[nb], ck[nb].n * (uint32_t)sizeof(E));
-      bulk_copy_g2s(sm.buf[nb], payload + ck[nb].j0, ck[nb].n * (uint32_t)sizeof(E), &sm.bar[nb]);
+  const int nx = qhi[0] - qlo[0] + 1, ny = qhi[1] - qlo[1] + 1;
+  const int nrows = ny * (D == 3 ? qhi[2] - qlo[2] + 1 : 1);
+  for (int rg = 0; rg < nrows; rg += 32) {
+    // this group's rows: one lane each
+    uint32_t rs = 0, rn = 0;
+    const int ri = rg + lane;
+    if (ri < nrows) {
+      const int y = qlo[1] + ri % ny, z = D == 3 ? qlo[2] + ri / ny : 0;
+      const int64_t b0 = P.bin_base + qlo[0] + B * (y + B * (int64_t)z);
+      rs = a.offsets[b0];
+      rn = a.offsets[b0 + nx] - rs;
     }
-    mbar_wait_bounded(&sm.bar[cb], (phase >> cb) & 1u, a.err);
-    phase ^= 1u << cb;
-    const Chunk& C = ck[cb];
-    bool surv = false;
-    if ((uint32_t)lane < C.n) {
-      const E& ent = sm.buf[cb][lane];
-      const uint32_t id = ent.id;
-      bool canon = ((id >> 29) & 1u) || C.x == cur.qlo[0];
-      canon = canon && (((id >> 30) & 1u) || C.y == cur.qlo[1]);
-      if (D == 3) canon = canon && (((id >> 31) & 1u) || C.z == cur.qlo[2]);
-      if (canon) {
-        wc.cand++;
-        const uint32_t f = id & kIdMask;
-        float nh[3] = {0.f, 0.f, 0.f};
-        if constexpr (D == 3) {
-          nh[0] = ent.n[0];
-          nh[1] = ent.n[1];
-          nh[2] = ent.n[2];
-        }
-        float V[D * D];
+    const uint32_t incl = warp_inclusive_scan<uint32_t>(rn);
+    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t rv = incl - rn;
+    const uint32_t nch = (T + 31u) / 32u;
+    if (nch == 0) continue;
+    int cb = 0;
+    issue_chunk<E>(payload, rs, rn, rv, 0u, T, sm.buf[0], &sm.bar[0], lane);
+    for (uint32_t c = 0; c < nch; ++c) {
+      const int nb = cb ^ 1;
+      const bool more = c + 1 < nch;
+      if (more) issue_chunk<E>(payload, rs, rn, rv, c + 1, T, sm.buf[nb], &sm.bar[nb], lane);
+      mbar_wait_bounded(&sm.bar[cb], (phase >> cb) & 1u, a.err);
+      phase ^= 1u << cb;
+      const uint32_t n = T - 32u * c < 32u ? T - 32u * c : 32u;
+      bool surv = false;
+      if ((uint32_t)lane < n) {
+        const E& ent = sm.buf[cb][lane];
+        const uint32_t id = ent.id;
+        // visit a face only in the first bin of its range inside the query box
+        bool canon = ((id >> 29) & 1u) || (int)ent.bin[0] == qlo[0];
+        canon = canon && (((id >> 30) & 1u) || (int)ent.bin[1] == qlo[1]);
+        if (D == 3) canon = canon && (((id >> 31) & 1u) || (int)ent.bin[2] == qlo[2]);
+        if (canon) {
+          wc.cand++;
+          const uint32_t f = id & kIdMask;
+          float nh[3] = {0.f, 0.f, 0.f};
+          if constexpr (D == 3) {
+            nh[0] = ent.n[0];
+            nh[1] = ent.n[1];
+            nh[2] = ent.n[2];
+          }
+          float V[D * D];
 #pragma unroll
-        for (int j = 0; j < D * D; ++j) V[j] = ent.v[j];
-        surv = setup_face<D>(V, nh, F, sm.surv[lane]);
-        sm.surv[lane].face = f;
+          for (int j = 0; j < D * D; ++j) V[j] = ent.v[j];
+          surv = setup_face<D>(V, nh, F, sm.surv[lane]);
+          sm.surv[lane].face = f;
+        }
       }
-    }
-    unsigned m = __ballot_sync(0xffffffffu, surv);
-    __syncwarp();
-    wc.surv += __popc(m);
-    while (m) {
-      const int s = __ffs(m) - 1;
-      m &= m - 1;
-      const Surv<D>& S = sm.surv[s];
-      bool r0 = false, r1 = false;
-      if (lane_cell && !(kMarkOnly && h0)) {
-        int t = cell_test<D>(S, o0);
-        if (t == 2) t = resolve_fp64<D>(a, gid, S.face, b, lane, &wc.fb, &wc.band) ? 1 : 0;
-        r0 = t != 0;
-      }
-      if (D == 3 && !(kMarkOnly && h1)) {
-        int t = cell_test<D>(S, o1);
-        if (t == 2) t = resolve_fp64<D>(a, gid, S.face, b, lane + 32, &wc.fb, &wc.band) ? 1 : 0;
-        r1 = t != 0;
-      }
-      h0 |= r0;
-      h1 |= r1;
-      on_surv(S.face, r0, r1);
-    }
-    __syncwarp();
-    have = more;
-    ++k;
-    // marking only: once every cell of the block is marked, the rest of the walk cannot change the mask
-    if (kMarkOnly && have && __all_sync(0xffffffffu, (h0 || !lane_cell) && (D == 2 || h1))) {
-      mbar_wait_bounded(&sm.bar[nb], (phase >> nb) & 1u, a.err);  // the copy already in flight
-      phase ^= 1u << nb;
+      unsigned m = __ballot_sync(0xffffffffu, surv);
       __syncwarp();
-      break;
+      wc.surv += __popc(m);
+      while (m) {
+        const int s = __ffs(m) - 1;
+        m &= m - 1;
+        const Surv<D>& S = sm.surv[s];
+        int t0 = 0, t1 = 0;
+        if (!(kMarkOnly && h0 && h1)) cell_test2<D>(S, o0, o1, t0, t1);
+        bool r0 = false, r1 = false;
+        if (lane_cell && !(kMarkOnly && h0)) {
+          if (t0 == 2) t0 = resolve_fp64<D>(a, gid, S.face, b, lane, &wc.fb, &wc.band) ? 1 : 0;
+          r0 = t0 != 0;
+        }
+        if (D == 3 && !(kMarkOnly && h1)) {
+          if (t1 == 2) t1 = resolve_fp64<D>(a, gid, S.face, b, lane + 32, &wc.fb, &wc.band) ? 1 : 0;
+          r1 = t1 != 0;
+        }
+        h0 |= r0;
+        h1 |= r1;
+        on_surv(S.face, r0, r1);
+      }
+      __syncwarp();
+      // marking only: once every cell of the block is marked, the rest of the walk cannot change the mask
+      if (kMarkOnly && __all_sync(0xffffffffu, (h0 || !lane_cell) && (D == 2 || h1))) {
+        if (more) {
+          mbar_wait_bounded(&sm.bar[nb], (phase >> nb) & 1u, a.err);  // the copy already in flight
+          phase ^= 1u << nb;
+          __syncwarp();
+        }
+        return;
+      }
+      cb = nb;
     }
   }
 }
