@@ -23,8 +23,11 @@ namespace amr {
 
 namespace {
 
-constexpr int kLThreads = 128;  // threads per block
-constexpr int kLRows = 128;     // adjacent cells per tile (one per thread in phases 0 and 2)
+#ifndef AMR_LINK_TILE
+#define AMR_LINK_TILE 128
+#endif
+constexpr int kLThreads = AMR_LINK_TILE;  // threads per block
+constexpr int kLRows = AMR_LINK_TILE;     // adjacent cells per tile (one per thread in phases 0 and 2)
 static_assert(kLThreads == kLRows, "phase 0 and 2 map thread i to row i");
 
 __constant__ int c_d2q9[9][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}, {1, 1}, {-1, 1}, {-1, -1}, {1, -1}};

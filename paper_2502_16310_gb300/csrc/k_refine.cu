@@ -664,12 +664,14 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
           bad = true;
         ++c0;
       }
-      if (r1) {
-        if (c1 < n1 && can1)
-          a.adj_ids[off1 + c1] = f;
-        else
-          bad = true;
-        ++c1;
+      if constexpr (D == 3) {
+        if (r1) {
+          if (c1 < n1 && can1)
+            a.adj_ids[off1 + c1] = f;
+          else
+            bad = true;
+          ++c1;
+        }
       }
     };
     const uint64_t desc = a.lv.recs ? a.lv.rec_desc[blk] : ~0ull;
