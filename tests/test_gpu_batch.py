@@ -168,3 +168,60 @@ def test_autotune_picks_a_candidate():
     g.close()
     (ref,), _ = _single(w)
     _same(ref, res, "tuned")
+
+
+@pytest.mark.slow
+def test_c5_batched_sampled():
+    """The 48-geometry workload in one batch (bin densities from the autotuner, graph replay), checked
+    against the oracle on seeded samples of six geometries: bins in full, blocks, adjacency and links
+    sampled."""
+    import torch
+
+    from oracle.oracle import Domain, OracleGeometry
+    from paper_2502_16310_gb300 import AmrBatch, AmrGeom
+    from synth import batched_workloads
+
+    ws = batched_workloads(48)
+    data = [(torch.from_numpy(w.verts).cuda(), torch.from_numpy(w.idx).cuda()) for w in ws]
+    for w, (v, ix) in zip(ws, data):
+        g = AmrGeom(3, (w.root,) * 3)
+        g.load(v, ix)
+        w.bins, _, _ = g.autotune(w.n_levels, w.d_abs, w.d_rel, 19, True, True, b_candidates=[16, 32, 64, 128],
+                                  w_candidates=[4])
+        g.close()
+    b = AmrBatch(3)
+    for w, (v, ix) in zip(ws, data):
+        b.add(v, ix, w.root, w.n_levels, w.d_abs, w.d_rel, w.bins)
+    for _ in range(2):
+        b.run(19, True, True, use_graph=True)
+    rng = np.random.default_rng(55)
+    big = int(np.argmax([w.n_faces for w in ws]))
+    deep = int(np.argmax([w.n_levels * 1000 + w.root for w in ws]))
+    pick = sorted({big, deep, *rng.choice(len(ws), size=4, replace=False).tolist()})
+    for i in pick:
+        w = ws[i]
+        out = _host(b.view(i))
+        geo = OracleGeometry(3, w.verts, w.idx)
+        # bins of this geometry, in full, from the single-geometry path at the tuned density
+        g = AmrGeom(3, (w.root,) * 3)
+        g.load(*data[i])
+        bins = g.bin(w.bins)
+        off_g = bins["offsets"].cpu().numpy().view(np.uint32)
+        ids_g = bins["ids"].cpu().numpy().view(np.uint32)
+        g.close()
+        off_o, ids_o = geo.bin(Domain.unit(3, w.root), w.bins)
+        U.compare_bins(off_g, ids_g, off_o, ids_o)
+        lv = out["levels"]
+        for L in range(len(lv)):
+            U.compare_level(geo, 3, L, lv[L]["blocks"], lv[L]["mask"].view(np.uint64), sample=40, rng=rng)
+            if L + 1 < len(lv):
+                U.check_children(3, lv[L]["blocks"], lv[L]["mask"].view(np.uint64), lv[L + 1]["blocks"],
+                                 lv[L + 1]["parent"])
+        fin = lv[-1]
+        U.compare_adjacency(geo, 3, len(lv) - 1, fin["blocks"], fin["mask"].view(np.uint64),
+                            out["adj_cell"].astype(np.uint32), out["adj_off"].astype(np.uint32),
+                            out["adj_ids"].astype(np.uint32), sample=60, rng=rng)
+        U.compare_links(geo, 3, len(lv) - 1, 19, fin["blocks"], out["adj_cell"].astype(np.uint32),
+                        out["link_cell"].astype(np.uint32), out["link_dir"], out["link_q"],
+                        out["link_face"].astype(np.uint32), sample=60, rng=rng)
+    b.close()
