@@ -177,6 +177,7 @@ def run_ours(args, rank, world, local):
     n_cand, n_surv = res["n_candidates"], res["n_survivors"]
     n_fb, n_band = res["n_fallback"], res["n_band"]
     blocks = [int(lv["blocks"].shape[0]) for lv in res["levels"]]
+    nnz = int(g.bin(w.bins)["ids"].shape[0])  # (face, bin) incidences
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -226,6 +227,7 @@ def run_ours(args, rank, world, local):
     t_refine = kern.get("refine_level", {}).get("ms_per_step", float("nan"))
     dom = max(kern.items(), key=lambda kv: kv[1]["ms_per_step"])
     roof = roofline(dom[0], dom[1], w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks)
+    binning = bin_roofline(w, nnz, t_bin)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -239,6 +241,7 @@ def run_ours(args, rank, world, local):
                    "fp64_fallbacks_per_step": n_fb, "band_cases_per_step": n_band},
         "faces_binned_per_s": w.n_faces / (t_bin * 1e-3) if t_bin > 0 else None,
         "cell_face_tests_per_s": (n_surv * (64 if w.dim == 3 else 16)) / (t_refine * 1e-3) if t_refine > 0 else None,
+        "binning": binning,
         "kernels_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in kern.items()},
         "wall_s": wall,
         "gpu_launches": int(launches),
@@ -402,6 +405,23 @@ def roofline(name, k, w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks):
     a = byts / t / 1e9
     return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
             "traffic": None, "peak_source": src}
+
+
+def bin_roofline(w, nnz, t_bin_ms):
+    """HBM roofline of the binning kernels (count, scan, scatter) together: algorithmic bytes =
+    face coordinates read by the count and scatter passes (2 x 4 D^2 per face), the per-face bin range
+    written and read back (2 x 4 D), the counter array zeroed, counted, scanned and read as offsets
+    (16 bytes per bin) and, per (face, bin) incidence, its 4-byte id and its payload entry."""
+    hbm, src = measured_peaks()
+    D = w.dim
+    entry = 64 if D == 3 else 32
+    nb = w.bins ** D
+    byts = 2 * 4 * D * D * w.n_faces + 2 * 4 * D * w.n_faces + 16 * nb + (4 + entry) * nnz
+    t = t_bin_ms * 1e-3
+    a = byts / t / 1e9 if t > 0 else 0.0
+    return {"kernels": ["bin_count", "bin_scan", "bin_scatter"], "bound": "hbm", "faces_per_s": w.n_faces / t,
+            "incidences": nnz, "bytes": byts, "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+            "peak_source": src}
 
 
 def run_e2e(g, w, args, dev):

@@ -465,10 +465,10 @@ amr_status amr_bin_all(amr_ctx* ctx) {
   TRY(ensure(ctx, ctx->payload, esz * (size_t)tot));
   ScatterArgs sa{};
   sa.f = fa;
-  sa.nrm = static_cast<const float*>(ctx->nrm.p);
   sa.offsets = offsets;
   sa.ids = static_cast<uint32_t*>(ctx->ids.p);
   sa.payload = ctx->payload.p;
+  sa.rec = static_cast<const FaceRec3*>(ctx->frec.p);
   timed(ctx, st, "bin_scatter", [&] { return launch_scatter(sa, st); });
   CK(cudaGetLastError());
   ctx->n_bins = nb;

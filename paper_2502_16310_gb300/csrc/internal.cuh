@@ -173,44 +173,77 @@ __device__ __forceinline__ int bin_coord(double x, double o, double s, int B) {
   return (int)t;
 }
 
+// The same bin coordinate, decided in FP32 where that is certain.  The FP32
+// estimate t = ((x - o_hi) - o_lo) * s32 differs from (x - o) s by less than
+// 5u (|x| + |o|) |s|, and the FP64 value above by no more than that plus a few
+// FP64 ulps; when t lies farther than 8u (|x| + |o|) |s| from every integer,
+// both floors agree.  Otherwise (and for non-finite input) the FP64 formula
+// decides, so the result is always that of bin_coord.
+__device__ __forceinline__ int bin_coord_fast(float x, const GeomParams& P, int c) {
+  const float d = (x - P.org_hi[c]) - P.org_lo[c];
+  const float t = d * P.scale32[c];
+  const float err = 8.0f * kU32 * (fabsf(x) + fabsf(P.org_hi[c])) * fabsf(P.scale32[c]);
+  const float k = floorf(t);
+  if (t - k > err && (k + 1.0f) - t > err) {
+    if (!(k >= 0.0f)) return 0;
+    if (k > (float)(P.B - 1)) return P.B - 1;
+    return (int)k;
+  }
+  return bin_coord((double)x, P.origin[c], P.bin_scale[c], P.B);
+}
+
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
 // Decoupled look-back over ticket-ordered tiles (single-pass prefix sums).
 // state[t] = flag(2 bits: 1 aggregate, 2 inclusive prefix) << 62 | value.
-// Called by thread 0 of the CTA with the tile's aggregate; returns the
-// exclusive prefix of the tile.  A wait that exceeds kSpinLimit polls sets
-// ERR_TIMEOUT and returns what it has (the caller's output is then invalid,
-// and the host reports AMR_ETIMEOUT).
-__device__ __forceinline__ uint64_t lookback_exclusive(uint64_t* state, long long tile, uint64_t aggregate,
-                                                       unsigned* err) {
+// Called by one whole warp of the CTA with the tile's aggregate (all lanes the
+// same value); every lane returns the tile's exclusive prefix.  The warp reads
+// the 32 preceding tiles' states at once: when all tiles after the nearest
+// inclusive one have published, their aggregates and that prefix are summed
+// (one round trip for the common case); without an inclusive one in the
+// window, the window moves 32 tiles back.  A wait that exceeds kSpinLimit polls
+// sets ERR_TIMEOUT and returns what it has (the caller's output is then
+// invalid, and the host reports AMR_ETIMEOUT).
+__device__ __forceinline__ uint64_t lookback_warp(uint64_t* state, long long tile, uint64_t aggregate,
+                                                  unsigned* err) {
   constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kVal = (1ull << 62) - 1;
+  const int lane = threadIdx.x & 31;
   if (tile == 0) {
-    atomicExch(reinterpret_cast<unsigned long long*>(state), (unsigned long long)(kInc | (aggregate & kVal)));
+    if (lane == 0)
+      atomicExch(reinterpret_cast<unsigned long long*>(state), (unsigned long long)(kInc | (aggregate & kVal)));
     return 0;
   }
-  atomicExch(reinterpret_cast<unsigned long long*>(state + tile), (unsigned long long)(kAgg | (aggregate & kVal)));
+  if (lane == 0)
+    atomicExch(reinterpret_cast<unsigned long long*>(state + tile), (unsigned long long)(kAgg | (aggregate & kVal)));
   uint64_t prefix = 0;
-  long long t = tile - 1;
+  long long base = tile - 1;  // lane l looks at tile base - l
   long long spins = 0;
-  while (t >= 0) {
-    const uint64_t s = ld_volatile_u64(state + t);
-    const uint64_t f = s >> 62;
-    if (f == 0) {
+  for (;;) {
+    const long long t = base - lane;
+    const uint64_t s = t >= 0 ? ld_volatile_u64(state + t) : kInc;  // before tile 0: prefix 0
+    const uint32_t f = (uint32_t)(s >> 62);
+    const unsigned inc = __ballot_sync(0xffffffffu, f == 2u);
+    const int first = inc ? __ffs(inc) - 1 : 32;  // nearest tile with an inclusive prefix
+    if (__ballot_sync(0xffffffffu, f == 0u && lane <= first)) {
       if (++spins > kSpinLimit) {
-        atomicOr(err, ERR_TIMEOUT);
+        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
         break;
       }
       __nanosleep(20);
       continue;
     }
-    prefix += s & kVal;
-    if (f == 2) break;
-    --t;
+    uint64_t v = lane <= first ? (s & kVal) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    prefix += v;
+    if (first < 32) break;
+    base -= 32;
   }
-  atomicExch(reinterpret_cast<unsigned long long*>(state + tile),
-             (unsigned long long)(kInc | ((prefix + aggregate) & kVal)));
+  if (lane == 0)
+    atomicExch(reinterpret_cast<unsigned long long*>(state + tile),
+               (unsigned long long)(kInc | ((prefix + aggregate) & kVal)));
   return prefix;
 }
 
@@ -321,10 +354,10 @@ int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint
                      cudaStream_t st);
 struct ScatterArgs {
   FaceBinArgs f;
-  const float* nrm;   // 3D face normals (hi parts are copied into the entries)
   const uint32_t* offsets;
   uint32_t* ids;
   void* payload;
+  const FaceRec3* rec;      // 3D face records (vertices and normal copied into the entries)
 };
 int launch_scatter(const ScatterArgs& a, cudaStream_t st);
 

@@ -123,8 +123,8 @@ __global__ void k_face_bins(FaceBinArgs a) {
         mn = fminf(mn, x);
         mx = fmaxf(mx, x);
       }
-      lo[c] = bin_coord((double)mn, P.origin[c], P.bin_scale[c], P.B);
-      hi[c] = bin_coord((double)mx, P.origin[c], P.bin_scale[c], P.B);
+      lo[c] = bin_coord_fast(mn, P, c);
+      hi[c] = bin_coord_fast(mx, P, c);
       a.frange[(int64_t)c * a.nf + f] = (uint32_t)lo[c] | ((uint32_t)hi[c] << 16);
     }
     const int64_t B = P.B;
@@ -136,14 +136,16 @@ __global__ void k_face_bins(FaceBinArgs a) {
 
 // Scatter: every (face, bin) incidence claims a slot of the bin by decrementing
 // the bin's count (which leaves the counts zeroed for the next call) and writes
-// the face id and its coordinates there.
+// the face id and its payload entry (coordinates, normal, id | first-bin
+// flags, bin coordinates) there.
 template <int D>
 __global__ void k_scatter(ScatterArgs a) {
   using E = typename EntryT<D>::type;
   E* payload = static_cast<E*>(a.payload);
   const int64_t nf = a.f.nf;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
-    const GeomParams P = geom_row(a.f.g0, a.f.table, a.f.face_gid, f);
+    const GeomParams& P = a.f.table ? a.f.table[a.f.face_gid ? a.f.face_gid[f] : 0u] : a.f.g0;
+    const int64_t B = P.B, bin_base = P.bin_base;
     int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
 #pragma unroll
     for (int c = 0; c < D; ++c) {
@@ -151,18 +153,22 @@ __global__ void k_scatter(ScatterArgs a) {
       lo[c] = (int)(r & 0xffffu);
       hi[c] = (int)(r >> 16);
     }
-    E e;
-#pragma unroll
-    for (int j = 0; j < D * D; ++j) e.v[j] = a.f.X[(int64_t)j * nf + f];
+    E e{};
     if constexpr (D == 3) {
+      // the face record's first 48 bytes are the entry's vertices and normal
+      const float4* R = reinterpret_cast<const float4*>(a.rec + f);
+      float4* q = reinterpret_cast<float4*>(&e);
+      q[0] = __ldg(R);
+      q[1] = __ldg(R + 1);
+      q[2] = __ldg(R + 2);
+    } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) e.n[c] = a.nrm[(int64_t)c * nf + f];
+      for (int j = 0; j < 4; ++j) e.v[j] = a.f.X[(int64_t)j * nf + f];
     }
-    const int64_t B = P.B;
     for (int z = lo[2]; z <= hi[2]; ++z)
       for (int y = lo[1]; y <= hi[1]; ++y)
         for (int x = lo[0]; x <= hi[0]; ++x) {
-          const int64_t b = P.bin_base + x + B * (y + B * (int64_t)z);
+          const int64_t b = bin_base + x + B * (y + B * (int64_t)z);
           const uint32_t old = atomicSub(&a.f.count[b], 1u);
           const int64_t pos = (int64_t)a.offsets[b] + old - 1;
           a.ids[pos] = (uint32_t)f;
@@ -206,6 +212,8 @@ __global__ void __launch_bounds__(kThreads) k_scan(const T* __restrict__ in, T* 
     return;
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  static_assert(ITEMS * sizeof(T) % 16 == 0, "a thread's items are whole 16-byte vectors");
+  const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) == 0;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
     __syncthreads();
@@ -214,12 +222,24 @@ __global__ void __launch_bounds__(kThreads) k_scan(const T* __restrict__ in, T* 
     const int64_t base = tile * (int64_t)kThreads * ITEMS + (int64_t)threadIdx.x * ITEMS;
     uint64_t v[ITEMS];
     uint64_t sum = 0;
+    const bool full = vec && base + ITEMS <= n;
+    if (full) {
+      // ITEMS * sizeof(T) bytes as 16-byte loads
+      T t[ITEMS];
+      const uint4* src = reinterpret_cast<const uint4*>(in + base);
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const int64_t j = base + i;
-      v[i] = j < n ? (uint64_t)in[j] : 0ull;
-      sum += v[i];
+      for (int q = 0; q < (int)(ITEMS * sizeof(T) / 16); ++q) reinterpret_cast<uint4*>(t)[q] = src[q];
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) v[i] = (uint64_t)t[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const int64_t j = base + i;
+        v[i] = j < n ? (uint64_t)in[j] : 0ull;
+      }
     }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) sum += v[i];
     const uint64_t incl = warp_inclusive_scan<unsigned long long>(sum);
     if (lane == 31) s_warp[wid] = incl;
     __syncthreads();
@@ -230,19 +250,33 @@ __global__ void __launch_bounds__(kThreads) k_scan(const T* __restrict__ in, T* 
     }
     __syncthreads();
     const uint64_t warp_excl = wid > 0 ? s_warp[wid - 1] : 0ull;
-    if (threadIdx.x == 0) {
+    if (wid == 0) {
       const uint64_t agg = s_warp[kThreads / 32 - 1];
-      const uint64_t pre = lookback_exclusive(state, tile, agg, err);
-      s_prefix = pre;
-      if (tile == ntiles - 1) *total = pre + agg;
+      const uint64_t pre = lookback_warp(state, tile, agg, err);
+      if (lane == 0) {
+        s_prefix = pre;
+        if (tile == ntiles - 1) *total = pre + agg;
+      }
     }
     __syncthreads();
     uint64_t run = s_prefix + warp_excl + incl - sum;
+    if (full) {
+      T t[ITEMS];
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-      const int64_t j = base + i;
-      if (j < n) out[j] = (T)run;
-      run += v[i];
+      for (int i = 0; i < ITEMS; ++i) {
+        t[i] = (T)run;
+        run += v[i];
+      }
+      uint4* dst = reinterpret_cast<uint4*>(out + base);
+#pragma unroll
+      for (int q = 0; q < (int)(ITEMS * sizeof(T) / 16); ++q) dst[q] = reinterpret_cast<const uint4*>(t)[q];
+    } else {
+#pragma unroll
+      for (int i = 0; i < ITEMS; ++i) {
+        const int64_t j = base + i;
+        if (j < n) out[j] = (T)run;
+        run += v[i];
+      }
     }
     __syncthreads();
   }
@@ -302,7 +336,7 @@ __global__ void k_face_gid(const GeomParams* __restrict__ table, int n_geom, int
   }
 }
 
-constexpr int kScanItemsU32 = 8;
+constexpr int kScanItemsU32 = 16;
 constexpr int kScanItemsU64 = 4;
 
 size_t scan_scratch(int64_t n, int items) {
@@ -362,6 +396,9 @@ int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint
   for (int c = 0; c < 3; ++c) {
     a.g0.origin[c] = g.origin[c];
     a.g0.bin_scale[c] = g.scale[c];
+    a.g0.org_hi[c] = (float)g.origin[c];
+    a.g0.org_lo[c] = (float)(g.origin[c] - (double)a.g0.org_hi[c]);
+    a.g0.scale32[c] = (float)g.scale[c];
   }
   a.frange = frange;
   a.count = count;

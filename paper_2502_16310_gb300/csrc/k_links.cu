@@ -467,13 +467,15 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
     }
     __syncthreads();
     const uint32_t wex = wid > 0 ? s_warp[wid - 1] : 0u;
-    if (tid == 0) {
+    if (wid == 0) {
       const uint64_t agg = s_warp[NW - 1];
-      const uint64_t pre = lookback_exclusive(state, tile, agg, a.err);
-      s_prefix = pre;
-      if (tile == ntiles - 1) {
-        *a.n_links = pre + agg;
-        if ((int64_t)(link0 + pre + agg) > a.link_cap) atomicOr(a.err, ERR_OVERFLOW);
+      const uint64_t pre = lookback_warp(state, tile, agg, a.err);
+      if (lane == 0) {
+        s_prefix = pre;
+        if (tile == ntiles - 1) {
+          *a.n_links = pre + agg;
+          if ((int64_t)(link0 + pre + agg) > a.link_cap) atomicOr(a.err, ERR_OVERFLOW);
+        }
       }
     }
     __syncthreads();

@@ -786,14 +786,16 @@ __global__ void __launch_bounds__(kChThreads) k_children(ChildrenArgs a, uint64_
     }
     __syncthreads();
     const uint32_t wex = wid > 0 ? s_warp[wid - 1] : 0u;
-    if (threadIdx.x == 0) {
+    if (wid == 0) {
       const uint64_t agg = s_warp[kChThreads / 32 - 1];
-      const uint64_t pre = lookback_exclusive(state, tile, agg, a.err);
-      s_prefix = pre;
-      if (tile == ntiles - 1) {
-        const uint64_t tot = (pre + agg) * NCH;
-        *a.total = tot;
-        if ((int64_t)tot > a.cap_out) atomicOr(a.err, ERR_OVERFLOW);
+      const uint64_t pre = lookback_warp(state, tile, agg, a.err);
+      if (lane == 0) {
+        s_prefix = pre;
+        if (tile == ntiles - 1) {
+          const uint64_t tot = (pre + agg) * NCH;
+          *a.total = tot;
+          if ((int64_t)tot > a.cap_out) atomicOr(a.err, ERR_OVERFLOW);
+        }
       }
     }
     __syncthreads();
