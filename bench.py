@@ -176,6 +176,7 @@ def run_ours(args, rank, world, local):
     n_pairs = int(res["adj_ids"].shape[0])
     n_cand, n_surv = res["n_candidates"], res["n_survivors"]
     n_fb, n_band = res["n_fallback"], res["n_band"]
+    n_lcand = res.get("n_link_candidates", 0)
     blocks = [int(lv["blocks"].shape[0]) for lv in res["levels"]]
     nnz = int(g.bin(w.bins)["ids"].shape[0])  # (face, bin) incidences
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -238,7 +239,8 @@ def run_ours(args, rank, world, local):
                    "adjacent_finest_cells": n_adj, "adjacent_pairs": n_pairs, "links": n_links,
                    "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)",
                    "level_loop": "CUDA graph replay" if use_graph else "eager",
-                   "fp64_fallbacks_per_step": n_fb, "band_cases_per_step": n_band},
+                   "fp64_fallbacks_per_step": n_fb, "band_cases_per_step": n_band,
+                   "block_face_candidates": n_cand, "block_survivors": n_surv, "link_candidates": n_lcand},
         "faces_binned_per_s": w.n_faces / (t_bin * 1e-3) if t_bin > 0 else None,
         "cell_face_tests_per_s": (n_surv * (64 if w.dim == 3 else 16)) / (t_refine * 1e-3) if t_refine > 0 else None,
         "binning": binning,

@@ -533,6 +533,10 @@ RefineLevel level_args(amr_ctx* ctx, const Plan& P, int L) {
   a.work = ctx->d_work;
   a.err = ctx->d_err;
   a.warps = P.warps;
+  // blocks per work fetch: batches hide the fetch latency where every warp has many blocks;
+  // single blocks keep the load balanced where there are few (and heavy ones cluster)
+  const int64_t per_warp = ctx->lv[L].cap / ((int64_t)ctx->num_sms * 16);
+  a.batch = per_warp >= 32 ? 4 : (per_warp >= 8 ? 2 : 1);
   return a;
 }
 
@@ -783,6 +787,7 @@ amr_status collect(amr_ctx* ctx, const Plan& P, cudaStream_t st, amr_refine_resu
   r.n_band = (int64_t)(cnt[CNT_BAND] + cnt[CNT_LINK_BAND]);
   r.n_candidates = (int64_t)cnt[CNT_CANDIDATES];
   r.n_survivors = (int64_t)cnt[CNT_SURVIVORS];
+  r.n_link_candidates = (int64_t)cnt[CNT_LINK_CAND];
   // per-level block pointers for the adjoint
   TRY(ensure(ctx, ctx->lvl_ptrs, sizeof(void*) * AMR_MAX_LEVELS));
   const int32_t** hp = reinterpret_cast<const int32_t**>(h + 256);

@@ -31,6 +31,7 @@ enum : int {
   CNT_SURVIVORS = 3,
   CNT_LINK_FALLBACK = 4,
   CNT_LINK_BAND = 5,
+  CNT_LINK_CAND = 6,
   CNT_N = 8,
 };
 
@@ -406,7 +407,9 @@ struct RefineLevel {
   unsigned* work;              // dynamic work counter (zeroed before launch)
   unsigned* err;
   int warps;                   // warps per CTA (tunable)
+  int batch;                   // consecutive blocks a warp takes per work fetch (1..kMaxBatch)
 };
+constexpr int kMaxBatch = 8;
 int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st);
 
 struct EmitArgs {

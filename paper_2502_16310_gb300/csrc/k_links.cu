@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
     if (blockIdx.x == 0 && tid == 0) *a.n_links = 0;
     return;
   }
-  unsigned long long n_fb = 0, n_band = 0;
+  unsigned long long n_fb = 0, n_band = 0, n_cand = 0;  // n_cand: warp-uniform
   for (;;) {
     if (tid == 0) {
       s_tile = atomicAdd(ticket, 1u);
@@ -384,6 +384,7 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
         const uint32_t nc = __popc(cand);
         const uint32_t incl = warp_inclusive_scan<uint32_t>(nc);
         const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+        n_cand += T;
         uint32_t pos = incl - nc;
         for (uint32_t m = cand; m; m &= m - 1) s_q[wid][pos++] = (uint16_t)(lane | (__ffs(m) << 5));
         __syncwarp();
@@ -505,6 +506,7 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
   if (lane == 0) {
     if (n_fb) atomicAdd(&a.counters[CNT_LINK_FALLBACK], n_fb);
     if (n_band) atomicAdd(&a.counters[CNT_LINK_BAND], n_band);
+    if (n_cand) atomicAdd(&a.counters[CNT_LINK_CAND], n_cand);
   }
 }
 

@@ -501,15 +501,25 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
   const int64_t n = launch_count(a.n_blocks, a.n_dev, a.err);
   constexpr int NC = D == 3 ? 64 : 16;
   WarpCounters wc;
+  // work in batches of a.batch consecutive blocks: one atomic and one coalesced
+  // load of the batch's coordinates and geometry ids per batch
+  const int batch = a.batch > 0 ? (a.batch < kMaxBatch ? a.batch : kMaxBatch) : 1;
   for (;;) {
-    unsigned blk = 0;
-    if (lane == 0) blk = atomicAdd(a.work, 1u);
-    blk = __shfl_sync(0xffffffffu, blk, 0);
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(a.work, (unsigned)batch);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n) break;
+    int cv = 0;
+    uint32_t gv = 0;
+    if (lane < batch * D && (int64_t)base + lane / D < n) cv = a.blocks[(int64_t)base * D + lane];
+    if (a.gid && lane < batch && (int64_t)base + lane < n) gv = a.gid[base + lane];
+  for (int q = 0; q < batch; ++q) {
+    const unsigned blk = base + (unsigned)q;
     if (blk >= n) break;
     int b[3] = {0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < D; ++c) b[c] = a.blocks[(int64_t)blk * D + c];
-    const uint32_t gid = a.gid ? a.gid[blk] : 0u;
+    for (int c = 0; c < D; ++c) b[c] = __shfl_sync(0xffffffffu, cv, q * D + c);
+    const uint32_t gid = __shfl_sync(0xffffffffu, gv, q);
     const GeomParams& P = a.table ? a.table[gid] : a.g0;
     // per-cell face counts and survivor records only where the block's geometry ends here
     const bool fin = a.blockcnt && a.level == P.n_levels - 1;
@@ -576,6 +586,7 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
       if (lane == 0) a.blockcnt[blk] = fin ? ((uint64_t)pairs | ((uint64_t)__popcll(m) << 32)) : 0ull;
     }
   }
+  }
   // flush warp counters
   unsigned long long v[4] = {wc.fb, wc.band, wc.cand, wc.surv};
 #pragma unroll
@@ -607,14 +618,22 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
   const int64_t n = launch_count(a.lv.n_blocks, a.lv.n_dev, a.lv.err);
   const uint64_t run_cells = a.run ? a.run[0] : 0ull, run_pairs = a.run ? a.run[1] : 0ull;
   WarpCounters wc;
+  // 32 blocks per atomic: each lane reads one block's mask, the warp then takes
+  // the marked blocks of the group one after another
   for (;;) {
-    unsigned blk = 0;
-    if (lane == 0) blk = atomicAdd(a.lv.work, 1u);
-    blk = __shfl_sync(0xffffffffu, blk, 0);
-    if (blk >= n) break;
-    const uint64_t mask = a.lv.mask[blk];
-    if (mask == 0) continue;
-    const uint32_t gid = a.lv.gid ? a.lv.gid[blk] : 0u;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(a.lv.work, 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n) break;
+    const bool in_range = (int64_t)base + lane < n;
+    const uint64_t my_mask = in_range ? a.lv.mask[base + lane] : 0ull;
+    const uint32_t my_gid = in_range && a.lv.gid ? a.lv.gid[base + lane] : 0u;
+    unsigned todo = __ballot_sync(0xffffffffu, my_mask != 0);
+  while (todo) {
+    const int q = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const unsigned blk = base + (unsigned)q;
+    const uint32_t gid = __shfl_sync(0xffffffffu, my_gid, q);
     const GeomParams& P = a.lv.table ? a.lv.table[gid] : a.lv.g0;
     if (a.lv.level != P.n_levels - 1) continue;
     int b[3] = {0, 0, 0};
@@ -736,6 +755,7 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
         L[k] = v;
       }
     }
+  }
   }
 }
 
