@@ -147,16 +147,76 @@ double sat_margin(int dim, const double* v, double r) {
   return m;
 }
 
+// ---------------------------------------------------------------------------
+// Point predicate (Alg. 1, Sec. "Face Detection"): a cell centre is adjacent
+// to a face when its Euclidean distance to the closed face is at most the
+// near-wall distance.  The paper checks spheres around the vertices, cylinders
+// around the edges and the prism over the face; together they are exactly the
+// points within that distance of the face, so the oracle evaluates the
+// distance itself: the distance to the plane when the point's projection lies
+// in the closed triangle, else the smallest distance to the three edges.
+// ---------------------------------------------------------------------------
+
+// Distance from the origin to the closed segment a-b.
+double point_segment_dist(const double* a, const double* b, int dim) {
+  double e[3] = {0, 0, 0}, ae = 0.0, ee = 0.0;
+  for (int c = 0; c < dim; ++c) {
+    e[c] = b[c] - a[c];
+    ae += -a[c] * e[c];
+    ee += e[c] * e[c];
+  }
+  const double t = ee > 0.0 ? std::min(1.0, std::max(0.0, ae / ee)) : 0.0;
+  double d2 = 0.0;
+  for (int c = 0; c < dim; ++c) {
+    const double q = a[c] + t * e[c];
+    d2 += q * q;
+  }
+  return std::sqrt(d2);
+}
+
+// Distance from the origin to the closed face with vertices v[dim][dim]
+// (given relative to the point).
+double point_face_dist(int dim, const double* v) {
+  double p[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int k = 0; k < dim; ++k)
+    for (int c = 0; c < dim; ++c) p[k][c] = v[k * dim + c];
+  if (dim == 2) return point_segment_dist(p[0], p[1], 2);
+  const double u[3] = {p[1][0] - p[0][0], p[1][1] - p[0][1], p[1][2] - p[0][2]};
+  const double w[3] = {p[2][0] - p[0][0], p[2][1] - p[0][1], p[2][2] - p[0][2]};
+  const double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+  const double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  if (nn > 0.0) {
+    // the projection is in the closed triangle iff it is on the same side of
+    // (or on) all three edge lines within the plane
+    bool neg = true, pos = true;
+    for (int k = 0; k < 3; ++k) {
+      const double* a = p[k];
+      const double* b = p[(k + 1) % 3];
+      const double e[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      const double m[3] = {e[1] * n[2] - e[2] * n[1], e[2] * n[0] - e[0] * n[2], e[0] * n[1] - e[1] * n[0]};
+      const double s = -(a[0] * m[0] + a[1] * m[1] + a[2] * m[2]);  // (origin - a) . (e x n)
+      if (s > 0.0) neg = false;
+      if (s < 0.0) pos = false;
+    }
+    if (neg || pos) return std::fabs(p[0][0] * n[0] + p[0][1] * n[1] + p[0][2] * n[2]) / std::sqrt(nn);
+  }
+  return std::min(point_segment_dist(p[0], p[1], 3),
+                  std::min(point_segment_dist(p[1], p[2], 3), point_segment_dist(p[2], p[0], 3)));
+}
+
 void cell_centre(const orc_domain& d, int level, const int32_t* cell, double* x) {
   const double h = level_h(d, level);
   for (int a = 0; a < d.dim; ++a) x[a] = d.origin[a] + ((double)cell[a] + 0.5) * h;
 }
 
-double face_margin(const orc_geom& g, int64_t f, const double* x, double r) {
+// Signed adjacency margin of cell centre x and face f (<= 0: adjacent).
+// pred 0 (box): SAT margin of the box x +- r; pred 1 (point): distance - d.
+double face_margin(const orc_geom& g, int64_t f, const double* x, double r, int pred, double d) {
   double loc[9];
   const int D = g.dim;
   for (int k = 0; k < D; ++k)
     for (int c = 0; c < D; ++c) loc[k * D + c] = g.X[(size_t)f * D * D + k * D + c] - x[c];
+  if (pred == 1) return point_face_dist(D, loc) - d;
   return sat_margin(D, loc, r);
 }
 
@@ -344,11 +404,12 @@ void orc_face_bin_range(const orc_geom* g, int64_t f, int32_t* lo, int32_t* hi) 
 }
 
 double orc_sat_margin(int dim, const double* verts_local, double r) { return sat_margin(dim, verts_local, r); }
+double orc_point_face_dist(int dim, const double* verts_local) { return point_face_dist(dim, verts_local); }
 
 // Sec. "Identification of Cells Near the Boundary": every cell of every block
 // of the level checks the faces of the bins around it; a block is marked when
 // any of its cells is adjacent.  The mask keeps the per-cell result.
-int orc_refine_blocks(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel,
+int orc_refine_blocks(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel, int pred,
                       const int32_t* blocks, int64_t n, uint64_t* mask, uint64_t* band, int64_t* n_band_pairs,
                       int64_t* n_candidates) {
   if (!g || g->B < 1 || !dom || dom->dim != g->dim) return 1;
@@ -378,7 +439,7 @@ int orc_refine_blocks(const orc_geom* g, const orc_domain* dom, int level, doubl
       }
       bool adj = false, robust = false, near = false;
       for (uint32_t f : cand) {
-        const double m = face_margin(*g, f, x, r);
+        const double m = face_margin(*g, f, x, r, pred, dL);
         if (m <= 0.0) adj = true;
         if (m < -tol) robust = true;
         if (std::fabs(m) <= tol) {
@@ -420,13 +481,14 @@ int64_t orc_children(int dim, const int32_t* blocks, int64_t n, const uint64_t* 
 
 // The faces a cell identifies (Sec. "Identification of Cells Near the Boundary":
 // the cell may store the faces it detects for the solver routines).
-int64_t orc_cell_faces(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel,
+int64_t orc_cell_faces(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel, int pred,
                        const int32_t* cells, int64_t n, int64_t* counts, uint32_t* ids, uint8_t* band,
                        int64_t cap) {
   if (!g || g->B < 1 || !dom) return -1;
   const int D = g->dim;
   const double h = level_h(*dom, level);
-  const double r = 0.5 * h + d_abs + d_rel * h;
+  const double dL = d_abs + d_rel * h;
+  const double r = 0.5 * h + dL;
   const double tol = kBand * h;
   std::vector<uint32_t> cand;
   int64_t tot = 0;
@@ -440,7 +502,7 @@ int64_t orc_cell_faces(const orc_geom* g, const orc_domain* dom, int level, doub
     gather_candidates(*g, lo, hi, true, cand);
     int64_t cnt = 0;
     for (uint32_t f : cand) {
-      const double m = face_margin(*g, f, x, r);
+      const double m = face_margin(*g, f, x, r, pred, dL);
       if (m <= 0.0 || std::fabs(m) <= tol) {
         // pairs inside the band are listed too, flagged, so a comparison can accept either answer
         if (tot < cap) {

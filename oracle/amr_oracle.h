@@ -12,7 +12,9 @@
  *               overlaps, B bins per axis over the domain
  *               (Sec. "Spatial Binning Algorithm");
  *   3. near-wall refinement: a cell is adjacent to a face when the cell box,
- *               inflated by the near-wall distance, intersects the closed face;
+ *               inflated by the near-wall distance, intersects the closed face
+ *               (pred 0, box), or when the cell centre lies within the
+ *               near-wall distance of the closed face (pred 1, point: Alg. 1);
  *               flagged blocks split into 2^D children; adjacent cells of the
  *               finest level list their faces and form wall links with the
  *               lattice directions (Sec. "Cell-Face Identification Algorithms").
@@ -63,10 +65,15 @@ void orc_face_bin_range(const orc_geom* g, int64_t f, int32_t* lo, int32_t* hi);
  * Positive = separated by that distance along the best axis, <= 0 = intersect. */
 double orc_sat_margin(int dim, const double* verts_local, double r);
 
+/* Euclidean distance from the origin to the closed face whose vertices are
+ * given relative to it (verts_local[dim][dim]); the point predicate of Alg. 1. */
+double orc_point_face_dist(int dim, const double* verts_local);
+
 /* Refinement of a list of blocks of one level: per block the adjacency bit of
  * every cell (mask) and the cells whose decision lies within the 1e-6*h_L
- * margin band (band).  Counters may be NULL. */
-int orc_refine_blocks(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel,
+ * margin band (band).  pred: 0 = box predicate, 1 = point predicate (margin =
+ * distance - d_L).  Counters may be NULL. */
+int orc_refine_blocks(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel, int pred,
                       const int32_t* blocks, int64_t n, uint64_t* mask, uint64_t* band,
                       int64_t* n_band_pairs, int64_t* n_candidates);
 
@@ -78,7 +85,7 @@ int64_t orc_children(int dim, const int32_t* blocks, int64_t n, const uint64_t* 
 /* Adjacent faces of given cells (global cell coords [n][dim] at `level`),
  * ascending face ids.  counts[n]; ids/band written up to `cap` entries
  * (band[e] = 1 when that pair's margin is within the band).  Returns total entries. */
-int64_t orc_cell_faces(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel,
+int64_t orc_cell_faces(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel, int pred,
                        const int32_t* cells, int64_t n, int64_t* counts, uint32_t* ids, uint8_t* band,
                        int64_t cap);
 

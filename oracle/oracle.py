@@ -59,11 +59,13 @@ def _load():
             lib.orc_sat_margin.restype = C.c_double
             lib.orc_sat_margin.argtypes = [C.c_int, P, C.c_double]
             lib.orc_refine_blocks.restype = C.c_int
-            lib.orc_refine_blocks.argtypes = [P, P, C.c_int, C.c_double, C.c_double, P, i64, P, P, P, P]
+            lib.orc_refine_blocks.argtypes = [P, P, C.c_int, C.c_double, C.c_double, C.c_int, P, i64, P, P, P, P]
+            lib.orc_point_face_dist.restype = C.c_double
+            lib.orc_point_face_dist.argtypes = [C.c_int, P]
             lib.orc_children.restype = i64
             lib.orc_children.argtypes = [C.c_int, P, i64, P, P, P]
             lib.orc_cell_faces.restype = i64
-            lib.orc_cell_faces.argtypes = [P, P, C.c_int, C.c_double, C.c_double, P, i64, P, P, P, i64]
+            lib.orc_cell_faces.argtypes = [P, P, C.c_int, C.c_double, C.c_double, C.c_int, P, i64, P, P, P, i64]
             lib.orc_cell_links.restype = C.c_int
             lib.orc_cell_links.argtypes = [P, P, C.c_int, C.c_int, P, i64, P, P, P]
             lib.orc_lattice_dir.restype = C.c_int
@@ -169,14 +171,15 @@ class OracleGeometry:
         return lo[:self.dim], hi[:self.dim]
 
     # -- step 3 ----------------------------------------------------------
-    def refine_blocks(self, level: int, blocks: np.ndarray, d_abs=0.0, d_rel=1.0, count_candidates=False):
+    def refine_blocks(self, level: int, blocks: np.ndarray, d_abs=0.0, d_rel=1.0, count_candidates=False, pred=0):
         b = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, self.dim)
         n = b.shape[0]
         mask = np.zeros(max(n, 1), np.uint64)
         band = np.zeros(max(n, 1), np.uint64)
         nbp = C.c_int64(0)
         ncand = C.c_int64(0)
-        rc = _load().orc_refine_blocks(self._h, C.byref(self._cdom), level, d_abs, d_rel, _p(b), n, _p(mask),
+        rc = _load().orc_refine_blocks(self._h, C.byref(self._cdom), level, d_abs, d_rel, int(pred), _p(b), n,
+                                       _p(mask),
                                        _p(band), C.byref(nbp), C.byref(ncand) if count_candidates else None)
         if rc:
             raise ValueError("orc_refine_blocks failed")
@@ -192,17 +195,19 @@ class OracleGeometry:
         lib.orc_children(self.dim, _p(b), b.shape[0], _p(m), _p(cb), _p(cp))
         return cb[:k], cp[:k]
 
-    def cell_faces(self, level: int, cells: np.ndarray, d_abs=0.0, d_rel=1.0):
+    def cell_faces(self, level: int, cells: np.ndarray, d_abs=0.0, d_rel=1.0, pred=0):
         """Per cell: ascending adjacent face ids; band flags mark pairs inside the margin band."""
         lib = _load()
         c = np.ascontiguousarray(cells, dtype=np.int32).reshape(-1, self.dim)
         n = c.shape[0]
         counts = np.zeros(max(n, 1), np.int64)
-        tot = int(lib.orc_cell_faces(self._h, C.byref(self._cdom), level, d_abs, d_rel, _p(c), n, _p(counts),
+        tot = int(lib.orc_cell_faces(self._h, C.byref(self._cdom), level, d_abs, d_rel, int(pred), _p(c), n,
+                                     _p(counts),
                                      None, None, 0))
         ids = np.zeros(max(tot, 1), np.uint32)
         band = np.zeros(max(tot, 1), np.uint8)
-        lib.orc_cell_faces(self._h, C.byref(self._cdom), level, d_abs, d_rel, _p(c), n, _p(counts), _p(ids),
+        lib.orc_cell_faces(self._h, C.byref(self._cdom), level, d_abs, d_rel, int(pred), _p(c), n, _p(counts),
+                           _p(ids),
                            _p(band), tot)
         off = np.zeros(n + 1, np.int64)
         off[1:] = np.cumsum(counts[:n])
@@ -240,6 +245,12 @@ class OracleGeometry:
         return out
 
 
+def point_face_dist(dim: int, verts_local: np.ndarray) -> float:
+    """Distance from the origin to the closed face (vertices relative to the point), Alg. 1's predicate."""
+    v = np.ascontiguousarray(verts_local, dtype=np.float64).reshape(dim, dim)
+    return float(_load().orc_point_face_dist(dim, _p(v)))
+
+
 def sat_margin(dim: int, verts_local: np.ndarray, r: float) -> float:
     v = np.ascontiguousarray(verts_local, dtype=np.float64)
     return float(_load().orc_sat_margin(dim, _p(v), float(r)))
@@ -264,7 +275,7 @@ def cells_of_mask(dim: int, blocks: np.ndarray, mask: np.ndarray):
 
 
 def run_pipeline(dim, verts, idx, *, root, n_levels, B, lattice, d_abs=0.0, d_rel=1.0, links=True,
-                 max_level_blocks=None):
+                 max_level_blocks=None, pred=0):
     """Whole oracle pass: bins, every level's blocks/masks/band masks, finest-level adjacency and links."""
     geo = OracleGeometry(dim, verts, idx)
     dom = Domain.unit(dim, root)
@@ -274,7 +285,7 @@ def run_pipeline(dim, verts, idx, *, root, n_levels, B, lattice, d_abs=0.0, d_re
     for L in range(n_levels):
         if max_level_blocks is not None and blocks.shape[0] > max_level_blocks:
             raise ValueError("level too large for the oracle")
-        mask, band, nbp, _ = geo.refine_blocks(L, blocks, d_abs, d_rel)
+        mask, band, nbp, _ = geo.refine_blocks(L, blocks, d_abs, d_rel, pred=pred)
         lv = {"blocks": blocks, "mask": mask, "band": band, "n_band_pairs": nbp}
         levels.append(lv)
         if L + 1 < n_levels:
@@ -286,7 +297,7 @@ def run_pipeline(dim, verts, idx, *, root, n_levels, B, lattice, d_abs=0.0, d_re
     bi, ci, cells = cells_of_mask(dim, fin["blocks"], fin["mask"])
     out["adj_block"], out["adj_bit"], out["adj_cells"] = bi, ci, cells
     L = n_levels - 1
-    out["adj_off"], out["adj_ids"], out["adj_band"] = geo.cell_faces(L, cells, d_abs, d_rel)
+    out["adj_off"], out["adj_ids"], out["adj_band"] = geo.cell_faces(L, cells, d_abs, d_rel, pred=pred)
     if links:
         out["q"], out["q_face"], out["q_band"] = geo.cell_links(L, lattice, cells)
     return out
