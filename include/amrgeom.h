@@ -121,8 +121,15 @@ AMR_API amr_status amr_bin_faces(amr_ctx* ctx, int bin_density, amr_bins_view* o
 /* Step 3 — near-wall refinement (Sec. "Cell-Face Identification Algorithms").
  * n_levels total levels (n_levels - 1 refinement passes), 1 <= n_levels <= AMR_MAX_LEVELS.
  * lattice: 0 (no links), 9 (D2Q9, dim 2) or 19 (D3Q19, dim 3).
- * want_links requires want_adjacency and d_L >= h_L/2 on the finest level, so
- * that every face a link crosses is in the cell's adjacency list.
+ * predicate: when a cell is adjacent to a face (Sec. "Face Detection"):
+ *   AMR_PRED_BOX   (0, default) the cell box inflated by d_L meets the closed face
+ *                  (separating-axis test);
+ *   AMR_PRED_POINT (1) the cell centre lies within distance d_L of the closed face
+ *                  (the paper's Alg. 1: spheres, cylinders and prism of radius d_spec;
+ *                  the paper's absolute d_spec is d_abs with d_rel = 0).
+ * want_links requires want_adjacency and, on the finest level, d_L >= h_L/2 (box)
+ * or d_L >= sqrt(2) h_L (point), so that every face a link crosses is in the
+ * cell's adjacency list; otherwise AMR_EINVAL.
  * Eager calls read back each level's size; graph calls read back once at the end
  * and re-run eagerly (transparently) if a size outgrew the captured capacities. */
 typedef struct {
@@ -135,7 +142,9 @@ typedef struct {
   int use_graph;              /* 1: replay the level loop as one captured CUDA graph when the inputs match
                                  the previous call (the first call runs eagerly and captures) */
   int warps_per_cta;          /* warps per thread block of the refine kernels, 0 = default (4), max 8 */
+  int predicate;              /* AMR_PRED_BOX (0) or AMR_PRED_POINT (1) */
 } amr_refine_params;
+enum { AMR_PRED_BOX = 0, AMR_PRED_POINT = 1 };
 
 /* Results.  Level arrays are per level 0..n_levels-1.
  *   block_coords[L]  device i32 [N_L][dim]

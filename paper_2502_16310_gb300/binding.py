@@ -54,7 +54,10 @@ class amr_bins_view(C.Structure):
 class amr_refine_params(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("d_abs", C.c_double), ("d_rel", C.c_double), ("lattice", C.c_int),
                 ("want_adjacency", C.c_int), ("want_links", C.c_int), ("use_graph", C.c_int),
-                ("warps_per_cta", C.c_int)]
+                ("warps_per_cta", C.c_int), ("predicate", C.c_int)]
+
+
+AMR_PRED_BOX, AMR_PRED_POINT = 0, 1
 
 
 class amr_refine_result(C.Structure):
@@ -193,11 +196,9 @@ def amr_bin_faces(ctx, bin_density: int) -> amr_bins_view:
 
 
 def amr_refine_near_wall(ctx, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True,
-                         want_links=True, use_graph=False, warps_per_cta=0) -> amr_refine_result:
-    p = amr_refine_params()
-    p.n_levels, p.d_abs, p.d_rel, p.lattice = int(n_levels), float(d_abs), float(d_rel), int(lattice)
-    p.want_adjacency, p.want_links = int(bool(want_adjacency)), int(bool(want_links))
-    p.use_graph, p.warps_per_cta = int(bool(use_graph)), int(warps_per_cta)
+                         want_links=True, use_graph=False, warps_per_cta=0,
+                         predicate=AMR_PRED_BOX) -> amr_refine_result:
+    p = _params(n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph, warps_per_cta, predicate)
     r = amr_refine_result()
     _check(ctx, lib().amr_refine_near_wall(ctx, C.byref(p), C.byref(r)))
     return r
@@ -212,11 +213,12 @@ def amr_sync(ctx):
 
 
 def _params(n_levels=1, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=True, use_graph=False,
-            warps_per_cta=0):
+            warps_per_cta=0, predicate=AMR_PRED_BOX):
     p = amr_refine_params()
     p.n_levels, p.d_abs, p.d_rel, p.lattice = int(n_levels), float(d_abs), float(d_rel), int(lattice)
     p.want_adjacency, p.want_links = int(bool(want_adjacency)), int(bool(want_links))
     p.use_graph, p.warps_per_cta = int(bool(use_graph)), int(warps_per_cta)
+    p.predicate = int(predicate)
     return p
 
 
@@ -374,12 +376,14 @@ class AmrGeom:
         return self.bins
 
     def refine(self, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=None,
-               use_graph=False, warps_per_cta=0):
-        """Step 3: near-wall refinement; returns per-level tensors, adjacency CSR and links (borrowed)."""
+               use_graph=False, warps_per_cta=0, predicate=AMR_PRED_BOX):
+        """Step 3: near-wall refinement; returns per-level tensors, adjacency CSR and links (borrowed).
+        predicate: AMR_PRED_BOX (inflated cell box meets the face) or AMR_PRED_POINT (cell centre within
+        d of the face, the paper's Alg. 1)."""
         if want_links is None:
             want_links = lattice != 0
         r = amr_refine_near_wall(self.ctx, n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph,
-                                 warps_per_cta)
+                                 warps_per_cta, predicate)
         return self._wrap(r, want_adjacency, want_links)
 
     def _wrap(self, r, want_adjacency, want_links):
@@ -547,10 +551,11 @@ class AmrBatch:
     def set_bins(self, i, B):
         _bcheck(self.b, lib().amr_batch_set_bins(self.b, int(i), int(B)))
 
-    def run(self, lattice=0, want_adjacency=True, want_links=None, use_graph=False, warps_per_cta=0):
+    def run(self, lattice=0, want_adjacency=True, want_links=None, use_graph=False, warps_per_cta=0,
+            predicate=AMR_PRED_BOX):
         if want_links is None:
             want_links = lattice != 0
-        p = _params(1, 0.0, 1.0, lattice, want_adjacency, want_links, use_graph, warps_per_cta)
+        p = _params(1, 0.0, 1.0, lattice, want_adjacency, want_links, use_graph, warps_per_cta, predicate)
         r = amr_refine_result()
         _bcheck(self.b, lib().amr_batch_run(self.b, C.byref(p), C.byref(r)))
         self.want = (want_adjacency or want_links, want_links)

@@ -62,12 +62,12 @@ constexpr int SC_WORDS = 72;
 struct GraphKey {
   uint64_t layout_gen = 0;
   int64_t nf = 0, n_geom = 0;
-  int n_levels = 0, lattice = 0, adjacency = 0, links = 0, warps = 0, B = 0;
+  int n_levels = 0, lattice = 0, adjacency = 0, links = 0, warps = 0, B = 0, pred = 0;
   double d_abs = 0, d_rel = 0;
   bool operator==(const GraphKey& o) const {
     return layout_gen == o.layout_gen && nf == o.nf && n_geom == o.n_geom && n_levels == o.n_levels &&
            lattice == o.lattice && adjacency == o.adjacency && links == o.links && warps == o.warps && B == o.B &&
-           d_abs == o.d_abs && d_rel == o.d_rel;
+           pred == o.pred && d_abs == o.d_abs && d_rel == o.d_rel;
   }
 };
 
@@ -485,7 +485,7 @@ struct Plan {
   bool fin_at[AMR_MAX_LEVELS];      // some geometry ends at this level
   bool cont_after[AMR_MAX_LEVELS];  // some geometry continues below this level
   bool adjacency, links;
-  int lattice, warps;
+  int lattice, warps, pred;
   int64_t n_roots;
 };
 
@@ -500,9 +500,15 @@ Plan make_plan(const amr_ctx* ctx, const amr_refine_params* p) {
   P.adjacency = p->want_adjacency != 0 || P.links;
   P.lattice = p->lattice;
   P.warps = p->warps_per_cta > 0 ? p->warps_per_cta : 4;
+  P.pred = p->predicate;
   for (const auto& g : ctx->geoms) P.n_roots += roots_of(g, ctx->dom.dim);
   return P;
 }
+
+// Smallest d_L / h_L for which every face a link segment (length up to sqrt(2) h)
+// can cross is in the cell's adjacency list: the inflated cell box contains the
+// segment once d_L >= h_L / 2; the ball of the point predicate once d_L >= sqrt(2) h_L.
+double link_reach(int pred) { return pred == AMR_PRED_POINT ? 1.4142135623730951 : 0.5; }
 
 RefineLevel level_args(amr_ctx* ctx, const Plan& P, int L) {
   RefineLevel a{};
@@ -533,6 +539,7 @@ RefineLevel level_args(amr_ctx* ctx, const Plan& P, int L) {
   a.work = ctx->d_work;
   a.err = ctx->d_err;
   a.warps = P.warps;
+  a.pred = P.pred;
   // blocks per work fetch: batches hide the fetch latency where every warp has many blocks;
   // single blocks keep the load balanced where there are few (and heavy ones cluster)
   const int64_t per_warp = ctx->lv[L].cap / ((int64_t)ctx->num_sms * 16);
@@ -816,6 +823,7 @@ amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine
   key.warps = P.warps;
   key.d_abs = prm->d_abs;
   key.d_rel = prm->d_rel;
+  key.pred = prm->predicate;
   const bool want_graph = prm->use_graph != 0;
   if (want_graph && ctx->gexec && ctx->gkey == key) {
     // replay on the graph stream, ordered after the caller's stream
@@ -1013,12 +1021,15 @@ amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_
   if (NL < 1 || NL > AMR_MAX_LEVELS) return fail(ctx, AMR_EINVAL, "n_levels must be in [1, %d]", AMR_MAX_LEVELS);
   if (!(prm->d_abs >= 0.0) || !(prm->d_rel >= 0.0)) return fail(ctx, AMR_EINVAL, "negative near-wall distance");
   if (prm->warps_per_cta < 0 || prm->warps_per_cta > 8) return fail(ctx, AMR_EINVAL, "warps_per_cta in [0, 8]");
+  if (prm->predicate != AMR_PRED_BOX && prm->predicate != AMR_PRED_POINT)
+    return fail(ctx, AMR_EINVAL, "predicate must be AMR_PRED_BOX (0) or AMR_PRED_POINT (1)");
   if (prm->want_links) {
     if (!((D == 2 && prm->lattice == 9) || (D == 3 && prm->lattice == 19)))
       return fail(ctx, AMR_EINVAL, "lattice must be 9 (D2Q9) in 2D or 19 (D3Q19) in 3D");
     const double hf = ctx->dom.h0 * std::ldexp(1.0, -(NL - 1));
-    if (prm->d_abs + prm->d_rel * hf < 0.5 * hf)
-      return fail(ctx, AMR_EINVAL, "links need d_L >= h_L/2 on the finest level");
+    if (prm->d_abs + prm->d_rel * hf < link_reach(prm->predicate) * hf)
+      return fail(ctx, AMR_EINVAL, "links need d_L >= %s h_L on the finest level",
+                  prm->predicate == AMR_PRED_POINT ? "sqrt(2)" : "1/2");
   }
   int64_t N0 = 1;
   for (int a = 0; a < D; ++a) N0 *= ctx->dom.root_blocks[a];
@@ -1467,7 +1478,8 @@ amr_status amr_batch_run(amr_batch* b, const amr_refine_params* prm, amr_refine_
       return fail(ctx, AMR_EINVAL, "lattice must be 9 (D2Q9) in 2D or 19 (D3Q19) in 3D");
     for (auto& x : b->in) {
       const double hf = x.dom.h0 * std::ldexp(1.0, -(x.n_levels - 1));
-      if (x.d_abs + x.d_rel * hf < 0.5 * hf) return fail(ctx, AMR_EINVAL, "links need d_L >= h_L/2");
+      if (x.d_abs + x.d_rel * hf < link_reach(prm->predicate) * hf)
+        return fail(ctx, AMR_EINVAL, "links need d_L >= %s h_L", prm->predicate == AMR_PRED_POINT ? "sqrt(2)" : "1/2");
     }
   }
   ctx->refined = false;

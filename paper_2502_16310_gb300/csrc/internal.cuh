@@ -407,6 +407,7 @@ struct RefineLevel {
   unsigned* work;              // dynamic work counter (zeroed before launch)
   unsigned* err;
   int warps;                   // warps per CTA (tunable)
+  int pred;                    // adjacency predicate: 0 box (SAT of the inflated cell), 1 point (Alg. 1)
   int batch;                   // consecutive blocks a warp takes per work fetch (1..kMaxBatch)
 };
 constexpr int kMaxBatch = 8;

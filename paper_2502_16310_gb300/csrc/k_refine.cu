@@ -117,6 +117,50 @@ __device__ __noinline__ double margin_fp64_2(const float* V, const double* xc, d
   return m;
 }
 
+// FP64 distance from the point xc to the closed face (vertices absolute FP32):
+// the plane distance when the projection lies in the closed triangle, else the
+// smallest distance to the three edges (the point predicate of Alg. 1).
+__device__ __forceinline__ double seg_dist2_fp64(const double* a, const double* b, int dim) {
+  double e[3] = {0, 0, 0}, ae = 0.0, ee = 0.0;
+  for (int c = 0; c < dim; ++c) {
+    e[c] = __dsub_rn(b[c], a[c]);
+    ae = __fma_rn(-a[c], e[c], ae);
+    ee = __fma_rn(e[c], e[c], ee);
+  }
+  const double t = ee > 0.0 ? fmin(1.0, fmax(0.0, ae / ee)) : 0.0;
+  double d2 = 0.0;
+  for (int c = 0; c < dim; ++c) {
+    const double q = __fma_rn(t, e[c], a[c]);
+    d2 = __fma_rn(q, q, d2);
+  }
+  return d2;
+}
+
+__device__ __noinline__ double point_dist_fp64(const float* V, const double* xc, int dim) {
+  double p[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int k = 0; k < dim; ++k)
+    for (int c = 0; c < dim; ++c) p[k][c] = __dsub_rn((double)V[dim * k + c], xc[c]);
+  if (dim == 2) return sqrt(seg_dist2_fp64(p[0], p[1], 2));
+  const double u[3] = {p[1][0] - p[0][0], p[1][1] - p[0][1], p[1][2] - p[0][2]};
+  const double w[3] = {p[2][0] - p[0][0], p[2][1] - p[0][1], p[2][2] - p[0][2]};
+  const double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+  const double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  if (nn > 0.0) {
+    bool neg = true, pos = true;
+    for (int k = 0; k < 3; ++k) {
+      const double* a = p[k];
+      const double* b = p[(k + 1) % 3];
+      const double e[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      const double m[3] = {e[1] * n[2] - e[2] * n[1], e[2] * n[0] - e[0] * n[2], e[0] * n[1] - e[1] * n[0]};
+      const double sk = -(a[0] * m[0] + a[1] * m[1] + a[2] * m[2]);
+      if (sk > 0.0) neg = false;
+      if (sk < 0.0) pos = false;
+    }
+    if (neg || pos) return fabs(p[0][0] * n[0] + p[0][1] * n[1] + p[0][2] * n[2]) / sqrt(nn);
+  }
+  return sqrt(fmin(seg_dist2_fp64(p[0], p[1], 3), fmin(seg_dist2_fp64(p[1], p[2], 3), seg_dist2_fp64(p[2], p[0], 3))));
+}
+
 // Block-frame quantities shared by all lanes of the warp for one block.
 template <int D>
 struct BlockFrame {
@@ -249,6 +293,115 @@ __device__ __forceinline__ void cell_test2(const Surv<D>& S, const float* o0, co
   r1 = sep1 ? 0 : (in1 ? 1 : 2);
 }
 
+// Point predicate: survivor data in the block frame, stored over the
+// thresholds of the box predicate.  3D layout: t[0..2] = vertex k (xyz) with
+// 1/|n|^2 (0: zero-area face) and the error scale in .w of t[0] / t[1];
+// t[3..5] = edge e_k = p_{k+1} - p_k with 1/|e_k|^2; t[6..8] = m_k = e_k x n
+// with the edge-function error scale in t[6].w; t[9] = n.
+// Error analysis (u = 2^-24, L = bound on |coordinates| in the frame, vertex
+// offsets plus cell-centre offsets): every difference w = x - p_k carries one
+// rounding (<= 2uL per component), the squared edge and plane distances are
+// sums of a few products of such terms and are within 64 u (2 sqrt(3) L)^2 of
+// their exact values; an edge function m_k . w_k is within 96 u L |e_k|_1 |n|_1.
+template <int D>
+__device__ __forceinline__ void setup_point(const float* V, const float* nh, const BlockFrame<D>& F, Surv<D>& S) {
+  float p[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  float P = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      p[k][c] = V[D * k + c] - F.Xb[c];
+      P = fmaxf(P, fabsf(p[k][c]));
+    }
+  const float L = P + F.O;
+  const float E = 64.0f * kU32 * 12.0f * L * L;
+  if constexpr (D == 3) {
+    float e[3][3], m[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) e[k][c] = p[(k + 1) % 3][c] - p[k][c];
+    const float nn = nh[0] * nh[0] + nh[1] * nh[1] + nh[2] * nh[2];
+    const float n1 = fabsf(nh[0]) + fabsf(nh[1]) + fabsf(nh[2]);
+    float m1 = 0.f;  // bound on |m_k|_1 and on its rounding, max_k |e_k|_1 |n|_1
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      m[k][0] = e[k][1] * nh[2] - e[k][2] * nh[1];
+      m[k][1] = e[k][2] * nh[0] - e[k][0] * nh[2];
+      m[k][2] = e[k][0] * nh[1] - e[k][1] * nh[0];
+      m1 = fmaxf(m1, (fabsf(e[k][0]) + fabsf(e[k][1]) + fabsf(e[k][2])) * n1);
+    }
+    S.t[0] = make_float4(p[0][0], p[0][1], p[0][2], nn > 0.f ? 1.0f / nn : 0.f);
+    S.t[1] = make_float4(p[1][0], p[1][1], p[1][2], E);
+    S.t[2] = make_float4(p[2][0], p[2][1], p[2][2], 0.f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float ee = e[k][0] * e[k][0] + e[k][1] * e[k][1] + e[k][2] * e[k][2];
+      S.t[3 + k] = make_float4(e[k][0], e[k][1], e[k][2], ee > 0.f ? 1.0f / ee : 0.f);
+      S.t[6 + k] = make_float4(m[k][0], m[k][1], m[k][2], k == 0 ? 96.0f * kU32 * m1 * L : 0.f);
+    }
+    S.t[9] = make_float4(nh[0], nh[1], nh[2], 0.f);
+  } else {
+    const float e0 = p[1][0] - p[0][0], e1 = p[1][1] - p[0][1];
+    const float ee = e0 * e0 + e1 * e1;
+    S.t[0] = make_float4(p[0][0], p[0][1], e0, e1);
+    S.t[1] = make_float4(ee > 0.f ? 1.0f / ee : 0.f, E, 0.f, 0.f);
+  }
+}
+
+// Squared distance from w (= x - p) to the segment p + s e, s in [0, 1].
+__device__ __forceinline__ float seg_dist2(float wx, float wy, float wz, const float4& e) {
+  const float s = fminf(1.0f, fmaxf(0.0f, (wx * e.x + wy * e.y + wz * e.z) * e.w));
+  const float qx = fmaf(-s, e.x, wx), qy = fmaf(-s, e.y, wy), qz = fmaf(-s, e.z, wz);
+  return qx * qx + qy * qy + qz * qz;
+}
+
+// Point-predicate test of one cell centre o: 0 = farther than d, 1 = within
+// d, 2 = not certified (FP64).  The plane distance A is a lower bound of the
+// distance and the nearest edge distance Bv an upper bound; A applies when the
+// projection is certainly inside the triangle, Bv when it is certainly outside.
+template <int D>
+__device__ __forceinline__ int point_test(const Surv<D>& S, const float* o, float R2) {
+  if constexpr (D == 3) {
+    const float4 t0 = S.t[0], t1 = S.t[1], t2 = S.t[2];
+    const float E = t1.w;
+    const float w[3][3] = {{o[0] - t0.x, o[1] - t0.y, o[2] - t0.z},
+                           {o[0] - t1.x, o[1] - t1.y, o[2] - t1.z},
+                           {o[0] - t2.x, o[1] - t2.y, o[2] - t2.z}};
+    float Bv = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Bv = fminf(Bv, seg_dist2(w[k][0], w[k][1], w[k][2], S.t[3 + k]));
+    if (Bv <= R2 - E) return 1;
+    const float4 n = S.t[9];
+    const float pn = w[0][0] * n.x + w[0][1] * n.y + w[0][2] * n.z;
+    const float A = t0.w > 0.f ? pn * pn * t0.w : 0.f;
+    if (A > R2 + E) return 0;
+    const float es = S.t[6].w;
+    bool neg = true, pos = true, lo = false, hi = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 m = S.t[6 + k];
+      const float sk = w[k][0] * m.x + w[k][1] * m.y + w[k][2] * m.z;
+      if (!(sk < -es)) neg = false;
+      if (!(sk > es)) pos = false;
+      if (sk < -es) lo = true;
+      if (sk > es) hi = true;
+    }
+    const bool inside = t0.w > 0.f && (neg || pos);
+    const bool outside = t0.w == 0.f || (lo && hi);
+    if (inside) return A < R2 - E ? 1 : 2;
+    if (outside) return Bv > R2 + E ? 0 : 2;
+    return 2;
+  } else {
+    const float4 t0 = S.t[0], t1 = S.t[1];
+    const float d2 = seg_dist2(o[0] - t0.x, o[1] - t0.y, 0.f, make_float4(t0.z, t0.w, 0.f, t1.x));
+    if (d2 <= R2 - t1.y) return 1;
+    if (d2 > R2 + t1.y) return 0;
+    return 2;
+  }
+}
+
 struct WarpCounters {
   unsigned long long fb = 0, band = 0, cand = 0, surv = 0;
 };
@@ -267,7 +420,8 @@ __device__ __noinline__ bool resolve_fp64(const RefineLevel& a, uint32_t gid, ui
     xc[c] = __dadd_rn(G.origin[c], __dmul_rn((double)(4 * b[c] + li) + 0.5, G.h));
   }
   const double r = __dadd_rn(0.5 * G.h, G.d);
-  const double m = D == 3 ? margin_fp64_3(V, xc, r) : margin_fp64_2(V, xc, r);
+  const double m = a.pred == 1 ? point_dist_fp64(V, xc, D) - G.d
+                               : (D == 3 ? margin_fp64_3(V, xc, r) : margin_fp64_2(V, xc, r));
   ++*fb;
   if (fabs(m) <= kBandRel * G.h) ++*band;
   return m <= 0.0;
@@ -376,7 +530,10 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
   }
   F.h = hf;
   F.r = fmaf(0.5f, hf, g.d);
-  F.rb = fmaf(2.0f, hf, g.d);
+  // block-level cull: the box around the block centre that holds every cell's
+  // test region (point predicate: the cell centres' box, 1.5 h, inflated by d)
+  F.rb = a.pred == 1 ? fmaf(1.5f, hf, g.d) : fmaf(2.0f, hf, g.d);
+  const float R2 = g.d * g.d;
   F.O = O;
   // cell centres of this lane in the frame: lo + (l + 1/2) h
   float o0[3] = {0, 0, 0}, o1[3] = {0, 0, 0};
@@ -439,6 +596,7 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
 #pragma unroll
           for (int j = 0; j < D * D; ++j) V[j] = ent.v[j];
           surv = setup_face<D>(V, nh, F, sm.surv[lane]);
+          if (surv && a.pred == 1) setup_point<D>(V, nh, F, sm.surv[lane]);
           sm.surv[lane].face = f;
         }
       }
@@ -450,7 +608,14 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
         m &= m - 1;
         const Surv<D>& S = sm.surv[s];
         int t0 = 0, t1 = 0;
-        if (!(kMarkOnly && h0 && h1)) cell_test2<D>(S, o0, o1, t0, t1);
+        if (!(kMarkOnly && h0 && h1)) {
+          if (a.pred == 1) {
+            t0 = point_test<D>(S, o0, R2);
+            t1 = D == 3 ? point_test<D>(S, o1, R2) : 0;
+          } else {
+            cell_test2<D>(S, o0, o1, t0, t1);
+          }
+        }
         bool r0 = false, r1 = false;
         if (lane_cell && !(kMarkOnly && h0)) {
           if (t0 == 2) t0 = resolve_fp64<D>(a, gid, S.face, b, lane, &wc.fb, &wc.band) ? 1 : 0;

@@ -5,8 +5,9 @@ Criteria (per output):
   * bins: identical sets of face ids per bin (order within a bin is unspecified
     on the GPU);
   * masks / blocks: identical outside the cells whose oracle decision lies in the
-    1e-6*h margin band; children lists identical to the canonical children of
-    the GPU's own masks (pure integer work);
+    1e-6*h margin band (box predicate: SAT margin; point predicate: distance
+    minus d); children lists identical to the canonical children of the GPU's
+    own masks (pure integer work);
   * adjacency lists: identical except for (cell, face) pairs in the band;
   * links: identical hit/miss outside the oracle's 1e-6 band, q within 1e-5
     absolute; the face must be one the oracle hits at that q (ties).
@@ -23,7 +24,7 @@ def to_np(t, dtype=None):
     return a.view(dtype) if dtype is not None else a
 
 
-def run_gpu(w, *, B=None, n_levels=None, want_links=True, facelist=False, d_abs=None, d_rel=None):
+def run_gpu(w, *, B=None, n_levels=None, want_links=True, facelist=False, d_abs=None, d_rel=None, predicate=0):
     """Whole CUDA pass for a workload; returns the AmrGeom and host copies of every output."""
     import torch
 
@@ -39,7 +40,7 @@ def run_gpu(w, *, B=None, n_levels=None, want_links=True, facelist=False, d_abs=
         g.load(v, torch.from_numpy(w.idx).cuda())
     bins = g.bin(B)
     res = g.refine(n_levels, w.d_abs if d_abs is None else d_abs, w.d_rel if d_rel is None else d_rel,
-                   w.lattice if want_links else 0, True, want_links)
+                   w.lattice if want_links else 0, True, want_links, predicate=predicate)
     torch.cuda.synchronize()
     out = {"offsets": to_np(bins["offsets"], np.uint32), "ids": to_np(bins["ids"], np.uint32), "levels": []}
     for lv in res["levels"]:
@@ -75,7 +76,7 @@ def cells_of(dim, blocks, block_idx, bits):
     return (4 * blocks[block_idx] + loc).astype(np.int32)
 
 
-def compare_level(geo, dim, level, blocks, mask_gpu, sample=None, d_abs=0.0, d_rel=1.0, rng=None):
+def compare_level(geo, dim, level, blocks, mask_gpu, sample=None, d_abs=0.0, d_rel=1.0, rng=None, pred=0):
     """Oracle masks for (a sample of) the GPU's blocks; returns (n_checked, n_band_cells)."""
     idx = np.arange(blocks.shape[0])
     if sample is not None and blocks.shape[0] > sample:
@@ -83,7 +84,7 @@ def compare_level(geo, dim, level, blocks, mask_gpu, sample=None, d_abs=0.0, d_r
         idx = np.sort(rng.choice(blocks.shape[0], size=sample, replace=False))
     if idx.size == 0:
         return 0, 0
-    m_o, band, _, _ = geo.refine_blocks(level, blocks[idx], d_abs, d_rel)
+    m_o, band, _, _ = geo.refine_blocks(level, blocks[idx], d_abs, d_rel, pred=pred)
     diff = (m_o ^ mask_gpu[idx]) & ~band
     bad = np.nonzero(diff)[0]
     assert bad.size == 0, (f"level {level}: {bad.size} blocks differ outside the band, e.g. block "
@@ -107,7 +108,7 @@ def check_children(dim, blocks, mask, child_blocks, child_parent):
 
 
 def compare_adjacency(geo, dim, level, fin_blocks, fin_mask, adj_cell, adj_off, adj_ids, sample=None,
-                      d_abs=0.0, d_rel=1.0, rng=None):
+                      d_abs=0.0, d_rel=1.0, rng=None, pred=0):
     nc = 64 if dim == 3 else 16
     # the adjacent cell list is exactly the set bits of the finest masks, ascending
     bits = ((fin_mask[:, None] >> np.arange(nc, dtype=np.uint64)[None, :]) & np.uint64(1)).astype(bool)
@@ -121,7 +122,7 @@ def compare_adjacency(geo, dim, level, fin_blocks, fin_mask, adj_cell, adj_off, 
         rng = rng or np.random.default_rng(1)
         rows = np.sort(rng.choice(rows.size, size=sample, replace=False))
     cells = cells_of(dim, fin_blocks, (adj_cell[rows] // nc).astype(np.int64), (adj_cell[rows] % nc).astype(np.int64))
-    o_off, o_ids, o_band = geo.cell_faces(level, cells, d_abs, d_rel)
+    o_off, o_ids, o_band = geo.cell_faces(level, cells, d_abs, d_rel, pred=pred)
     n_band = 0
     for k, r in enumerate(rows):
         g = adj_ids[adj_off[r]:adj_off[r + 1]]
@@ -138,7 +139,7 @@ def compare_adjacency(geo, dim, level, fin_blocks, fin_mask, adj_cell, adj_off, 
 
 
 def compare_links(geo, dim, level, lattice, fin_blocks, adj_cell, link_cell, link_dir, link_q, link_face,
-                  sample=None, rng=None, d_abs=0.0, d_rel=1.0):
+                  sample=None, rng=None, d_abs=0.0, d_rel=1.0, pred=0):
     nc = 64 if dim == 3 else 16
     Q1 = 18 if lattice == 19 else 8
     n_adj = adj_cell.shape[0]
@@ -160,7 +161,7 @@ def compare_links(geo, dim, level, lattice, fin_blocks, adj_cell, link_cell, lin
     gq, gf = dense_q[rows], dense_f[rows]
     # a link inherits the band of its face's adjacency decision: links are formed against the
     # cell's adjacency list, and a face in the adjacency band may be listed or not
-    a_off, a_ids, a_band = geo.cell_faces(level, cells, d_abs, d_rel)
+    a_off, a_ids, a_band = geo.cell_faces(level, cells, d_abs, d_rel, pred=pred)
     inherit = np.zeros_like(b_o)
     for i in range(cells.shape[0]):
         bset = set(a_ids[a_off[i]:a_off[i + 1]][a_band[a_off[i]:a_off[i + 1]]].tolist())
