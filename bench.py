@@ -256,6 +256,7 @@ def run_ours(args, rank, world, local):
     if not args.no_extras and world == 1:
         line["adjoint"] = run_adjoint(args, dev, flush)
         line["batched"] = run_batched(args, dev, flush)
+        line["paper_setups"] = run_paper_setups(args, dev, flush)
     return line
 
 
@@ -375,6 +376,51 @@ def run_batched(args, dev, flush):
             "near_wall_cells": cells, "single_ms": t_single, "batched_ms": t_batch,
             "single_cells_per_s": cells / (t_single * 1e-3), "batched_cells_per_s": cells / (t_batch * 1e-3),
             "batched_over_single": t_single / t_batch, "generate_s": gen_s, "tune_s": tune_s}
+
+
+def run_paper_setups(args, dev, flush, bins=(1, 2, 8, 16), reps=3):
+    """The paper's two speed-up setups (point predicate, absolute d_spec, refined twice) at its bin
+    densities: bin-setup and face-detection (marking) times per B, and the blocks per level (which exact
+    binning keeps independent of B)."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+    from synth import workload
+
+    out = {}
+    for name in ("p2", "p3"):
+        w = workload(name)
+        g = AmrGeom(w.dim, (w.root,) * w.dim)
+        v = torch.from_numpy(w.verts).to(dev)
+        ix = torch.from_numpy(w.idx).to(dev)
+        rows = {"workload": w.description, "faces": w.n_faces, "B": [], "bin_ms": [], "detect_ms": [],
+                "blocks_per_level": [], "near_wall_cells": []}
+        for B in bins:
+            def step():
+                g.load(v, ix)
+                g.bin(B)
+                return g.refine(w.n_levels, w.d_abs, w.d_rel, 0, False, False, predicate=w.predicate)
+
+            res = step()
+            torch.cuda.synchronize()
+            g.timing(True)
+            g.timing_reset()
+            for k in range(reps):
+                flush.fill_(k & 0xff)
+                step()
+            torch.cuda.synchronize()
+            tk = g.timings()
+            g.timing(False)
+            t_bin = sum(tk[k][0] for k in ("bin_count", "bin_scan", "bin_scatter") if k in tk) / reps
+            t_det = tk.get("refine_level", (0.0, 0))[0] / reps
+            rows["B"].append(B)
+            rows["bin_ms"].append(round(t_bin, 4))
+            rows["detect_ms"].append(round(t_det, 4))
+            rows["blocks_per_level"].append([int(lv["blocks"].shape[0]) for lv in res["levels"]])
+            rows["near_wall_cells"].append(near_wall_cells(res))
+        g.close()
+        out[name] = rows
+    return out
 
 
 def roofline(name, k, w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks):

@@ -46,6 +46,7 @@ class Workload:
     lattice: int               # 9 (D2Q9) or 19 (D3Q19)
     d_abs: float = 0.0
     d_rel: float = 1.0
+    predicate: int = 0         # 0: box (inflated cell meets the face), 1: point (centre within d, Alg. 1)
     adjoint: bool = False
     description: str = ""
     meta: dict = field(default_factory=dict)
@@ -92,6 +93,26 @@ def _c4():
                                 "256^3 bins, D3Q19, q adjoint")
 
 
+def _p2():
+    # the paper's 2D speed-up setup: 12,800 edges in the middle of a 256^2 grid on [0,1]^2,
+    # d_spec = 0.1, refined twice (radius not stated: 0.25)
+    v, f = G.circle_polygon(12800, 0.25, (0.5, 0.5))
+    return Workload("p2", 2, v, f, root=64, n_levels=3, bins=16, lattice=9, d_abs=0.1, d_rel=0.0, predicate=1,
+                    description="paper 2D setup: circle r=0.25, 12,800 segments, 256^2 cells (64^2 roots), "
+                                "3 levels, d_spec=0.1, point predicate")
+
+
+def _p3():
+    # the paper's 3D setup with a synthetic stand-in for the 112,402-face bunny: a geodesic
+    # sphere of frequency 75 (112,500 triangles), SH-perturbed and anisotropic like c3;
+    # 64^3 grid on [0,1]^3, d_spec = 0.05, refined twice
+    u, f = G.geodesic_sphere_unit(75)
+    v, f = G.perturbed_surface(u, f, seed=31, lmax=8)
+    return Workload("p3", 3, v, f, root=16, n_levels=3, bins=16, lattice=19, d_abs=0.05, d_rel=0.0, predicate=1,
+                    description="paper 3D setup: SH-perturbed geodesic sphere (112,500 tris, bunny-scale), "
+                                "64^3 cells (16^3 roots), 3 levels, d_spec=0.05, point predicate")
+
+
 def batched_workloads(n: int = 48, base_seed: int = 5000):
     """The batched workload: ``n`` perturbed geodesic spheres of uneven size and depth.
 
@@ -117,8 +138,8 @@ def batched_workloads(n: int = 48, base_seed: int = 5000):
 
 
 def workload(name: str) -> Workload:
-    """Build one named workload (c1..c4); c5 is ``batched_workloads()``."""
-    return {"c1": _c1, "c2": _c2, "c3": _c3, "c4": _c4}[name]()
+    """Build one named workload (c1..c4, the paper's setups p2 / p3); c5 is ``batched_workloads()``."""
+    return {"c1": _c1, "c2": _c2, "c3": _c3, "c4": _c4, "p2": _p2, "p3": _p3}[name]()
 
 
 def small_workload(kind: str, *, seed: int = 11):

@@ -124,3 +124,38 @@ def test_point_c2_sampled():
     w = workload("c2")
     h_fin = 1.0 / (4 * w.root * 2 ** (w.n_levels - 1))
     _check(w, 2.0 * h_fin, sample=300)
+
+
+@pytest.mark.parametrize("name", ["p2", "p3"])
+def test_paper_setups_sampled(name):
+    """The paper's speed-up setups (absolute d_spec = 0.1 / 0.05, refined twice), marking only as in
+    the paper: every level's masks on seeded samples of blocks, children exact, at B = 1 and B = 16."""
+    import torch
+
+    from oracle.oracle import Domain, OracleGeometry, root_blocks
+    from paper_2502_16310_gb300 import AmrGeom
+
+    w = workload(name)
+    geo = OracleGeometry(w.dim, w.verts, w.idx)
+    geo.bin(Domain.unit(w.dim, w.root), 16)
+    rng = np.random.default_rng(11)
+    masks = []
+    for B in (1, 16):
+        g = AmrGeom(w.dim, (w.root,) * w.dim)
+        g.load(torch.from_numpy(w.verts).cuda(), torch.from_numpy(w.idx).cuda())
+        g.bin(B)
+        res = g.refine(w.n_levels, w.d_abs, w.d_rel, 0, False, False, predicate=PRED_POINT)
+        torch.cuda.synchronize()
+        lv = [{"blocks": x["blocks"].cpu().numpy(), "mask": x["mask"].cpu().numpy().view(np.uint64),
+               "parent": None if x["parent"] is None else x["parent"].cpu().numpy()} for x in res["levels"]]
+        g.close()
+        assert np.array_equal(lv[0]["blocks"], root_blocks(w.dim, (w.root,) * w.dim))
+        for L in range(len(lv)):
+            U.compare_level(geo, w.dim, L, lv[L]["blocks"], lv[L]["mask"], sample=100, d_abs=w.d_abs,
+                            d_rel=w.d_rel, rng=rng, pred=PRED_POINT)
+            if L + 1 < len(lv):
+                U.check_children(w.dim, lv[L]["blocks"], lv[L]["mask"], lv[L + 1]["blocks"], lv[L + 1]["parent"])
+        masks.append([x["mask"] for x in lv])
+    # exact binning: the marks do not depend on B (the paper needs its propagation step for that)
+    for a, b in zip(*masks):
+        assert np.array_equal(a, b)
