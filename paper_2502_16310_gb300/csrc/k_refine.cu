@@ -499,7 +499,7 @@ __device__ __forceinline__ void issue_chunk(const E* payload, uint32_t s, uint32
 // row); entries then arrive in shared memory by TMA bulk copies in chunks of
 // 32, double-buffered: the next chunk is requested before the warp tests the
 // current one.
-template <int D, bool kMarkOnly, typename OnSurv>
+template <int D, int PRED, bool kMarkOnly, typename OnSurv>
 __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParams& P, uint32_t gid, const int* b,
                                            WarpSmem<D>& sm, uint32_t& phase, int lane, WarpCounters& wc, bool& h0,
                                            bool& h1, OnSurv on_surv) {
@@ -532,7 +532,7 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
   F.r = fmaf(0.5f, hf, g.d);
   // block-level cull: the box around the block centre that holds every cell's
   // test region (point predicate: the cell centres' box, 1.5 h, inflated by d)
-  F.rb = a.pred == 1 ? fmaf(1.5f, hf, g.d) : fmaf(2.0f, hf, g.d);
+  F.rb = PRED == 1 ? fmaf(1.5f, hf, g.d) : fmaf(2.0f, hf, g.d);
   const float R2 = g.d * g.d;
   F.O = O;
   // cell centres of this lane in the frame: lo + (l + 1/2) h
@@ -596,7 +596,9 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
 #pragma unroll
           for (int j = 0; j < D * D; ++j) V[j] = ent.v[j];
           surv = setup_face<D>(V, nh, F, sm.surv[lane]);
-          if (surv && a.pred == 1) setup_point<D>(V, nh, F, sm.surv[lane]);
+          if constexpr (PRED == 1) {
+            if (surv) setup_point<D>(V, nh, F, sm.surv[lane]);
+          }
           sm.surv[lane].face = f;
         }
       }
@@ -609,7 +611,7 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
         const Surv<D>& S = sm.surv[s];
         int t0 = 0, t1 = 0;
         if (!(kMarkOnly && h0 && h1)) {
-          if (a.pred == 1) {
+          if constexpr (PRED == 1) {
             t0 = point_test<D>(S, o0, R2);
             t1 = D == 3 ? point_test<D>(S, o1, R2) : 0;
           } else {
@@ -656,7 +658,7 @@ __device__ __forceinline__ int64_t launch_count(int64_t n, const uint64_t* n_dev
   return (int64_t)nd;
 }
 
-template <int D>
+template <int D, int PRED>
 __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   WarpSmem<D>& sm = reinterpret_cast<WarpSmem<D>*>(s_raw)[threadIdx.x >> 5];
@@ -692,7 +694,7 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
     bool h0 = false, h1 = false;
     if (fin) {
       uint32_t K = 0;  // records of this block (warp-uniform)
-      walk_block<D, false>(a, P, gid, b, sm, phase, lane, wc, h0, h1, [&](uint32_t f, bool r0, bool r1) {
+      walk_block<D, PRED, false>(a, P, gid, b, sm, phase, lane, wc, h0, h1, [&](uint32_t f, bool r0, bool r1) {
         cnt0 += r0 ? 1u : 0u;
         cnt1 += r1 ? 1u : 0u;
         if (a.recs) {
@@ -728,7 +730,7 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
         __syncwarp();
       }
     } else {
-      walk_block<D, true>(a, P, gid, b, sm, phase, lane, wc, h0, h1, [](uint32_t, bool, bool) {});
+      walk_block<D, PRED, true>(a, P, gid, b, sm, phase, lane, wc, h0, h1, [](uint32_t, bool, bool) {});
       cnt0 = h0 ? 1u : 0u;
       cnt1 = h1 ? 1u : 0u;
     }
@@ -772,7 +774,7 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
 // faces of its cells at offsets given by the block-level scan and the per-cell
 // counts, then sorts each list.  Rows and pairs continue after the running
 // totals of earlier levels.
-template <int D>
+template <int D, int PRED>
 __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   WarpSmem<D>& sm = reinterpret_cast<WarpSmem<D>*>(s_raw)[threadIdx.x >> 5];
@@ -902,7 +904,7 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
       continue;
     }
     bool h0 = false, h1 = false;
-    walk_block<D, false>(a.lv, P, gid, b, sm, phase, lane, wc, h0, h1,
+    walk_block<D, PRED, false>(a.lv, P, gid, b, sm, phase, lane, wc, h0, h1,
                          [&](uint32_t fc, bool r0, bool r1) { put(r0, r1, fc); });
     if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
     if (!can0 || !can1) continue;
@@ -1031,13 +1033,14 @@ int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st) {
   const int warps = a.warps > 0 ? a.warps : 4;
   const int g = grid_warps(num_sms, a.n_blocks, warps, a.n_dev != nullptr);
   const size_t smem = (size_t)warps * (a.dim == 3 ? sizeof(WarpSmem<3>) : sizeof(WarpSmem<2>));
-  if (a.dim == 3) {
-    allow_smem(k_refine<3>, smem);
-    k_refine<3><<<g, warps * 32, smem, st>>>(a);
-  } else {
-    allow_smem(k_refine<2>, smem);
-    k_refine<2><<<g, warps * 32, smem, st>>>(a);
-  }
+  auto go = [&](auto kernel) {
+    allow_smem(kernel, smem);
+    kernel<<<g, warps * 32, smem, st>>>(a);
+  };
+  if (a.dim == 3)
+    a.pred == 1 ? go(k_refine<3, 1>) : go(k_refine<3, 0>);
+  else
+    a.pred == 1 ? go(k_refine<2, 1>) : go(k_refine<2, 0>);
   return 1;
 }
 
@@ -1046,13 +1049,14 @@ int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st) {
   const int warps = a.lv.warps > 0 ? a.lv.warps : 4;
   const int g = grid_warps(num_sms, a.lv.n_blocks, warps, a.lv.n_dev != nullptr);
   const size_t smem = (size_t)warps * (a.lv.dim == 3 ? sizeof(WarpSmem<3>) : sizeof(WarpSmem<2>));
-  if (a.lv.dim == 3) {
-    allow_smem(k_adjacency<3>, smem);
-    k_adjacency<3><<<g, warps * 32, smem, st>>>(a);
-  } else {
-    allow_smem(k_adjacency<2>, smem);
-    k_adjacency<2><<<g, warps * 32, smem, st>>>(a);
-  }
+  auto go = [&](auto kernel) {
+    allow_smem(kernel, smem);
+    kernel<<<g, warps * 32, smem, st>>>(a);
+  };
+  if (a.lv.dim == 3)
+    a.lv.pred == 1 ? go(k_adjacency<3, 1>) : go(k_adjacency<3, 0>);
+  else
+    a.lv.pred == 1 ? go(k_adjacency<2, 1>) : go(k_adjacency<2, 0>);
   return 1;
 }
 
