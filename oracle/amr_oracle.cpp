@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <unordered_map>
 #include <vector>
 
 struct orc_geom {
@@ -298,6 +299,71 @@ void face_local(const orc_geom& g, int64_t f, const double* o, double (*p)[3], c
     }
 }
 
+// ---------------------------------------------------------------------------
+// The paper's own binning (Sec. "Spatial Binning Algorithm", Fig. "Discretization
+// of edges and triangles"): a face is discretised into points and belongs to
+// every bin that holds at least one of them.  A segment v0-v1 gives the n + 1
+// points v0 + (i/n)(v1 - v0), n = max(1, ceil(|v1 - v0| / s)); a triangle
+// discretises its first edge v0-v1 so, then every segment from such a point to
+// the opposite vertex v2 likewise.  s = half a bin length (the paper only says
+// the number of nodes scales with the size of the face).  All arithmetic is FP64
+// with one rounding per operation, in this order, so that another
+// implementation can reproduce the points exactly.
+// ---------------------------------------------------------------------------
+
+int seg_points(const double* a, const double* b, int dim, double s) {
+  double l2 = 0.0;
+  for (int c = 0; c < dim; ++c) {
+    const double e = b[c] - a[c];
+    l2 = l2 + e * e;
+  }
+  const double n = std::ceil(std::sqrt(l2) / s);
+  return n < 1.0 ? 1 : (n > 4096.0 ? 4096 : (int)n);
+}
+
+template <typename F>
+void for_each_sample(const double* v, int dim, double s, F&& visit) {
+  const double* v0 = v;
+  const double* v1 = v + dim;
+  const int n = seg_points(v0, v1, dim, s);
+  for (int i = 0; i <= n; ++i) {
+    const double t = (double)i / (double)n;
+    double p[3] = {0, 0, 0};
+    for (int c = 0; c < dim; ++c) p[c] = v0[c] + t * (v1[c] - v0[c]);
+    if (dim == 2) {
+      visit(p);
+      continue;
+    }
+    const double* v2 = v + 2 * dim;
+    const int m = seg_points(p, v2, 3, s);
+    for (int j = 0; j <= m; ++j) {
+      const double u = (double)j / (double)m;
+      double q[3];
+      for (int c = 0; c < 3; ++c) q[c] = p[c] + u * (v2[c] - p[c]);
+      visit(q);
+    }
+  }
+}
+
+double sample_spacing(const orc_domain& d, int B) {
+  double ext = kInf;
+  for (int a = 0; a < d.dim; ++a) ext = std::min(ext, (4.0 * (double)d.root[a]) * d.h0);
+  return 0.5 * (ext / (double)B);
+}
+
+// ---------------------------------------------------------------------------
+// Refinement-mark propagation (Sec. "Spatial Binning Algorithm", Fig.
+// "propagation"): each round, every marked block marks its 3^D - 1 neighbours of
+// the same level that exist, through an intermediate value so that a block
+// marked in this round does not spread further in the same round.
+// ---------------------------------------------------------------------------
+
+uint64_t block_key(const int32_t* c, int dim) {
+  uint64_t k = 0;
+  for (int a = 0; a < dim; ++a) k = (k << 21) | (uint64_t)(uint32_t)c[a];
+  return k;
+}
+
 }  // namespace
 
 extern "C" {
@@ -389,6 +455,72 @@ int orc_bins_build(orc_geom* g, const orc_domain* dom, int B) {
   return 0;
 }
 
+// The paper's sampled binning: bins holding at least one sample point of the face.
+int orc_bins_build_sampled(orc_geom* g, const orc_domain* dom, int B) {
+  if (!g || !dom || B < 1 || dom->dim != g->dim) return 1;
+  if (orc_bins_build(g, dom, B)) return 1;  // the AABB ranges (blo / bhi) and the domain
+  const int D = g->dim;
+  const double s = sample_spacing(*dom, B);
+  int64_t nb = (int64_t)B * B * (D == 3 ? B : 1);
+  std::vector<std::vector<uint32_t>> lists((size_t)nb);
+  std::vector<int64_t> bins;
+  for (int64_t f = 0; f < g->nf; ++f) {
+    bins.clear();
+    for_each_sample(&g->X[(size_t)f * D * D], D, s, [&](const double* q) {
+      int32_t c[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) c[a] = bin_coord(*dom, B, a, q[a]);
+      bins.push_back(bin_linear(D, B, c));
+    });
+    std::sort(bins.begin(), bins.end());
+    bins.erase(std::unique(bins.begin(), bins.end()), bins.end());
+    for (int64_t b : bins) lists[(size_t)b].push_back((uint32_t)f);
+  }
+  g->offsets.assign((size_t)nb + 1, 0);
+  g->ids.clear();
+  for (int64_t b = 0; b < nb; ++b) {
+    g->offsets[(size_t)b] = (uint32_t)g->ids.size();
+    g->ids.insert(g->ids.end(), lists[(size_t)b].begin(), lists[(size_t)b].end());
+  }
+  g->offsets[(size_t)nb] = (uint32_t)g->ids.size();
+  return 0;
+}
+
+int64_t orc_face_samples(const orc_geom* g, int64_t f, double spacing, double* pts, int64_t cap) {
+  if (!g || f < 0 || f >= g->nf) return -1;
+  const int D = g->dim;
+  int64_t k = 0;
+  for_each_sample(&g->X[(size_t)f * D * D], D, spacing, [&](const double* q) {
+    if (pts && k < cap)
+      for (int c = 0; c < D; ++c) pts[k * D + c] = q[c];
+    ++k;
+  });
+  return k;
+}
+
+int orc_propagate(int dim, const int32_t* blocks, int64_t n, uint8_t* flags, int rounds) {
+  std::unordered_map<uint64_t, int64_t> where;
+  where.reserve((size_t)n * 2);
+  for (int64_t b = 0; b < n; ++b) where[block_key(blocks + b * dim, dim)] = b;
+  for (int r = 0; r < rounds; ++r) {
+    for (int64_t b = 0; b < n; ++b) {
+      if (flags[b] != 1) continue;
+      const int32_t* c = blocks + b * dim;
+      const int nz = dim == 3 ? 1 : 0;
+      for (int dz = -nz; dz <= nz; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int32_t q[3] = {c[0] + dx, c[1] + dy, dim == 3 ? c[2] + dz : 0};
+            if (q[0] < 0 || q[1] < 0 || q[2] < 0) continue;
+            const auto it = where.find(block_key(q, dim));
+            if (it != where.end() && flags[it->second] == 0) flags[it->second] = 2;
+          }
+    }
+    for (int64_t b = 0; b < n; ++b)
+      if (flags[b] == 2) flags[b] = 1;
+  }
+  return 0;
+}
+
 int64_t orc_bins_nnz(const orc_geom* g) { return (int64_t)g->ids.size(); }
 
 void orc_bins_copy(const orc_geom* g, uint32_t* offsets, uint32_t* ids) {
@@ -410,8 +542,8 @@ double orc_point_face_dist(int dim, const double* verts_local) { return point_fa
 // of the level checks the faces of the bins around it; a block is marked when
 // any of its cells is adjacent.  The mask keeps the per-cell result.
 int orc_refine_blocks(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel, int pred,
-                      const int32_t* blocks, int64_t n, uint64_t* mask, uint64_t* band, int64_t* n_band_pairs,
-                      int64_t* n_candidates) {
+                      int search, const int32_t* blocks, int64_t n, uint64_t* mask, uint64_t* band,
+                      int64_t* n_band_pairs, int64_t* n_candidates) {
   if (!g || g->B < 1 || !dom || dom->dim != g->dim) return 1;
   const int D = g->dim;
   const double h = level_h(*dom, level);
@@ -432,7 +564,10 @@ int orc_refine_blocks(const orc_geom* g, const orc_domain* dom, int level, doubl
         lo[a] = x[a] - r;
         hi[a] = x[a] + r;
       }
-      gather_candidates(*g, lo, hi, true, cand);
+      if (search == 1)
+        gather_candidates(*g, x, x, false, cand);  // the paper's binned search: the faces of the cell's own bin
+      else
+        gather_candidates(*g, lo, hi, true, cand);
       if (n_candidates) {
         gather_candidates(*g, lo, hi, false, cand_exact);
         ncand += (int64_t)cand_exact.size();
@@ -482,7 +617,7 @@ int64_t orc_children(int dim, const int32_t* blocks, int64_t n, const uint64_t* 
 // The faces a cell identifies (Sec. "Identification of Cells Near the Boundary":
 // the cell may store the faces it detects for the solver routines).
 int64_t orc_cell_faces(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel, int pred,
-                       const int32_t* cells, int64_t n, int64_t* counts, uint32_t* ids, uint8_t* band,
+                       int search, const int32_t* cells, int64_t n, int64_t* counts, uint32_t* ids, uint8_t* band,
                        int64_t cap) {
   if (!g || g->B < 1 || !dom) return -1;
   const int D = g->dim;
@@ -499,7 +634,10 @@ int64_t orc_cell_faces(const orc_geom* g, const orc_domain* dom, int level, doub
       lo[a] = x[a] - r;
       hi[a] = x[a] + r;
     }
-    gather_candidates(*g, lo, hi, true, cand);
+    if (search == 1)
+      gather_candidates(*g, x, x, false, cand);
+    else
+      gather_candidates(*g, lo, hi, true, cand);
     int64_t cnt = 0;
     for (uint32_t f : cand) {
       const double m = face_margin(*g, f, x, r, pred, dL);

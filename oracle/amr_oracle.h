@@ -57,6 +57,21 @@ int64_t orc_geom_nfaces(const orc_geom* g);
 /* Binning with B bins per axis over the domain box. */
 int orc_bins_build(orc_geom* g, const orc_domain* dom, int B);
 int64_t orc_bins_nnz(const orc_geom* g);
+
+/* The paper's sampled binning (Sec. "Spatial Binning Algorithm"): the face is
+ * discretised into points (first edge, then segments to the opposite vertex,
+ * spacing at most half a bin length) and belongs to every bin holding one of
+ * them.  Replaces the bins like orc_bins_build. */
+int orc_bins_build_sampled(orc_geom* g, const orc_domain* dom, int B);
+
+/* The sample points of face f at the given spacing (pts[cap][dim], may be NULL);
+ * returns their number. */
+int64_t orc_face_samples(const orc_geom* g, int64_t f, double spacing, double* pts, int64_t cap);
+
+/* Refinement-mark propagation: `rounds` two-phase rounds in which every block with
+ * flags == 1 marks (flags = 1) the existing blocks of the list among its 3^D - 1
+ * neighbours of the same level. */
+int orc_propagate(int dim, const int32_t* blocks, int64_t n, uint8_t* flags, int rounds);
 void orc_bins_copy(const orc_geom* g, uint32_t* offsets, uint32_t* ids);
 void orc_face_bin_range(const orc_geom* g, int64_t f, int32_t* lo, int32_t* hi);
 
@@ -72,8 +87,11 @@ double orc_point_face_dist(int dim, const double* verts_local);
 /* Refinement of a list of blocks of one level: per block the adjacency bit of
  * every cell (mask) and the cells whose decision lies within the 1e-6*h_L
  * margin band (band).  pred: 0 = box predicate, 1 = point predicate (margin =
- * distance - d_L).  Counters may be NULL. */
+ * distance - d_L).  search: 0 = the faces of every bin the cell's inflated box
+ * overlaps, 1 = the faces of the bin holding the cell centre (the paper's binned
+ * search).  Counters may be NULL. */
 int orc_refine_blocks(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel, int pred,
+                      int search,
                       const int32_t* blocks, int64_t n, uint64_t* mask, uint64_t* band,
                       int64_t* n_band_pairs, int64_t* n_candidates);
 
@@ -86,6 +104,7 @@ int64_t orc_children(int dim, const int32_t* blocks, int64_t n, const uint64_t* 
  * ascending face ids.  counts[n]; ids/band written up to `cap` entries
  * (band[e] = 1 when that pair's margin is within the band).  Returns total entries. */
 int64_t orc_cell_faces(const orc_geom* g, const orc_domain* dom, int level, double d_abs, double d_rel, int pred,
+                       int search,
                        const int32_t* cells, int64_t n, int64_t* counts, uint32_t* ids, uint8_t* band,
                        int64_t cap);
 

@@ -59,13 +59,21 @@ def _load():
             lib.orc_sat_margin.restype = C.c_double
             lib.orc_sat_margin.argtypes = [C.c_int, P, C.c_double]
             lib.orc_refine_blocks.restype = C.c_int
-            lib.orc_refine_blocks.argtypes = [P, P, C.c_int, C.c_double, C.c_double, C.c_int, P, i64, P, P, P, P]
+            lib.orc_refine_blocks.argtypes = [P, P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, P, i64, P, P,
+                                              P, P]
+            lib.orc_bins_build_sampled.restype = C.c_int
+            lib.orc_bins_build_sampled.argtypes = [P, P, C.c_int]
+            lib.orc_face_samples.restype = i64
+            lib.orc_face_samples.argtypes = [P, i64, C.c_double, P, i64]
+            lib.orc_propagate.restype = C.c_int
+            lib.orc_propagate.argtypes = [C.c_int, P, i64, P, C.c_int]
             lib.orc_point_face_dist.restype = C.c_double
             lib.orc_point_face_dist.argtypes = [C.c_int, P]
             lib.orc_children.restype = i64
             lib.orc_children.argtypes = [C.c_int, P, i64, P, P, P]
             lib.orc_cell_faces.restype = i64
-            lib.orc_cell_faces.argtypes = [P, P, C.c_int, C.c_double, C.c_double, C.c_int, P, i64, P, P, P, i64]
+            lib.orc_cell_faces.argtypes = [P, P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, P, i64, P, P, P,
+                                           i64]
             lib.orc_cell_links.restype = C.c_int
             lib.orc_cell_links.argtypes = [P, P, C.c_int, C.c_int, P, i64, P, P, P]
             lib.orc_lattice_dir.restype = C.c_int
@@ -151,11 +159,13 @@ class OracleGeometry:
             self._h = None
 
     # -- step 2 ----------------------------------------------------------
-    def bin(self, dom: Domain, B: int):
+    def bin(self, dom: Domain, B: int, sampled: bool = False):
+        """Step 2: exact AABB binning, or (sampled=True) the paper's sampled-point binning."""
         lib = _load()
         self._cdom = dom.c()
-        if lib.orc_bins_build(self._h, C.byref(self._cdom), int(B)):
-            raise ValueError("orc_bins_build failed")
+        build = lib.orc_bins_build_sampled if sampled else lib.orc_bins_build
+        if build(self._h, C.byref(self._cdom), int(B)):
+            raise ValueError("binning failed")
         self.dom, self.B = dom, int(B)
         nb = B ** self.dim
         nnz = int(lib.orc_bins_nnz(self._h))
@@ -171,19 +181,29 @@ class OracleGeometry:
         return lo[:self.dim], hi[:self.dim]
 
     # -- step 3 ----------------------------------------------------------
-    def refine_blocks(self, level: int, blocks: np.ndarray, d_abs=0.0, d_rel=1.0, count_candidates=False, pred=0):
+    def refine_blocks(self, level: int, blocks: np.ndarray, d_abs=0.0, d_rel=1.0, count_candidates=False, pred=0,
+                      search=0):
         b = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, self.dim)
         n = b.shape[0]
         mask = np.zeros(max(n, 1), np.uint64)
         band = np.zeros(max(n, 1), np.uint64)
         nbp = C.c_int64(0)
         ncand = C.c_int64(0)
-        rc = _load().orc_refine_blocks(self._h, C.byref(self._cdom), level, d_abs, d_rel, int(pred), _p(b), n,
+        rc = _load().orc_refine_blocks(self._h, C.byref(self._cdom), level, d_abs, d_rel, int(pred), int(search),
+                                       _p(b), n,
                                        _p(mask),
                                        _p(band), C.byref(nbp), C.byref(ncand) if count_candidates else None)
         if rc:
             raise ValueError("orc_refine_blocks failed")
         return mask[:n], band[:n], int(nbp.value), int(ncand.value)
+
+    def face_samples(self, f: int, spacing: float) -> np.ndarray:
+        """The sample points of face f of the paper's sampled binning, [k][dim]."""
+        lib = _load()
+        k = int(lib.orc_face_samples(self._h, int(f), float(spacing), None, 0))
+        pts = np.zeros((max(k, 1), self.dim), np.float64)
+        lib.orc_face_samples(self._h, int(f), float(spacing), _p(pts), k)
+        return pts[:k]
 
     def children(self, blocks: np.ndarray, mask: np.ndarray):
         lib = _load()
@@ -195,18 +215,20 @@ class OracleGeometry:
         lib.orc_children(self.dim, _p(b), b.shape[0], _p(m), _p(cb), _p(cp))
         return cb[:k], cp[:k]
 
-    def cell_faces(self, level: int, cells: np.ndarray, d_abs=0.0, d_rel=1.0, pred=0):
+    def cell_faces(self, level: int, cells: np.ndarray, d_abs=0.0, d_rel=1.0, pred=0, search=0):
         """Per cell: ascending adjacent face ids; band flags mark pairs inside the margin band."""
         lib = _load()
         c = np.ascontiguousarray(cells, dtype=np.int32).reshape(-1, self.dim)
         n = c.shape[0]
         counts = np.zeros(max(n, 1), np.int64)
-        tot = int(lib.orc_cell_faces(self._h, C.byref(self._cdom), level, d_abs, d_rel, int(pred), _p(c), n,
+        tot = int(lib.orc_cell_faces(self._h, C.byref(self._cdom), level, d_abs, d_rel, int(pred), int(search),
+                                     _p(c), n,
                                      _p(counts),
                                      None, None, 0))
         ids = np.zeros(max(tot, 1), np.uint32)
         band = np.zeros(max(tot, 1), np.uint8)
-        lib.orc_cell_faces(self._h, C.byref(self._cdom), level, d_abs, d_rel, int(pred), _p(c), n, _p(counts),
+        lib.orc_cell_faces(self._h, C.byref(self._cdom), level, d_abs, d_rel, int(pred), int(search), _p(c), n,
+                           _p(counts),
                            _p(ids),
                            _p(band), tot)
         off = np.zeros(n + 1, np.int64)
@@ -245,6 +267,19 @@ class OracleGeometry:
         return out
 
 
+def propagate(dim: int, blocks: np.ndarray, flags: np.ndarray, rounds: int) -> np.ndarray:
+    """The paper's refinement-mark propagation over one level's block list; returns new flags (0/1)."""
+    b = np.ascontiguousarray(blocks, dtype=np.int32).reshape(-1, dim)
+    f = np.ascontiguousarray((np.asarray(flags) != 0).astype(np.uint8))
+    _load().orc_propagate(dim, _p(b), b.shape[0], _p(f), int(rounds))
+    return f
+
+
+def propagation_rounds(d_spec: float, block_len: float) -> int:
+    """N_prop = 1 + floor(d_spec / block length)."""
+    return 1 + int(np.floor(d_spec / block_len))
+
+
 def point_face_dist(dim: int, verts_local: np.ndarray) -> float:
     """Distance from the origin to the closed face (vertices relative to the point), Alg. 1's predicate."""
     v = np.ascontiguousarray(verts_local, dtype=np.float64).reshape(dim, dim)
@@ -275,21 +310,24 @@ def cells_of_mask(dim: int, blocks: np.ndarray, mask: np.ndarray):
 
 
 def run_pipeline(dim, verts, idx, *, root, n_levels, B, lattice, d_abs=0.0, d_rel=1.0, links=True,
-                 max_level_blocks=None, pred=0):
+                 max_level_blocks=None, pred=0, sampled=False, search=0, propagate_rounds=0):
     """Whole oracle pass: bins, every level's blocks/masks/band masks, finest-level adjacency and links."""
     geo = OracleGeometry(dim, verts, idx)
     dom = Domain.unit(dim, root)
-    off, ids = geo.bin(dom, B)
+    off, ids = geo.bin(dom, B, sampled=sampled)
     blocks = root_blocks(dim, (root,) * dim)
     levels = []
     for L in range(n_levels):
         if max_level_blocks is not None and blocks.shape[0] > max_level_blocks:
             raise ValueError("level too large for the oracle")
-        mask, band, nbp, _ = geo.refine_blocks(L, blocks, d_abs, d_rel, pred=pred)
-        lv = {"blocks": blocks, "mask": mask, "band": band, "n_band_pairs": nbp}
+        mask, band, nbp, _ = geo.refine_blocks(L, blocks, d_abs, d_rel, pred=pred, search=search)
+        flag = (mask != 0).astype(np.uint8)
+        if propagate_rounds and L + 1 < n_levels:
+            flag = propagate(dim, blocks, flag, propagate_rounds)
+        lv = {"blocks": blocks, "mask": mask, "band": band, "n_band_pairs": nbp, "flag": flag}
         levels.append(lv)
         if L + 1 < n_levels:
-            cb, cp = geo.children(blocks, mask)
+            cb, cp = geo.children(blocks, flag.astype(np.uint64))
             lv["child_parent"] = cp
             blocks = cb
     out = {"geo": geo, "dom": dom, "offsets": off, "ids": ids, "levels": levels}
@@ -297,7 +335,7 @@ def run_pipeline(dim, verts, idx, *, root, n_levels, B, lattice, d_abs=0.0, d_re
     bi, ci, cells = cells_of_mask(dim, fin["blocks"], fin["mask"])
     out["adj_block"], out["adj_bit"], out["adj_cells"] = bi, ci, cells
     L = n_levels - 1
-    out["adj_off"], out["adj_ids"], out["adj_band"] = geo.cell_faces(L, cells, d_abs, d_rel, pred=pred)
+    out["adj_off"], out["adj_ids"], out["adj_band"] = geo.cell_faces(L, cells, d_abs, d_rel, pred=pred, search=search)
     if links:
         out["q"], out["q_face"], out["q_band"] = geo.cell_links(L, lattice, cells)
     return out
