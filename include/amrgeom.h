@@ -118,6 +118,16 @@ typedef struct {
 } amr_bins_view;
 AMR_API amr_status amr_bin_faces(amr_ctx* ctx, int bin_density, amr_bins_view* out);
 
+/* Step 2, the paper's own membership (Sec. "Spatial Binning Algorithm", Fig.
+ * "Discretization of edges and triangles"): each face is discretised into points
+ * (its first edge into n + 1 points, n = ceil(length / s); in 3D every segment
+ * from such a point to the opposite vertex likewise; s = half a bin length) and
+ * belongs to every bin that holds one of them.  A subset of amr_bin_faces' bins;
+ * meant for the paper's binned search (amr_refine_params.search =
+ * AMR_SEARCH_OWN_BIN), which requires it or exact bins.  Same view and errors as
+ * amr_bin_faces; single-geometry contexts only. */
+AMR_API amr_status amr_bin_faces_sampled(amr_ctx* ctx, int bin_density, amr_bins_view* out);
+
 /* Step 3 — near-wall refinement (Sec. "Cell-Face Identification Algorithms").
  * n_levels total levels (n_levels - 1 refinement passes), 1 <= n_levels <= AMR_MAX_LEVELS.
  * lattice: 0 (no links), 9 (D2Q9, dim 2) or 19 (D3Q19, dim 3).
@@ -143,8 +153,16 @@ typedef struct {
                                  the previous call (the first call runs eagerly and captures) */
   int warps_per_cta;          /* warps per thread block of the refine kernels, 0 = default (4), max 8 */
   int predicate;              /* AMR_PRED_BOX (0) or AMR_PRED_POINT (1) */
+  int search;                 /* AMR_SEARCH_QUERY_BOX (0): every bin the cell's test region overlaps (exact
+                                 for any bin density); AMR_SEARCH_OWN_BIN (1): only the bin holding the cell
+                                 centre, the paper's binned face detection (needs AMR_PRED_POINT, no links) */
+  int propagate;              /* refinement-mark propagation rounds after each level that is refined further
+                                 (Sec. "Spatial Binning Algorithm"): 0 none, -1 the paper's
+                                 1 + floor(d_L / block length), k > 0 exactly k; each round marks the existing
+                                 neighbour blocks (3^D - 1) of every marked block; single-geometry only */
 } amr_refine_params;
 enum { AMR_PRED_BOX = 0, AMR_PRED_POINT = 1 };
+enum { AMR_SEARCH_QUERY_BOX = 0, AMR_SEARCH_OWN_BIN = 1 };
 
 /* Results.  Level arrays are per level 0..n_levels-1.
  *   block_coords[L]  device i32 [N_L][dim]

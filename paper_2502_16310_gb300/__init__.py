@@ -9,12 +9,15 @@ kernels behind the C ABI of ``include/amrgeom.h``; this package is its binding.
 from .binding import (  # noqa: F401
     AMR_PRED_BOX,
     AMR_PRED_POINT,
+    AMR_SEARCH_OWN_BIN,
+    AMR_SEARCH_QUERY_BOX,
     EXPORTED,
     AmrError,
     AmrBatch,
     AmrGeom,
     amr_autotune,
     amr_bin_faces,
+    amr_bin_faces_sampled,
     amr_bin_faces_static,
     amr_create,
     amr_destroy,

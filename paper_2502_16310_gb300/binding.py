@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECUDA", 4
                 5: "AMR_ETIMEOUT", 6: "AMR_ESTATE", 7: "AMR_EDEVICE_CHECK"}
 
 EXPORTED = ["amr_create", "amr_destroy", "amr_status_str", "amr_last_error", "amr_set_stream", "amr_geom_load",
-            "amr_bin_faces", "amr_refine_near_wall", "amr_sync", "amr_timing_enable", "amr_timing_reset",
+            "amr_bin_faces", "amr_bin_faces_sampled", "amr_refine_near_wall", "amr_sync", "amr_timing_enable", "amr_timing_reset",
             "amr_timing_get", "amr_launch_count", "amr_bin_faces_static", "amr_q_backward", "amr_autotune",
             "amr_batch_create", "amr_batch_destroy", "amr_batch_add", "amr_batch_set_bins", "amr_batch_run",
             "amr_batch_get_view", "amr_batch_q_backward", "amr_batch_last_error", "amr_batch_launch_count"]
@@ -54,10 +54,11 @@ class amr_bins_view(C.Structure):
 class amr_refine_params(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("d_abs", C.c_double), ("d_rel", C.c_double), ("lattice", C.c_int),
                 ("want_adjacency", C.c_int), ("want_links", C.c_int), ("use_graph", C.c_int),
-                ("warps_per_cta", C.c_int), ("predicate", C.c_int)]
+                ("warps_per_cta", C.c_int), ("predicate", C.c_int), ("search", C.c_int), ("propagate", C.c_int)]
 
 
 AMR_PRED_BOX, AMR_PRED_POINT = 0, 1
+AMR_SEARCH_QUERY_BOX, AMR_SEARCH_OWN_BIN = 0, 1
 
 
 class amr_refine_result(C.Structure):
@@ -109,6 +110,8 @@ def lib(build_if_missing: bool = True):
         L.amr_geom_load.argtypes = [P, P, i64, P, i64]
         L.amr_bin_faces.restype = C.c_int
         L.amr_bin_faces.argtypes = [P, C.c_int, C.POINTER(amr_bins_view)]
+        L.amr_bin_faces_sampled.restype = C.c_int
+        L.amr_bin_faces_sampled.argtypes = [P, C.c_int, C.POINTER(amr_bins_view)]
         L.amr_refine_near_wall.restype = C.c_int
         L.amr_refine_near_wall.argtypes = [P, C.POINTER(amr_refine_params), C.POINTER(amr_refine_result)]
         L.amr_sync.restype = C.c_int
@@ -195,10 +198,17 @@ def amr_bin_faces(ctx, bin_density: int) -> amr_bins_view:
     return v
 
 
+def amr_bin_faces_sampled(ctx, bin_density: int) -> amr_bins_view:
+    v = amr_bins_view()
+    _check(ctx, lib().amr_bin_faces_sampled(ctx, int(bin_density), C.byref(v)))
+    return v
+
+
 def amr_refine_near_wall(ctx, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True,
-                         want_links=True, use_graph=False, warps_per_cta=0,
-                         predicate=AMR_PRED_BOX) -> amr_refine_result:
-    p = _params(n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph, warps_per_cta, predicate)
+                         want_links=True, use_graph=False, warps_per_cta=0, predicate=AMR_PRED_BOX,
+                         search=AMR_SEARCH_QUERY_BOX, propagate=0) -> amr_refine_result:
+    p = _params(n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph, warps_per_cta, predicate,
+                search, propagate)
     r = amr_refine_result()
     _check(ctx, lib().amr_refine_near_wall(ctx, C.byref(p), C.byref(r)))
     return r
@@ -213,12 +223,12 @@ def amr_sync(ctx):
 
 
 def _params(n_levels=1, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=True, use_graph=False,
-            warps_per_cta=0, predicate=AMR_PRED_BOX):
+            warps_per_cta=0, predicate=AMR_PRED_BOX, search=AMR_SEARCH_QUERY_BOX, propagate=0):
     p = amr_refine_params()
     p.n_levels, p.d_abs, p.d_rel, p.lattice = int(n_levels), float(d_abs), float(d_rel), int(lattice)
     p.want_adjacency, p.want_links = int(bool(want_adjacency)), int(bool(want_links))
     p.use_graph, p.warps_per_cta = int(bool(use_graph)), int(warps_per_cta)
-    p.predicate = int(predicate)
+    p.predicate, p.search, p.propagate = int(predicate), int(search), int(propagate)
     return p
 
 
@@ -368,22 +378,24 @@ class AmrGeom:
             amr_geom_load(self.ctx, v.data_ptr(), v.shape[0], ix.data_ptr(), ix.shape[0])
         return self
 
-    def bin(self, B: int):
-        """Step 2: CSR bins; returns dict(offsets, ids) as borrowed int32 CUDA tensors (uint32 bits)."""
-        v = amr_bin_faces(self.ctx, B)
+    def bin(self, B: int, sampled: bool = False):
+        """Step 2: CSR bins; returns dict(offsets, ids) as borrowed int32 CUDA tensors (uint32 bits).
+        sampled: the paper's sampled-point membership instead of the exact AABB overlap."""
+        v = amr_bin_faces_sampled(self.ctx, B) if sampled else amr_bin_faces(self.ctx, B)
         self.bins = {"B": v.B, "n_bins": v.n_bins, "nnz": v.nnz,
                      "offsets": _u32(v.offsets, v.n_bins + 1), "ids": _u32(v.ids, v.nnz)}
         return self.bins
 
     def refine(self, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=None,
-               use_graph=False, warps_per_cta=0, predicate=AMR_PRED_BOX):
+               use_graph=False, warps_per_cta=0, predicate=AMR_PRED_BOX, search=AMR_SEARCH_QUERY_BOX, propagate=0):
         """Step 3: near-wall refinement; returns per-level tensors, adjacency CSR and links (borrowed).
         predicate: AMR_PRED_BOX (inflated cell box meets the face) or AMR_PRED_POINT (cell centre within
-        d of the face, the paper's Alg. 1)."""
+        d of the face, the paper's Alg. 1); search / propagate: the paper's binned search (own bin only)
+        and its mark propagation (-1: 1 + floor(d / block length) rounds)."""
         if want_links is None:
             want_links = lattice != 0
         r = amr_refine_near_wall(self.ctx, n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph,
-                                 warps_per_cta, predicate)
+                                 warps_per_cta, predicate, search, propagate)
         return self._wrap(r, want_adjacency, want_links)
 
     def _wrap(self, r, want_adjacency, want_links):

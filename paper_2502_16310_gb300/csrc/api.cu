@@ -62,12 +62,12 @@ constexpr int SC_WORDS = 72;
 struct GraphKey {
   uint64_t layout_gen = 0;
   int64_t nf = 0, n_geom = 0;
-  int n_levels = 0, lattice = 0, adjacency = 0, links = 0, warps = 0, B = 0, pred = 0;
+  int n_levels = 0, lattice = 0, adjacency = 0, links = 0, warps = 0, B = 0, pred = 0, search = 0, prop = 0;
   double d_abs = 0, d_rel = 0;
   bool operator==(const GraphKey& o) const {
     return layout_gen == o.layout_gen && nf == o.nf && n_geom == o.n_geom && n_levels == o.n_levels &&
            lattice == o.lattice && adjacency == o.adjacency && links == o.links && warps == o.warps && B == o.B &&
-           pred == o.pred && d_abs == o.d_abs && d_rel == o.d_rel;
+           pred == o.pred && search == o.search && prop == o.prop && d_abs == o.d_abs && d_rel == o.d_rel;
   }
 };
 
@@ -95,11 +95,12 @@ struct amr_ctx {
   bool multi = false;
   DevBuf table, face_gid;
   // buffers
-  DevBuf X, nrm, frec, recs, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
+  DevBuf X, nrm, frec, recs, hkeys, hvals, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
   LevelBufs lv[AMR_MAX_LEVELS];
   DevBuf adj_cell, adj_off, adj_ids, link_cell, link_dir, link_q, link_face;
   int64_t cap_cells = 0, cap_pairs = 0, cap_links = 0;
   int64_t cap_recs = 0, want_recs = 0;  // survivor record staging (entries)
+  bool sampled_bins = false;             // the last binning used the paper's sampled membership
   // adjoint
   DevBuf idx, vert_off, vert_corners, face_off, face_links, sort_keys, grad_face, sort_scratch, group_cnt, lvl_ptrs;
   bool vert_groups = false, face_groups = false;
@@ -384,7 +385,7 @@ amr_status amr_ctx_init(amr_ctx* ctx) {
 void amr_ctx_free(amr_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   drop_graph(ctx);
-  DevBuf* all[] = {&ctx->X, &ctx->frec, &ctx->recs, &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
+  DevBuf* all[] = {&ctx->X, &ctx->frec, &ctx->recs, &ctx->hkeys, &ctx->hvals, &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
                    &ctx->count,     &ctx->offsets,      &ctx->ids,        &ctx->payload,    &ctx->scratch,
                    &ctx->misc,      &ctx->scal,         &ctx->adj_cell,   &ctx->adj_off,    &ctx->adj_ids,
                    &ctx->link_cell, &ctx->link_dir,     &ctx->link_q,     &ctx->link_face,  &ctx->idx,
@@ -443,6 +444,13 @@ amr_status amr_bin_all(amr_ctx* ctx) {
   fa.face_gid = ctx->multi ? static_cast<const uint32_t*>(ctx->face_gid.p) : nullptr;
   fa.frange = static_cast<uint32_t*>(ctx->frange.p);
   fa.count = static_cast<uint32_t*>(ctx->count.p);
+  if (ctx->sampled_bins && !ctx->multi) {
+    // the paper's sampled membership: spacing half a bin length (the shortest axis's bin)
+    double ext = 1e300;
+    for (int a = 0; a < D; ++a) ext = std::min(ext, (4.0 * (double)ctx->dom.root_blocks[a]) * ctx->dom.h0);
+    fa.sampled = 1;
+    fa.sample_s = 0.5 * (ext / (double)ctx->geoms[0].B);
+  }
   uint32_t* offsets = static_cast<uint32_t*>(ctx->offsets.p);
   timed(ctx, st, "bin_count", [&] { return launch_face_bins(fa, st); });
   timed(ctx, st, "bin_scan", [&] {
@@ -485,7 +493,7 @@ struct Plan {
   bool fin_at[AMR_MAX_LEVELS];      // some geometry ends at this level
   bool cont_after[AMR_MAX_LEVELS];  // some geometry continues below this level
   bool adjacency, links;
-  int lattice, warps, pred;
+  int lattice, warps, pred, search, propagate;
   int64_t n_roots;
 };
 
@@ -501,6 +509,8 @@ Plan make_plan(const amr_ctx* ctx, const amr_refine_params* p) {
   P.lattice = p->lattice;
   P.warps = p->warps_per_cta > 0 ? p->warps_per_cta : 4;
   P.pred = p->predicate;
+  P.search = p->search;
+  P.propagate = p->propagate;
   for (const auto& g : ctx->geoms) P.n_roots += roots_of(g, ctx->dom.dim);
   return P;
 }
@@ -540,6 +550,7 @@ RefineLevel level_args(amr_ctx* ctx, const Plan& P, int L) {
   a.err = ctx->d_err;
   a.warps = P.warps;
   a.pred = P.pred;
+  a.search = P.search;
   // blocks per work fetch: batches hide the fetch latency where every warp has many blocks;
   // single blocks keep the load balanced where there are few (and heavy ones cluster)
   const int64_t per_warp = ctx->lv[L].cap / ((int64_t)ctx->num_sms * 16);
@@ -599,6 +610,23 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st)
     RefineLevel a = level_args(ctx, P, L);
     CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), st));
     timed(ctx, st, "refine_level", [&] { return launch_refine(a, ctx->num_sms, st); });
+    if (P.cont_after[L] && P.propagate != 0) {
+      // the paper's mark propagation over this level's blocks (flags 0/1 in place)
+      const GeomParams& g0 = ctx->geoms[0];
+      const double hL = std::ldexp(g0.h0, -L);
+      const int rounds = P.propagate > 0 ? P.propagate
+                                         : 1 + (int)std::floor((g0.d_abs + g0.d_rel * hL) / (4.0 * hL));
+      const uint32_t slots = propagate_hash_slots(lb.cap);
+      if (eager) {
+        TRY(ensure(ctx, ctx->hkeys, sizeof(unsigned long long) * slots));
+        TRY(ensure(ctx, ctx->hvals, sizeof(uint32_t) * slots));
+      }
+      timed(ctx, st, "propagate", [&] {
+        return launch_propagate(D, a.blocks, lb.cap, ctx->d_scal + SC_N + L, a.flag, rounds,
+                                static_cast<unsigned long long*>(ctx->hkeys.p), static_cast<uint32_t*>(ctx->hvals.p),
+                                slots, ctx->d_err, st);
+      });
+    }
     if (P.cont_after[L]) {
       LevelBufs& nx = ctx->lv[L + 1];
       if (eager) {
@@ -618,6 +646,7 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st)
       ca.gid = a.gid;
       ca.blocks = a.blocks;
       ca.mask = a.mask;
+      ca.flag = a.flag;
       ca.n = lb.cap;
       ca.n_dev = ctx->d_scal + SC_N + L;
       ca.child_blocks = static_cast<int32_t*>(nx.blocks.p);
@@ -824,6 +853,8 @@ amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine
   key.d_abs = prm->d_abs;
   key.d_rel = prm->d_rel;
   key.pred = prm->predicate;
+  key.search = prm->search;
+  key.prop = prm->propagate;
   const bool want_graph = prm->use_graph != 0;
   if (want_graph && ctx->gexec && ctx->gkey == key) {
     // replay on the graph stream, ordered after the caller's stream
@@ -991,7 +1022,7 @@ amr_status amr_geom_load(amr_ctx* ctx, const float* coords, int64_t n_verts, con
   return AMR_OK;
 }
 
-amr_status amr_bin_faces(amr_ctx* ctx, int B, amr_bins_view* out) {
+static amr_status bin_faces_impl(amr_ctx* ctx, int B, amr_bins_view* out, bool sampled) {
   if (!ctx || !out) return AMR_EINVAL;
   if (ctx->multi) return fail(ctx, AMR_ESTATE, "amr_bin_faces on a batch context");
   if (!ctx->loaded) return fail(ctx, AMR_ESTATE, "amr_bin_faces before amr_geom_load");
@@ -1002,6 +1033,7 @@ amr_status amr_bin_faces(amr_ctx* ctx, int B, amr_bins_view* out) {
   ctx->binned = ctx->refined = false;
   const GeomParams prev = ctx->geoms[0];
   ctx->geoms[0] = amr_make_row(ctx->dom, B, prev.n_levels, prev.d_abs, prev.d_rel);
+  ctx->sampled_bins = sampled;
   TRY(amr_bin_all(ctx));
   ctx->B = B;
   out->B = B;
@@ -1011,6 +1043,10 @@ amr_status amr_bin_faces(amr_ctx* ctx, int B, amr_bins_view* out) {
   out->ids = static_cast<const uint32_t*>(ctx->ids.p);
   return AMR_OK;
 }
+
+amr_status amr_bin_faces(amr_ctx* ctx, int B, amr_bins_view* out) { return bin_faces_impl(ctx, B, out, false); }
+
+amr_status amr_bin_faces_sampled(amr_ctx* ctx, int B, amr_bins_view* out) { return bin_faces_impl(ctx, B, out, true); }
 
 amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_refine_result* out) {
   if (!ctx || !prm || !out) return AMR_EINVAL;
@@ -1023,6 +1059,18 @@ amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_
   if (prm->warps_per_cta < 0 || prm->warps_per_cta > 8) return fail(ctx, AMR_EINVAL, "warps_per_cta in [0, 8]");
   if (prm->predicate != AMR_PRED_BOX && prm->predicate != AMR_PRED_POINT)
     return fail(ctx, AMR_EINVAL, "predicate must be AMR_PRED_BOX (0) or AMR_PRED_POINT (1)");
+  if (prm->search != AMR_SEARCH_QUERY_BOX && prm->search != AMR_SEARCH_OWN_BIN)
+    return fail(ctx, AMR_EINVAL, "search must be AMR_SEARCH_QUERY_BOX (0) or AMR_SEARCH_OWN_BIN (1)");
+  if (prm->search == AMR_SEARCH_OWN_BIN && (prm->predicate != AMR_PRED_POINT || prm->want_links))
+    return fail(ctx, AMR_EINVAL, "the own-bin search needs the point predicate and no links");
+  if (ctx->sampled_bins && prm->search != AMR_SEARCH_OWN_BIN)
+    return fail(ctx, AMR_EINVAL, "sampled bins only serve the own-bin search");
+  if (prm->propagate < -1) return fail(ctx, AMR_EINVAL, "propagate must be >= -1");
+  if (prm->propagate != 0) {
+    for (int a = 0; a < D; ++a)
+      if ((int64_t)ctx->dom.root_blocks[a] << (NL - 1) >= (1ll << 21))
+        return fail(ctx, AMR_EINVAL, "propagation needs block coordinates below 2^21 on every level");
+  }
   if (prm->want_links) {
     if (!((D == 2 && prm->lattice == 9) || (D == 3 && prm->lattice == 19)))
       return fail(ctx, AMR_EINVAL, "lattice must be 9 (D2Q9) in 2D or 19 (D3Q19) in 3D");
@@ -1473,6 +1521,10 @@ amr_status amr_batch_run(amr_batch* b, const amr_refine_params* prm, amr_refine_
   for (auto& x : b->in)
     if (x.B < 1) return fail(ctx, AMR_ESTATE, "a geometry has no bin density (set it or tune it)");
   if (prm->warps_per_cta < 0 || prm->warps_per_cta > 8) return fail(ctx, AMR_EINVAL, "warps_per_cta in [0, 8]");
+  if (prm->predicate != AMR_PRED_BOX && prm->predicate != AMR_PRED_POINT)
+    return fail(ctx, AMR_EINVAL, "predicate must be AMR_PRED_BOX (0) or AMR_PRED_POINT (1)");
+  if (prm->search != AMR_SEARCH_QUERY_BOX || prm->propagate != 0)
+    return fail(ctx, AMR_EINVAL, "batches use the query-box search without propagation");
   if (prm->want_links) {
     if (!((D == 2 && prm->lattice == 9) || (D == 3 && prm->lattice == 19)))
       return fail(ctx, AMR_EINVAL, "lattice must be 9 (D2Q9) in 2D or 19 (D3Q19) in 3D");

@@ -349,6 +349,8 @@ struct FaceBinArgs {
   const uint32_t* face_gid;
   uint32_t* frange;
   uint32_t* count;
+  int sampled;                 // 1: the paper's sampled-point membership (single geometry)
+  double sample_s;             // sample spacing (half a bin length)
 };
 int launch_face_bins(const FaceBinArgs& a, cudaStream_t st);
 int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint32_t* frange, uint32_t* count,
@@ -408,6 +410,7 @@ struct RefineLevel {
   unsigned* err;
   int warps;                   // warps per CTA (tunable)
   int pred;                    // adjacency predicate: 0 box (SAT of the inflated cell), 1 point (Alg. 1)
+  int search;                  // candidates: 0 the bins of the inflated query box, 1 the cell's own bin (point only)
   int batch;                   // consecutive blocks a warp takes per work fetch (1..kMaxBatch)
 };
 constexpr int kMaxBatch = 8;
@@ -432,6 +435,7 @@ struct ChildrenArgs {
   const uint32_t* gid;
   const int32_t* blocks;
   const uint64_t* mask;
+  const uint8_t* flag;         // nullable: marked for refinement (flag != 0) instead of mask != 0
   int64_t n;                   // count, or capacity when n_dev is set
   const uint64_t* n_dev;
   int32_t* child_blocks;
@@ -442,6 +446,14 @@ struct ChildrenArgs {
   unsigned* err;
 };
 size_t children_scratch_bytes(int64_t n);
+
+// Mark propagation over one level (flags 0/1 in place): `rounds` two-phase rounds
+// through a hash of the block coordinates (keys/vals: `slots` entries, a power of
+// two >= 2 x capacity, from propagate_hash_slots; coordinates below 2^21).
+uint32_t propagate_hash_slots(int64_t cap);
+int launch_propagate(int dim, const int32_t* blocks, int64_t cap, const uint64_t* n_dev, uint8_t* flags,
+                     int rounds, unsigned long long* keys, uint32_t* vals, uint32_t slots, unsigned* err,
+                     cudaStream_t st);
 int launch_children(const ChildrenArgs& a, void* scratch, int num_sms, cudaStream_t st);
 // Level-0 blocks of every geometry of the table (x fastest within each), with their geometry ids.
 int launch_root_blocks(int dim, const int* root, int32_t* blocks, int64_t n, cudaStream_t st);

@@ -107,6 +107,101 @@ __global__ void k_face_normals(const float* __restrict__ X, int64_t nf, float* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// The paper's sampled-point bin membership (Sec. "Spatial Binning Algorithm",
+// Fig. "Discretization of edges and triangles"): the face is discretised into
+// points, its first edge v0-v1 into n + 1 points v0 + (i/n)(v1 - v0) with
+// n = max(1, ceil(|v1 - v0| / s)), then (3D) every segment from such a point to
+// the opposite vertex likewise; the face belongs to every bin holding a point.
+// FP64, one rounding per operation in this order (the definition's order), so
+// that the points and their bins are reproducible exactly.
+// ---------------------------------------------------------------------------
+template <int Dm>
+__device__ __forceinline__ int seg_points(const double* a, const double* b, double s) {
+  double l2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < Dm; ++c) {
+    const double e = __dsub_rn(b[c], a[c]);
+    l2 = __dadd_rn(l2, __dmul_rn(e, e));
+  }
+  const double n = ceil(__ddiv_rn(__dsqrt_rn(l2), s));
+  return n < 1.0 ? 1 : (n > 4096.0 ? 4096 : (int)n);
+}
+
+template <int D, typename F>
+__device__ __forceinline__ void for_each_sample(const double* v, double s, F&& visit) {
+  const double* v0 = v;
+  const double* v1 = v + D;
+  const int n = seg_points<D>(v0, v1, s);
+  for (int i = 0; i <= n; ++i) {
+    const double t = __ddiv_rn((double)i, (double)n);
+    double p[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < D; ++c) p[c] = __dadd_rn(v0[c], __dmul_rn(t, __dsub_rn(v1[c], v0[c])));
+    if constexpr (D == 2) {
+      visit(p);
+    } else {
+      const double* v2 = v + 6;
+      const int m = seg_points<3>(p, v2, s);
+      for (int j = 0; j <= m; ++j) {
+        const double u = __ddiv_rn((double)j, (double)m);
+        double q[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[c] = __dadd_rn(p[c], __dmul_rn(u, __dsub_rn(v2[c], p[c])));
+        visit(q);
+      }
+    }
+  }
+}
+
+// Every bin (x, y, z) of face f's sampled membership, once.  Samples can only
+// leave the AABB bin range [lo, hi] by rounding (one bin at most), so a bitmask
+// over the range widened by one bin collects them; faces whose widened range
+// has more than 64 bins test every bin of that range against all samples.
+template <int D, typename F>
+__device__ void sampled_bins(const float* X, int64_t nf, int64_t f, const GeomParams& P, double s, const int* lo,
+                             const int* hi, F&& visit) {
+  double v[9];
+#pragma unroll
+  for (int j = 0; j < D * D; ++j) v[j] = (double)X[(int64_t)j * nf + f];
+  int wl[3] = {0, 0, 0}, wn[3] = {1, 1, 1};
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    wl[c] = lo[c] > 0 ? lo[c] - 1 : 0;
+    const int wh = hi[c] < P.B - 1 ? hi[c] + 1 : P.B - 1;
+    wn[c] = wh - wl[c] + 1;
+  }
+  auto cell = [&](const double* q, int* c) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) c[a] = bin_coord(q[a], P.origin[a], P.bin_scale[a], P.B);
+  };
+  if (wn[0] * wn[1] * wn[2] <= 64) {
+    uint64_t m = 0;
+    for_each_sample<D>(v, s, [&](const double* q) {
+      int c[3] = {0, 0, 0};
+      cell(q, c);
+      const int k = (c[0] - wl[0]) + wn[0] * ((c[1] - wl[1]) + wn[1] * (c[2] - wl[2]));
+      if (k >= 0 && k < 64) m |= 1ull << k;  // (always: rounding moves a sample by < 1 bin)
+    });
+    for (; m; m &= m - 1) {
+      const int k = __ffsll((long long)m) - 1;
+      visit(wl[0] + k % wn[0], wl[1] + (k / wn[0]) % wn[1], wl[2] + k / (wn[0] * wn[1]));
+    }
+    return;
+  }
+  for (int z = wl[2]; z < wl[2] + wn[2]; ++z)
+    for (int y = wl[1]; y < wl[1] + wn[1]; ++y)
+      for (int x = wl[0]; x < wl[0] + wn[0]; ++x) {
+        bool hit = false;
+        for_each_sample<D>(v, s, [&](const double* q) {
+          int c[3] = {0, 0, 0};
+          cell(q, c);
+          hit = hit || (c[0] == x && c[1] == y && c[2] == z);
+        });
+        if (hit) visit(x, y, z);
+      }
+}
+
 // Per face: bin range of its AABB along each axis (packed lo | hi << 16, bins of
 // its own geometry) and one count per (face, bin) incidence.
 template <int D>
@@ -128,6 +223,12 @@ __global__ void k_face_bins(FaceBinArgs a) {
       a.frange[(int64_t)c * a.nf + f] = (uint32_t)lo[c] | ((uint32_t)hi[c] << 16);
     }
     const int64_t B = P.B;
+    if (a.sampled) {
+      sampled_bins<D>(a.X, a.nf, f, P, a.sample_s, lo, hi, [&](int x, int y, int z) {
+        atomicAdd(&a.count[P.bin_base + x + B * (y + B * (int64_t)z)], 1u);
+      });
+      continue;
+    }
     for (int z = lo[2]; z <= hi[2]; ++z)
       for (int y = lo[1]; y <= hi[1]; ++y)
         for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&a.count[P.bin_base + x + B * (y + B * (int64_t)z)], 1u);
@@ -165,24 +266,29 @@ __global__ void k_scatter(ScatterArgs a) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) e.v[j] = a.f.X[(int64_t)j * nf + f];
     }
+    auto put = [&](int x, int y, int z) {
+      const int64_t b = bin_base + x + B * (y + B * (int64_t)z);
+      const uint32_t old = atomicSub(&a.f.count[b], 1u);
+      const int64_t pos = (int64_t)a.offsets[b] + old - 1;
+      a.ids[pos] = (uint32_t)f;
+      uint32_t flags = (x == lo[0] ? (1u << 29) : 0u) | (y == lo[1] ? (1u << 30) : 0u);
+      if (D == 3) flags |= (z == lo[2] ? (1u << 31) : 0u);
+      e.id = (uint32_t)f | flags;
+      e.bin[0] = (uint32_t)x;
+      e.bin[1] = (uint32_t)y;
+      e.bin[2] = (uint32_t)z;
+      const float4* src = reinterpret_cast<const float4*>(&e);
+      float4* dst = reinterpret_cast<float4*>(payload + pos);
+#pragma unroll
+      for (int q = 0; q < (int)(sizeof(E) / 16); ++q) dst[q] = src[q];
+    };
+    if (a.f.sampled) {
+      sampled_bins<D>(a.f.X, nf, f, P, a.f.sample_s, lo, hi, put);
+      continue;
+    }
     for (int z = lo[2]; z <= hi[2]; ++z)
       for (int y = lo[1]; y <= hi[1]; ++y)
-        for (int x = lo[0]; x <= hi[0]; ++x) {
-          const int64_t b = bin_base + x + B * (y + B * (int64_t)z);
-          const uint32_t old = atomicSub(&a.f.count[b], 1u);
-          const int64_t pos = (int64_t)a.offsets[b] + old - 1;
-          a.ids[pos] = (uint32_t)f;
-          uint32_t flags = (x == lo[0] ? (1u << 29) : 0u) | (y == lo[1] ? (1u << 30) : 0u);
-          if (D == 3) flags |= (z == lo[2] ? (1u << 31) : 0u);
-          e.id = (uint32_t)f | flags;
-          e.bin[0] = (uint32_t)x;
-          e.bin[1] = (uint32_t)y;
-          e.bin[2] = (uint32_t)z;
-          const float4* src = reinterpret_cast<const float4*>(&e);
-          float4* dst = reinterpret_cast<float4*>(payload + pos);
-#pragma unroll
-          for (int q = 0; q < (int)(sizeof(E) / 16); ++q) dst[q] = src[q];
-        }
+        for (int x = lo[0]; x <= hi[0]; ++x) put(x, y, z);
   }
 }
 

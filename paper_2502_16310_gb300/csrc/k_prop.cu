@@ -1,0 +1,129 @@
+// k_prop.cu — refinement-mark propagation over one level's block list.
+//
+// Paper (Sec. "Spatial Binning Algorithm", Fig. "propagation"): with binned
+// face detection a cell can miss faces within the near-wall distance that lie
+// in other bins, so blocks marked for refinement also mark their neighbouring
+// blocks, N_prop = 1 + floor(d_spec / block length) times; each round goes
+// through an intermediate value so that marks set in a round do not spread in
+// the same round.  Neighbours are the 3^D - 1 blocks of the same level around a
+// block that exist in the level's list, found through an open-addressing hash
+// of the block coordinates built once per level.
+#include "internal.cuh"
+
+namespace amr {
+
+namespace {
+
+constexpr int kPThreads = 256;
+constexpr unsigned long long kEmpty = 0ull;
+
+__device__ __forceinline__ unsigned long long block_key(const int32_t* c, int dim) {
+  unsigned long long k = 0;
+  for (int a = 0; a < dim; ++a) k = (k << 21) | (unsigned long long)((uint32_t)c[a] & 0x1fffffu);
+  return k + 1ull;  // 0 marks an empty slot
+}
+
+__device__ __forceinline__ uint32_t hash_slot(unsigned long long k, uint32_t mask) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  return (uint32_t)k & mask;
+}
+
+__device__ __forceinline__ int64_t count_of(int64_t cap, const uint64_t* n_dev) {
+  if (!n_dev) return cap;
+  const int64_t n = (int64_t)*n_dev;
+  return n < cap ? n : cap;
+}
+
+__global__ void k_hash_insert(int dim, const int32_t* __restrict__ blocks, int64_t cap, const uint64_t* n_dev,
+                              unsigned long long* keys, uint32_t* vals, uint32_t hmask, unsigned* err) {
+  const int64_t n = count_of(cap, n_dev);
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = block_key(blocks + b * dim, dim);
+    uint32_t s = hash_slot(k, hmask);
+    for (uint32_t probe = 0;; ++probe) {
+      if (probe > hmask) {  // table full: cannot happen with twice the capacity
+        atomicOr(err, ERR_OVERFLOW);
+        break;
+      }
+      const unsigned long long prev = atomicCAS(keys + s, kEmpty, k);
+      if (prev == kEmpty || prev == k) {
+        vals[s] = (uint32_t)b;
+        break;
+      }
+      s = (s + 1) & hmask;
+    }
+  }
+}
+
+__device__ __forceinline__ int64_t hash_find(const unsigned long long* keys, const uint32_t* vals, uint32_t hmask,
+                                             unsigned long long k) {
+  uint32_t s = hash_slot(k, hmask);
+  for (uint32_t probe = 0; probe <= hmask; ++probe) {
+    const unsigned long long v = keys[s];
+    if (v == k) return (int64_t)vals[s];
+    if (v == kEmpty) return -1;
+    s = (s + 1) & hmask;
+  }
+  return -1;
+}
+
+// Round, first half: every marked block (flag 1) gives its unmarked existing
+// neighbours the intermediate value 2.
+__global__ void k_prop_mark(int dim, const int32_t* __restrict__ blocks, int64_t cap, const uint64_t* n_dev,
+                            uint8_t* flags, const unsigned long long* keys, const uint32_t* vals, uint32_t hmask) {
+  const int64_t n = count_of(cap, n_dev);
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    if (flags[b] != 1) continue;
+    const int32_t* c = blocks + b * dim;
+    const int nz = dim == 3 ? 1 : 0;
+    for (int dz = -nz; dz <= nz; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (dx == 0 && dy == 0 && dz == 0) continue;
+          const int32_t q[3] = {c[0] + dx, c[1] + dy, dim == 3 ? c[2] + dz : 0};
+          if (q[0] < 0 || q[1] < 0 || q[2] < 0) continue;
+          const int64_t i = hash_find(keys, vals, hmask, block_key(q, dim));
+          if (i >= 0 && flags[i] == 0) flags[i] = 2;
+        }
+  }
+}
+
+// Round, second half: intermediate values become marks.
+__global__ void k_prop_commit(int64_t cap, const uint64_t* n_dev, uint8_t* flags) {
+  const int64_t n = count_of(cap, n_dev);
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x)
+    if (flags[b] == 2) flags[b] = 1;
+}
+
+int grid_of(int64_t n) {
+  int64_t g = (n + kPThreads - 1) / kPThreads;
+  if (g < 1) g = 1;
+  if (g > 152 * 8) g = 152 * 8;
+  return (int)g;
+}
+
+}  // namespace
+
+uint32_t propagate_hash_slots(int64_t cap) {
+  uint32_t s = 1024;
+  while ((int64_t)s < 2 * cap && s < (1u << 31)) s <<= 1;
+  return s;
+}
+
+int launch_propagate(int dim, const int32_t* blocks, int64_t cap, const uint64_t* n_dev, uint8_t* flags,
+                     int rounds, unsigned long long* keys, uint32_t* vals, uint32_t slots, unsigned* err,
+                     cudaStream_t st) {
+  if (rounds <= 0 || cap <= 0) return 0;
+  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * slots, st);
+  const int g = grid_of(cap);
+  k_hash_insert<<<g, kPThreads, 0, st>>>(dim, blocks, cap, n_dev, keys, vals, slots - 1, err);
+  for (int r = 0; r < rounds; ++r) {
+    k_prop_mark<<<g, kPThreads, 0, st>>>(dim, blocks, cap, n_dev, flags, keys, vals, slots - 1);
+    k_prop_commit<<<g, kPThreads, 0, st>>>(cap, n_dev, flags);
+  }
+  return 1 + 2 * rounds;
+}
+
+}  // namespace amr

@@ -49,7 +49,7 @@ struct Surv<2> {
   float4 t[3];
   float e[2];
   uint32_t face;
-  uint32_t pad;
+  uint32_t pad[1];
 };
 
 // FP64 separating-axis margin of the box [x_c - r, x_c + r]^3 and the closed
@@ -532,9 +532,34 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
   F.r = fmaf(0.5f, hf, g.d);
   // block-level cull: the box around the block centre that holds every cell's
   // test region (point predicate: the cell centres' box, 1.5 h, inflated by d)
-  F.rb = PRED == 1 ? fmaf(1.5f, hf, g.d) : fmaf(2.0f, hf, g.d);
+  constexpr bool kPoint = PRED >= 1;   // point predicate (Alg. 1)
+  constexpr bool kOwnBin = PRED == 2;  // the paper's binned search: each cell only sees its own bin
+  F.rb = kPoint ? fmaf(1.5f, hf, g.d) : fmaf(2.0f, hf, g.d);
   const float R2 = g.d * g.d;
   F.O = O;
+  // the paper's binned search: the query box is the bins of the block's cell
+  // centres, and each cell only takes the entries of its own bin (bins of the
+  // FP64 cell centres, as the definition computes them)
+  uint32_t own0 = 0, own1 = 0, oz0 = 0, oz1 = 0;
+  if constexpr (kOwnBin) {
+    const double hL = scalbn(P.h0, -a.level);
+    auto centre_bin = [&](int c, int l) {
+      const double x = __dadd_rn(P.origin[c], __dmul_rn((double)(4 * b[c] + l) + 0.5, hL));
+      return bin_coord(x, P.origin[c], P.bin_scale[c], P.B);
+    };
+    uint32_t cb0[3] = {0, 0, 0}, cb1[3] = {0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      qlo[c] = centre_bin(c, 0);
+      qhi[c] = centre_bin(c, 3);
+      cb0[c] = (uint32_t)centre_bin(c, (lane >> (2 * c)) & 3);
+      if (D == 3) cb1[c] = (uint32_t)centre_bin(c, ((lane + 32) >> (2 * c)) & 3);
+    }
+    own0 = cb0[0] | (cb0[1] << 16);
+    oz0 = cb0[2];
+    own1 = cb1[0] | (cb1[1] << 16);
+    oz1 = cb1[2];
+  }
   // cell centres of this lane in the frame: lo + (l + 1/2) h
   float o0[3] = {0, 0, 0}, o1[3] = {0, 0, 0};
   const bool lane_cell = D == 3 || lane < 16;
@@ -580,9 +605,9 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
         const E& ent = sm.buf[cb][lane];
         const uint32_t id = ent.id;
         // visit a face only in the first bin of its range inside the query box
-        bool canon = ((id >> 29) & 1u) || (int)ent.bin[0] == qlo[0];
-        canon = canon && (((id >> 30) & 1u) || (int)ent.bin[1] == qlo[1]);
-        if (D == 3) canon = canon && (((id >> 31) & 1u) || (int)ent.bin[2] == qlo[2]);
+        bool canon = kOwnBin || ((id >> 29) & 1u) || (int)ent.bin[0] == qlo[0];
+        canon = canon && (kOwnBin || ((id >> 30) & 1u) || (int)ent.bin[1] == qlo[1]);
+        if (D == 3) canon = canon && (kOwnBin || ((id >> 31) & 1u) || (int)ent.bin[2] == qlo[2]);
         if (canon) {
           wc.cand++;
           const uint32_t f = id & kIdMask;
@@ -596,8 +621,12 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
 #pragma unroll
           for (int j = 0; j < D * D; ++j) V[j] = ent.v[j];
           surv = setup_face<D>(V, nh, F, sm.surv[lane]);
-          if constexpr (PRED == 1) {
+          if constexpr (kPoint) {
             if (surv) setup_point<D>(V, nh, F, sm.surv[lane]);
+          }
+          if constexpr (kOwnBin) {
+            sm.surv[lane].pad[0] = ent.bin[0] | (ent.bin[1] << 16);
+            if constexpr (D == 3) sm.surv[lane].pad[1] = ent.bin[2];
           }
           sm.surv[lane].face = f;
         }
@@ -611,7 +640,11 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
         const Surv<D>& S = sm.surv[s];
         int t0 = 0, t1 = 0;
         if (!(kMarkOnly && h0 && h1)) {
-          if constexpr (PRED == 1) {
+          if constexpr (kOwnBin) {
+            const uint32_t sz = D == 3 ? S.pad[1] : 0u;
+            t0 = (own0 == S.pad[0] && oz0 == sz) ? point_test<D>(S, o0, R2) : 0;
+            t1 = D == 3 && own1 == S.pad[0] && oz1 == sz ? point_test<D>(S, o1, R2) : 0;
+          } else if constexpr (kPoint) {
             t0 = point_test<D>(S, o0, R2);
             t1 = D == 3 ? point_test<D>(S, o1, R2) : 0;
           } else {
@@ -956,7 +989,7 @@ __global__ void __launch_bounds__(kChThreads) k_children(ChildrenArgs a, uint64_
     for (int i = 0; i < kChItems; ++i) {
       const int64_t j = base + i;
       bool emit = false;
-      if (j < n && a.mask[j] != 0) {
+      if (j < n && (a.flag ? a.flag[j] != 0 : a.mask[j] != 0)) {
         const GeomParams P = geom_row(a.g0, a.table, a.gid, j);
         emit = a.level < P.n_levels - 1;
       }
@@ -1037,10 +1070,11 @@ int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st) {
     allow_smem(kernel, smem);
     kernel<<<g, warps * 32, smem, st>>>(a);
   };
+  const int mode = a.search == 1 ? 2 : (a.pred == 1 ? 1 : 0);
   if (a.dim == 3)
-    a.pred == 1 ? go(k_refine<3, 1>) : go(k_refine<3, 0>);
+    mode == 2 ? go(k_refine<3, 2>) : (mode == 1 ? go(k_refine<3, 1>) : go(k_refine<3, 0>));
   else
-    a.pred == 1 ? go(k_refine<2, 1>) : go(k_refine<2, 0>);
+    mode == 2 ? go(k_refine<2, 2>) : (mode == 1 ? go(k_refine<2, 1>) : go(k_refine<2, 0>));
   return 1;
 }
 
@@ -1053,10 +1087,11 @@ int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st) {
     allow_smem(kernel, smem);
     kernel<<<g, warps * 32, smem, st>>>(a);
   };
+  const int mode = a.lv.search == 1 ? 2 : (a.lv.pred == 1 ? 1 : 0);
   if (a.lv.dim == 3)
-    a.lv.pred == 1 ? go(k_adjacency<3, 1>) : go(k_adjacency<3, 0>);
+    mode == 2 ? go(k_adjacency<3, 2>) : (mode == 1 ? go(k_adjacency<3, 1>) : go(k_adjacency<3, 0>));
   else
-    a.lv.pred == 1 ? go(k_adjacency<2, 1>) : go(k_adjacency<2, 0>);
+    mode == 2 ? go(k_adjacency<2, 2>) : (mode == 1 ? go(k_adjacency<2, 1>) : go(k_adjacency<2, 0>));
   return 1;
 }
 
