@@ -378,10 +378,12 @@ def run_batched(args, dev, flush):
             "batched_over_single": t_single / t_batch, "generate_s": gen_s, "tune_s": tune_s}
 
 
-def run_paper_setups(args, dev, flush, bins=(1, 2, 8, 16), reps=3):
+def run_paper_setups(args, dev, flush, bins=(1, 2, 4, 8, 16), reps=3):
     """The paper's two speed-up setups (point predicate, absolute d_spec, refined twice) at its bin
-    densities: bin-setup and face-detection (marking) times per B, and the blocks per level (which exact
-    binning keeps independent of B)."""
+    densities, each in two modes: `exact` (AABB bins, every bin the test region overlaps: the marks do
+    not depend on B) and `paper` (the paper's sampled bins, face detection in the cell's own bin, then
+    1 + floor(d / block length) propagation rounds: the inserted blocks vary with B).  Per B: bin-setup
+    and face-detection (marking, with propagation) times and the blocks per level."""
     import torch
 
     from paper_2502_16310_gb300 import AmrGeom
@@ -390,35 +392,40 @@ def run_paper_setups(args, dev, flush, bins=(1, 2, 8, 16), reps=3):
     out = {}
     for name in ("p2", "p3"):
         w = workload(name)
-        g = AmrGeom(w.dim, (w.root,) * w.dim)
         v = torch.from_numpy(w.verts).to(dev)
         ix = torch.from_numpy(w.idx).to(dev)
-        rows = {"workload": w.description, "faces": w.n_faces, "B": [], "bin_ms": [], "detect_ms": [],
-                "blocks_per_level": [], "near_wall_cells": []}
-        for B in bins:
-            def step():
-                g.load(v, ix)
-                g.bin(B)
-                return g.refine(w.n_levels, w.d_abs, w.d_rel, 0, False, False, predicate=w.predicate)
+        rows = {"workload": w.description, "faces": w.n_faces, "B": list(bins)}
+        for mode in ("exact", "paper"):
+            g = AmrGeom(w.dim, (w.root,) * w.dim)
+            r = {"bin_ms": [], "detect_ms": [], "blocks_per_level": [], "near_wall_cells": []}
+            for B in bins:
+                def step():
+                    g.load(v, ix)
+                    if mode == "exact":
+                        g.bin(B)
+                        return g.refine(w.n_levels, w.d_abs, w.d_rel, 0, False, False, predicate=w.predicate)
+                    g.bin(B, sampled=True)
+                    return g.refine(w.n_levels, w.d_abs, w.d_rel, 0, False, False, predicate=w.predicate,
+                                    search=1, propagate=-1)
 
-            res = step()
-            torch.cuda.synchronize()
-            g.timing(True)
-            g.timing_reset()
-            for k in range(reps):
-                flush.fill_(k & 0xff)
-                step()
-            torch.cuda.synchronize()
-            tk = g.timings()
-            g.timing(False)
-            t_bin = sum(tk[k][0] for k in ("bin_count", "bin_scan", "bin_scatter") if k in tk) / reps
-            t_det = tk.get("refine_level", (0.0, 0))[0] / reps
-            rows["B"].append(B)
-            rows["bin_ms"].append(round(t_bin, 4))
-            rows["detect_ms"].append(round(t_det, 4))
-            rows["blocks_per_level"].append([int(lv["blocks"].shape[0]) for lv in res["levels"]])
-            rows["near_wall_cells"].append(near_wall_cells(res))
-        g.close()
+                res = step()
+                torch.cuda.synchronize()
+                g.timing(True)
+                g.timing_reset()
+                for k in range(reps):
+                    flush.fill_(k & 0xff)
+                    step()
+                torch.cuda.synchronize()
+                tk = g.timings()
+                g.timing(False)
+                t_bin = sum(tk[k][0] for k in ("bin_count", "bin_scan", "bin_scatter") if k in tk) / reps
+                t_det = sum(tk[k][0] for k in ("refine_level", "propagate") if k in tk) / reps
+                r["bin_ms"].append(round(t_bin, 4))
+                r["detect_ms"].append(round(t_det, 4))
+                r["blocks_per_level"].append([int(lv["blocks"].shape[0]) for lv in res["levels"]])
+                r["near_wall_cells"].append(near_wall_cells(res))
+            g.close()
+            rows[mode] = r
         out[name] = rows
     return out
 
