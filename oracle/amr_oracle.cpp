@@ -521,6 +521,69 @@ int orc_propagate(int dim, const int32_t* blocks, int64_t n, uint8_t* flags, int
   return 0;
 }
 
+// Node classification (the next step the paper names towards boundary
+// conditions: which nodes are fluid and which are solid).  A node is solid when
+// it lies inside the closed boundary mesh.  Inside is decided by the generalized
+// winding number w: the sum of the signed solid angles the faces subtend at the
+// node divided by 4 pi (2D: the signed angles of the segments divided by 2 pi),
+// which is +-1 inside a closed, consistently oriented mesh and 0 outside, so
+// solid iff |w| > 1/2 whatever the orientation.  Nodes within 1e-6 h of the
+// mesh are band cases (either class is accepted).
+double orc_winding_number(const orc_geom* g, const double* x) {
+  const int D = g->dim;
+  double w = 0.0;
+  for (int64_t f = 0; f < g->nf; ++f) {
+    const double* v = &g->X[(size_t)f * D * D];
+    if (D == 2) {
+      const double a[2] = {v[0] - x[0], v[1] - x[1]};
+      const double b[2] = {v[2] - x[0], v[3] - x[1]};
+      w += std::atan2(a[0] * b[1] - a[1] * b[0], a[0] * b[0] + a[1] * b[1]);
+      continue;
+    }
+    double a[3], b[3], c[3];
+    for (int k = 0; k < 3; ++k) {
+      a[k] = v[k] - x[k];
+      b[k] = v[3 + k] - x[k];
+      c[k] = v[6 + k] - x[k];
+    }
+    const double la = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double lb = std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    const double lc = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    const double det = a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+                       a[2] * (b[0] * c[1] - b[1] * c[0]);
+    const double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    const double ac = a[0] * c[0] + a[1] * c[1] + a[2] * c[2];
+    const double bc = b[0] * c[0] + b[1] * c[1] + b[2] * c[2];
+    w += 2.0 * std::atan2(det, la * lb * lc + ab * lc + ac * lb + bc * la);
+  }
+  const double pi = 3.14159265358979323846;
+  return D == 2 ? w / (2.0 * pi) : w / (4.0 * pi);
+}
+
+int orc_classify(const orc_geom* g, const orc_domain* dom, int level, const int32_t* cells, int64_t n,
+                 uint8_t* solid, uint8_t* band) {
+  if (!g || !dom || dom->dim != g->dim) return 1;
+  const int D = g->dim;
+  const double h = level_h(*dom, level);
+  for (int64_t i = 0; i < n; ++i) {
+    double x[3] = {0, 0, 0};
+    cell_centre(*dom, level, cells + i * D, x);
+    const double w = orc_winding_number(g, x);
+    if (solid) solid[i] = std::fabs(w) > 0.5 ? 1 : 0;
+    if (band) {
+      double dmin = kInf;
+      for (int64_t f = 0; f < g->nf; ++f) {
+        double loc[9];
+        for (int k = 0; k < D; ++k)
+          for (int c = 0; c < D; ++c) loc[k * D + c] = g->X[(size_t)f * D * D + k * D + c] - x[c];
+        dmin = std::min(dmin, point_face_dist(D, loc));
+      }
+      band[i] = dmin <= kBand * h ? 1 : 0;
+    }
+  }
+  return 0;
+}
+
 int64_t orc_bins_nnz(const orc_geom* g) { return (int64_t)g->ids.size(); }
 
 void orc_bins_copy(const orc_geom* g, uint32_t* offsets, uint32_t* ids) {

@@ -95,6 +95,13 @@ int orc_refine_blocks(const orc_geom* g, const orc_domain* dom, int level, doubl
                       const int32_t* blocks, int64_t n, uint64_t* mask, uint64_t* band,
                       int64_t* n_band_pairs, int64_t* n_candidates);
 
+/* Node classification: generalized winding number of the closed mesh at x
+ * (+-1 inside a closed, consistently oriented mesh, 0 outside), and per cell
+ * centre solid = |w| > 1/2, band = the centre lies within 1e-6*h_L of the mesh. */
+double orc_winding_number(const orc_geom* g, const double* x);
+int orc_classify(const orc_geom* g, const orc_domain* dom, int level, const int32_t* cells, int64_t n,
+                 uint8_t* solid, uint8_t* band);
+
 /* Children of the flagged blocks (mask != 0), canonical order.  child_* may be
  * NULL to only count. Returns the number of children. */
 int64_t orc_children(int dim, const int32_t* blocks, int64_t n, const uint64_t* mask,

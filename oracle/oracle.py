@@ -65,6 +65,10 @@ def _load():
             lib.orc_bins_build_sampled.argtypes = [P, P, C.c_int]
             lib.orc_face_samples.restype = i64
             lib.orc_face_samples.argtypes = [P, i64, C.c_double, P, i64]
+            lib.orc_winding_number.restype = C.c_double
+            lib.orc_winding_number.argtypes = [P, P]
+            lib.orc_classify.restype = C.c_int
+            lib.orc_classify.argtypes = [P, P, C.c_int, P, i64, P, P]
             lib.orc_propagate.restype = C.c_int
             lib.orc_propagate.argtypes = [C.c_int, P, i64, P, C.c_int]
             lib.orc_point_face_dist.restype = C.c_double
@@ -196,6 +200,24 @@ class OracleGeometry:
         if rc:
             raise ValueError("orc_refine_blocks failed")
         return mask[:n], band[:n], int(nbp.value), int(ncand.value)
+
+    def winding_number(self, x) -> float:
+        """Generalized winding number of the mesh at point x."""
+        p = np.zeros(3, np.float64)
+        xs = np.asarray(x, dtype=np.float64).reshape(-1)
+        p[:xs.size] = xs
+        return float(_load().orc_winding_number(self._h, _p(p)))
+
+    def classify(self, level: int, cells: np.ndarray, dom: "Domain" = None):
+        """Per cell centre: solid (inside the closed mesh) and band (within 1e-6 h of the mesh)."""
+        lib = _load()
+        cd = dom.c() if dom is not None else self._cdom
+        c = np.ascontiguousarray(cells, dtype=np.int32).reshape(-1, self.dim)
+        n = c.shape[0]
+        solid = np.zeros(max(n, 1), np.uint8)
+        band = np.zeros(max(n, 1), np.uint8)
+        lib.orc_classify(self._h, C.byref(cd), level, _p(c), n, _p(solid), _p(band))
+        return solid[:n].astype(bool), band[:n].astype(bool)
 
     def face_samples(self, f: int, spacing: float) -> np.ndarray:
         """The sample points of face f of the paper's sampled binning, [k][dim]."""
