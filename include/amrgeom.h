@@ -218,6 +218,25 @@ AMR_API amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* p
  * bitwise identical results.  ESTATE without links; EINVAL for host pointers. */
 AMR_API amr_status amr_q_backward(amr_ctx* ctx, const float* grad_q, float* grad_out);
 
+/* Node classification (not in the paper's method: the next step it names towards
+ * the LBM boundary conditions).  After amr_refine_near_wall with adjacency on an
+ * exactly binned single-geometry context: for every adjacent cell of the finest
+ * level (row i of adj_cell), *cell_solid[i] = 1 when its centre lies inside the
+ * closed boundary mesh, else 0 (fluid).  Decided by the parity of the faces a ray
+ * from the centre along +x crosses (each face once; FP32 box cull, FP64 crossing
+ * test); a ray through an edge or vertex, or a centre on a face, falls back to the
+ * generalized winding number of the whole mesh (|w| > 1/2 = solid), counted in
+ * *n_fallback (nullable).  The mesh must be closed (either orientation).
+ * cell_solid: BORROWED device u8 [n_adj_cells], valid until the next refinement.
+ * Errors: ESTATE (no refinement with adjacency, batch context), EINVAL (sampled bins). */
+AMR_API amr_status amr_classify_nodes(amr_ctx* ctx, const uint8_t** cell_solid, int64_t* n_fallback);
+
+/* Restricts the wall links of the last refinement to fluid cells (after
+ * amr_classify_nodes): a stable compaction of link_cell / link_dir / link_q /
+ * link_face in place; *out is the updated result (n_links and the same borrowed
+ * arrays).  The q adjoint then applies to the kept links.  Errors: ESTATE. */
+AMR_API amr_status amr_fluid_links(amr_ctx* ctx, amr_refine_result* out);
+
 /* Wait for all work of the context; report device-side check failures. */
 AMR_API amr_status amr_sync(amr_ctx* ctx);
 

@@ -29,8 +29,9 @@ STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECUDA", 4
                 5: "AMR_ETIMEOUT", 6: "AMR_ESTATE", 7: "AMR_EDEVICE_CHECK"}
 
 EXPORTED = ["amr_create", "amr_destroy", "amr_status_str", "amr_last_error", "amr_set_stream", "amr_geom_load",
-            "amr_bin_faces", "amr_bin_faces_sampled", "amr_refine_near_wall", "amr_sync", "amr_timing_enable", "amr_timing_reset",
-            "amr_timing_get", "amr_launch_count", "amr_bin_faces_static", "amr_q_backward", "amr_autotune",
+            "amr_bin_faces", "amr_bin_faces_sampled", "amr_refine_near_wall", "amr_sync", "amr_timing_enable",
+            "amr_timing_reset", "amr_timing_get", "amr_launch_count", "amr_bin_faces_static", "amr_q_backward",
+            "amr_classify_nodes", "amr_fluid_links", "amr_autotune",
             "amr_batch_create", "amr_batch_destroy", "amr_batch_add", "amr_batch_set_bins", "amr_batch_run",
             "amr_batch_get_view", "amr_batch_q_backward", "amr_batch_last_error", "amr_batch_launch_count"]
 
@@ -126,6 +127,10 @@ def lib(build_if_missing: bool = True):
         L.amr_launch_count.argtypes = [P]
         L.amr_q_backward.restype = C.c_int
         L.amr_q_backward.argtypes = [P, P, P]
+        L.amr_classify_nodes.restype = C.c_int
+        L.amr_classify_nodes.argtypes = [P, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]
+        L.amr_fluid_links.restype = C.c_int
+        L.amr_fluid_links.argtypes = [P, C.POINTER(amr_refine_result)]
         L.amr_autotune.restype = C.c_int
         L.amr_autotune.argtypes = [P, C.POINTER(amr_refine_params), P, C.c_int, P, C.c_int, C.POINTER(C.c_int),
                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -345,6 +350,7 @@ class AmrGeom:
         self.ctx = amr_create(dim, self.root, origin, h0, handle)
         self._keep = []
         self.bins = None
+        self.last_result = None
         self.result = None
 
     def close(self):
@@ -396,6 +402,7 @@ class AmrGeom:
             want_links = lattice != 0
         r = amr_refine_near_wall(self.ctx, n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph,
                                  warps_per_cta, predicate, search, propagate)
+        self.last_result = r
         return self._wrap(r, want_adjacency, want_links)
 
     def _wrap(self, r, want_adjacency, want_links):
@@ -427,6 +434,25 @@ class AmrGeom:
             out["link_face"] = _u32(r.link_face, nl)
         self.result = out
         return out
+
+    def classify(self):
+        """Node classes of the last refine's adjacent cells (row order of adj_cell): a borrowed uint8
+        CUDA tensor, 1 = solid (inside the closed mesh), 0 = fluid; and the number of cells decided by
+        the winding-number fallback."""
+        import torch
+
+        ptr = C.c_void_p()
+        nfb = C.c_int64()
+        _check(self.ctx, lib().amr_classify_nodes(self.ctx, C.byref(ptr), C.byref(nfb)))
+        n = int(self.last_result.n_adj_cells) if self.last_result is not None else 0
+        return _view(ptr.value, (n,), torch.uint8), int(nfb.value)
+
+    def fluid_links(self):
+        """Keep only the links of fluid cells (after classify); returns the updated link tensors."""
+        r = amr_refine_result()
+        _check(self.ctx, lib().amr_fluid_links(self.ctx, C.byref(r)))
+        self.last_result = r
+        return self._wrap(r, True, True)
 
     def q_backward(self, grad_q):
         """d(loss)/d(load input) from d(loss)/d(link_q) of the last refine (shape of the load input)."""

@@ -95,12 +95,13 @@ struct amr_ctx {
   bool multi = false;
   DevBuf table, face_gid;
   // buffers
-  DevBuf X, nrm, frec, recs, hkeys, hvals, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
+  DevBuf X, nrm, frec, recs, hkeys, hvals, cls, flbase, tl_cell, tl_dir, tl_q, tl_face, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
   LevelBufs lv[AMR_MAX_LEVELS];
   DevBuf adj_cell, adj_off, adj_ids, link_cell, link_dir, link_q, link_face;
   int64_t cap_cells = 0, cap_pairs = 0, cap_links = 0;
   int64_t cap_recs = 0, want_recs = 0;  // survivor record staging (entries)
   bool sampled_bins = false;             // the last binning used the paper's sampled membership
+  bool classified = false;               // cls holds the classes of the last refinement's adjacent cells
   // adjoint
   DevBuf idx, vert_off, vert_corners, face_off, face_links, sort_keys, grad_face, sort_scratch, group_cnt, lvl_ptrs;
   bool vert_groups = false, face_groups = false;
@@ -385,7 +386,8 @@ amr_status amr_ctx_init(amr_ctx* ctx) {
 void amr_ctx_free(amr_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   drop_graph(ctx);
-  DevBuf* all[] = {&ctx->X, &ctx->frec, &ctx->recs, &ctx->hkeys, &ctx->hvals, &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
+  DevBuf* all[] = {&ctx->X, &ctx->frec, &ctx->recs, &ctx->hkeys, &ctx->hvals, &ctx->cls, &ctx->flbase,
+                   &ctx->tl_cell, &ctx->tl_dir, &ctx->tl_q, &ctx->tl_face, &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
                    &ctx->count,     &ctx->offsets,      &ctx->ids,        &ctx->payload,    &ctx->scratch,
                    &ctx->misc,      &ctx->scal,         &ctx->adj_cell,   &ctx->adj_off,    &ctx->adj_ids,
                    &ctx->link_cell, &ctx->link_dir,     &ctx->link_q,     &ctx->link_face,  &ctx->idx,
@@ -1083,6 +1085,7 @@ amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_
   for (int a = 0; a < D; ++a) N0 *= ctx->dom.root_blocks[a];
   if (N0 > (1ll << 31)) return fail(ctx, AMR_EINVAL, "too many root blocks");
   ctx->refined = false;
+  ctx->classified = false;
   ctx->face_groups = false;
   ctx->n_links = 0;
   GeomParams& g = ctx->geoms[0];
@@ -1197,6 +1200,96 @@ amr_status amr_q_backward(amr_ctx* ctx, const float* grad_q, float* grad_out) {
   if ((nl > 0 && !is_device_ptr(grad_q)) || !is_device_ptr(grad_out))
     return fail(ctx, AMR_EINVAL, "gradients must be device pointers");
   return amr_backward(ctx, grad_q, grad_out);
+}
+
+amr_status amr_classify_nodes(amr_ctx* ctx, const uint8_t** cell_solid, int64_t* n_fallback) {
+  if (!ctx || !cell_solid) return AMR_EINVAL;
+  if (ctx->multi) return fail(ctx, AMR_ESTATE, "node classification on a batch context");
+  if (!ctx->refined || !ctx->last.adj_cell)
+    return fail(ctx, AMR_ESTATE, "amr_classify_nodes needs a preceding refinement with adjacency");
+  if (ctx->sampled_bins) return fail(ctx, AMR_EINVAL, "node classification needs exact bins");
+  const amr_refine_result& r = ctx->last;
+  const int64_t n = r.n_adj_cells;
+  cudaStream_t st = ctx->stream;
+  TRY(ensure(ctx, ctx->cls, (size_t)(n > 0 ? n : 1)));
+  CK(cudaMemsetAsync(ctx->counters + CNT_CLASS_FALLBACK, 0, sizeof(unsigned long long), st));
+  ClassifyArgs a{};
+  a.dim = ctx->dom.dim;
+  a.level = r.n_levels - 1;
+  a.g0 = ctx->geoms[0];
+  a.blocks = r.block_coords[r.n_levels - 1];
+  a.adj_cell = r.adj_cell;
+  a.row0 = 0;
+  a.n_rows = n;
+  a.offsets = static_cast<const uint32_t*>(ctx->offsets.p);
+  a.payload = ctx->payload.p;
+  a.X = static_cast<const float*>(ctx->X.p);
+  a.nf = ctx->nf;
+  a.cls = static_cast<uint8_t*>(ctx->cls.p);
+  a.counters = ctx->counters;
+  a.err = ctx->d_err;
+  timed(ctx, st, "classify", [&] { return launch_classify(a, st); });
+  CK(cudaGetLastError());
+  char* h = static_cast<char*>(ctx->h_pinned);
+  CK(cudaMemcpyAsync(h, ctx->counters + CNT_CLASS_FALLBACK, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TRY(sync_check(ctx, st));
+  TRY(device_error(ctx, *reinterpret_cast<unsigned*>(h + 64)));
+  if (n_fallback) *n_fallback = (int64_t)*reinterpret_cast<unsigned long long*>(h);
+  ctx->classified = true;
+  *cell_solid = static_cast<const uint8_t*>(ctx->cls.p);
+  return AMR_OK;
+}
+
+amr_status amr_fluid_links(amr_ctx* ctx, amr_refine_result* out) {
+  if (!ctx || !out) return AMR_EINVAL;
+  if (!ctx->refined || !ctx->classified || ctx->n_links < 0)
+    return fail(ctx, AMR_ESTATE, "amr_fluid_links needs links and a preceding amr_classify_nodes");
+  const int64_t n = ctx->n_links;
+  cudaStream_t st = ctx->stream;
+  if (n > 0) {
+    const int64_t nb = fluid_blocks(n);
+    TRY(ensure(ctx, ctx->group_cnt, sizeof(uint32_t) * (size_t)(nb + 1)));
+    TRY(ensure(ctx, ctx->flbase, sizeof(uint32_t) * (size_t)(nb + 1)));
+    TRY(ensure(ctx, ctx->scratch, scan_u32_scratch_bytes(nb)));
+    TRY(ensure(ctx, ctx->tl_cell, sizeof(uint32_t) * (size_t)n));
+    TRY(ensure(ctx, ctx->tl_dir, (size_t)n));
+    TRY(ensure(ctx, ctx->tl_q, sizeof(float) * (size_t)n));
+    TRY(ensure(ctx, ctx->tl_face, sizeof(uint32_t) * (size_t)n));
+    const uint8_t* cls = static_cast<const uint8_t*>(ctx->cls.p);
+    auto* lc = static_cast<uint32_t*>(ctx->link_cell.p);
+    auto* ld = static_cast<uint8_t*>(ctx->link_dir.p);
+    auto* lq = static_cast<float*>(ctx->link_q.p);
+    auto* lf = static_cast<uint32_t*>(ctx->link_face.p);
+    timed(ctx, st, "fluid_links", [&] {
+      int k = launch_fluid_count(lc, cls, n, static_cast<uint32_t*>(ctx->group_cnt.p), st);
+      k += launch_scan_u32(static_cast<const uint32_t*>(ctx->group_cnt.p), static_cast<uint32_t*>(ctx->flbase.p), nb,
+                           ctx->d_tot, ctx->scratch.p, ctx->d_err, st);
+      k += launch_fluid_move(lc, ld, lq, lf, cls, n, static_cast<const uint32_t*>(ctx->flbase.p),
+                             static_cast<uint32_t*>(ctx->tl_cell.p), static_cast<uint8_t*>(ctx->tl_dir.p),
+                             static_cast<float*>(ctx->tl_q.p), static_cast<uint32_t*>(ctx->tl_face.p), st);
+      return k;
+    });
+    uint64_t kept = 0;
+    unsigned e = 0;
+    char* h = static_cast<char*>(ctx->h_pinned);
+    CK(cudaMemcpyAsync(h + 128, ctx->d_tot, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    TRY(sync_check(ctx, st));
+    kept = *reinterpret_cast<uint64_t*>(h + 128);
+    e = *reinterpret_cast<unsigned*>(h + 64);
+    TRY(device_error(ctx, e));
+    // back into the context's link arrays (graph replays keep writing there)
+    CK(cudaMemcpyAsync(lc, ctx->tl_cell.p, sizeof(uint32_t) * kept, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ld, ctx->tl_dir.p, kept, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(lq, ctx->tl_q.p, sizeof(float) * kept, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(lf, ctx->tl_face.p, sizeof(uint32_t) * kept, cudaMemcpyDeviceToDevice, st));
+    ctx->n_links = (int64_t)kept;
+  }
+  ctx->face_groups = false;
+  ctx->last.n_links = ctx->n_links;
+  *out = ctx->last;
+  return AMR_OK;
 }
 
 amr_status amr_timing_enable(amr_ctx* ctx, int on) {

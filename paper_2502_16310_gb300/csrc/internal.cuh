@@ -32,6 +32,7 @@ enum : int {
   CNT_LINK_FALLBACK = 4,
   CNT_LINK_BAND = 5,
   CNT_LINK_CAND = 6,
+  CNT_CLASS_FALLBACK = 7,
   CNT_N = 8,
 };
 
@@ -446,6 +447,31 @@ struct ChildrenArgs {
   unsigned* err;
 };
 size_t children_scratch_bytes(int64_t n);
+
+// Node classification of the finest adjacent cells (rows [row0, row0 + n_rows) of
+// the adjacency CSR): cls[row] = 1 solid (inside the closed mesh), 0 fluid.
+struct ClassifyArgs {
+  int dim;
+  int level;
+  GeomParams g0;
+  const int32_t* blocks;       // the finest level's blocks
+  const uint32_t* adj_cell;
+  int64_t row0, n_rows;
+  const uint32_t* offsets;     // exact bins
+  const void* payload;
+  const float* X;              // faces (SoA), for the winding-number fallback
+  int64_t nf;
+  uint8_t* cls;
+  unsigned long long* counters;
+  unsigned* err;
+};
+int launch_classify(const ClassifyArgs& a, cudaStream_t st);
+// Stable compaction of the link arrays to the links of fluid cells.
+int64_t fluid_blocks(int64_t n);
+int launch_fluid_count(const uint32_t* link_cell, const uint8_t* cls, int64_t n, uint32_t* cnt, cudaStream_t st);
+int launch_fluid_move(const uint32_t* link_cell, const uint8_t* link_dir, const float* link_q,
+                      const uint32_t* link_face, const uint8_t* cls, int64_t n, const uint32_t* base,
+                      uint32_t* o_cell, uint8_t* o_dir, float* o_q, uint32_t* o_face, cudaStream_t st);
 
 // Mark propagation over one level (flags 0/1 in place): `rounds` two-phase rounds
 // through a hash of the block coordinates (keys/vals: `slots` entries, a power of
