@@ -252,12 +252,45 @@ def run_ours(args, rank, world, local):
     }
     if not args.no_e2e:
         line["e2e"] = run_e2e(g, w, args, dev)
+    if not args.no_extras and world == 1:
+        line["classify"] = run_classify(g, w, verts, idx, flush)
     g.close()
     if not args.no_extras and world == 1:
         line["adjoint"] = run_adjoint(args, dev, flush)
         line["batched"] = run_batched(args, dev, flush)
         line["paper_setups"] = run_paper_setups(args, dev, flush)
     return line
+
+
+def run_classify(g, w, verts, idx, flush, reps=5):
+    """Node classification of the finest adjacent cells (fluid / solid) and the restriction of the
+    links to fluid cells, on the bench workload: CUDA-event times on the context stream."""
+    import torch
+
+    g.load(verts, idx)
+    g.bin(w.bins)
+    res = g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True)
+    n_links = int(res["link_q"].shape[0])
+    st = g.stream
+    ms = []
+    for k in range(reps):
+        flush.fill_(k & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        cls, nfb = g.classify()
+        b.record(st)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    solid = float(cls.float().mean().item()) if cls.numel() else 0.0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    out = g.fluid_links()
+    b.record(st)
+    torch.cuda.synchronize()
+    return {"cells": int(cls.numel()), "classify_ms": sum(ms) / len(ms), "solid_fraction": solid,
+            "winding_fallbacks": nfb, "links": n_links, "fluid_links": int(out["link_q"].shape[0]),
+            "fluid_links_ms": a.elapsed_time(b),
+            "note": "classify/fluid_links times include their host round trip (one read-back each)"}
 
 
 def _timed_steps(fn, n, flush, stream):
