@@ -259,6 +259,7 @@ def run_ours(args, rank, world, local):
         line["adjoint"] = run_adjoint(args, dev, flush)
         line["batched"] = run_batched(args, dev, flush)
         line["paper_setups"] = run_paper_setups(args, dev, flush)
+        line["moving"] = run_moving(args, dev, flush)
     return line
 
 
@@ -291,6 +292,49 @@ def run_classify(g, w, verts, idx, flush, reps=5):
             "winding_fallbacks": nfb, "links": n_links, "fluid_links": int(out["link_q"].shape[0]),
             "fluid_links_ms": a.elapsed_time(b),
             "note": "classify/fluid_links times include their host round trip (one read-back each)"}
+
+
+def run_moving(args, dev, flush, steps=10):
+    """Re-adaptation of a moving wall: the c2 sphere translated by a quarter of the finest cell per step;
+    each step is load (new vertices) + bin + refine (graph replay, the previous hierarchy kept) + the
+    new/old block maps.  CUDA-event time per step and the blocks created / removed on the finest level."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+    from synth import workload
+
+    w = workload("c2")
+    g = AmrGeom(3, (w.root,) * 3)
+    idx = torch.from_numpy(w.idx).to(dev)
+    h_fin = 1.0 / (4 * w.root * 2 ** (w.n_levels - 1))
+    base = torch.from_numpy(w.verts).to(dev)
+    delta = torch.tensor([0.25 * h_fin, 0.1 * h_fin, 0.05 * h_fin], device=dev)
+    st = g.stream
+
+    def step(k):
+        g.load(base + k * delta, idx)
+        g.bin(w.bins)
+        g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=True, keep_previous=True)
+        return g.adapt_diff()
+
+    for k in range(3):
+        step(k)
+    ms, created, removed = [], [], []
+    for k in range(3, 3 + steps):
+        flush.fill_(k & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        d = step(k)
+        b.record(st)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        created.append(d[-1]["created"])
+        removed.append(d[-1]["removed"])
+    g.close()
+    return {"workload": "c2 sphere moving 0.25 h_fin per step", "ms_per_step": sum(ms) / len(ms),
+            "finest_created_per_step": sum(created) / len(created),
+            "finest_removed_per_step": sum(removed) / len(removed),
+            "note": "includes the host read-back of the refine sizes and of the map counts"}
 
 
 def _timed_steps(fn, n, flush, stream):

@@ -160,6 +160,8 @@ typedef struct {
                                  (Sec. "Spatial Binning Algorithm"): 0 none, -1 the paper's
                                  1 + floor(d_L / block length), k > 0 exactly k; each round marks the existing
                                  neighbour blocks (3^D - 1) of every marked block; single-geometry only */
+  int keep_previous;          /* 1: keep the previous call's block lists for amr_adapt_diff (re-adaptation of
+                                 a moving or changing geometry); single-geometry only */
 } amr_refine_params;
 enum { AMR_PRED_BOX = 0, AMR_PRED_POINT = 1 };
 enum { AMR_SEARCH_QUERY_BOX = 0, AMR_SEARCH_OWN_BIN = 1 };
@@ -236,6 +238,25 @@ AMR_API amr_status amr_classify_nodes(amr_ctx* ctx, const uint8_t** cell_solid, 
  * link_face in place; *out is the updated result (n_links and the same borrowed
  * arrays).  The q adjoint then applies to the kept links.  Errors: ESTATE. */
 AMR_API amr_status amr_fluid_links(amr_ctx* ctx, amr_refine_result* out);
+
+/* Re-adaptation bookkeeping (not in the paper's method: its dynamic re-adaptation
+ * and coarsening are future work).  After two successive amr_refine_near_wall
+ * calls on one context, the second with keep_previous = 1, per level L:
+ *   new_to_old[L][i] = index of the new block i in the previous call's level-L
+ *                      list, -1 when it did not exist (a block created by refinement);
+ *   old_to_new[L][j] = index of the previous block j in the new list, -1 when it
+ *                      is gone (a block removed by coarsening);
+ * with the counts.  Levels beyond either hierarchy's depth map to -1.  All
+ * device arrays are BORROWED until the next refinement.  Errors: ESTATE (no
+ * kept previous hierarchy). */
+typedef struct {
+  int n_levels;                            /* levels of the new hierarchy */
+  int64_t n_new[AMR_MAX_LEVELS], n_old[AMR_MAX_LEVELS];
+  int64_t n_created[AMR_MAX_LEVELS], n_removed[AMR_MAX_LEVELS];
+  const int32_t* new_to_old[AMR_MAX_LEVELS];  /* device [n_new[L]] */
+  const int32_t* old_to_new[AMR_MAX_LEVELS];  /* device [n_old[L]] */
+} amr_adapt_diff;
+AMR_API amr_status amr_adapt_diff_get(amr_ctx* ctx, amr_adapt_diff* out);
 
 /* Wait for all work of the context; report device-side check failures. */
 AMR_API amr_status amr_sync(amr_ctx* ctx);

@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECUDA", 4
 EXPORTED = ["amr_create", "amr_destroy", "amr_status_str", "amr_last_error", "amr_set_stream", "amr_geom_load",
             "amr_bin_faces", "amr_bin_faces_sampled", "amr_refine_near_wall", "amr_sync", "amr_timing_enable",
             "amr_timing_reset", "amr_timing_get", "amr_launch_count", "amr_bin_faces_static", "amr_q_backward",
-            "amr_classify_nodes", "amr_fluid_links", "amr_autotune",
+            "amr_classify_nodes", "amr_fluid_links", "amr_adapt_diff_get", "amr_autotune",
             "amr_batch_create", "amr_batch_destroy", "amr_batch_add", "amr_batch_set_bins", "amr_batch_run",
             "amr_batch_get_view", "amr_batch_q_backward", "amr_batch_last_error", "amr_batch_launch_count"]
 
@@ -55,7 +55,14 @@ class amr_bins_view(C.Structure):
 class amr_refine_params(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("d_abs", C.c_double), ("d_rel", C.c_double), ("lattice", C.c_int),
                 ("want_adjacency", C.c_int), ("want_links", C.c_int), ("use_graph", C.c_int),
-                ("warps_per_cta", C.c_int), ("predicate", C.c_int), ("search", C.c_int), ("propagate", C.c_int)]
+                ("warps_per_cta", C.c_int), ("predicate", C.c_int), ("search", C.c_int), ("propagate", C.c_int),
+                ("keep_previous", C.c_int)]
+
+
+class amr_adapt_diff(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("n_new", C.c_int64 * MAX_LEVELS), ("n_old", C.c_int64 * MAX_LEVELS),
+                ("n_created", C.c_int64 * MAX_LEVELS), ("n_removed", C.c_int64 * MAX_LEVELS),
+                ("new_to_old", C.c_void_p * MAX_LEVELS), ("old_to_new", C.c_void_p * MAX_LEVELS)]
 
 
 AMR_PRED_BOX, AMR_PRED_POINT = 0, 1
@@ -131,6 +138,8 @@ def lib(build_if_missing: bool = True):
         L.amr_classify_nodes.argtypes = [P, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]
         L.amr_fluid_links.restype = C.c_int
         L.amr_fluid_links.argtypes = [P, C.POINTER(amr_refine_result)]
+        L.amr_adapt_diff_get.restype = C.c_int
+        L.amr_adapt_diff_get.argtypes = [P, C.POINTER(amr_adapt_diff)]
         L.amr_autotune.restype = C.c_int
         L.amr_autotune.argtypes = [P, C.POINTER(amr_refine_params), P, C.c_int, P, C.c_int, C.POINTER(C.c_int),
                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -211,9 +220,9 @@ def amr_bin_faces_sampled(ctx, bin_density: int) -> amr_bins_view:
 
 def amr_refine_near_wall(ctx, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True,
                          want_links=True, use_graph=False, warps_per_cta=0, predicate=AMR_PRED_BOX,
-                         search=AMR_SEARCH_QUERY_BOX, propagate=0) -> amr_refine_result:
+                         search=AMR_SEARCH_QUERY_BOX, propagate=0, keep_previous=False) -> amr_refine_result:
     p = _params(n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph, warps_per_cta, predicate,
-                search, propagate)
+                search, propagate, keep_previous)
     r = amr_refine_result()
     _check(ctx, lib().amr_refine_near_wall(ctx, C.byref(p), C.byref(r)))
     return r
@@ -228,12 +237,13 @@ def amr_sync(ctx):
 
 
 def _params(n_levels=1, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=True, use_graph=False,
-            warps_per_cta=0, predicate=AMR_PRED_BOX, search=AMR_SEARCH_QUERY_BOX, propagate=0):
+            warps_per_cta=0, predicate=AMR_PRED_BOX, search=AMR_SEARCH_QUERY_BOX, propagate=0, keep_previous=False):
     p = amr_refine_params()
     p.n_levels, p.d_abs, p.d_rel, p.lattice = int(n_levels), float(d_abs), float(d_rel), int(lattice)
     p.want_adjacency, p.want_links = int(bool(want_adjacency)), int(bool(want_links))
     p.use_graph, p.warps_per_cta = int(bool(use_graph)), int(warps_per_cta)
     p.predicate, p.search, p.propagate = int(predicate), int(search), int(propagate)
+    p.keep_previous = int(bool(keep_previous))
     return p
 
 
@@ -393,7 +403,8 @@ class AmrGeom:
         return self.bins
 
     def refine(self, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=None,
-               use_graph=False, warps_per_cta=0, predicate=AMR_PRED_BOX, search=AMR_SEARCH_QUERY_BOX, propagate=0):
+               use_graph=False, warps_per_cta=0, predicate=AMR_PRED_BOX, search=AMR_SEARCH_QUERY_BOX, propagate=0,
+               keep_previous=False):
         """Step 3: near-wall refinement; returns per-level tensors, adjacency CSR and links (borrowed).
         predicate: AMR_PRED_BOX (inflated cell box meets the face) or AMR_PRED_POINT (cell centre within
         d of the face, the paper's Alg. 1); search / propagate: the paper's binned search (own bin only)
@@ -401,7 +412,7 @@ class AmrGeom:
         if want_links is None:
             want_links = lattice != 0
         r = amr_refine_near_wall(self.ctx, n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph,
-                                 warps_per_cta, predicate, search, propagate)
+                                 warps_per_cta, predicate, search, propagate, keep_previous)
         self.last_result = r
         return self._wrap(r, want_adjacency, want_links)
 
@@ -446,6 +457,21 @@ class AmrGeom:
         _check(self.ctx, lib().amr_classify_nodes(self.ctx, C.byref(ptr), C.byref(nfb)))
         n = int(self.last_result.n_adj_cells) if self.last_result is not None else 0
         return _view(ptr.value, (n,), torch.uint8), int(nfb.value)
+
+    def adapt_diff(self):
+        """Per level (after a refine with keep_previous): new_to_old / old_to_new index maps (borrowed int32
+        CUDA tensors, -1 = created / removed) and the counts."""
+        import torch
+
+        d = amr_adapt_diff()
+        _check(self.ctx, lib().amr_adapt_diff_get(self.ctx, C.byref(d)))
+        out = []
+        for L in range(max(d.n_levels, 0)):
+            nn, no = int(d.n_new[L]), int(d.n_old[L])
+            out.append({"new_to_old": _view(d.new_to_old[L], (nn,), torch.int32),
+                        "old_to_new": _view(d.old_to_new[L], (no,), torch.int32),
+                        "created": int(d.n_created[L]), "removed": int(d.n_removed[L])})
+        return out
 
     def fluid_links(self):
         """Keep only the links of fluid cells (after classify); returns the updated link tensors."""

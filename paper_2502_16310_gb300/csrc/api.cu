@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "amrgeom.h"
@@ -46,6 +47,8 @@ struct TimingSlot {
 
 struct LevelBufs {
   DevBuf blocks, gid, parent, mask, flag, cellcnt, blockcnt, base, desc;
+  DevBuf prev, n2o, o2n;  // previous call's blocks (kept on request) and the re-adaptation maps
+  int64_t n_prev = 0;
   int64_t cap = 0;  // capacity in blocks
 };
 
@@ -102,6 +105,7 @@ struct amr_ctx {
   int64_t cap_recs = 0, want_recs = 0;  // survivor record staging (entries)
   bool sampled_bins = false;             // the last binning used the paper's sampled membership
   bool classified = false;               // cls holds the classes of the last refinement's adjacent cells
+  int prev_levels = -1;                  // levels of the kept previous hierarchy (-1: none kept)
   // adjoint
   DevBuf idx, vert_off, vert_corners, face_off, face_links, sort_keys, grad_face, sort_scratch, group_cnt, lvl_ptrs;
   bool vert_groups = false, face_groups = false;
@@ -1084,10 +1088,28 @@ amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_
   int64_t N0 = 1;
   for (int a = 0; a < D; ++a) N0 *= ctx->dom.root_blocks[a];
   if (N0 > (1ll << 31)) return fail(ctx, AMR_EINVAL, "too many root blocks");
+  // keep the previous hierarchy's block lists for amr_adapt_diff_get
+  ctx->prev_levels = -1;
+  if (prm->keep_previous) {
+    // the block lists of the last successful refinement are still in the level buffers
+    // (loading and binning do not touch them)
+    const int pl = ctx->last.n_levels;
+    for (int L = 0; L < pl; ++L) {
+      const int64_t n = ctx->last.n_blocks[L];
+      LevelBufs& lb = ctx->lv[L];
+      TRY(ensure(ctx, lb.prev, sizeof(int32_t) * D * (size_t)(n > 0 ? n : 1)));
+      if (n > 0)
+        CK(cudaMemcpyAsync(lb.prev.p, lb.blocks.p, sizeof(int32_t) * D * (size_t)n, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+      lb.n_prev = n;
+    }
+    ctx->prev_levels = pl;
+  }
   ctx->refined = false;
   ctx->classified = false;
   ctx->face_groups = false;
   ctx->n_links = 0;
+  ctx->last.n_levels = 0;  // until this refinement succeeds
   GeomParams& g = ctx->geoms[0];
   g.n_levels = NL;
   g.d_abs = prm->d_abs;
@@ -1289,6 +1311,68 @@ amr_status amr_fluid_links(amr_ctx* ctx, amr_refine_result* out) {
   ctx->face_groups = false;
   ctx->last.n_links = ctx->n_links;
   *out = ctx->last;
+  return AMR_OK;
+}
+
+amr_status amr_adapt_diff_get(amr_ctx* ctx, amr_adapt_diff* out) {
+  if (!ctx || !out) return AMR_EINVAL;
+  if (ctx->multi) return fail(ctx, AMR_ESTATE, "re-adaptation maps on a batch context");
+  if (!ctx->refined || ctx->prev_levels < 0)
+    return fail(ctx, AMR_ESTATE, "amr_adapt_diff_get needs a refinement with keep_previous after another");
+  const int D = ctx->dom.dim;
+  const amr_refine_result& r = ctx->last;
+  cudaStream_t st = ctx->stream;
+  amr_adapt_diff d{};
+  d.n_levels = r.n_levels;
+  int64_t cap = 1;
+  for (int L = 0; L < AMR_MAX_LEVELS; ++L) {
+    const int64_t nn = L < r.n_levels ? r.n_blocks[L] : 0, no = L < ctx->prev_levels ? ctx->lv[L].n_prev : 0;
+    cap = std::max(cap, std::max(nn, no));
+  }
+  const uint32_t slots = propagate_hash_slots(cap);
+  TRY(ensure(ctx, ctx->hkeys, sizeof(unsigned long long) * slots));
+  TRY(ensure(ctx, ctx->hvals, sizeof(uint32_t) * slots));
+  unsigned long long* cnt = ctx->counters;  // [0 .. 2 * levels) as scratch for the missing counts
+  const int nl = std::max(r.n_levels, ctx->prev_levels);
+  if (2 * nl > CNT_N) {
+    TRY(ensure(ctx, ctx->group_cnt, sizeof(unsigned long long) * 2 * (size_t)nl));
+    cnt = static_cast<unsigned long long*>(ctx->group_cnt.p);
+  }
+  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 2 * (size_t)nl, st));
+  for (int L = 0; L < nl; ++L) {
+    LevelBufs& lb = ctx->lv[L];
+    const int64_t nn = L < r.n_levels ? r.n_blocks[L] : 0;
+    const int64_t no = L < ctx->prev_levels ? lb.n_prev : 0;
+    TRY(ensure(ctx, lb.n2o, sizeof(int32_t) * (size_t)(nn > 0 ? nn : 1)));
+    TRY(ensure(ctx, lb.o2n, sizeof(int32_t) * (size_t)(no > 0 ? no : 1)));
+    const int32_t* nb = static_cast<const int32_t*>(lb.blocks.p);
+    const int32_t* ob = static_cast<const int32_t*>(lb.prev.p);
+    timed(ctx, st, "adapt_diff", [&] {
+      int k = launch_block_map(D, ob, no, nb, nn, static_cast<int32_t*>(lb.n2o.p), cnt + 2 * L,
+                               static_cast<unsigned long long*>(ctx->hkeys.p), static_cast<uint32_t*>(ctx->hvals.p),
+                               slots, ctx->d_err, st);
+      k += launch_block_map(D, nb, nn, ob, no, static_cast<int32_t*>(lb.o2n.p), cnt + 2 * L + 1,
+                            static_cast<unsigned long long*>(ctx->hkeys.p), static_cast<uint32_t*>(ctx->hvals.p),
+                            slots, ctx->d_err, st);
+      return k;
+    });
+    d.n_new[L] = nn;
+    d.n_old[L] = no;
+    d.new_to_old[L] = static_cast<const int32_t*>(lb.n2o.p);
+    d.old_to_new[L] = static_cast<const int32_t*>(lb.o2n.p);
+  }
+  CK(cudaGetLastError());
+  std::vector<unsigned long long> h(2 * (size_t)nl);
+  CK(cudaMemcpyAsync(h.data(), cnt, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost, st));
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TRY(sync_check(ctx, st));
+  TRY(device_error(ctx, e));
+  for (int L = 0; L < nl; ++L) {
+    d.n_created[L] = (int64_t)h[2 * L];
+    d.n_removed[L] = (int64_t)h[2 * L + 1];
+  }
+  *out = d;
   return AMR_OK;
 }
 

@@ -480,6 +480,11 @@ uint32_t propagate_hash_slots(int64_t cap);
 int launch_propagate(int dim, const int32_t* blocks, int64_t cap, const uint64_t* n_dev, uint8_t* flags,
                      int rounds, unsigned long long* keys, uint32_t* vals, uint32_t slots, unsigned* err,
                      cudaStream_t st);
+// out[i] = index of query block i in the reference list, -1 if absent; *n_missing += the absent
+// count (hash of `slots` >= 2 x max(n_ref) entries).
+int launch_block_map(int dim, const int32_t* ref, int64_t n_ref, const int32_t* query, int64_t n_query,
+                     int32_t* out, unsigned long long* n_missing, unsigned long long* keys, uint32_t* vals,
+                     uint32_t slots, unsigned* err, cudaStream_t st);
 int launch_children(const ChildrenArgs& a, void* scratch, int num_sms, cudaStream_t st);
 // Level-0 blocks of every geometry of the table (x fastest within each), with their geometry ids.
 int launch_root_blocks(int dim, const int* root, int32_t* blocks, int64_t n, cudaStream_t st);

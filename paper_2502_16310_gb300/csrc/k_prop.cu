@@ -127,3 +127,44 @@ int launch_propagate(int dim, const int32_t* blocks, int64_t cap, const uint64_t
 }
 
 }  // namespace amr
+
+// ---------------------------------------------------------------------------
+// Re-adaptation bookkeeping (moving geometry): between two successive
+// hierarchies, per level, the index of every block of one list in the other
+// list (-1: none).  new -> old = -1 marks a block created by refinement; old ->
+// new = -1 a block removed by coarsening.  The same coordinate hash as above.
+// ---------------------------------------------------------------------------
+namespace amr {
+
+namespace {
+
+__global__ void k_map_lookup(int dim, const int32_t* __restrict__ query, int64_t n, const unsigned long long* keys,
+                             const uint32_t* vals, uint32_t hmask, int32_t* out, unsigned long long* n_missing) {
+  unsigned long long miss = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = hash_find(keys, vals, hmask, block_key(query + i * dim, dim));
+    out[i] = (int32_t)j;
+    miss += j < 0 ? 1ull : 0ull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) miss += __shfl_xor_sync(0xffffffffu, miss, o);
+  if ((threadIdx.x & 31) == 0 && miss) atomicAdd(n_missing, miss);
+}
+
+}  // namespace
+
+int launch_block_map(int dim, const int32_t* ref, int64_t n_ref, const int32_t* query, int64_t n_query,
+                     int32_t* out, unsigned long long* n_missing, unsigned long long* keys, uint32_t* vals,
+                     uint32_t slots, unsigned* err, cudaStream_t st) {
+  if (n_query <= 0) return 0;
+  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * slots, st);
+  int k = 0;
+  if (n_ref > 0) {
+    k_hash_insert<<<grid_of(n_ref), kPThreads, 0, st>>>(dim, ref, n_ref, nullptr, keys, vals, slots - 1, err);
+    ++k;
+  }
+  k_map_lookup<<<grid_of(n_query), kPThreads, 0, st>>>(dim, query, n_query, keys, vals, slots - 1, out, n_missing);
+  return k + 1;
+}
+
+}  // namespace amr

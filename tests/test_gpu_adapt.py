@@ -1,0 +1,84 @@
+"""Re-adaptation maps between two successive hierarchies (moving geometry): per level, every new
+block's index in the previous list (-1 = created by refinement) and every previous block's index
+in the new list (-1 = removed by coarsening).  Integer work: compared exactly with maps built on
+the host from the two block lists."""
+import numpy as np
+import pytest
+
+from synth import small_workload
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+def _maps(a, b):
+    """index of each row of b in a (-1 when absent)"""
+    where = {tuple(r): i for i, r in enumerate(a.tolist())}
+    return np.array([where.get(tuple(r), -1) for r in b.tolist()], np.int64)
+
+
+def _refine(g, w, v, levels=None, keep=False, use_graph=False):
+    import torch
+
+    g.load(torch.from_numpy(v).cuda(), torch.from_numpy(w.idx).cuda())
+    g.bin(w.bins)
+    res = g.refine(levels or w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=use_graph,
+                   keep_previous=keep)
+    torch.cuda.synchronize()
+    return [U.to_np(lv["blocks"]).copy() for lv in res["levels"]]
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_moving_sphere_maps(use_graph):
+    from paper_2502_16310_gb300 import AmrGeom
+
+    w = small_workload("sphere3")
+    g = AmrGeom(3, (w.root,) * 3)
+    shift = np.array([0.011, -0.004, 0.007], np.float32)
+    old = _refine(g, w, w.verts, use_graph=use_graph)
+    for step in range(3):  # several moves: graph replays keep the previous lists too
+        new = _refine(g, w, w.verts + (step + 1) * shift, keep=True, use_graph=use_graph)
+        d = g.adapt_diff()
+        assert len(d) == len(new)
+        for L in range(len(new)):
+            n2o, o2n = _maps(old[L], new[L]), _maps(new[L], old[L])
+            assert np.array_equal(U.to_np(d[L]["new_to_old"]).astype(np.int64), n2o), (step, L)
+            assert np.array_equal(U.to_np(d[L]["old_to_new"]).astype(np.int64), o2n), (step, L)
+            assert d[L]["created"] == int((n2o < 0).sum()) and d[L]["removed"] == int((o2n < 0).sum())
+        assert d[-1]["created"] > 0 and d[-1]["removed"] > 0  # the finest level moved with the wall
+        old = new
+    g.close()
+
+
+def test_identity_and_depth_change():
+    from paper_2502_16310_gb300 import AmrGeom
+
+    w = small_workload("bumpy3")
+    g = AmrGeom(3, (w.root,) * 3)
+    a = _refine(g, w, w.verts)
+    b = _refine(g, w, w.verts, keep=True)
+    d = g.adapt_diff()
+    for L in range(len(b)):
+        assert np.array_equal(U.to_np(d[L]["new_to_old"]), np.arange(b[L].shape[0]))
+        assert d[L]["created"] == 0 and d[L]["removed"] == 0
+    # one level shallower: the dropped level's previous blocks are all removed
+    c = _refine(g, w, w.verts, levels=w.n_levels - 1, keep=True)
+    d = g.adapt_diff()
+    assert len(d) == len(c) == len(b) - 1
+    for L in range(len(c)):
+        assert d[L]["created"] == 0 and d[L]["removed"] == 0
+    g.close()
+    del a
+
+
+def test_adapt_diff_state_error():
+    from paper_2502_16310_gb300 import AmrError, AmrGeom
+    from paper_2502_16310_gb300 import binding as Bd
+
+    w = small_workload("sphere3")
+    g = AmrGeom(3, (w.root,) * 3)
+    _refine(g, w, w.verts)
+    with pytest.raises(AmrError) as e:
+        g.adapt_diff()  # no previous hierarchy was kept
+    assert e.value.status == Bd.AMR_ESTATE
+    g.close()
