@@ -204,6 +204,8 @@ typedef struct {
   int64_t n_candidates;       /* (block, face) candidate pairs read from the bins, all levels */
   int64_t n_survivors;        /* candidates that passed the block-level test */
   int64_t n_link_candidates;  /* (cell, face, direction) triples that passed the plane-range filter */
+  int graph_replay;           /* 1: the level loop ran as a replay of the captured graph; 0: eagerly (first
+                                 call, changed inputs or layout, or sizes beyond the graph's capacities) */
 } amr_refine_result;
 AMR_API amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* params, amr_refine_result* out);
 

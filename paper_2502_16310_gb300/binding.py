@@ -77,7 +77,8 @@ class amr_refine_result(C.Structure):
                 ("adj_off", C.c_void_p), ("adj_ids", C.c_void_p), ("n_links", C.c_int64),
                 ("link_cell", C.c_void_p), ("link_dir", C.c_void_p), ("link_q", C.c_void_p),
                 ("link_face", C.c_void_p), ("n_fallback", C.c_int64), ("n_band", C.c_int64),
-                ("n_candidates", C.c_int64), ("n_survivors", C.c_int64), ("n_link_candidates", C.c_int64)]
+                ("n_candidates", C.c_int64), ("n_survivors", C.c_int64), ("n_link_candidates", C.c_int64),
+                ("graph_replay", C.c_int)]
 
 
 class amr_batch_view(C.Structure):
@@ -431,7 +432,7 @@ class AmrGeom:
             })
         out = {"levels": levels, "n_fallback": int(r.n_fallback), "n_band": int(r.n_band),
                "n_candidates": int(r.n_candidates), "n_survivors": int(r.n_survivors),
-               "n_link_candidates": int(r.n_link_candidates)}
+               "n_link_candidates": int(r.n_link_candidates), "graph_replay": bool(r.graph_replay)}
         if want_adjacency or want_links:
             na, npairs = int(r.n_adj_cells), int(r.n_adj_pairs)
             out["adj_cell"] = _u32(r.adj_cell, na)

@@ -98,7 +98,7 @@ struct amr_ctx {
   bool multi = false;
   DevBuf table, face_gid;
   // buffers
-  DevBuf X, nrm, frec, recs, hkeys, hvals, cls, flbase, tl_cell, tl_dir, tl_q, tl_face, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
+  DevBuf X, nrm, frec, recs, hkeys, hvals, mkeys, mvals, cls, flbase, tl_cell, tl_dir, tl_q, tl_face, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
   LevelBufs lv[AMR_MAX_LEVELS];
   DevBuf adj_cell, adj_off, adj_ids, link_cell, link_dir, link_q, link_face;
   int64_t cap_cells = 0, cap_pairs = 0, cap_links = 0;
@@ -157,10 +157,10 @@ amr_status fail(amr_ctx* c, amr_status s, const char* fmt, ...) {
     if (s_ != AMR_OK) return s_;     \
   } while (0)
 
-amr_status ensure(amr_ctx* ctx, DevBuf& b, size_t bytes) {
+// Grow a buffer that no captured graph reads (the layout generation stays).
+amr_status ensure_aux(amr_ctx* ctx, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return AMR_OK;
-  ++ctx->layout_gen;
   if (b.p) {
     CK(cudaFreeAsync(b.p, ctx->stream));
     b.p = nullptr;
@@ -175,6 +175,13 @@ amr_status ensure(amr_ctx* ctx, DevBuf& b, size_t bytes) {
   }
   b.cap = want;
   return AMR_OK;
+}
+
+// Grow a buffer; a move invalidates the captured graph (new layout generation).
+amr_status ensure(amr_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (b.cap >= (bytes == 0 ? 16 : bytes)) return AMR_OK;
+  ++ctx->layout_gen;
+  return ensure_aux(ctx, b, bytes);
 }
 
 // Grow keeping the first `keep` bytes.
@@ -390,7 +397,7 @@ amr_status amr_ctx_init(amr_ctx* ctx) {
 void amr_ctx_free(amr_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   drop_graph(ctx);
-  DevBuf* all[] = {&ctx->X, &ctx->frec, &ctx->recs, &ctx->hkeys, &ctx->hvals, &ctx->cls, &ctx->flbase,
+  DevBuf* all[] = {&ctx->X, &ctx->frec, &ctx->recs, &ctx->hkeys, &ctx->hvals, &ctx->mkeys, &ctx->mvals, &ctx->cls, &ctx->flbase,
                    &ctx->tl_cell, &ctx->tl_dir, &ctx->tl_q, &ctx->tl_face, &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
                    &ctx->count,     &ctx->offsets,      &ctx->ids,        &ctx->payload,    &ctx->scratch,
                    &ctx->misc,      &ctx->scal,         &ctx->adj_cell,   &ctx->adj_off,    &ctx->adj_ids,
@@ -401,7 +408,8 @@ void amr_ctx_free(amr_ctx* ctx) {
   for (DevBuf* b : all) release(ctx, *b);
   for (int L = 0; L < AMR_MAX_LEVELS; ++L) {
     LevelBufs& l = ctx->lv[L];
-    DevBuf* lb[] = {&l.blocks, &l.gid, &l.parent, &l.mask, &l.flag, &l.cellcnt, &l.blockcnt, &l.base};
+    DevBuf* lb[] = {&l.blocks, &l.gid,  &l.parent, &l.mask, &l.flag, &l.cellcnt,
+                    &l.blockcnt, &l.base, &l.desc,   &l.prev, &l.n2o,  &l.o2n};
     for (DevBuf* b : lb) release(ctx, *b);
   }
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
@@ -566,9 +574,14 @@ RefineLevel level_args(amr_ctx* ctx, const Plan& P, int L) {
 
 __global__ void k_set_u64(uint64_t* p, uint64_t v) { *p = v; }
 
+// Capacity for a size learnt by an eager pass that a captured graph will reuse:
+// room for the sizes to drift between calls (a moving wall) without an overflow.
+int64_t with_slack(int64_t n) { return n + n / 8 + 256; }
+
 // One pass over all levels.  eager: learn sizes with read-backs and grow
-// buffers; otherwise (capture) use the capacities as they are.
-amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st) {
+// buffers (with slack when a graph is captured next); otherwise (capture) use
+// the capacities as they are.
+amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cudaStream_t st) {
   const int D = ctx->dom.dim;
   const int NCH = D == 3 ? 8 : 4;
   const int NCell = D == 3 ? 64 : 16;
@@ -596,8 +609,9 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st)
   for (int L = 0; L < P.NL; ++L) {
     LevelBufs& lb = ctx->lv[L];
     if (eager) {
-      lb.cap = N;
-      const size_t n1 = (size_t)(N > 0 ? N : 1);
+      // level 0: the roots; deeper levels: set when their parents were compacted
+      if (L == 0) lb.cap = N;
+      const size_t n1 = (size_t)(lb.cap > 0 ? lb.cap : 1);
       TRY(ensure(ctx, lb.mask, sizeof(uint64_t) * n1));
       TRY(ensure(ctx, lb.flag, n1));
       if (P.fin_at[L] && P.adjacency) {
@@ -606,7 +620,7 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st)
         TRY(ensure(ctx, lb.base, sizeof(uint64_t) * n1));
         TRY(ensure(ctx, lb.desc, sizeof(uint64_t) * n1));
         // record staging: what the last pass needed, at least a few per block
-        int64_t want = ctx->want_recs > 4 * N + 1024 ? ctx->want_recs : 4 * N + 1024;
+        int64_t want = ctx->want_recs > 4 * lb.cap + 1024 ? ctx->want_recs : 4 * lb.cap + 1024;
         if (want > ctx->cap_recs) {
           TRY(ensure(ctx, ctx->recs, sizeof(SurvRec) * (size_t)want));
           ctx->cap_recs = want;
@@ -642,7 +656,7 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st)
         TRY(ensure(ctx, nx.blocks, sizeof(int32_t) * D * c1));
         TRY(ensure(ctx, nx.parent, sizeof(int32_t) * c1));
         if (ctx->multi) TRY(ensure(ctx, nx.gid, sizeof(uint32_t) * c1));
-        TRY(ensure(ctx, ctx->scratch, children_scratch_bytes(N)));
+        TRY(ensure(ctx, ctx->scratch, children_scratch_bytes(lb.cap)));
       }
       ChildrenArgs ca{};
       ca.dim = D;
@@ -670,7 +684,8 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st)
         TRY(device_error(ctx, e));
         if ((int64_t)nn > (1ll << 32) / NCell) return fail(ctx, AMR_EOVERFLOW, "level %d has too many blocks", L + 1);
         N = (int64_t)nn;
-        nx.cap = N;
+        const int64_t bound = nx.cap;  // what the child buffers were sized for
+        nx.cap = slack ? std::min(with_slack(N), bound) : N;
       }
     }
     if (P.fin_at[L] && P.adjacency) {
@@ -692,8 +707,8 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, cudaStream_t st)
         if (run_pairs + pairs >= (int64_t)0xffffffffll)
           return fail(ctx, AMR_EOVERFLOW, "too many adjacent (cell, face) pairs");
         const int64_t need_c = run_cells + cells, need_p = run_pairs + pairs;
-        if (need_c + 1 > ctx->cap_cells) ctx->cap_cells = need_c + 1;
-        if (need_p > ctx->cap_pairs) ctx->cap_pairs = need_p;
+        if (need_c + 1 > ctx->cap_cells) ctx->cap_cells = slack ? with_slack(need_c + 1) : need_c + 1;
+        if (need_p > ctx->cap_pairs) ctx->cap_pairs = slack ? with_slack(need_p) : need_p;
         TRY(ensure_keep(ctx, ctx->adj_cell, sizeof(uint32_t) * (size_t)(ctx->cap_cells + 1),
                         sizeof(uint32_t) * (size_t)run_cells));
         TRY(ensure_keep(ctx, ctx->adj_off, sizeof(uint32_t) * (size_t)(ctx->cap_cells + 1),
@@ -873,6 +888,7 @@ amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine
     amr_refine_result r{};
     const amr_status s = collect(ctx, P, ctx->stream, &r);
     if (s == AMR_OK) {
+      r.graph_replay = 1;
       *out = r;
       if (ctx->want_recs > ctx->cap_recs) drop_graph(ctx);  // next call: eager pass with more staging
       return AMR_OK;
@@ -880,7 +896,7 @@ amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine
     if (s != AMR_EOVERFLOW) return s;
     drop_graph(ctx);  // sizes outgrew the capacities: redo eagerly
   }
-  TRY(engine_pass(ctx, P, true, ctx->stream));
+  TRY(engine_pass(ctx, P, true, want_graph, ctx->stream));
   TRY(collect(ctx, P, ctx->stream, out));
   if (want_graph) {
     drop_graph(ctx);
@@ -890,7 +906,7 @@ amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
     amr_status s = AMR_OK;
-    if (e == cudaSuccess) s = engine_pass(ctx, P, false, ctx->gstream);
+    if (e == cudaSuccess) s = engine_pass(ctx, P, false, false, ctx->gstream);
     const cudaError_t e2 = cudaStreamEndCapture(ctx->gstream, &graph);
     ctx->capturing = false;
     ctx->graph_launches = ctx->launches - before;
@@ -1097,7 +1113,7 @@ amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_
     for (int L = 0; L < pl; ++L) {
       const int64_t n = ctx->last.n_blocks[L];
       LevelBufs& lb = ctx->lv[L];
-      TRY(ensure(ctx, lb.prev, sizeof(int32_t) * D * (size_t)(n > 0 ? n : 1)));
+      TRY(ensure_aux(ctx, lb.prev, sizeof(int32_t) * D * (size_t)(n > 0 ? n : 1)));
       if (n > 0)
         CK(cudaMemcpyAsync(lb.prev.p, lb.blocks.p, sizeof(int32_t) * D * (size_t)n, cudaMemcpyDeviceToDevice,
                            ctx->stream));
@@ -1330,8 +1346,8 @@ amr_status amr_adapt_diff_get(amr_ctx* ctx, amr_adapt_diff* out) {
     cap = std::max(cap, std::max(nn, no));
   }
   const uint32_t slots = propagate_hash_slots(cap);
-  TRY(ensure(ctx, ctx->hkeys, sizeof(unsigned long long) * slots));
-  TRY(ensure(ctx, ctx->hvals, sizeof(uint32_t) * slots));
+  TRY(ensure_aux(ctx, ctx->mkeys, sizeof(unsigned long long) * slots));
+  TRY(ensure_aux(ctx, ctx->mvals, sizeof(uint32_t) * slots));
   unsigned long long* cnt = ctx->counters;  // [0 .. 2 * levels) as scratch for the missing counts
   const int nl = std::max(r.n_levels, ctx->prev_levels);
   if (2 * nl > CNT_N) {
@@ -1343,16 +1359,16 @@ amr_status amr_adapt_diff_get(amr_ctx* ctx, amr_adapt_diff* out) {
     LevelBufs& lb = ctx->lv[L];
     const int64_t nn = L < r.n_levels ? r.n_blocks[L] : 0;
     const int64_t no = L < ctx->prev_levels ? lb.n_prev : 0;
-    TRY(ensure(ctx, lb.n2o, sizeof(int32_t) * (size_t)(nn > 0 ? nn : 1)));
-    TRY(ensure(ctx, lb.o2n, sizeof(int32_t) * (size_t)(no > 0 ? no : 1)));
+    TRY(ensure_aux(ctx, lb.n2o, sizeof(int32_t) * (size_t)(nn > 0 ? nn : 1)));
+    TRY(ensure_aux(ctx, lb.o2n, sizeof(int32_t) * (size_t)(no > 0 ? no : 1)));
     const int32_t* nb = static_cast<const int32_t*>(lb.blocks.p);
     const int32_t* ob = static_cast<const int32_t*>(lb.prev.p);
     timed(ctx, st, "adapt_diff", [&] {
       int k = launch_block_map(D, ob, no, nb, nn, static_cast<int32_t*>(lb.n2o.p), cnt + 2 * L,
-                               static_cast<unsigned long long*>(ctx->hkeys.p), static_cast<uint32_t*>(ctx->hvals.p),
+                               static_cast<unsigned long long*>(ctx->mkeys.p), static_cast<uint32_t*>(ctx->mvals.p),
                                slots, ctx->d_err, st);
       k += launch_block_map(D, nb, nn, ob, no, static_cast<int32_t*>(lb.o2n.p), cnt + 2 * L + 1,
-                            static_cast<unsigned long long*>(ctx->hkeys.p), static_cast<uint32_t*>(ctx->hvals.p),
+                            static_cast<unsigned long long*>(ctx->mkeys.p), static_cast<uint32_t*>(ctx->mvals.p),
                             slots, ctx->d_err, st);
       return k;
     });

@@ -82,3 +82,45 @@ def test_adapt_diff_state_error():
         g.adapt_diff()  # no previous hierarchy was kept
     assert e.value.status == Bd.AMR_ESTATE
     g.close()
+
+
+def _arrays(res):
+    out = [U.to_np(lv["blocks"]).copy() for lv in res["levels"]]
+    for k in ("adj_cell", "adj_off", "adj_ids", "link_cell", "link_dir", "link_q", "link_face"):
+        out.append(U.to_np(res[k]).view(np.uint8).copy())
+    return out
+
+
+def test_graph_replays_follow_a_moving_wall():
+    """A wall moving by a fraction of the finest cell per step keeps replaying the captured level loop
+    (the capacities leave room for the sizes to drift), with results identical to eager calls."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+
+    w = small_workload("sphere3")
+    g, e = AmrGeom(3, (w.root,) * 3), AmrGeom(3, (w.root,) * 3)
+    h_fin = 1.0 / (4 * w.root * 2 ** (w.n_levels - 1))
+    delta = np.array([0.25, 0.1, 0.05], np.float32) * np.float32(h_fin)
+    idx = torch.from_numpy(w.idx).cuda()
+    replays = []
+    for k in range(6):
+        v = torch.from_numpy(w.verts + np.float32(k) * delta).cuda()
+        got = []
+        for ctx, graph in ((g, True), (e, False)):
+            ctx.load(v, idx)
+            ctx.bin(w.bins)
+            res = ctx.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=graph,
+                             keep_previous=graph and k > 0)
+            torch.cuda.synchronize()
+            got.append(_arrays(res))
+            if graph:
+                replays.append(res["graph_replay"])
+        assert len(got[0]) == len(got[1])
+        for a, b in zip(*got):
+            assert np.array_equal(a, b), k
+        if k > 0:
+            g.adapt_diff()  # its buffers are outside the graph: the next step still replays
+    assert replays[0] is False and all(replays[1:]), replays
+    g.close()
+    e.close()
