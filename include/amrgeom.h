@@ -162,9 +162,15 @@ typedef struct {
                                  neighbour blocks (3^D - 1) of every marked block; single-geometry only */
   int keep_previous;          /* 1: keep the previous call's block lists for amr_adapt_diff (re-adaptation of
                                  a moving or changing geometry); single-geometry only */
+  int face_pass;              /* levels whose only output is the mask (every level above the finest, and the
+                                 finest without adjacency): AMR_FACE_PASS_AUTO (0) marks them face by face where
+                                 that is expected to be cheaper than the block walk, _OFF (1) never, _ON (2)
+                                 wherever it applies (single geometry, AMR_SEARCH_QUERY_BOX, block coordinates
+                                 below 2^21).  Results are identical either way. */
 } amr_refine_params;
 enum { AMR_PRED_BOX = 0, AMR_PRED_POINT = 1 };
 enum { AMR_SEARCH_QUERY_BOX = 0, AMR_SEARCH_OWN_BIN = 1 };
+enum { AMR_FACE_PASS_AUTO = 0, AMR_FACE_PASS_OFF = 1, AMR_FACE_PASS_ON = 2 };
 
 /* Results.  Level arrays are per level 0..n_levels-1.
  *   block_coords[L]  device i32 [N_L][dim]
@@ -204,6 +210,8 @@ typedef struct {
   int64_t n_candidates;       /* (block, face) candidate pairs read from the bins, all levels */
   int64_t n_survivors;        /* candidates that passed the block-level test */
   int64_t n_link_candidates;  /* (cell, face, direction) triples that passed the plane-range filter */
+  int64_t n_face_setups;      /* faces set up by the face-by-face marking (face_pass), all its levels */
+  int64_t n_face_tests;       /* (face, cell) tests it ran */
   int graph_replay;           /* 1: the level loop ran as a replay of the captured graph; 0: eagerly (first
                                  call, changed inputs or layout, or sizes beyond the graph's capacities) */
 } amr_refine_result;

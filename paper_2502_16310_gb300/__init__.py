@@ -7,6 +7,9 @@ lists and lattice wall links.  The compute runs in hand-written sm_103a CUDA
 kernels behind the C ABI of ``include/amrgeom.h``; this package is its binding.
 """
 from .binding import (  # noqa: F401
+    AMR_FACE_PASS_AUTO,
+    AMR_FACE_PASS_OFF,
+    AMR_FACE_PASS_ON,
     AMR_PRED_BOX,
     AMR_PRED_POINT,
     AMR_SEARCH_OWN_BIN,

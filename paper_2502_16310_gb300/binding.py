@@ -56,7 +56,7 @@ class amr_refine_params(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("d_abs", C.c_double), ("d_rel", C.c_double), ("lattice", C.c_int),
                 ("want_adjacency", C.c_int), ("want_links", C.c_int), ("use_graph", C.c_int),
                 ("warps_per_cta", C.c_int), ("predicate", C.c_int), ("search", C.c_int), ("propagate", C.c_int),
-                ("keep_previous", C.c_int)]
+                ("keep_previous", C.c_int), ("face_pass", C.c_int)]
 
 
 class amr_adapt_diff(C.Structure):
@@ -67,6 +67,7 @@ class amr_adapt_diff(C.Structure):
 
 AMR_PRED_BOX, AMR_PRED_POINT = 0, 1
 AMR_SEARCH_QUERY_BOX, AMR_SEARCH_OWN_BIN = 0, 1
+AMR_FACE_PASS_AUTO, AMR_FACE_PASS_OFF, AMR_FACE_PASS_ON = 0, 1, 2
 
 
 class amr_refine_result(C.Structure):
@@ -78,7 +79,7 @@ class amr_refine_result(C.Structure):
                 ("link_cell", C.c_void_p), ("link_dir", C.c_void_p), ("link_q", C.c_void_p),
                 ("link_face", C.c_void_p), ("n_fallback", C.c_int64), ("n_band", C.c_int64),
                 ("n_candidates", C.c_int64), ("n_survivors", C.c_int64), ("n_link_candidates", C.c_int64),
-                ("graph_replay", C.c_int)]
+                ("n_face_setups", C.c_int64), ("n_face_tests", C.c_int64), ("graph_replay", C.c_int)]
 
 
 class amr_batch_view(C.Structure):
@@ -221,9 +222,10 @@ def amr_bin_faces_sampled(ctx, bin_density: int) -> amr_bins_view:
 
 def amr_refine_near_wall(ctx, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True,
                          want_links=True, use_graph=False, warps_per_cta=0, predicate=AMR_PRED_BOX,
-                         search=AMR_SEARCH_QUERY_BOX, propagate=0, keep_previous=False) -> amr_refine_result:
+                         search=AMR_SEARCH_QUERY_BOX, propagate=0, keep_previous=False,
+                         face_pass=AMR_FACE_PASS_AUTO) -> amr_refine_result:
     p = _params(n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph, warps_per_cta, predicate,
-                search, propagate, keep_previous)
+                search, propagate, keep_previous, face_pass)
     r = amr_refine_result()
     _check(ctx, lib().amr_refine_near_wall(ctx, C.byref(p), C.byref(r)))
     return r
@@ -238,13 +240,15 @@ def amr_sync(ctx):
 
 
 def _params(n_levels=1, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=True, use_graph=False,
-            warps_per_cta=0, predicate=AMR_PRED_BOX, search=AMR_SEARCH_QUERY_BOX, propagate=0, keep_previous=False):
+            warps_per_cta=0, predicate=AMR_PRED_BOX, search=AMR_SEARCH_QUERY_BOX, propagate=0, keep_previous=False,
+            face_pass=0):
     p = amr_refine_params()
     p.n_levels, p.d_abs, p.d_rel, p.lattice = int(n_levels), float(d_abs), float(d_rel), int(lattice)
     p.want_adjacency, p.want_links = int(bool(want_adjacency)), int(bool(want_links))
     p.use_graph, p.warps_per_cta = int(bool(use_graph)), int(warps_per_cta)
     p.predicate, p.search, p.propagate = int(predicate), int(search), int(propagate)
     p.keep_previous = int(bool(keep_previous))
+    p.face_pass = int(face_pass)
     return p
 
 
@@ -405,15 +409,16 @@ class AmrGeom:
 
     def refine(self, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=None,
                use_graph=False, warps_per_cta=0, predicate=AMR_PRED_BOX, search=AMR_SEARCH_QUERY_BOX, propagate=0,
-               keep_previous=False):
+               keep_previous=False, face_pass=0):
         """Step 3: near-wall refinement; returns per-level tensors, adjacency CSR and links (borrowed).
         predicate: AMR_PRED_BOX (inflated cell box meets the face) or AMR_PRED_POINT (cell centre within
         d of the face, the paper's Alg. 1); search / propagate: the paper's binned search (own bin only)
-        and its mark propagation (-1: 1 + floor(d / block length) rounds)."""
+        and its mark propagation (-1: 1 + floor(d / block length) rounds); face_pass: AMR_FACE_PASS_AUTO /
+        _OFF / _ON, how mask-only levels are marked (identical results)."""
         if want_links is None:
             want_links = lattice != 0
         r = amr_refine_near_wall(self.ctx, n_levels, d_abs, d_rel, lattice, want_adjacency, want_links, use_graph,
-                                 warps_per_cta, predicate, search, propagate, keep_previous)
+                                 warps_per_cta, predicate, search, propagate, keep_previous, face_pass)
         self.last_result = r
         return self._wrap(r, want_adjacency, want_links)
 
@@ -432,7 +437,8 @@ class AmrGeom:
             })
         out = {"levels": levels, "n_fallback": int(r.n_fallback), "n_band": int(r.n_band),
                "n_candidates": int(r.n_candidates), "n_survivors": int(r.n_survivors),
-               "n_link_candidates": int(r.n_link_candidates), "graph_replay": bool(r.graph_replay)}
+               "n_link_candidates": int(r.n_link_candidates), "n_face_setups": int(r.n_face_setups),
+               "n_face_tests": int(r.n_face_tests), "graph_replay": bool(r.graph_replay)}
         if want_adjacency or want_links:
             na, npairs = int(r.n_adj_cells), int(r.n_adj_pairs)
             out["adj_cell"] = _u32(r.adj_cell, na)

@@ -66,11 +66,13 @@ struct GraphKey {
   uint64_t layout_gen = 0;
   int64_t nf = 0, n_geom = 0;
   int n_levels = 0, lattice = 0, adjacency = 0, links = 0, warps = 0, B = 0, pred = 0, search = 0, prop = 0;
+  uint32_t face_levels = 0;  // levels marked face by face
   double d_abs = 0, d_rel = 0;
   bool operator==(const GraphKey& o) const {
     return layout_gen == o.layout_gen && nf == o.nf && n_geom == o.n_geom && n_levels == o.n_levels &&
            lattice == o.lattice && adjacency == o.adjacency && links == o.links && warps == o.warps && B == o.B &&
-           pred == o.pred && search == o.search && prop == o.prop && d_abs == o.d_abs && d_rel == o.d_rel;
+           pred == o.pred && search == o.search && prop == o.prop && face_levels == o.face_levels &&
+           d_abs == o.d_abs && d_rel == o.d_rel;
   }
 };
 
@@ -115,6 +117,9 @@ struct amr_ctx {
   unsigned* d_err = nullptr;
   unsigned* d_work = nullptr;
   uint64_t* d_tot = nullptr;
+  unsigned long long* d_fstat = nullptr;  // face-size statistics of the last binning (see FaceBinArgs)
+  double face_ext_max = INFINITY;         // largest face AABB side (domain units), from the last binning
+  double face_ext_mean = INFINITY;        // mean over faces of the largest AABB side / h0
   uint64_t* d_scal = nullptr;
   void* h_pinned = nullptr;  // 2 KB
   amr_refine_result last{};
@@ -256,7 +261,7 @@ amr_status sync_check(amr_ctx* ctx, cudaStream_t st) {
 // Copy the device error word and the first totals to pinned memory and wait.
 amr_status read_back(amr_ctx* ctx, cudaStream_t st, unsigned* err_out, uint64_t* tot_out, int n_tot) {
   char* h = static_cast<char*>(ctx->h_pinned);
-  CK(cudaMemcpyAsync(h, ctx->d_tot, sizeof(uint64_t) * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h, ctx->d_tot, sizeof(uint64_t) * 8, cudaMemcpyDeviceToHost, st));  // totals and face stats
   CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   TRY(sync_check(ctx, st));
   if (tot_out)
@@ -388,6 +393,7 @@ amr_status amr_ctx_init(amr_ctx* ctx) {
   ctx->d_err = reinterpret_cast<unsigned*>(m + sizeof(unsigned long long) * CNT_N);
   ctx->d_work = ctx->d_err + 1;
   ctx->d_tot = reinterpret_cast<uint64_t*>(m + sizeof(unsigned long long) * CNT_N + 64);
+  ctx->d_fstat = reinterpret_cast<unsigned long long*>(ctx->d_tot + 4);  // within the totals' 64 bytes
   ctx->d_scal = static_cast<uint64_t*>(ctx->scal.p);
   cudaMemsetAsync(ctx->misc.p, 0, ctx->misc.cap, ctx->stream);
   cudaMemsetAsync(ctx->scal.p, 0, ctx->scal.cap, ctx->stream);
@@ -465,6 +471,10 @@ amr_status amr_bin_all(amr_ctx* ctx) {
     fa.sampled = 1;
     fa.sample_s = 0.5 * (ext / (double)ctx->geoms[0].B);
   }
+  if (!ctx->multi) {
+    fa.fstat = ctx->d_fstat;
+    CK(cudaMemsetAsync(ctx->d_fstat, 0, sizeof(unsigned long long) * 2, st));
+  }
   uint32_t* offsets = static_cast<uint32_t*>(ctx->offsets.p);
   timed(ctx, st, "bin_count", [&] { return launch_face_bins(fa, st); });
   timed(ctx, st, "bin_scan", [&] {
@@ -472,8 +482,17 @@ amr_status amr_bin_all(amr_ctx* ctx) {
   });
   CK(cudaGetLastError());
   unsigned e = 0;
-  uint64_t tot = 0;
-  TRY(read_back(ctx, st, &e, &tot, 1));
+  uint64_t tw[6] = {0, 0, 0, 0, 0, 0};
+  TRY(read_back(ctx, st, &e, tw, 6));
+  const uint64_t tot = tw[0];
+  ctx->face_ext_max = ctx->face_ext_mean = INFINITY;
+  if (!ctx->multi) {
+    const uint32_t bits = (uint32_t)tw[4];
+    float mx;
+    std::memcpy(&mx, &bits, sizeof mx);
+    ctx->face_ext_max = nf > 0 ? (double)mx : 0.0;
+    ctx->face_ext_mean = nf > 0 ? (double)tw[5] / 65536.0 / (double)nf : 0.0;
+  }
   if (e) {
     ctx->count_clean = false;
     return device_error(ctx, e);
@@ -506,10 +525,37 @@ struct Plan {
   int NL;                           // levels of the deepest geometry
   bool fin_at[AMR_MAX_LEVELS];      // some geometry ends at this level
   bool cont_after[AMR_MAX_LEVELS];  // some geometry continues below this level
+  bool face_at[AMR_MAX_LEVELS];     // level marked face by face (k_mark_faces) instead of by the block walk
   bool adjacency, links;
   int lattice, warps, pred, search, propagate;
   int64_t n_roots;
 };
+
+// Face-by-face marking applies to a level whose only output is the mask, for
+// one geometry with the whole-domain search, block coordinates that fit the
+// hash key and faces whose cell ranges stay small (the largest face of the last
+// binning, widened by d, covers at most kMaxFaceCells cells of the level).
+constexpr double kMaxFaceCells = 32768.0;
+// Automatic choice: face by face where the mean face covers at most this many
+// cells of the level (the block walk is cheaper once faces span many cells).
+constexpr double kAutoFaceCells = 1024.0;
+
+// Cells of level L in the range of a face whose largest AABB side is ext:
+// (ext + 2 d_L) / h_L + pad per axis (pad 4 bounds the rounding of the range
+// ends and the cell-box reach; pad 1 estimates the typical range).
+double face_cells(const amr_ctx* ctx, int L, double ext, double pad) {
+  const GeomParams& g = ctx->geoms[0];
+  const double hL = std::ldexp(g.h0, -L), dL = g.d_abs + g.d_rel * hL;
+  return std::pow(ext / hL + 2.0 * dL / hL + pad, (double)ctx->dom.dim);
+}
+
+bool face_pass_applies(const amr_ctx* ctx, const Plan& P, int L) {
+  if (ctx->multi || P.search != AMR_SEARCH_QUERY_BOX || (P.fin_at[L] && P.adjacency)) return false;
+  const GeomParams& g = ctx->geoms[0];
+  for (int c = 0; c < ctx->dom.dim; ++c)
+    if (((int64_t)g.root[c] << L) >= (1ll << 21)) return false;
+  return face_cells(ctx, L, ctx->face_ext_max, 4.0) <= kMaxFaceCells;
+}
 
 Plan make_plan(const amr_ctx* ctx, const amr_refine_params* p) {
   Plan P{};
@@ -526,6 +572,11 @@ Plan make_plan(const amr_ctx* ctx, const amr_refine_params* p) {
   P.search = p->search;
   P.propagate = p->propagate;
   for (const auto& g : ctx->geoms) P.n_roots += roots_of(g, ctx->dom.dim);
+  for (int L = 0; L < P.NL; ++L) {
+    P.face_at[L] = p->face_pass != AMR_FACE_PASS_OFF && face_pass_applies(ctx, P, L);
+    if (p->face_pass == AMR_FACE_PASS_AUTO && P.face_at[L])
+      P.face_at[L] = face_cells(ctx, L, ctx->face_ext_mean * ctx->geoms[0].h0, 1.0) <= kAutoFaceCells;
+  }
   return P;
 }
 
@@ -629,7 +680,32 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
     }
     RefineLevel a = level_args(ctx, P, L);
     CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), st));
-    timed(ctx, st, "refine_level", [&] { return launch_refine(a, ctx->num_sms, st); });
+    if (P.face_at[L]) {
+      // face by face: masks and flags start clear; deeper levels find their blocks through the hash
+      CK(cudaMemsetAsync(a.mask, 0, sizeof(uint64_t) * (size_t)(lb.cap > 0 ? lb.cap : 1), st));
+      CK(cudaMemsetAsync(a.flag, 0, (size_t)(lb.cap > 0 ? lb.cap : 1), st));
+      MarkArgs m{};
+      m.lv = a;
+      m.rec = static_cast<const FaceRec3*>(ctx->frec.p);
+      if (L > 0) {
+        const uint32_t slots = propagate_hash_slots(lb.cap);
+        if (eager) {
+          TRY(ensure(ctx, ctx->hkeys, sizeof(unsigned long long) * slots));
+          TRY(ensure(ctx, ctx->hvals, sizeof(uint32_t) * slots));
+        }
+        m.keys = static_cast<const unsigned long long*>(ctx->hkeys.p);
+        m.vals = static_cast<const uint32_t*>(ctx->hvals.p);
+        m.hmask = slots - 1;
+        timed(ctx, st, "block_hash", [&] {
+          return launch_hash_build(D, a.blocks, lb.cap, a.n_dev, static_cast<unsigned long long*>(ctx->hkeys.p),
+                                   static_cast<uint32_t*>(ctx->hvals.p), slots, ctx->d_err, st);
+        });
+      }
+      timed(ctx, st, "mark_faces", [&] { return launch_mark_faces(m, ctx->num_sms, st); });
+      if (a.blockcnt) CK(cudaMemsetAsync(a.blockcnt, 0, sizeof(uint64_t) * (size_t)(lb.cap > 0 ? lb.cap : 1), st));
+    } else {
+      timed(ctx, st, "refine_level", [&] { return launch_refine(a, ctx->num_sms, st); });
+    }
     if (P.cont_after[L] && P.propagate != 0) {
       // the paper's mark propagation over this level's blocks (flags 0/1 in place)
       const GeomParams& g0 = ctx->geoms[0];
@@ -805,11 +881,13 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
 // Read every size of the last pass (one synchronisation) and fill the result.
 amr_status collect(amr_ctx* ctx, const Plan& P, cudaStream_t st, amr_refine_result* out) {
   char* h = static_cast<char*>(ctx->h_pinned);
+  // pinned layout: [0, 8 CNT_N) counters, 128 error word, 256 level pointers, 512 scalars
+  static_assert(sizeof(unsigned long long) * CNT_N <= 128, "counters overlap the error word");
   CK(cudaMemcpyAsync(h, ctx->counters, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + 128, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h + 512, ctx->d_scal, sizeof(uint64_t) * SC_WORDS, cudaMemcpyDeviceToHost, st));
   TRY(sync_check(ctx, st));
-  const unsigned e = *reinterpret_cast<unsigned*>(h + 64);
+  const unsigned e = *reinterpret_cast<unsigned*>(h + 128);
   TRY(device_error(ctx, e));
   const uint64_t* sc = reinterpret_cast<const uint64_t*>(h + 512);
   const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(h);
@@ -845,6 +923,8 @@ amr_status collect(amr_ctx* ctx, const Plan& P, cudaStream_t st, amr_refine_resu
   r.n_candidates = (int64_t)cnt[CNT_CANDIDATES];
   r.n_survivors = (int64_t)cnt[CNT_SURVIVORS];
   r.n_link_candidates = (int64_t)cnt[CNT_LINK_CAND];
+  r.n_face_setups = (int64_t)cnt[CNT_FACE_SETUPS];
+  r.n_face_tests = (int64_t)cnt[CNT_FACE_TESTS];
   // per-level block pointers for the adjoint
   TRY(ensure(ctx, ctx->lvl_ptrs, sizeof(void*) * AMR_MAX_LEVELS));
   const int32_t** hp = reinterpret_cast<const int32_t**>(h + 256);
@@ -876,6 +956,8 @@ amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine
   key.pred = prm->predicate;
   key.search = prm->search;
   key.prop = prm->propagate;
+  for (int L = 0; L < P.NL; ++L)
+    if (P.face_at[L]) key.face_levels |= 1u << L;
   const bool want_graph = prm->use_graph != 0;
   if (want_graph && ctx->gexec && ctx->gkey == key) {
     // replay on the graph stream, ordered after the caller's stream
@@ -1088,6 +1170,8 @@ amr_status amr_refine_near_wall(amr_ctx* ctx, const amr_refine_params* prm, amr_
   if (ctx->sampled_bins && prm->search != AMR_SEARCH_OWN_BIN)
     return fail(ctx, AMR_EINVAL, "sampled bins only serve the own-bin search");
   if (prm->propagate < -1) return fail(ctx, AMR_EINVAL, "propagate must be >= -1");
+  if (prm->face_pass < AMR_FACE_PASS_AUTO || prm->face_pass > AMR_FACE_PASS_ON)
+    return fail(ctx, AMR_EINVAL, "face_pass must be AMR_FACE_PASS_AUTO (0), _OFF (1) or _ON (2)");
   if (prm->propagate != 0) {
     for (int a = 0; a < D; ++a)
       if ((int64_t)ctx->dom.root_blocks[a] << (NL - 1) >= (1ll << 21))

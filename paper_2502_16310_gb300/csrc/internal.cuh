@@ -33,7 +33,9 @@ enum : int {
   CNT_LINK_BAND = 5,
   CNT_LINK_CAND = 6,
   CNT_CLASS_FALLBACK = 7,
-  CNT_N = 8,
+  CNT_FACE_SETUPS = 8,  // faces set up by the face-centric marking
+  CNT_FACE_TESTS = 9,   // (face, cell) tests run by it
+  CNT_N = 10,
 };
 
 // Per-geometry parameters.  A launch may cover the blocks (faces) of many
@@ -249,6 +251,35 @@ __device__ __forceinline__ uint64_t lookback_warp(uint64_t* state, long long til
   return prefix;
 }
 
+// --- block-coordinate hash (open addressing, linear probing) --------------
+// Key: the block's coordinates, 21 bits per axis, plus one (0 marks an empty
+// slot); value: the block's index in its level's list.
+__device__ __forceinline__ unsigned long long block_key(const int32_t* c, int dim) {
+  unsigned long long k = 0;
+  for (int a = 0; a < dim; ++a) k = (k << 21) | (unsigned long long)((uint32_t)c[a] & 0x1fffffu);
+  return k + 1ull;
+}
+
+__device__ __forceinline__ uint32_t hash_slot(unsigned long long k, uint32_t mask) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  return (uint32_t)k & mask;
+}
+
+// Index stored for key k, or -1.
+__device__ __forceinline__ int64_t hash_find(const unsigned long long* keys, const uint32_t* vals, uint32_t hmask,
+                                             unsigned long long k) {
+  uint32_t s = hash_slot(k, hmask);
+  for (uint32_t probe = 0; probe <= hmask; ++probe) {
+    const unsigned long long v = keys[s];
+    if (v == k) return (int64_t)vals[s];
+    if (v == 0ull) return -1;
+    s = (s + 1) & hmask;
+  }
+  return -1;
+}
+
 // --- shared-memory barriers and TMA bulk copies (inline PTX, sm_90+) -------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -352,6 +383,8 @@ struct FaceBinArgs {
   uint32_t* count;
   int sampled;                 // 1: the paper's sampled-point membership (single geometry)
   double sample_s;             // sample spacing (half a bin length)
+  unsigned long long* fstat;   // nullable: [0] max over faces of the largest AABB side (FP32 bits),
+                               // [1] sum over faces of that side / h0, fixed point 2^-16 (zeroed before)
 };
 int launch_face_bins(const FaceBinArgs& a, cudaStream_t st);
 int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint32_t* frange, uint32_t* count,
@@ -417,6 +450,20 @@ struct RefineLevel {
 constexpr int kMaxBatch = 8;
 int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st);
 
+// Face-centric marking of a level without adjacency output (single geometry,
+// box or point predicate, whole-domain search): lv.mask / lv.flag zeroed and
+// lv.work zeroed before the launch; blocks found through the level-0 root
+// order or, deeper, the coordinate hash (keys / vals, hmask = slots - 1).
+struct MarkArgs {
+  RefineLevel lv;
+  const FaceRec3* rec;  // 3D face records (2D reads lv.X)
+  const unsigned long long* keys;
+  const uint32_t* vals;
+  uint32_t hmask;
+};
+constexpr int kFaceBatch = 8;  // faces a warp takes per work fetch
+int launch_mark_faces(const MarkArgs& m, int num_sms, cudaStream_t st);
+
 struct EmitArgs {
   RefineLevel lv;
   const uint64_t* block_base;  // exclusive scan of blockcnt over this level
@@ -477,6 +524,9 @@ int launch_fluid_move(const uint32_t* link_cell, const uint8_t* link_dir, const 
 // through a hash of the block coordinates (keys/vals: `slots` entries, a power of
 // two >= 2 x capacity, from propagate_hash_slots; coordinates below 2^21).
 uint32_t propagate_hash_slots(int64_t cap);
+// Hash of a level's block coordinates -> index (the count from n_dev when given, bounded by cap).
+int launch_hash_build(int dim, const int32_t* blocks, int64_t cap, const uint64_t* n_dev, unsigned long long* keys,
+                      uint32_t* vals, uint32_t slots, unsigned* err, cudaStream_t st);
 int launch_propagate(int dim, const int32_t* blocks, int64_t cap, const uint64_t* n_dev, uint8_t* flags,
                      int rounds, unsigned long long* keys, uint32_t* vals, uint32_t slots, unsigned* err,
                      cudaStream_t st);

@@ -206,9 +206,12 @@ __device__ void sampled_bins(const float* X, int64_t nf, int64_t f, const GeomPa
 // its own geometry) and one count per (face, bin) incidence.
 template <int D>
 __global__ void k_face_bins(FaceBinArgs a) {
+  float ext_max = 0.f;             // face-size statistics (the refine plans its marking from them)
+  unsigned long long ext_sum = 0;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.nf; f += (int64_t)gridDim.x * blockDim.x) {
     const GeomParams P = geom_row(a.g0, a.table, a.face_gid, f);
     int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    float ext = 0.f;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       float mn = a.X[(int64_t)c * a.nf + f], mx = mn;
@@ -218,10 +221,15 @@ __global__ void k_face_bins(FaceBinArgs a) {
         mn = fminf(mn, x);
         mx = fmaxf(mx, x);
       }
+      ext = fmaxf(ext, mx - mn);
       lo[c] = bin_coord_fast(mn, P, c);
       hi[c] = bin_coord_fast(mx, P, c);
       a.frange[(int64_t)c * a.nf + f] = (uint32_t)lo[c] | ((uint32_t)hi[c] << 16);
     }
+    if (!(ext <= 3.0e38f)) ext = INFINITY;  // a non-finite coordinate
+    ext_max = fmaxf(ext_max, ext);
+    const float rel = ext / P.h0_hi * 65536.0f;
+    ext_sum += rel < 1.0e12f ? (unsigned long long)rel : 1000000000000ull;
     const int64_t B = P.B;
     if (a.sampled) {
       sampled_bins<D>(a.X, a.nf, f, P, a.sample_s, lo, hi, [&](int x, int y, int z) {
@@ -232,6 +240,17 @@ __global__ void k_face_bins(FaceBinArgs a) {
     for (int z = lo[2]; z <= hi[2]; ++z)
       for (int y = lo[1]; y <= hi[1]; ++y)
         for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&a.count[P.bin_base + x + B * (y + B * (int64_t)z)], 1u);
+  }
+  if (a.fstat) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ext_max = fmaxf(ext_max, __shfl_xor_sync(0xffffffffu, ext_max, o));
+      ext_sum += __shfl_xor_sync(0xffffffffu, ext_sum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (ext_max > 0.f) atomicMax(a.fstat, (unsigned long long)__float_as_uint(ext_max));  // >= 0: bits order
+      if (ext_sum) atomicAdd(a.fstat + 1, ext_sum);
+    }
   }
 }
 

@@ -17,19 +17,6 @@ namespace {
 constexpr int kPThreads = 256;
 constexpr unsigned long long kEmpty = 0ull;
 
-__device__ __forceinline__ unsigned long long block_key(const int32_t* c, int dim) {
-  unsigned long long k = 0;
-  for (int a = 0; a < dim; ++a) k = (k << 21) | (unsigned long long)((uint32_t)c[a] & 0x1fffffu);
-  return k + 1ull;  // 0 marks an empty slot
-}
-
-__device__ __forceinline__ uint32_t hash_slot(unsigned long long k, uint32_t mask) {
-  k ^= k >> 33;
-  k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33;
-  return (uint32_t)k & mask;
-}
-
 __device__ __forceinline__ int64_t count_of(int64_t cap, const uint64_t* n_dev) {
   if (!n_dev) return cap;
   const int64_t n = (int64_t)*n_dev;
@@ -55,18 +42,6 @@ __global__ void k_hash_insert(int dim, const int32_t* __restrict__ blocks, int64
       s = (s + 1) & hmask;
     }
   }
-}
-
-__device__ __forceinline__ int64_t hash_find(const unsigned long long* keys, const uint32_t* vals, uint32_t hmask,
-                                             unsigned long long k) {
-  uint32_t s = hash_slot(k, hmask);
-  for (uint32_t probe = 0; probe <= hmask; ++probe) {
-    const unsigned long long v = keys[s];
-    if (v == k) return (int64_t)vals[s];
-    if (v == kEmpty) return -1;
-    s = (s + 1) & hmask;
-  }
-  return -1;
 }
 
 // Round, first half: every marked block (flag 1) gives its unmarked existing
@@ -110,6 +85,14 @@ uint32_t propagate_hash_slots(int64_t cap) {
   uint32_t s = 1024;
   while ((int64_t)s < 2 * cap && s < (1u << 31)) s <<= 1;
   return s;
+}
+
+int launch_hash_build(int dim, const int32_t* blocks, int64_t cap, const uint64_t* n_dev, unsigned long long* keys,
+                      uint32_t* vals, uint32_t slots, unsigned* err, cudaStream_t st) {
+  if (cap <= 0) return 0;
+  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * slots, st);
+  k_hash_insert<<<grid_of(cap), kPThreads, 0, st>>>(dim, blocks, cap, n_dev, keys, vals, slots - 1, err);
+  return 1;
 }
 
 int launch_propagate(int dim, const int32_t* blocks, int64_t cap, const uint64_t* n_dev, uint8_t* flags,

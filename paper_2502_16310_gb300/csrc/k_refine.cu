@@ -52,18 +52,30 @@ struct Surv<2> {
   uint32_t pad[1];
 };
 
-// FP64 separating-axis margin of the box [x_c - r, x_c + r]^3 and the closed
-// triangle (vertices absolute FP32), normalised gap of the best axis.
-__device__ __noinline__ double margin_fp64_3(const float* V, const double* xc, double r) {
+// FP64 decision of the separating-axis test of the box [x_c - r, x_c + r]^3
+// and the closed triangle (vertices absolute FP32).  The margin of the
+// definition is max over the 13 axes of gap_a / |a| (gap_a = the FP64 gap
+// between the projected intervals); its sign is that of the largest gap_a, so
+// the pair is adjacent exactly when no axis has gap_a > 0, and no square root
+// or division is needed (a quotient of normal magnitudes does not underflow).
+// *band: the margin lies within tol of 0, tested as gap_a^2 <= tol^2 |a|^2 on
+// the deciding axes (a diagnostic count).  An axis with gap_a > tol |a| settles
+// the pair at once: separated, outside the band.
+__device__ __noinline__ bool sat_adjacent_fp64_3(const float* V, const double* xc, double r, double tol,
+                                                 bool* band) {
   double p[3][3];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int c = 0; c < 3; ++c) p[k][c] = __dsub_rn((double)V[3 * k + c], xc[c]);
-  double m = -1e300;
-  auto axis = [&](double a0, double a1, double a2) {
-    const double l2 = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(a0, a0), __dmul_rn(a1, a1)), __dmul_rn(a2, a2)));
-    if (l2 == 0.0) return;
+  const double tol2 = tol * tol;
+  bool sep = false;        // some axis with a positive gap
+  bool pos_small = true;   // every positive gap within tol |a|
+  bool near0 = false;      // some axis with gap >= -tol |a|
+  // false: the pair is settled (separated beyond the band)
+  auto axis = [&](double a0, double a1, double a2) -> bool {
+    const double l2sq = __dadd_rn(__dadd_rn(__dmul_rn(a0, a0), __dmul_rn(a1, a1)), __dmul_rn(a2, a2));
+    if (l2sq == 0.0) return true;
     double lo = 1e300, hi = -1e300;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -73,25 +85,34 @@ __device__ __noinline__ double margin_fp64_3(const float* V, const double* xc, d
     }
     const double R = __dmul_rn(r, __dadd_rn(__dadd_rn(fabs(a0), fabs(a1)), fabs(a2)));
     const double g = fmax(__dsub_rn(lo, R), __dsub_rn(-R, hi));
-    m = fmax(m, g / l2);
+    const bool small = __dmul_rn(g, g) <= __dmul_rn(tol2, l2sq);
+    if (g > 0.0) {
+      sep = true;
+      if (!small) {
+        pos_small = false;
+        return false;
+      }
+    } else if (small) {
+      near0 = true;
+    }
+    return true;
   };
-  axis(1.0, 0.0, 0.0);
-  axis(0.0, 1.0, 0.0);
-  axis(0.0, 0.0, 1.0);
+  *band = false;
+  if (!axis(1.0, 0.0, 0.0) || !axis(0.0, 1.0, 0.0) || !axis(0.0, 0.0, 1.0)) return false;
   const double u0 = __dsub_rn(p[1][0], p[0][0]), u1 = __dsub_rn(p[1][1], p[0][1]), u2 = __dsub_rn(p[1][2], p[0][2]);
   const double w0 = __dsub_rn(p[2][0], p[0][0]), w1 = __dsub_rn(p[2][1], p[0][1]), w2 = __dsub_rn(p[2][2], p[0][2]);
-  axis(__dsub_rn(__dmul_rn(u1, w2), __dmul_rn(u2, w1)), __dsub_rn(__dmul_rn(u2, w0), __dmul_rn(u0, w2)),
-       __dsub_rn(__dmul_rn(u0, w1), __dmul_rn(u1, w0)));
+  if (!axis(__dsub_rn(__dmul_rn(u1, w2), __dmul_rn(u2, w1)), __dsub_rn(__dmul_rn(u2, w0), __dmul_rn(u0, w2)),
+            __dsub_rn(__dmul_rn(u0, w1), __dmul_rn(u1, w0))))
+    return false;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int k1 = (k + 1) % 3;
     const double ex = __dsub_rn(p[k1][0], p[k][0]), ey = __dsub_rn(p[k1][1], p[k][1]),
                  ez = __dsub_rn(p[k1][2], p[k][2]);
-    axis(0.0, -ez, ey);
-    axis(ez, 0.0, -ex);
-    axis(-ey, ex, 0.0);
+    if (!axis(0.0, -ez, ey) || !axis(ez, 0.0, -ex) || !axis(-ey, ex, 0.0)) return false;
   }
-  return m;
+  *band = sep ? pos_small : near0;
+  return !sep;
 }
 
 __device__ __noinline__ double margin_fp64_2(const float* V, const double* xc, double r) {
@@ -420,9 +441,14 @@ __device__ __noinline__ bool resolve_fp64(const RefineLevel& a, uint32_t gid, ui
     xc[c] = __dadd_rn(G.origin[c], __dmul_rn((double)(4 * b[c] + li) + 0.5, G.h));
   }
   const double r = __dadd_rn(0.5 * G.h, G.d);
-  const double m = a.pred == 1 ? point_dist_fp64(V, xc, D) - G.d
-                               : (D == 3 ? margin_fp64_3(V, xc, r) : margin_fp64_2(V, xc, r));
   ++*fb;
+  if (D == 3 && a.pred != 1) {
+    bool in_band = false;
+    const bool adj = sat_adjacent_fp64_3(V, xc, r, kBandRel * G.h, &in_band);
+    if (in_band) ++*band;
+    return adj;
+  }
+  const double m = a.pred == 1 ? point_dist_fp64(V, xc, D) - G.d : margin_fp64_2(V, xc, r);
   if (fabs(m) <= kBandRel * G.h) ++*band;
   return m <= 0.0;
 }
@@ -1045,6 +1071,316 @@ __global__ void __launch_bounds__(kChThreads) k_children(ChildrenArgs a, uint64_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Face-centric marking of a level whose masks are the only output (no
+// adjacency lists): one warp per face tests the cells of the level whose test
+// region can meet the face (the face's AABB widened by d, in cells) and ORs
+// the hits into their blocks' masks.  Coarse levels are where this pays: a
+// block there sees hundreds of faces, each of which the block walk tests
+// against all of the block's cells, while a face covers only a few cells.
+// The decisions are the block walk's: the same certified FP32 tests, in a
+// frame at the lower corner of the face's cell range (the error bounds need
+// only the frame's offset bounds P and O), and the same FP64 resolution.
+// ---------------------------------------------------------------------------
+
+// One cell's SAT test against a survivor: the projections of cell_test2.
+template <int D>
+__device__ __forceinline__ int cell_test1(const Surv<D>& S, const float* o) {
+  bool sep = false, in = true;
+  auto upd = [&](float x, const float4& t) {
+    sep |= (x < t.x) | (x > t.y);
+    in &= (x > t.z) & (x < t.w);
+  };
+  if constexpr (D == 3) {
+#pragma unroll
+    for (int ai = 0; ai < 3; ++ai) upd(o[ai], S.t[ai]);
+    const float4 q0 = S.en[0], q1 = S.en[1], q2 = S.en[2];
+    const float e[3][3] = {{q0.x, q0.y, q0.z}, {q0.w, q1.x, q1.y}, {q1.z, q1.w, q2.x}};
+    upd(fmaf(o[2], q2.w, fmaf(o[1], q2.z, o[0] * q2.y)), S.t[3]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float ex = e[k][0], ey = e[k][1], ez = e[k][2];
+      upd(fmaf(o[2], ey, -o[1] * ez), S.t[4 + 3 * k]);
+      upd(fmaf(o[0], ez, -o[2] * ex), S.t[5 + 3 * k]);
+      upd(fmaf(o[1], ex, -o[0] * ey), S.t[6 + 3 * k]);
+    }
+  } else {
+    upd(o[0], S.t[0]);
+    upd(o[1], S.t[1]);
+    upd(fmaf(o[1], S.e[0], -o[0] * S.e[1]), S.t[2]);
+  }
+  return sep ? 0 : (in ? 1 : 2);
+}
+
+// setup_face without the block cull, lane-parallel: lane ai < 13 (2D: 3)
+// computes axis ai with setup_face's arithmetic; lane 0 stores the edges.
+template <int D>
+__device__ __forceinline__ void setup_face_lanes(const float* V, const float* nh, const BlockFrame<D>& F, Surv<D>& S,
+                                                 int lane) {
+  constexpr int NA = D == 3 ? 13 : 3;
+  float p[3][3];
+  float P = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      p[k][c] = V[D * k + c] - F.Xb[c];
+      P = fmaxf(P, fabsf(p[k][c]));
+    }
+  const float scale = kEpsK * kU32 * (P + F.O + F.r);
+  if (lane < NA) {
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    if constexpr (D == 3) {
+      if (lane < 3) {
+        ax = lane == 0 ? 1.f : 0.f;
+        ay = lane == 1 ? 1.f : 0.f;
+        az = lane == 2 ? 1.f : 0.f;
+      } else if (lane == 3) {
+        ax = nh[0];
+        ay = nh[1];
+        az = nh[2];
+      } else {
+        const int k = (lane - 4) / 3, i = (lane - 4) % 3;
+        float ex = 0.f, ey = 0.f, ez = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+          if (kk == k) {
+            const int kn = (kk + 1) % 3;
+            ex = V[3 * kn + 0] - V[3 * kk + 0];
+            ey = V[3 * kn + 1] - V[3 * kk + 1];
+            ez = V[3 * kn + 2] - V[3 * kk + 2];
+          }
+        if (i == 0) {
+          ax = 0.f;
+          ay = -ez;
+          az = ey;
+        } else if (i == 1) {
+          ax = ez;
+          ay = 0.f;
+          az = -ex;
+        } else {
+          ax = -ey;
+          ay = ex;
+          az = 0.f;
+        }
+      }
+    } else {
+      if (lane < 2) {
+        ax = lane == 0 ? 1.f : 0.f;
+        ay = lane == 1 ? 1.f : 0.f;
+      } else {
+        ax = -(V[3] - V[1]);
+        ay = V[2] - V[0];
+      }
+    }
+    const float A1 = fabsf(ax) + fabsf(ay) + fabsf(az);
+    float4 t = make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
+    if (A1 != 0.0f) {
+      float tmin = INFINITY, tmax = -INFINITY;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float s = D == 3 ? fmaf(p[k][2], az, fmaf(p[k][1], ay, p[k][0] * ax)) : fmaf(p[k][1], ay, p[k][0] * ax);
+        tmin = fminf(tmin, s);
+        tmax = fmaxf(tmax, s);
+      }
+      const float eps = scale * A1;
+      const float R = F.r * A1;
+      const float lo = tmin - R, hi = tmax + R;
+      t = make_float4(lo - eps, hi + eps, lo + eps, hi - eps);
+    }
+    S.t[lane] = t;
+  }
+  if (lane == 0) {
+    if constexpr (D == 3) {
+      float e[3][3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int k1 = (k + 1) % 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) e[k][c] = V[3 * k1 + c] - V[3 * k + c];
+      }
+      S.en[0] = make_float4(e[0][0], e[0][1], e[0][2], e[1][0]);
+      S.en[1] = make_float4(e[1][1], e[1][2], e[2][0], e[2][1]);
+      S.en[2] = make_float4(e[2][2], nh[0], nh[1], nh[2]);
+    } else {
+      S.e[0] = V[2] - V[0];
+      S.e[1] = V[3] - V[1];
+    }
+  }
+}
+
+constexpr int kMarkWarps = 4;  // warps per CTA of k_mark_faces
+constexpr int kMarkSlots = 64;  // blocks of a face's range looked up once per face (more: per cell)
+
+template <int D, int PRED>
+__global__ void __launch_bounds__(kMarkWarps * 32, 6) k_mark_faces(MarkArgs m) {
+  const RefineLevel& a = m.lv;
+  __shared__ Surv<D> s_surv[kMarkWarps];
+  __shared__ int32_t s_bi[kMarkWarps][kMarkSlots];    // block index of each slot of the range (-1: absent)
+  __shared__ uint64_t s_mk[kMarkWarps][kMarkSlots];   // its mask when the face started (skips marked cells)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  Surv<D>& S = s_surv[wid];
+  const GeomParams& P = a.g0;
+  const FastGeom g = fast_geom(P, a.level);
+  const float hf = g.h_hi;
+  const float inv_h = 1.0f / hf;
+  const int64_t nblk = launch_count(a.n_blocks, a.n_dev, a.err);
+  int ncell[3] = {1, 1, 1};
+#pragma unroll
+  for (int c = 0; c < D; ++c) ncell[c] = (4 * P.root[c]) << a.level;
+  // cell i meets the face's AABB [vmin, vmax] only if its test region does: box,
+  // origin + [i h - d, (i + 1) h + d]; point, its centre origin + (i + 1/2) h
+  // within [vmin - d, vmax + d]
+  constexpr bool kPoint = PRED == 1;
+  const float R2 = g.d * g.d;
+  WarpCounters wc;
+  unsigned long long n_tests = 0;
+  for (;;) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(a.work, (unsigned)kFaceBatch);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((int64_t)base >= a.nf) break;
+    for (int q = 0; q < kFaceBatch; ++q) {
+      const int64_t f = (int64_t)base + q;
+      if (f >= a.nf) break;
+      float V[D * D], nh[3] = {0.f, 0.f, 0.f};
+      if constexpr (D == 3) {
+        const float4* R = reinterpret_cast<const float4*>(m.rec + f);
+        const float4 r0 = __ldg(R), r1 = __ldg(R + 1), r2 = __ldg(R + 2);
+        V[0] = r0.x; V[1] = r0.y; V[2] = r0.z; V[3] = r0.w; V[4] = r1.x;
+        V[5] = r1.y; V[6] = r1.z; V[7] = r1.w; V[8] = r2.x;
+        nh[0] = r2.y; nh[1] = r2.z; nh[2] = r2.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) V[j] = __ldg(a.X + (int64_t)j * a.nf + f);
+      }
+      // cell range per axis: cells whose test region can meet the face's AABB
+      // (a superset: the margin covers the FP32 error of the cell coordinate)
+      int lo[3] = {0, 0, 0}, n[3] = {1, 1, 1};
+      BlockFrame<D> F;
+      float shift[3] = {0.f, 0.f, 0.f};
+      float O = 0.f;
+      bool empty = false;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        float vmin = V[c], vmax = V[c];
+#pragma unroll
+        for (int k = 1; k < D; ++k) {
+          vmin = fminf(vmin, V[D * k + c]);
+          vmax = fmaxf(vmax, V[D * k + c]);
+        }
+        const float margin = 1e-3f + 16.0f * kU32 * (fmaxf(fabsf(vmin), fabsf(vmax)) + fabsf(P.org_hi[c])) * inv_h;
+        const float xl = (vmin - P.org_hi[c] - g.d) * inv_h - (kPoint ? 0.5f : 1.0f);
+        const float xh = (vmax - P.org_hi[c] + g.d) * inv_h - (kPoint ? 0.5f : 0.0f);
+        if (!(xl <= xh)) empty = true;  // also a non-finite coordinate
+        const float tl = floorf(xl - margin), th = floorf(xh + margin);
+        const int il = tl < 0.f ? 0 : (tl > (float)(ncell[c] - 1) ? ncell[c] : (int)tl);
+        const int ih = th < 0.f ? -1 : (th > (float)(ncell[c] - 1) ? ncell[c] - 1 : (int)th);
+        if (ih < il) empty = true;
+        lo[c] = il;
+        n[c] = ih - il + 1;
+        float flo;
+        df_position(P.org_hi[c], P.org_lo[c], (float)il, g.h_hi, g.h_lo, F.Xb[c], flo);
+        shift[c] = flo;
+        F.cB[c] = 0.f;
+        O = fmaxf(O, (float)(n[c] + 1) * hf + 2.0f * fabsf(flo));
+      }
+      if (empty) continue;
+      F.h = hf;
+      F.r = fmaf(0.5f, hf, g.d);
+      F.rb = 0.f;
+      F.O = O;
+      wc.cand++;
+      __syncwarp();  // the previous face's tests are done with S
+      if constexpr (kPoint) {
+        if (lane == 0) setup_point<D>(V, nh, F, S);
+      } else {
+        setup_face_lanes<D>(V, nh, F, S, lane);
+      }
+      __syncwarp();
+      // the host keeps every range below 2^15 cells (largest face of the binning); a
+      // larger one here means inconsistent inputs: reported, not tested
+      const int64_t total = (int64_t)n[0] * n[1] * (D == 3 ? n[2] : 1);
+      if (total > (1 << 20)) {
+        if (lane == 0) atomicOr(a.err, ERR_OVERFLOW);
+        continue;
+      }
+      // index of the level's block with coordinates b, or -1 when the level does not have it
+      auto find = [&](const int* b) -> int64_t {
+        if (a.level == 0) {
+          const int64_t i = b[0] + (int64_t)P.root[0] * (b[1] + (int64_t)P.root[1] * b[2]);
+          return i < nblk ? i : -1;
+        }
+        return hash_find(m.keys, m.vals, m.hmask, block_key(b, D));
+      };
+      // the range's blocks: looked up once, one lane per block, when they fit the slots
+      int blo[3] = {0, 0, 0}, nbk[3] = {1, 1, 1};
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        blo[c] = lo[c] >> 2;
+        nbk[c] = ((lo[c] + n[c] - 1) >> 2) - blo[c] + 1;
+      }
+      const int nslot = nbk[0] * nbk[1] * nbk[2];
+      const bool slots = nslot <= kMarkSlots;
+      if (slots) {
+        for (int k = lane; k < nslot; k += 32) {
+          const int b[3] = {blo[0] + k % nbk[0], blo[1] + (k / nbk[0]) % nbk[1], blo[2] + k / (nbk[0] * nbk[1])};
+          const int64_t bi = find(b);
+          s_bi[wid][k] = (int32_t)bi;
+          s_mk[wid][k] = bi >= 0 ? a.mask[bi] : ~0ull;  // absent: every cell skipped
+        }
+        __syncwarp();
+      }
+      for (int j = lane; j < (int)total; j += 32) {
+        const int i0 = j % n[0], j1 = j / n[0];
+        const int i1 = D == 3 ? j1 % n[1] : j1, i2 = D == 3 ? j1 / n[1] : 0;
+        const int cell[3] = {lo[0] + i0, lo[1] + i1, D == 3 ? lo[2] + i2 : 0};
+        int b[3] = {cell[0] >> 2, cell[1] >> 2, D == 3 ? cell[2] >> 2 : 0};
+        const int local = (cell[0] & 3) | ((cell[1] & 3) << 2) | (D == 3 ? (cell[2] & 3) << 4 : 0);
+        const uint64_t bit = 1ull << local;
+        int64_t bi;
+        uint64_t mk;
+        if (slots) {
+          const int k = (b[0] - blo[0]) + nbk[0] * ((b[1] - blo[1]) + nbk[1] * (b[2] - blo[2]));
+          bi = s_bi[wid][k];
+          mk = s_mk[wid][k];
+        } else {
+          bi = find(b);
+          mk = bi >= 0 ? a.mask[bi] : ~0ull;
+        }
+        if (mk & bit) continue;  // absent block or already marked (a stale mask only costs a test)
+        ++n_tests;
+        const float l[3] = {(float)i0 + 0.5f, (float)i1 + 0.5f, (float)i2 + 0.5f};
+        float o[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < D; ++c) o[c] = fmaf(l[c], g.h_hi, fmaf(l[c], g.h_lo, shift[c]));
+        int t = kPoint ? point_test<D>(S, o, R2) : cell_test1<D>(S, o);
+        if (t == 2) {
+          // not certified in FP32: FP64, unless another face has marked the cell meanwhile
+          if (__ldcg(reinterpret_cast<const unsigned long long*>(a.mask + bi)) & bit) continue;
+          t = resolve_fp64<D>(a, 0u, (uint32_t)f, b, local, &wc.fb, &wc.band) ? 1 : 0;
+        }
+        if (t) {
+          atomicOr(reinterpret_cast<unsigned long long*>(a.mask + bi), (unsigned long long)bit);
+          a.flag[bi] = 1;
+        }
+      }
+    }
+  }
+  unsigned long long v[4] = {wc.fb, wc.band, wc.cand, n_tests};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  }
+  if (lane == 0) {
+    if (v[0]) atomicAdd(&a.counters[CNT_FALLBACK], v[0]);
+    if (v[1]) atomicAdd(&a.counters[CNT_BAND], v[1]);
+    if (v[2]) atomicAdd(&a.counters[CNT_FACE_SETUPS], v[2] / 32);  // every lane counted the same faces
+    if (v[3]) atomicAdd(&a.counters[CNT_FACE_TESTS], v[3]);
+  }
+}
+
 // Warps per SM kept resident: 32 (CTAs of `warps` warps).
 int grid_warps(int num_sms, int64_t n, int warps, bool persistent) {
   const int64_t cap = (int64_t)num_sms * (32 / warps > 0 ? 32 / warps : 1);
@@ -1092,6 +1428,24 @@ int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st) {
     mode == 2 ? go(k_adjacency<3, 2>) : (mode == 1 ? go(k_adjacency<3, 1>) : go(k_adjacency<3, 0>));
   else
     mode == 2 ? go(k_adjacency<2, 2>) : (mode == 1 ? go(k_adjacency<2, 1>) : go(k_adjacency<2, 0>));
+  return 1;
+}
+
+int launch_mark_faces(const MarkArgs& m, int num_sms, cudaStream_t st) {
+  if (m.lv.nf <= 0) return 0;
+  constexpr int kWarps = kMarkWarps;
+  int64_t need = (m.lv.nf + kFaceBatch - 1) / kFaceBatch;  // warps with work
+  int64_t g = (need + kWarps - 1) / kWarps;
+  const int64_t cap = (int64_t)num_sms * (32 / kWarps);
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  const int mode = m.lv.pred == 1 ? 1 : 0;
+  if (m.lv.dim == 3)
+    mode == 1 ? k_mark_faces<3, 1><<<(unsigned)g, kWarps * 32, 0, st>>>(m)
+              : k_mark_faces<3, 0><<<(unsigned)g, kWarps * 32, 0, st>>>(m);
+  else
+    mode == 1 ? k_mark_faces<2, 1><<<(unsigned)g, kWarps * 32, 0, st>>>(m)
+              : k_mark_faces<2, 0><<<(unsigned)g, kWarps * 32, 0, st>>>(m);
   return 1;
 }
 

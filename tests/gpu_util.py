@@ -24,7 +24,8 @@ def to_np(t, dtype=None):
     return a.view(dtype) if dtype is not None else a
 
 
-def run_gpu(w, *, B=None, n_levels=None, want_links=True, facelist=False, d_abs=None, d_rel=None, predicate=0):
+def run_gpu(w, *, B=None, n_levels=None, want_links=True, facelist=False, d_abs=None, d_rel=None, predicate=0,
+            face_pass=0, want_adjacency=True, root=None):
     """Whole CUDA pass for a workload; returns the AmrGeom and host copies of every output."""
     import torch
 
@@ -32,7 +33,7 @@ def run_gpu(w, *, B=None, n_levels=None, want_links=True, facelist=False, d_abs=
 
     B = w.bins if B is None else B
     n_levels = w.n_levels if n_levels is None else n_levels
-    g = AmrGeom(w.dim, (w.root,) * w.dim)
+    g = AmrGeom(w.dim, tuple(root) if root is not None else (w.root,) * w.dim)
     v = torch.from_numpy(w.verts).cuda()
     if facelist:
         g.load(torch.from_numpy(w.verts[w.idx]).cuda())
@@ -40,22 +41,24 @@ def run_gpu(w, *, B=None, n_levels=None, want_links=True, facelist=False, d_abs=
         g.load(v, torch.from_numpy(w.idx).cuda())
     bins = g.bin(B)
     res = g.refine(n_levels, w.d_abs if d_abs is None else d_abs, w.d_rel if d_rel is None else d_rel,
-                   w.lattice if want_links else 0, True, want_links, predicate=predicate)
+                   w.lattice if want_links else 0, want_adjacency or want_links, want_links, predicate=predicate,
+                   face_pass=face_pass)
     torch.cuda.synchronize()
     out = {"offsets": to_np(bins["offsets"], np.uint32), "ids": to_np(bins["ids"], np.uint32), "levels": []}
     for lv in res["levels"]:
         out["levels"].append({"blocks": to_np(lv["blocks"]), "mask": to_np(lv["mask"], np.uint64),
                               "flag": to_np(lv["flag"]),
                               "parent": None if lv["parent"] is None else to_np(lv["parent"])})
-    out["adj_cell"] = to_np(res["adj_cell"], np.uint32)
-    out["adj_off"] = to_np(res["adj_off"], np.uint32)
-    out["adj_ids"] = to_np(res["adj_ids"], np.uint32)
+    if want_adjacency or want_links:
+        out["adj_cell"] = to_np(res["adj_cell"], np.uint32)
+        out["adj_off"] = to_np(res["adj_off"], np.uint32)
+        out["adj_ids"] = to_np(res["adj_ids"], np.uint32)
     if want_links:
         out["link_cell"] = to_np(res["link_cell"], np.uint32)
         out["link_dir"] = to_np(res["link_dir"])
         out["link_q"] = to_np(res["link_q"])
         out["link_face"] = to_np(res["link_face"], np.uint32)
-    for k in ("n_fallback", "n_band", "n_candidates", "n_survivors"):
+    for k in ("n_fallback", "n_band", "n_candidates", "n_survivors", "n_face_setups", "n_face_tests"):
         out[k] = res[k]
     g.close()
     return out
