@@ -38,6 +38,7 @@ L2_FLUSH_BYTES = 512 << 20
 OPS_BLOCK_CANDIDATE = 120.0   # face setup up to the AABB cull (vertex offsets, edges, three box axes)
 OPS_BLOCK_SURVIVOR = 280.0    # the remaining ten axes of the block-level test for a survivor
 OPS_CELL_TEST = 80.0          # one cell against one survivor: 13 axes x (projection + interval test)
+OPS_FACE_SETUP = 400.0        # face-by-face marking, per (face, level): cell range, frame, 13 axis intervals
 OPS_LINK_FACE = 150.0         # per (adjacent cell, face): double-float offsets, plane offset, cross products
 OPS_LINK_DIR = 40.0           # per (adjacent cell, face, direction): den, three edge signs, t
 
@@ -177,6 +178,7 @@ def run_ours(args, rank, world, local):
     n_cand, n_surv = res["n_candidates"], res["n_survivors"]
     n_fb, n_band = res["n_fallback"], res["n_band"]
     n_lcand = res.get("n_link_candidates", 0)
+    n_fsetup, n_ftest = res.get("n_face_setups", 0), res.get("n_face_tests", 0)
     blocks = [int(lv["blocks"].shape[0]) for lv in res["levels"]]
     nnz = int(g.bin(w.bins)["ids"].shape[0])  # (face, bin) incidences
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -225,9 +227,12 @@ def run_ours(args, rank, world, local):
     g.timing(False)
     kern = {name: {"ms_per_step": v[0] / n_t, "launches_per_step": v[1] / n_t} for name, v in tk.items()}
     t_bin = sum(kern[k]["ms_per_step"] for k in ("bin_count", "bin_scan", "bin_scatter") if k in kern)
-    t_refine = kern.get("refine_level", {}).get("ms_per_step", float("nan"))
+    t_refine = kern.get("refine_level", {}).get("ms_per_step", 0.0)
+    t_mark = sum(kern[k]["ms_per_step"] for k in ("mark_faces", "block_hash") if k in kern)
     dom = max(kern.items(), key=lambda kv: kv[1]["ms_per_step"])
-    roof = roofline(dom[0], dom[1], w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks)
+    roof = roofline(dom[0], dom[1], w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks, n_fsetup, n_ftest)
+    NCe = 64 if w.dim == 3 else 16
+    n_tests = n_surv * NCe + n_ftest  # block-walk cell tests + face-by-face (face, cell) tests
     binning = bin_roofline(w, nnz, t_bin)
 
     line = {
@@ -240,9 +245,10 @@ def run_ours(args, rank, world, local):
                    "parallelism": f"replicas x{world}", "l2": "flushed between steps (512 MB write)",
                    "level_loop": "CUDA graph replay" if use_graph else "eager",
                    "fp64_fallbacks_per_step": n_fb, "band_cases_per_step": n_band,
-                   "block_face_candidates": n_cand, "block_survivors": n_surv, "link_candidates": n_lcand},
+                   "block_face_candidates": n_cand, "block_survivors": n_surv, "link_candidates": n_lcand,
+                   "face_pass_setups": n_fsetup, "face_pass_tests": n_ftest},
         "faces_binned_per_s": w.n_faces / (t_bin * 1e-3) if t_bin > 0 else None,
-        "cell_face_tests_per_s": (n_surv * (64 if w.dim == 3 else 16)) / (t_refine * 1e-3) if t_refine > 0 else None,
+        "cell_face_tests_per_s": n_tests / ((t_refine + t_mark) * 1e-3) if t_refine + t_mark > 0 else None,
         "binning": binning,
         "kernels_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in kern.items()},
         "wall_s": wall,
@@ -507,7 +513,7 @@ def run_paper_setups(args, dev, flush, bins=(1, 2, 4, 8, 16), reps=3):
     return out
 
 
-def roofline(name, k, w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks):
+def roofline(name, k, w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks, n_fsetup=0, n_ftest=0):
     """Roofline entry for the dominant kernel: algorithmic work per launch / average launch time."""
     hbm, src = measured_peaks()
     launches = max(k["launches_per_step"], 1e-9)
@@ -516,6 +522,11 @@ def roofline(name, k, w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks):
     alu_peak = N_SM * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12  # FP32-pipe Tops/s at the max SM clock
     if name == "refine_level":
         ops = (n_cand * OPS_BLOCK_CANDIDATE + n_surv * OPS_BLOCK_SURVIVOR + n_surv * NC * OPS_CELL_TEST) / launches
+        a = ops / t / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s (FP32 pipe)",
+                "frac": a / alu_peak, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2070 MHz"}
+    if name == "mark_faces":
+        ops = (n_fsetup * OPS_FACE_SETUP + n_ftest * OPS_CELL_TEST) / launches
         a = ops / t / 1e12
         return {"kernel": name, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s (FP32 pipe)",
                 "frac": a / alu_peak, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2070 MHz"}

@@ -369,13 +369,36 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
                            fabsf(A[0] * B[1]) + fabsf(A[1] * B[0]));
             }
             const float nn2 = sqrtf(nh[0] * nh[0] + nh[1] * nh[1] + nh[2] * nh[2]);
-            float4* W = s_pr[wid][lane].q;
-            W[0] = make_float4(C[0][0], C[0][1], C[0][2], C[1][0]);
-            W[1] = make_float4(C[1][1], C[1][2], C[2][0], C[2][1]);
-            W[2] = make_float4(C[2][2], M[0], M[1], M[2]);
-            W[3] = make_float4(num, eps_num, h32, nn2);
-            W[4] = make_float4(nh[0], nh[1], nh[2], __uint_as_float(f));
-            W[5] = make_float4(nl[0], nl[1], nl[2], __int_as_float(r));
+            // The two senses of a lattice line cross the face plane at one point, and the
+            // stage-2 edge functions of either sense are the same numbers (c enters with its
+            // sign twice).  Where they certify that point outside the face and the plane side
+            // is far from stage 2's uncertain band, stage 2 rejects both senses: drop the line.
+#pragma unroll
+            for (int l = 0; l < 9; ++l) {
+              if (!((cand >> (2 * l)) & 3u)) continue;
+              const int di = 2 * l + 1;
+              const float cx = dir_comp(kDirX, di), cy = dir_comp(kDirY, di), cz = dir_comp(kDirZ, di);
+              const float cl = fabsf(cx) + fabsf(cy) + fabsf(cz);
+              const float Dl = cx * nh[0] + cy * nh[1] + cz * nh[2];
+              if (!(fabsf(Dl) > 4.0e-5f * nn2)) continue;
+              const float sg = Dl > 0.f ? 1.f : -1.f;
+              bool out = false;
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                const float u = sg * (cx * C[k][0] + cy * C[k][1] + cz * C[k][2]);
+                if (u < -(8.0f * kU32 * cl * M[k])) out = true;
+              }
+              if (out) cand &= ~(3u << (2 * l));
+            }
+            if (cand) {
+              float4* W = s_pr[wid][lane].q;
+              W[0] = make_float4(C[0][0], C[0][1], C[0][2], C[1][0]);
+              W[1] = make_float4(C[1][1], C[1][2], C[2][0], C[2][1]);
+              W[2] = make_float4(C[2][2], M[0], M[1], M[2]);
+              W[3] = make_float4(num, eps_num, h32, nn2);
+              W[4] = make_float4(nh[0], nh[1], nh[2], __uint_as_float(f));
+              W[5] = make_float4(nl[0], nl[1], nl[2], __int_as_float(r));
+            }
           }
         }
       }
