@@ -1322,18 +1322,25 @@ __global__ void __launch_bounds__(kMarkWarps * 32, 6) k_mark_faces(MarkArgs m) {
       }
       const int nslot = nbk[0] * nbk[1] * nbk[2];
       const bool slots = nslot <= kMarkSlots;
+      // k = a + n b (0 <= a < n, k < 2^20): b = floor((k + 1/2) / n), exactly, from an FP32
+      // reciprocal (the quotient is at least 1/(2n) from an integer; the error is below 2^-21 k / n)
+      auto divn = [](int k, float inv) { return (int)(((float)k + 0.5f) * inv); };
+      const float inv_b0 = 1.0f / (float)nbk[0], inv_b1 = 1.0f / (float)nbk[1];
       if (slots) {
         for (int k = lane; k < nslot; k += 32) {
-          const int b[3] = {blo[0] + k % nbk[0], blo[1] + (k / nbk[0]) % nbk[1], blo[2] + k / (nbk[0] * nbk[1])};
+          const int k1 = divn(k, inv_b0), k2 = divn(k1, inv_b1);
+          const int b[3] = {blo[0] + k - k1 * nbk[0], blo[1] + k1 - k2 * nbk[1], blo[2] + k2};
           const int64_t bi = find(b);
           s_bi[wid][k] = (int32_t)bi;
           s_mk[wid][k] = bi >= 0 ? a.mask[bi] : ~0ull;  // absent: every cell skipped
         }
         __syncwarp();
       }
+      const float inv_n0 = 1.0f / (float)n[0], inv_n1 = 1.0f / (float)n[1];
       for (int j = lane; j < (int)total; j += 32) {
-        const int i0 = j % n[0], j1 = j / n[0];
-        const int i1 = D == 3 ? j1 % n[1] : j1, i2 = D == 3 ? j1 / n[1] : 0;
+        const int j1 = divn(j, inv_n0), j2 = D == 3 ? divn(j1, inv_n1) : 0;
+        const int i0 = j - j1 * n[0];
+        const int i1 = D == 3 ? j1 - j2 * n[1] : j1, i2 = j2;
         const int cell[3] = {lo[0] + i0, lo[1] + i1, D == 3 ? lo[2] + i2 : 0};
         int b[3] = {cell[0] >> 2, cell[1] >> 2, D == 3 ? cell[2] >> 2 : 0};
         const int local = (cell[0] & 3) | ((cell[1] & 3) << 2) | (D == 3 ? (cell[2] & 3) << 4 : 0);
