@@ -623,10 +623,11 @@ class AmrBatch:
         _bcheck(self.b, lib().amr_batch_set_bins(self.b, int(i), int(B)))
 
     def run(self, lattice=0, want_adjacency=True, want_links=None, use_graph=False, warps_per_cta=0,
-            predicate=AMR_PRED_BOX):
+            predicate=AMR_PRED_BOX, face_pass=AMR_FACE_PASS_AUTO):
         if want_links is None:
             want_links = lattice != 0
-        p = _params(1, 0.0, 1.0, lattice, want_adjacency, want_links, use_graph, warps_per_cta, predicate)
+        p = _params(1, 0.0, 1.0, lattice, want_adjacency, want_links, use_graph, warps_per_cta, predicate,
+                    face_pass=face_pass)
         r = amr_refine_result()
         _bcheck(self.b, lib().amr_batch_run(self.b, C.byref(p), C.byref(r)))
         self.want = (want_adjacency or want_links, want_links)

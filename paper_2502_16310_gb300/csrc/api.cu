@@ -118,8 +118,8 @@ struct amr_ctx {
   unsigned* d_work = nullptr;
   uint64_t* d_tot = nullptr;
   unsigned long long* d_fstat = nullptr;  // face-size statistics of the last binning (see FaceBinArgs)
-  double face_ext_max = INFINITY;         // largest face AABB side (domain units), from the last binning
-  double face_ext_mean = INFINITY;        // mean over faces of the largest AABB side / h0
+  double face_ext_max = INFINITY;         // largest face AABB side / h0 of its geometry, last binning
+  double face_ext_mean = INFINITY;        // mean over faces of that ratio
   uint64_t* d_scal = nullptr;
   void* h_pinned = nullptr;  // 2 KB
   amr_refine_result last{};
@@ -471,10 +471,8 @@ amr_status amr_bin_all(amr_ctx* ctx) {
     fa.sampled = 1;
     fa.sample_s = 0.5 * (ext / (double)ctx->geoms[0].B);
   }
-  if (!ctx->multi) {
-    fa.fstat = ctx->d_fstat;
-    CK(cudaMemsetAsync(ctx->d_fstat, 0, sizeof(unsigned long long) * 2, st));
-  }
+  fa.fstat = ctx->d_fstat;
+  CK(cudaMemsetAsync(ctx->d_fstat, 0, sizeof(unsigned long long) * 2, st));
   uint32_t* offsets = static_cast<uint32_t*>(ctx->offsets.p);
   timed(ctx, st, "bin_count", [&] { return launch_face_bins(fa, st); });
   timed(ctx, st, "bin_scan", [&] {
@@ -485,8 +483,7 @@ amr_status amr_bin_all(amr_ctx* ctx) {
   uint64_t tw[6] = {0, 0, 0, 0, 0, 0};
   TRY(read_back(ctx, st, &e, tw, 6));
   const uint64_t tot = tw[0];
-  ctx->face_ext_max = ctx->face_ext_mean = INFINITY;
-  if (!ctx->multi) {
+  {
     const uint32_t bits = (uint32_t)tw[4];
     float mx;
     std::memcpy(&mx, &bits, sizeof mx);
@@ -540,20 +537,37 @@ constexpr double kMaxFaceCells = 32768.0;
 // cells of the level (the block walk is cheaper once faces span many cells).
 constexpr double kAutoFaceCells = 1024.0;
 
-// Cells of level L in the range of a face whose largest AABB side is ext:
-// (ext + 2 d_L) / h_L + pad per axis (pad 4 bounds the rounding of the range
-// ends and the cell-box reach; pad 1 estimates the typical range).
+// Cells of level L in the range of a face whose largest AABB side is ext root
+// cells: (ext 2^L + 2 d_L / h_L + pad) per axis, with the largest d_L / h_L of
+// the geometries (pad 4 bounds the rounding of the range ends and the cell-box
+// reach; pad 1 estimates the typical range).
 double face_cells(const amr_ctx* ctx, int L, double ext, double pad) {
-  const GeomParams& g = ctx->geoms[0];
-  const double hL = std::ldexp(g.h0, -L), dL = g.d_abs + g.d_rel * hL;
-  return std::pow(ext / hL + 2.0 * dL / hL + pad, (double)ctx->dom.dim);
+  double dh = 0.0;
+  for (const auto& g : ctx->geoms) {
+    if (g.n_levels - 1 < L) continue;
+    const double hL = std::ldexp(g.h0, -L);
+    dh = std::max(dh, (g.d_abs + g.d_rel * hL) / hL);
+  }
+  return std::pow(ext * std::ldexp(1.0, L) + 2.0 * dh + pad, (double)ctx->dom.dim);
+}
+
+// Coordinate bits per axis of the block hash key: 21 for one geometry, else
+// what the geometry id leaves of 63 bits.
+int face_key_bits(const amr_ctx* ctx) {
+  if (!ctx->multi) return 21;
+  int gb = 1;
+  while (gb < 32 && ((size_t)1 << gb) < ctx->geoms.size()) ++gb;
+  return std::min(21, (63 - gb) / ctx->dom.dim);
 }
 
 bool face_pass_applies(const amr_ctx* ctx, const Plan& P, int L) {
-  if (ctx->multi || P.search != AMR_SEARCH_QUERY_BOX || (P.fin_at[L] && P.adjacency)) return false;
-  const GeomParams& g = ctx->geoms[0];
-  for (int c = 0; c < ctx->dom.dim; ++c)
-    if (((int64_t)g.root[c] << L) >= (1ll << 21)) return false;
+  if (P.search != AMR_SEARCH_QUERY_BOX) return false;
+  // some block of the level has the mask as its only output
+  if (!(P.cont_after[L] || !P.adjacency)) return false;
+  const int cb = face_key_bits(ctx);
+  for (const auto& g : ctx->geoms)
+    for (int c = 0; c < ctx->dom.dim; ++c)
+      if (((int64_t)g.root[c] << L) >= (1ll << cb)) return false;
   return face_cells(ctx, L, ctx->face_ext_max, 4.0) <= kMaxFaceCells;
 }
 
@@ -575,7 +589,7 @@ Plan make_plan(const amr_ctx* ctx, const amr_refine_params* p) {
   for (int L = 0; L < P.NL; ++L) {
     P.face_at[L] = p->face_pass != AMR_FACE_PASS_OFF && face_pass_applies(ctx, P, L);
     if (p->face_pass == AMR_FACE_PASS_AUTO && P.face_at[L])
-      P.face_at[L] = face_cells(ctx, L, ctx->face_ext_mean * ctx->geoms[0].h0, 1.0) <= kAutoFaceCells;
+      P.face_at[L] = face_cells(ctx, L, ctx->face_ext_mean, 1.0) <= kAutoFaceCells;
   }
   return P;
 }
@@ -687,6 +701,12 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
       MarkArgs m{};
       m.lv = a;
       m.rec = static_cast<const FaceRec3*>(ctx->frec.p);
+      m.face_gid = ctx->multi ? static_cast<const uint32_t*>(ctx->face_gid.p) : nullptr;
+      m.cb = face_key_bits(ctx);
+      m.skip_fin = P.fin_at[L] && P.adjacency;  // the walk below does the blocks that end here
+      // faces per work fetch: enough warps to fill the GPU (24 resident per SM)
+      const int64_t warps = (int64_t)ctx->num_sms * 24;
+      m.batch = (int)std::max<int64_t>(1, std::min<int64_t>(kFaceBatch, ctx->nf / (2 * warps)));
       if (L > 0) {
         const uint32_t slots = propagate_hash_slots(lb.cap);
         if (eager) {
@@ -697,12 +717,19 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
         m.vals = static_cast<const uint32_t*>(ctx->hvals.p);
         m.hmask = slots - 1;
         timed(ctx, st, "block_hash", [&] {
-          return launch_hash_build(D, a.blocks, lb.cap, a.n_dev, static_cast<unsigned long long*>(ctx->hkeys.p),
-                                   static_cast<uint32_t*>(ctx->hvals.p), slots, ctx->d_err, st);
+          return launch_hash_build(D, a.blocks, a.gid, m.cb, lb.cap, a.n_dev,
+                                   static_cast<unsigned long long*>(ctx->hkeys.p), static_cast<uint32_t*>(ctx->hvals.p),
+                                   slots, ctx->d_err, st);
         });
       }
-      timed(ctx, st, "mark_faces", [&] { return launch_mark_faces(m, ctx->num_sms, st); });
       if (a.blockcnt) CK(cudaMemsetAsync(a.blockcnt, 0, sizeof(uint64_t) * (size_t)(lb.cap > 0 ? lb.cap : 1), st));
+      timed(ctx, st, "mark_faces", [&] { return launch_mark_faces(m, ctx->num_sms, st); });
+      if (m.skip_fin) {
+        // blocks whose geometry ends here: the walk, which also records their faces
+        a.skip_mark_only = 1;
+        CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), st));
+        timed(ctx, st, "refine_level", [&] { return launch_refine(a, ctx->num_sms, st); });
+      }
     } else {
       timed(ctx, st, "refine_level", [&] { return launch_refine(a, ctx->num_sms, st); });
     }

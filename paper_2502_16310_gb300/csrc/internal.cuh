@@ -252,12 +252,16 @@ __device__ __forceinline__ uint64_t lookback_warp(uint64_t* state, long long til
 }
 
 // --- block-coordinate hash (open addressing, linear probing) --------------
-// Key: the block's coordinates, 21 bits per axis, plus one (0 marks an empty
-// slot); value: the block's index in its level's list.
-__device__ __forceinline__ unsigned long long block_key(const int32_t* c, int dim) {
-  unsigned long long k = 0;
-  for (int a = 0; a < dim; ++a) k = (k << 21) | (unsigned long long)((uint32_t)c[a] & 0x1fffffu);
+// Key: the geometry id above the block's coordinates, cb bits per axis, plus
+// one (0 marks an empty slot); value: the block's index in its level's list.
+__device__ __forceinline__ unsigned long long block_key_g(uint32_t gid, const int32_t* c, int dim, int cb) {
+  unsigned long long k = gid;
+  const uint32_t m = (1u << cb) - 1u;
+  for (int a = 0; a < dim; ++a) k = (k << cb) | (unsigned long long)((uint32_t)c[a] & m);
   return k + 1ull;
+}
+__device__ __forceinline__ unsigned long long block_key(const int32_t* c, int dim) {
+  return block_key_g(0u, c, dim, 21);
 }
 
 __device__ __forceinline__ uint32_t hash_slot(unsigned long long k, uint32_t mask) {
@@ -383,8 +387,9 @@ struct FaceBinArgs {
   uint32_t* count;
   int sampled;                 // 1: the paper's sampled-point membership (single geometry)
   double sample_s;             // sample spacing (half a bin length)
-  unsigned long long* fstat;   // nullable: [0] max over faces of the largest AABB side (FP32 bits),
-                               // [1] sum over faces of that side / h0, fixed point 2^-16 (zeroed before)
+  unsigned long long* fstat;   // nullable: [0] max over faces of the largest AABB side / h0 of the face's
+                               // geometry (FP32 bits), [1] the sum of that ratio, fixed point 2^-16
+                               // (zeroed before)
 };
 int launch_face_bins(const FaceBinArgs& a, cudaStream_t st);
 int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint32_t* frange, uint32_t* count,
@@ -446,22 +451,31 @@ struct RefineLevel {
   int pred;                    // adjacency predicate: 0 box (SAT of the inflated cell), 1 point (Alg. 1)
   int search;                  // candidates: 0 the bins of the inflated query box, 1 the cell's own bin (point only)
   int batch;                   // consecutive blocks a warp takes per work fetch (1..kMaxBatch)
+  int skip_mark_only;          // 1: blocks whose geometry continues below this level were marked face
+                               // by face; only the blocks whose geometry ends here are walked
 };
 constexpr int kMaxBatch = 8;
 int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st);
 
-// Face-centric marking of a level without adjacency output (single geometry,
-// box or point predicate, whole-domain search): lv.mask / lv.flag zeroed and
+// Face-by-face marking of the blocks of a level whose only output is the mask
+// (box or point predicate, whole-domain search): lv.mask / lv.flag zeroed and
 // lv.work zeroed before the launch; blocks found through the level-0 root
-// order or, deeper, the coordinate hash (keys / vals, hmask = slots - 1).
+// order or, deeper, the block hash (keys / vals, hmask = slots - 1, key bits cb).
+// With a geometry table (lv.table) every face reads its row through face_gid;
+// faces of geometries that ended above this level are skipped, and so are
+// those whose geometry ends here when skip_fin is set (the walk does those).
 struct MarkArgs {
   RefineLevel lv;
   const FaceRec3* rec;  // 3D face records (2D reads lv.X)
+  const uint32_t* face_gid;
   const unsigned long long* keys;
   const uint32_t* vals;
   uint32_t hmask;
+  int cb;
+  int skip_fin;
+  int batch;            // faces a warp takes per work fetch (1..kFaceBatch)
 };
-constexpr int kFaceBatch = 8;  // faces a warp takes per work fetch
+constexpr int kFaceBatch = 8;  // most faces a warp takes per work fetch
 int launch_mark_faces(const MarkArgs& m, int num_sms, cudaStream_t st);
 
 struct EmitArgs {
@@ -524,9 +538,11 @@ int launch_fluid_move(const uint32_t* link_cell, const uint8_t* link_dir, const 
 // through a hash of the block coordinates (keys/vals: `slots` entries, a power of
 // two >= 2 x capacity, from propagate_hash_slots; coordinates below 2^21).
 uint32_t propagate_hash_slots(int64_t cap);
-// Hash of a level's block coordinates -> index (the count from n_dev when given, bounded by cap).
-int launch_hash_build(int dim, const int32_t* blocks, int64_t cap, const uint64_t* n_dev, unsigned long long* keys,
-                      uint32_t* vals, uint32_t slots, unsigned* err, cudaStream_t st);
+// Hash of a level's blocks (geometry id, coordinates) -> index (the count from n_dev when given,
+// bounded by cap); gid nullable (single geometry), cb coordinate bits per axis of the key.
+int launch_hash_build(int dim, const int32_t* blocks, const uint32_t* gid, int cb, int64_t cap,
+                      const uint64_t* n_dev, unsigned long long* keys, uint32_t* vals, uint32_t slots,
+                      unsigned* err, cudaStream_t st);
 int launch_propagate(int dim, const int32_t* blocks, int64_t cap, const uint64_t* n_dev, uint8_t* flags,
                      int rounds, unsigned long long* keys, uint32_t* vals, uint32_t slots, unsigned* err,
                      cudaStream_t st);

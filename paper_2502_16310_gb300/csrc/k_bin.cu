@@ -227,9 +227,9 @@ __global__ void k_face_bins(FaceBinArgs a) {
       a.frange[(int64_t)c * a.nf + f] = (uint32_t)lo[c] | ((uint32_t)hi[c] << 16);
     }
     if (!(ext <= 3.0e38f)) ext = INFINITY;  // a non-finite coordinate
-    ext_max = fmaxf(ext_max, ext);
-    const float rel = ext / P.h0_hi * 65536.0f;
-    ext_sum += rel < 1.0e12f ? (unsigned long long)rel : 1000000000000ull;
+    const float rel = ext / P.h0_hi;        // in root cells of the face's own geometry
+    ext_max = fmaxf(ext_max, rel);
+    ext_sum += rel < 1.0e7f ? (unsigned long long)(rel * 65536.0f) : 655360000000ull;
     const int64_t B = P.B;
     if (a.sampled) {
       sampled_bins<D>(a.X, a.nf, f, P, a.sample_s, lo, hi, [&](int x, int y, int z) {

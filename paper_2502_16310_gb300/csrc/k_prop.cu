@@ -23,11 +23,12 @@ __device__ __forceinline__ int64_t count_of(int64_t cap, const uint64_t* n_dev) 
   return n < cap ? n : cap;
 }
 
-__global__ void k_hash_insert(int dim, const int32_t* __restrict__ blocks, int64_t cap, const uint64_t* n_dev,
-                              unsigned long long* keys, uint32_t* vals, uint32_t hmask, unsigned* err) {
+__global__ void k_hash_insert(int dim, const int32_t* __restrict__ blocks, const uint32_t* __restrict__ gid, int cb,
+                              int64_t cap, const uint64_t* n_dev, unsigned long long* keys, uint32_t* vals,
+                              uint32_t hmask, unsigned* err) {
   const int64_t n = count_of(cap, n_dev);
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long k = block_key(blocks + b * dim, dim);
+    const unsigned long long k = block_key_g(gid ? gid[b] : 0u, blocks + b * dim, dim, cb);
     uint32_t s = hash_slot(k, hmask);
     for (uint32_t probe = 0;; ++probe) {
       if (probe > hmask) {  // table full: cannot happen with twice the capacity
@@ -87,11 +88,12 @@ uint32_t propagate_hash_slots(int64_t cap) {
   return s;
 }
 
-int launch_hash_build(int dim, const int32_t* blocks, int64_t cap, const uint64_t* n_dev, unsigned long long* keys,
-                      uint32_t* vals, uint32_t slots, unsigned* err, cudaStream_t st) {
+int launch_hash_build(int dim, const int32_t* blocks, const uint32_t* gid, int cb, int64_t cap,
+                      const uint64_t* n_dev, unsigned long long* keys, uint32_t* vals, uint32_t slots,
+                      unsigned* err, cudaStream_t st) {
   if (cap <= 0) return 0;
   cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * slots, st);
-  k_hash_insert<<<grid_of(cap), kPThreads, 0, st>>>(dim, blocks, cap, n_dev, keys, vals, slots - 1, err);
+  k_hash_insert<<<grid_of(cap), kPThreads, 0, st>>>(dim, blocks, gid, cb, cap, n_dev, keys, vals, slots - 1, err);
   return 1;
 }
 
@@ -101,7 +103,7 @@ int launch_propagate(int dim, const int32_t* blocks, int64_t cap, const uint64_t
   if (rounds <= 0 || cap <= 0) return 0;
   cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * slots, st);
   const int g = grid_of(cap);
-  k_hash_insert<<<g, kPThreads, 0, st>>>(dim, blocks, cap, n_dev, keys, vals, slots - 1, err);
+  k_hash_insert<<<g, kPThreads, 0, st>>>(dim, blocks, nullptr, 21, cap, n_dev, keys, vals, slots - 1, err);
   for (int r = 0; r < rounds; ++r) {
     k_prop_mark<<<g, kPThreads, 0, st>>>(dim, blocks, cap, n_dev, flags, keys, vals, slots - 1);
     k_prop_commit<<<g, kPThreads, 0, st>>>(cap, n_dev, flags);
@@ -143,7 +145,8 @@ int launch_block_map(int dim, const int32_t* ref, int64_t n_ref, const int32_t* 
   cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * slots, st);
   int k = 0;
   if (n_ref > 0) {
-    k_hash_insert<<<grid_of(n_ref), kPThreads, 0, st>>>(dim, ref, n_ref, nullptr, keys, vals, slots - 1, err);
+    k_hash_insert<<<grid_of(n_ref), kPThreads, 0, st>>>(dim, ref, nullptr, 21, n_ref, nullptr, keys, vals, slots - 1,
+                                                        err);
     ++k;
   }
   k_map_lookup<<<grid_of(n_query), kPThreads, 0, st>>>(dim, query, n_query, keys, vals, slots - 1, out, n_missing);

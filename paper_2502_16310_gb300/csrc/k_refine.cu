@@ -749,6 +749,7 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
     const GeomParams& P = a.table ? a.table[gid] : a.g0;
     // per-cell face counts and survivor records only where the block's geometry ends here
     const bool fin = a.blockcnt && a.level == P.n_levels - 1;
+    if (a.skip_mark_only && !fin) continue;  // marked face by face
     uint32_t cnt0 = 0, cnt1 = 0;
     bool h0 = false, h1 = false;
     if (fin) {
@@ -1220,29 +1221,34 @@ __global__ void __launch_bounds__(kMarkWarps * 32, 6) k_mark_faces(MarkArgs m) {
   __shared__ uint64_t s_mk[kMarkWarps][kMarkSlots];   // its mask when the face started (skips marked cells)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   Surv<D>& S = s_surv[wid];
-  const GeomParams& P = a.g0;
-  const FastGeom g = fast_geom(P, a.level);
-  const float hf = g.h_hi;
-  const float inv_h = 1.0f / hf;
   const int64_t nblk = launch_count(a.n_blocks, a.n_dev, a.err);
-  int ncell[3] = {1, 1, 1};
-#pragma unroll
-  for (int c = 0; c < D; ++c) ncell[c] = (4 * P.root[c]) << a.level;
   // cell i meets the face's AABB [vmin, vmax] only if its test region does: box,
   // origin + [i h - d, (i + 1) h + d]; point, its centre origin + (i + 1/2) h
   // within [vmin - d, vmax + d]
   constexpr bool kPoint = PRED == 1;
-  const float R2 = g.d * g.d;
+  const int batch = m.batch > 0 ? (m.batch < kFaceBatch ? m.batch : kFaceBatch) : 1;
   WarpCounters wc;
   unsigned long long n_tests = 0;
   for (;;) {
     unsigned base = 0;
-    if (lane == 0) base = atomicAdd(a.work, (unsigned)kFaceBatch);
+    if (lane == 0) base = atomicAdd(a.work, (unsigned)batch);
     base = __shfl_sync(0xffffffffu, base, 0);
     if ((int64_t)base >= a.nf) break;
-    for (int q = 0; q < kFaceBatch; ++q) {
+    for (int q = 0; q < batch; ++q) {
       const int64_t f = (int64_t)base + q;
       if (f >= a.nf) break;
+      // the face's geometry: faces of geometries that ended above this level have nothing to mark;
+      // where the geometry ends here and the walk records this level, the walk marks its blocks
+      const uint32_t gid = a.table ? __ldg(m.face_gid + f) : 0u;
+      const GeomParams& P = a.table ? a.table[gid] : a.g0;
+      if (a.level > P.n_levels - 1 || (m.skip_fin && a.level == P.n_levels - 1)) continue;
+      const FastGeom g = fast_geom(P, a.level);
+      const float hf = g.h_hi;
+      const float inv_h = 1.0f / hf;
+      const float R2 = g.d * g.d;
+      int ncell[3] = {1, 1, 1};
+#pragma unroll
+      for (int c = 0; c < D; ++c) ncell[c] = (4 * P.root[c]) << a.level;
       float V[D * D], nh[3] = {0.f, 0.f, 0.f};
       if constexpr (D == 3) {
         const float4* R = reinterpret_cast<const float4*>(m.rec + f);
@@ -1308,10 +1314,10 @@ __global__ void __launch_bounds__(kMarkWarps * 32, 6) k_mark_faces(MarkArgs m) {
       // index of the level's block with coordinates b, or -1 when the level does not have it
       auto find = [&](const int* b) -> int64_t {
         if (a.level == 0) {
-          const int64_t i = b[0] + (int64_t)P.root[0] * (b[1] + (int64_t)P.root[1] * b[2]);
+          const int64_t i = P.root_base + b[0] + (int64_t)P.root[0] * (b[1] + (int64_t)P.root[1] * b[2]);
           return i < nblk ? i : -1;
         }
-        return hash_find(m.keys, m.vals, m.hmask, block_key(b, D));
+        return hash_find(m.keys, m.vals, m.hmask, block_key_g(gid, b, D, m.cb));
       };
       // the range's blocks: looked up once, one lane per block, when they fit the slots
       int blo[3] = {0, 0, 0}, nbk[3] = {1, 1, 1};
@@ -1365,7 +1371,7 @@ __global__ void __launch_bounds__(kMarkWarps * 32, 6) k_mark_faces(MarkArgs m) {
         if (t == 2) {
           // not certified in FP32: FP64, unless another face has marked the cell meanwhile
           if (__ldcg(reinterpret_cast<const unsigned long long*>(a.mask + bi)) & bit) continue;
-          t = resolve_fp64<D>(a, 0u, (uint32_t)f, b, local, &wc.fb, &wc.band) ? 1 : 0;
+          t = resolve_fp64<D>(a, gid, (uint32_t)f, b, local, &wc.fb, &wc.band) ? 1 : 0;
         }
         if (t) {
           atomicOr(reinterpret_cast<unsigned long long*>(a.mask + bi), (unsigned long long)bit);
@@ -1441,7 +1447,8 @@ int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st) {
 int launch_mark_faces(const MarkArgs& m, int num_sms, cudaStream_t st) {
   if (m.lv.nf <= 0) return 0;
   constexpr int kWarps = kMarkWarps;
-  int64_t need = (m.lv.nf + kFaceBatch - 1) / kFaceBatch;  // warps with work
+  const int batch = m.batch > 0 ? m.batch : kFaceBatch;
+  int64_t need = (m.lv.nf + batch - 1) / batch;  // warps with work
   int64_t g = (need + kWarps - 1) / kWarps;
   const int64_t cap = (int64_t)num_sms * (32 / kWarps);
   if (g > cap) g = cap;

@@ -14,7 +14,7 @@ from tests import gpu_util as U
 pytestmark = pytest.mark.gpu
 
 
-def _single(w, use_graph=False, repeats=1, B=None, warps=0):
+def _single(w, use_graph=False, repeats=1, B=None, warps=0, face_pass=0):
     import torch
 
     from paper_2502_16310_gb300 import AmrGeom
@@ -27,7 +27,7 @@ def _single(w, use_graph=False, repeats=1, B=None, warps=0):
         g.load(v, ix)
         g.bin(w.bins if B is None else B)
         res = g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=use_graph,
-                       warps_per_cta=warps)
+                       warps_per_cta=warps, face_pass=face_pass)
         outs.append(_host(res))
     launches = g.launch_count()
     g.close()
@@ -102,20 +102,23 @@ def _batch_set():
     return ws
 
 
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_matches_single(use_graph):
+@pytest.mark.parametrize("use_graph,face_pass", [(False, 1), (False, 2), (True, 0)])
+def test_batch_matches_single(use_graph, face_pass):
+    """Batched runs (block walk only, face by face wherever it applies, automatic) equal single-geometry
+    runs by the block walk alone, bit for bit."""
     import torch
 
     from paper_2502_16310_gb300 import AmrBatch
 
     ws = _batch_set()
-    singles = [_single(w)[0][0] for w in ws]
+    singles = [_single(w, face_pass=1)[0][0] for w in ws]
     b = AmrBatch(3)
     for w in ws:
         b.add(torch.from_numpy(w.verts).cuda(), torch.from_numpy(w.idx).cuda(), w.root, w.n_levels, w.d_abs, w.d_rel,
               w.bins)
     for rep in range(3 if use_graph else 1):
-        b.run(19, True, True, use_graph=use_graph)
+        r = b.run(19, True, True, use_graph=use_graph, face_pass=face_pass)
+        assert (r.n_face_setups > 0) == (face_pass != 1)
         for i, w in enumerate(ws):
             got = _host(b.view(i))
             _same(singles[i], got, f"geometry {i} rep {rep}")
