@@ -257,7 +257,7 @@ def run_ours(args, rank, world, local):
         "roofline": roof,
     }
     if not args.no_e2e:
-        line["e2e"] = run_e2e(g, w, args, dev)
+        line["e2e"] = run_e2e(w, args, dev)
     if not args.no_extras and world == 1:
         line["classify"] = run_classify(g, w, verts, idx, flush)
     g.close()
@@ -567,18 +567,27 @@ def bin_roofline(w, nnz, t_bin_ms):
             "peak_source": src}
 
 
-def run_e2e(g, w, args, dev):
-    """Same metric through the public API with host buffers: H2D of the inputs and D2H of every output."""
+def run_e2e(w, args, dev):
+    """Same metric through the public API with host buffers: every step uploads its inputs from pinned
+    host memory (inside amr_geom_load) and copies every output back to pinned host memory.  Two
+    contexts on two streams take the steps in turn, so a step's device-to-host copies overlap the next
+    step's upload and compute, as a user streaming results to the host would run it.  Host wall clock
+    from the first step of the timed region to the end of the last step's copies."""
     import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
 
     hv = torch.from_numpy(w.verts).pin_memory()
     hi = torch.from_numpy(w.idx).pin_memory()
     bi = hv.numel() * 4 + hi.numel() * 4
-    out_bufs = {}
-
     use_graph = not args.no_graph
+    ctxs, bufs = [], [{}, {}]
+    for _ in range(2):
+        with torch.cuda.stream(torch.cuda.Stream(device=dev)):
+            ctxs.append(AmrGeom(w.dim, (w.root,) * w.dim))
 
-    def step():
+    def step(k):
+        g, out_bufs = ctxs[k % 2], bufs[k % 2]
         g.load(hv, hi)
         g.bin(w.bins)
         res = g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=use_graph)
@@ -588,7 +597,7 @@ def run_e2e(g, w, args, dev):
             tensors += [lv["blocks"], lv["mask"]]
         tensors += [res["adj_cell"], res["adj_off"], res["adj_ids"], res["link_cell"], res["link_dir"],
                     res["link_q"], res["link_face"]]
-        with torch.cuda.stream(g.stream):  # the outputs' stream: no extra synchronisation
+        with torch.cuda.stream(g.stream):  # the outputs' stream: ordered after the refinement
             for j, t in enumerate(tensors):
                 buf = out_bufs.get(j)
                 if buf is None or buf.numel() < t.numel() or buf.dtype != t.dtype:
@@ -598,19 +607,22 @@ def run_e2e(g, w, args, dev):
                 nbytes += t.numel() * t.element_size()
         return res, nbytes
 
-    for _ in range(max(2, args.warmup)):
-        res, bo = step()
+    for k in range(2 * max(2, args.warmup)):
+        res, bo = step(k)
     torch.cuda.synchronize()
     cells = near_wall_cells(res)
-    K = max(3, args.steps // 2)
+    K = max(4, args.steps)
     t0 = time.perf_counter()
-    for _ in range(K):
-        res, bo = step()
-        torch.cuda.synchronize()
+    for k in range(K):
+        res, bo = step(k)
+    torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / K
+    for g in ctxs:
+        g.close()
     return {"value": cells / dt, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
             "ms_per_step": dt * 1e3, "level_loop": "CUDA graph replay" if use_graph else "eager",
-            "note": "host wall clock around load(host)->bin->refine->D2H of all outputs"}
+            "note": "host wall clock over K steps: load(pinned host) -> bin -> refine -> D2H of every output to "
+                    "pinned host; two contexts alternate so a step's D2H overlaps the next step's compute"}
 
 
 # ---------------------------------------------------------------------------

@@ -206,6 +206,8 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
   constexpr int NPR = D == 3 ? 32 : 1;
   __shared__ unsigned long long s_key[Q1][kLRows];
   __shared__ uint32_t s_off[kLRows + 1];
+  constexpr uint32_t kRowCap = 1024;    // pairs of a tile whose row is tabulated (more: binary search)
+  __shared__ uint8_t s_row[kRowCap];    // row of the tile's pair p0 + k
   __shared__ float s_o[2 * D][kLRows];
   __shared__ float s_h[kLRows];
   __shared__ PairRec s_pr[NW][NPR];
@@ -243,6 +245,11 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
       const int i = tid;
       s_off[i] = a.adj_off[first + (i < nr ? i : nr)];
       if (i == 0) s_off[kLRows] = a.adj_off[first + nr];
+      if (i < nr) {
+        // the row of each of this row's pairs (the first kRowCap pairs of the tile)
+        const uint32_t t0 = a.adj_off[first], e0 = a.adj_off[first + i], e1 = a.adj_off[first + i + 1];
+        for (uint32_t e = e0; e < e1 && e - t0 < kRowCap; ++e) s_row[e - t0] = (uint8_t)i;
+      }
 #pragma unroll
       for (int q = 0; q < Q1; ++q) s_key[q][i] = ~0ull;
       if (i < nr) {
@@ -274,15 +281,19 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
       int r = 0;
       uint32_t f = 0xffffffffu;
       if (e < p1) {
-        int lo = 0, hi = nr;  // s_off[lo] <= e < s_off[hi]
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (s_off[mid] <= e)
-            lo = mid;
-          else
-            hi = mid;
+        if (e - p0 < kRowCap) {
+          r = s_row[e - p0];
+        } else {
+          int lo = 0, hi = nr;  // s_off[lo] <= e < s_off[hi]
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= e)
+              lo = mid;
+            else
+              hi = mid;
+          }
+          r = lo;
         }
-        r = lo;
         f = a.adj_ids[e];
         if ((int64_t)f >= a.nf) f = 0xffffffffu;
       }
@@ -373,22 +384,26 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
             // stage-2 edge functions of either sense are the same numbers (c enters with its
             // sign twice).  Where they certify that point outside the face and the plane side
             // is far from stage 2's uncertain band, stage 2 rejects both senses: drop the line.
-#pragma unroll
-            for (int l = 0; l < 9; ++l) {
-              if (!((cand >> (2 * l)) & 3u)) continue;
-              const int di = 2 * l + 1;
-              const float cx = dir_comp(kDirX, di), cy = dir_comp(kDirY, di), cz = dir_comp(kDirZ, di);
-              const float cl = fabsf(cx) + fabsf(cy) + fabsf(cz);
-              const float Dl = cx * nh[0] + cy * nh[1] + cz * nh[2];
-              if (!(fabsf(Dl) > 4.0e-5f * nn2)) continue;
-              const float sg = Dl > 0.f ? 1.f : -1.f;
-              bool out = false;
+            // Line l's edge function k is c_l . C_k, a sum of at most two components of C_k,
+            // equal (up to the sign of a zero) to stage 2's value; all 9 lines at once.
+            {
+              const float Dl[9] = {nh[0], nh[1], nh[2], nh[0] + nh[1], nh[0] - nh[1], nh[0] + nh[2], nh[0] - nh[2],
+                                   nh[1] + nh[2], nh[1] - nh[2]};
+              uint32_t drop = 0;
 #pragma unroll
               for (int k = 0; k < 3; ++k) {
-                const float u = sg * (cx * C[k][0] + cy * C[k][1] + cz * C[k][2]);
-                if (u < -(8.0f * kU32 * cl * M[k])) out = true;
+                const float e1 = 8.0f * kU32 * 1.0f * M[k], e2 = 8.0f * kU32 * 2.0f * M[k];
+                const float U[9] = {C[k][0], C[k][1], C[k][2], C[k][0] + C[k][1], C[k][0] - C[k][1],
+                                    C[k][0] + C[k][2], C[k][0] - C[k][2], C[k][1] + C[k][2], C[k][1] - C[k][2]};
+#pragma unroll
+                for (int l = 0; l < 9; ++l) {
+                  const float u = Dl[l] > 0.f ? U[l] : -U[l];
+                  if (u < -(l < 3 ? e1 : e2)) drop |= 1u << l;
+                }
               }
-              if (out) cand &= ~(3u << (2 * l));
+#pragma unroll
+              for (int l = 0; l < 9; ++l)
+                if (((drop >> l) & 1u) && fabsf(Dl[l]) > 4.0e-5f * nn2) cand &= ~(3u << (2 * l));
             }
             if (cand) {
               float4* W = s_pr[wid][lane].q;
