@@ -20,6 +20,7 @@
 #include <cstring>
 #include <string>
 #include <algorithm>
+#include <initializer_list>
 #include <vector>
 
 #include "amrgeom.h"
@@ -122,6 +123,7 @@ struct amr_ctx {
   double face_ext_mean = INFINITY;        // mean over faces of that ratio
   uint64_t* d_scal = nullptr;
   void* h_pinned = nullptr;  // 2 KB
+  char* h_dev = nullptr;     // the same block as the device addresses it
   amr_refine_result last{};
   // graph mode
   cudaGraphExec_t gexec = nullptr;
@@ -251,6 +253,43 @@ void harvest_timing(amr_ctx* c) {
   c->pending.clear();
 }
 
+// Small transfers between the pinned host block and device memory run as one
+// tiny kernel (the block is mapped into the device's address space) instead of
+// on a copy engine, where they would queue behind any large copy that another
+// stream has in flight.  Up to four pieces of whole 32-bit words.
+struct WordCopy {
+  const uint32_t* src[4];
+  uint32_t* dst[4];
+  uint32_t words[4];
+};
+
+__global__ void k_copy_words(WordCopy c) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    for (uint32_t w = threadIdx.x; w < c.words[i]; w += blockDim.x) c.dst[i][w] = c.src[i][w];
+}
+
+struct Piece {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+
+amr_status small_copy(amr_ctx* ctx, cudaStream_t st, std::initializer_list<Piece> pieces) {
+  WordCopy c{};
+  int i = 0;
+  for (const Piece& p : pieces) {
+    c.dst[i] = static_cast<uint32_t*>(p.dst);
+    c.src[i] = static_cast<const uint32_t*>(p.src);
+    c.words[i] = (uint32_t)(p.bytes / 4);
+    ++i;
+  }
+  k_copy_words<<<1, 128, 0, st>>>(c);
+  ++ctx->launches;
+  CK(cudaGetLastError());
+  return AMR_OK;
+}
+
 amr_status sync_check(amr_ctx* ctx, cudaStream_t st) {
   CK(cudaStreamSynchronize(st));
   CK(cudaGetLastError());
@@ -261,8 +300,8 @@ amr_status sync_check(amr_ctx* ctx, cudaStream_t st) {
 // Copy the device error word and the first totals to pinned memory and wait.
 amr_status read_back(amr_ctx* ctx, cudaStream_t st, unsigned* err_out, uint64_t* tot_out, int n_tot) {
   char* h = static_cast<char*>(ctx->h_pinned);
-  CK(cudaMemcpyAsync(h, ctx->d_tot, sizeof(uint64_t) * 8, cudaMemcpyDeviceToHost, st));  // totals and face stats
-  CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TRY(small_copy(ctx, st, {{ctx->h_dev, ctx->d_tot, sizeof(uint64_t) * 8},  // totals and face stats
+                      {ctx->h_dev + 64, ctx->d_err, sizeof(unsigned)}}));
   TRY(sync_check(ctx, st));
   if (tot_out)
     for (int i = 0; i < n_tot; ++i) tot_out[i] = reinterpret_cast<uint64_t*>(h)[i];
@@ -273,8 +312,8 @@ amr_status read_back(amr_ctx* ctx, cudaStream_t st, unsigned* err_out, uint64_t*
 // One device scalar (u64) and the error word.
 amr_status read_scalar(amr_ctx* ctx, cudaStream_t st, int slot, uint64_t* v, unsigned* err_out) {
   char* h = static_cast<char*>(ctx->h_pinned);
-  CK(cudaMemcpyAsync(h + 128, ctx->d_scal + slot, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TRY(small_copy(ctx, st, {{ctx->h_dev + 128, ctx->d_scal + slot, sizeof(uint64_t)},
+                      {ctx->h_dev + 64, ctx->d_err, sizeof(unsigned)}}));
   TRY(sync_check(ctx, st));
   *v = *reinterpret_cast<uint64_t*>(h + 128);
   *err_out = *reinterpret_cast<unsigned*>(h + 64);
@@ -382,6 +421,9 @@ amr_status amr_ctx_init(amr_ctx* ctx) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 2048);
+  void* hd = nullptr;
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&hd, ctx->h_pinned, 0);
+  ctx->h_dev = static_cast<char*>(hd);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return AMR_ECUDA;
@@ -910,9 +952,9 @@ amr_status collect(amr_ctx* ctx, const Plan& P, cudaStream_t st, amr_refine_resu
   char* h = static_cast<char*>(ctx->h_pinned);
   // pinned layout: [0, 8 CNT_N) counters, 128 error word, 256 level pointers, 512 scalars
   static_assert(sizeof(unsigned long long) * CNT_N <= 128, "counters overlap the error word");
-  CK(cudaMemcpyAsync(h, ctx->counters, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h + 128, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h + 512, ctx->d_scal, sizeof(uint64_t) * SC_WORDS, cudaMemcpyDeviceToHost, st));
+  TRY(small_copy(ctx, st, {{ctx->h_dev, ctx->counters, sizeof(unsigned long long) * CNT_N},
+                      {ctx->h_dev + 128, ctx->d_err, sizeof(unsigned)},
+                      {ctx->h_dev + 512, ctx->d_scal, sizeof(uint64_t) * SC_WORDS}}));
   TRY(sync_check(ctx, st));
   const unsigned e = *reinterpret_cast<unsigned*>(h + 128);
   TRY(device_error(ctx, e));
@@ -956,7 +998,7 @@ amr_status collect(amr_ctx* ctx, const Plan& P, cudaStream_t st, amr_refine_resu
   TRY(ensure(ctx, ctx->lvl_ptrs, sizeof(void*) * AMR_MAX_LEVELS));
   const int32_t** hp = reinterpret_cast<const int32_t**>(h + 256);
   for (int L = 0; L < AMR_MAX_LEVELS; ++L) hp[L] = L < P.NL ? r.block_coords[L] : nullptr;
-  CK(cudaMemcpyAsync(ctx->lvl_ptrs.p, hp, sizeof(void*) * AMR_MAX_LEVELS, cudaMemcpyHostToDevice, st));
+  TRY(small_copy(ctx, st, {{ctx->lvl_ptrs.p, ctx->h_dev + 256, sizeof(void*) * AMR_MAX_LEVELS}}));
   CK(cudaStreamSynchronize(st));
   *out = r;
   return AMR_OK;
@@ -1380,8 +1422,8 @@ amr_status amr_classify_nodes(amr_ctx* ctx, const uint8_t** cell_solid, int64_t*
   timed(ctx, st, "classify", [&] { return launch_classify(a, st); });
   CK(cudaGetLastError());
   char* h = static_cast<char*>(ctx->h_pinned);
-  CK(cudaMemcpyAsync(h, ctx->counters + CNT_CLASS_FALLBACK, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  TRY(small_copy(ctx, st, {{ctx->h_dev, ctx->counters + CNT_CLASS_FALLBACK, sizeof(unsigned long long)},
+                      {ctx->h_dev + 64, ctx->d_err, sizeof(unsigned)}}));
   TRY(sync_check(ctx, st));
   TRY(device_error(ctx, *reinterpret_cast<unsigned*>(h + 64)));
   if (n_fallback) *n_fallback = (int64_t)*reinterpret_cast<unsigned long long*>(h);
@@ -1422,8 +1464,8 @@ amr_status amr_fluid_links(amr_ctx* ctx, amr_refine_result* out) {
     uint64_t kept = 0;
     unsigned e = 0;
     char* h = static_cast<char*>(ctx->h_pinned);
-    CK(cudaMemcpyAsync(h + 128, ctx->d_tot, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h + 64, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    TRY(small_copy(ctx, st, {{ctx->h_dev + 128, ctx->d_tot, sizeof(uint64_t)},
+                        {ctx->h_dev + 64, ctx->d_err, sizeof(unsigned)}}));
     TRY(sync_check(ctx, st));
     kept = *reinterpret_cast<uint64_t*>(h + 128);
     e = *reinterpret_cast<unsigned*>(h + 64);
@@ -1489,12 +1531,12 @@ amr_status amr_adapt_diff_get(amr_ctx* ctx, amr_adapt_diff* out) {
     d.old_to_new[L] = static_cast<const int32_t*>(lb.o2n.p);
   }
   CK(cudaGetLastError());
-  std::vector<unsigned long long> h(2 * (size_t)nl);
-  CK(cudaMemcpyAsync(h.data(), cnt, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost, st));
-  unsigned e = 0;
-  CK(cudaMemcpyAsync(&e, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  // counts at 1280 of the pinned block (2 x 16 levels at most), the error word at 64
+  TRY(small_copy(ctx, st, {{ctx->h_dev + 1280, cnt, sizeof(unsigned long long) * 2 * (size_t)nl},
+                      {ctx->h_dev + 64, ctx->d_err, sizeof(unsigned)}}));
   TRY(sync_check(ctx, st));
-  TRY(device_error(ctx, e));
+  const unsigned long long* h = reinterpret_cast<const unsigned long long*>(static_cast<char*>(ctx->h_pinned) + 1280);
+  TRY(device_error(ctx, *reinterpret_cast<const unsigned*>(static_cast<char*>(ctx->h_pinned) + 64)));
   for (int L = 0; L < nl; ++L) {
     d.n_created[L] = (int64_t)h[2 * L];
     d.n_removed[L] = (int64_t)h[2 * L + 1];
