@@ -67,7 +67,7 @@ struct GraphKey {
   uint64_t layout_gen = 0;
   int64_t nf = 0, n_geom = 0;
   int n_levels = 0, lattice = 0, adjacency = 0, links = 0, warps = 0, B = 0, pred = 0, search = 0, prop = 0;
-  uint32_t face_levels = 0;  // levels marked face by face
+  uint64_t face_levels = 0;  // signature of the per-geometry choice of face by face
   double d_abs = 0, d_rel = 0;
   bool operator==(const GraphKey& o) const {
     return layout_gen == o.layout_gen && nf == o.nf && n_geom == o.n_geom && n_levels == o.n_levels &&
@@ -118,9 +118,14 @@ struct amr_ctx {
   unsigned* d_err = nullptr;
   unsigned* d_work = nullptr;
   uint64_t* d_tot = nullptr;
-  unsigned long long* d_fstat = nullptr;  // face-size statistics of the last binning (see FaceBinArgs)
-  double face_ext_max = INFINITY;         // largest face AABB side / h0 of its geometry, last binning
-  double face_ext_mean = INFINITY;        // mean over faces of that ratio
+  DevBuf fstat;                           // per geometry: face-size statistics (see FaceBinArgs)
+  DevBuf spill;                           // per-warp spill of survivor records (once a call needed it)
+  bool want_spill = false;
+  void* h_stat = nullptr;                 // their mapped pinned copy (h_stat_dev as the device sees it)
+  char* h_stat_dev = nullptr;
+  size_t h_stat_cap = 0;
+  std::vector<double> face_ext_max;       // per geometry, last binning: largest face AABB side / h0
+  std::vector<double> face_ext_mean;      // and the mean of that ratio over its faces
   uint64_t* d_scal = nullptr;
   void* h_pinned = nullptr;  // 2 KB
   char* h_dev = nullptr;     // the same block as the device addresses it
@@ -435,7 +440,6 @@ amr_status amr_ctx_init(amr_ctx* ctx) {
   ctx->d_err = reinterpret_cast<unsigned*>(m + sizeof(unsigned long long) * CNT_N);
   ctx->d_work = ctx->d_err + 1;
   ctx->d_tot = reinterpret_cast<uint64_t*>(m + sizeof(unsigned long long) * CNT_N + 64);
-  ctx->d_fstat = reinterpret_cast<unsigned long long*>(ctx->d_tot + 4);  // within the totals' 64 bytes
   ctx->d_scal = static_cast<uint64_t*>(ctx->scal.p);
   cudaMemsetAsync(ctx->misc.p, 0, ctx->misc.cap, ctx->stream);
   cudaMemsetAsync(ctx->scal.p, 0, ctx->scal.cap, ctx->stream);
@@ -471,6 +475,9 @@ void amr_ctx_free(amr_ctx* ctx) {
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->h_stat) cudaFreeHost(ctx->h_stat);
+  release(ctx, ctx->fstat);
+  release(ctx, ctx->spill);
 }
 
 // Binning of every geometry of the table in one pass (count, scan, scatter).
@@ -513,24 +520,45 @@ amr_status amr_bin_all(amr_ctx* ctx) {
     fa.sampled = 1;
     fa.sample_s = 0.5 * (ext / (double)ctx->geoms[0].B);
   }
-  fa.fstat = ctx->d_fstat;
-  CK(cudaMemsetAsync(ctx->d_fstat, 0, sizeof(unsigned long long) * 2, st));
+  const size_t G = ctx->geoms.size(), stat_bytes = 2 * sizeof(unsigned long long) * G;
+  TRY(ensure_aux(ctx, ctx->fstat, stat_bytes));
+  if (ctx->h_stat_cap < stat_bytes) {
+    if (ctx->h_stat) cudaFreeHost(ctx->h_stat);
+    ctx->h_stat = nullptr;
+    ctx->h_stat_cap = 0;
+    void* hd = nullptr;
+    cudaError_t e1 = cudaMallocHost(&ctx->h_stat, stat_bytes);
+    if (e1 == cudaSuccess) e1 = cudaHostGetDevicePointer(&hd, ctx->h_stat, 0);
+    if (e1 != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, AMR_ENOMEM, "pinned allocation of %zu bytes failed", stat_bytes);
+    }
+    ctx->h_stat_dev = static_cast<char*>(hd);
+    ctx->h_stat_cap = stat_bytes;
+  }
+  fa.fstat = static_cast<unsigned long long*>(ctx->fstat.p);
+  CK(cudaMemsetAsync(ctx->fstat.p, 0, stat_bytes, st));
   uint32_t* offsets = static_cast<uint32_t*>(ctx->offsets.p);
   timed(ctx, st, "bin_count", [&] { return launch_face_bins(fa, st); });
   timed(ctx, st, "bin_scan", [&] {
     return launch_scan_u32(fa.count, offsets, nb, ctx->d_tot, ctx->scratch.p, ctx->d_err, st);
   });
   CK(cudaGetLastError());
+  TRY(small_copy(ctx, st, {{ctx->h_stat_dev, ctx->fstat.p, stat_bytes}}));
   unsigned e = 0;
-  uint64_t tw[6] = {0, 0, 0, 0, 0, 0};
-  TRY(read_back(ctx, st, &e, tw, 6));
-  const uint64_t tot = tw[0];
-  {
-    const uint32_t bits = (uint32_t)tw[4];
+  uint64_t tot = 0;
+  TRY(read_back(ctx, st, &e, &tot, 1));
+  ctx->face_ext_max.assign(G, 0.0);
+  ctx->face_ext_mean.assign(G, 0.0);
+  const unsigned long long* hs = static_cast<const unsigned long long*>(ctx->h_stat);
+  for (size_t g = 0; g < G; ++g) {
+    const int64_t f0 = ctx->multi ? ctx->geoms[g].face_base : 0;
+    const int64_t f1 = ctx->multi && g + 1 < G ? ctx->geoms[g + 1].face_base : nf;
+    const uint32_t bits = (uint32_t)hs[2 * g];
     float mx;
     std::memcpy(&mx, &bits, sizeof mx);
-    ctx->face_ext_max = nf > 0 ? (double)mx : 0.0;
-    ctx->face_ext_mean = nf > 0 ? (double)tw[5] / 65536.0 / (double)nf : 0.0;
+    ctx->face_ext_max[g] = f1 > f0 ? (double)mx : 0.0;
+    ctx->face_ext_mean[g] = f1 > f0 ? (double)hs[2 * g + 1] / 65536.0 / (double)(f1 - f0) : 0.0;
   }
   if (e) {
     ctx->count_clean = false;
@@ -564,32 +592,28 @@ struct Plan {
   int NL;                           // levels of the deepest geometry
   bool fin_at[AMR_MAX_LEVELS];      // some geometry ends at this level
   bool cont_after[AMR_MAX_LEVELS];  // some geometry continues below this level
-  bool face_at[AMR_MAX_LEVELS];     // level marked face by face (k_mark_faces) instead of by the block walk
+  bool face_at[AMR_MAX_LEVELS];     // some geometry's blocks of the level are marked face by face
+  bool walk_at[AMR_MAX_LEVELS];     // some geometry's blocks of the level are walked
   bool adjacency, links;
   int lattice, warps, pred, search, propagate;
   int64_t n_roots;
 };
 
-// Face-by-face marking applies to a level whose only output is the mask, for
-// one geometry with the whole-domain search, block coordinates that fit the
-// hash key and faces whose cell ranges stay small (the largest face of the last
-// binning, widened by d, covers at most kMaxFaceCells cells of the level).
+// Face-by-face marking applies to a geometry's blocks of a level whose only
+// output is the mask, with the whole-domain search, block coordinates that fit
+// the hash key and faces whose cell ranges stay small (the geometry's largest
+// face of the last binning, widened by d, covers at most kMaxFaceCells cells).
 constexpr double kMaxFaceCells = 32768.0;
-// Automatic choice: face by face where the mean face covers at most this many
-// cells of the level (the block walk is cheaper once faces span many cells).
+// Automatic choice: face by face where the geometry's mean face covers at most
+// this many cells of the level (the block walk is cheaper once faces span many cells).
 constexpr double kAutoFaceCells = 1024.0;
 
-// Cells of level L in the range of a face whose largest AABB side is ext root
-// cells: (ext 2^L + 2 d_L / h_L + pad) per axis, with the largest d_L / h_L of
-// the geometries (pad 4 bounds the rounding of the range ends and the cell-box
-// reach; pad 1 estimates the typical range).
-double face_cells(const amr_ctx* ctx, int L, double ext, double pad) {
-  double dh = 0.0;
-  for (const auto& g : ctx->geoms) {
-    if (g.n_levels - 1 < L) continue;
-    const double hL = std::ldexp(g.h0, -L);
-    dh = std::max(dh, (g.d_abs + g.d_rel * hL) / hL);
-  }
+// Cells of level L in the range of a face of geometry g whose largest AABB side
+// is ext root cells: (ext 2^L + 2 d_L / h_L + pad) per axis (pad 4 bounds the
+// rounding of the range ends and the cell-box reach; pad 1 estimates the typical range).
+double face_cells(const amr_ctx* ctx, const GeomParams& g, int L, double ext, double pad) {
+  const double hL = std::ldexp(g.h0, -L);
+  const double dh = (g.d_abs + g.d_rel * hL) / hL;
   return std::pow(ext * std::ldexp(1.0, L) + 2.0 * dh + pad, (double)ctx->dom.dim);
 }
 
@@ -600,17 +624,6 @@ int face_key_bits(const amr_ctx* ctx) {
   int gb = 1;
   while (gb < 32 && ((size_t)1 << gb) < ctx->geoms.size()) ++gb;
   return std::min(21, (63 - gb) / ctx->dom.dim);
-}
-
-bool face_pass_applies(const amr_ctx* ctx, const Plan& P, int L) {
-  if (P.search != AMR_SEARCH_QUERY_BOX) return false;
-  // some block of the level has the mask as its only output
-  if (!(P.cont_after[L] || !P.adjacency)) return false;
-  const int cb = face_key_bits(ctx);
-  for (const auto& g : ctx->geoms)
-    for (int c = 0; c < ctx->dom.dim; ++c)
-      if (((int64_t)g.root[c] << L) >= (1ll << cb)) return false;
-  return face_cells(ctx, L, ctx->face_ext_max, 4.0) <= kMaxFaceCells;
 }
 
 Plan make_plan(const amr_ctx* ctx, const amr_refine_params* p) {
@@ -628,12 +641,38 @@ Plan make_plan(const amr_ctx* ctx, const amr_refine_params* p) {
   P.search = p->search;
   P.propagate = p->propagate;
   for (const auto& g : ctx->geoms) P.n_roots += roots_of(g, ctx->dom.dim);
-  for (int L = 0; L < P.NL; ++L) {
-    P.face_at[L] = p->face_pass != AMR_FACE_PASS_OFF && face_pass_applies(ctx, P, L);
-    if (p->face_pass == AMR_FACE_PASS_AUTO && P.face_at[L])
-      P.face_at[L] = face_cells(ctx, L, ctx->face_ext_mean, 1.0) <= kAutoFaceCells;
-  }
   return P;
+}
+
+// Per geometry and level: face by face or the block walk (face_levels bits of
+// the geometry rows, uploaded with the table); the plan's face_at / walk_at say
+// which of the two launches a level needs.  Returns a signature of the choice.
+uint64_t assign_face_levels(amr_ctx* ctx, Plan& P, const amr_refine_params* p) {
+  const int cb = face_key_bits(ctx);
+  uint64_t sig = 1469598103934665603ull;
+  for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
+    GeomParams& g = ctx->geoms[gi];
+    uint32_t bits = 0;
+    const double emax = gi < ctx->face_ext_max.size() ? ctx->face_ext_max[gi] : INFINITY;
+    const double emean = gi < ctx->face_ext_mean.size() ? ctx->face_ext_mean[gi] : INFINITY;
+    for (int L = 0; L < g.n_levels && p->face_pass != AMR_FACE_PASS_OFF; ++L) {
+      bool ok = P.search == AMR_SEARCH_QUERY_BOX && (L < g.n_levels - 1 || !P.adjacency);
+      for (int c = 0; c < ctx->dom.dim && ok; ++c)
+        if (((int64_t)g.root[c] << L) >= (1ll << cb)) ok = false;
+      ok = ok && face_cells(ctx, g, L, emax, 4.0) <= kMaxFaceCells;
+      if (ok && p->face_pass == AMR_FACE_PASS_AUTO) ok = face_cells(ctx, g, L, emean, 1.0) <= kAutoFaceCells;
+      if (ok) bits |= 1u << L;
+    }
+    g.face_levels = bits;
+    for (int L = 0; L < g.n_levels; ++L) {
+      if ((bits >> L) & 1u)
+        P.face_at[L] = true;
+      else
+        P.walk_at[L] = true;
+    }
+    sig = (sig ^ bits) * 1099511628211ull;
+  }
+  return sig;
 }
 
 // Smallest d_L / h_L for which every face a link segment (length up to sqrt(2) h)
@@ -665,6 +704,7 @@ RefineLevel level_args(amr_ctx* ctx, const Plan& P, int L) {
     a.cap_recs = ctx->cap_recs;
     a.rec_count = ctx->d_scal + SC_REC + L;
     a.rec_desc = static_cast<uint64_t*>(ctx->lv[L].desc.p);
+    a.spill = ctx->want_spill ? static_cast<SurvRec*>(ctx->spill.p) : nullptr;
   }
   a.counters = ctx->counters;
   a.work = ctx->d_work;
@@ -732,6 +772,10 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
           TRY(ensure(ctx, ctx->recs, sizeof(SurvRec) * (size_t)want));
           ctx->cap_recs = want;
         }
+        // blocks with more survivor records than shared memory stages were seen: a spill area for
+        // every warp the refine launch can hold (32 per SM)
+        if (ctx->want_spill)
+          TRY(ensure(ctx, ctx->spill, sizeof(SurvRec) * (size_t)kSpillCap * 32 * (size_t)ctx->num_sms));
       }
     }
     RefineLevel a = level_args(ctx, P, L);
@@ -745,7 +789,6 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
       m.rec = static_cast<const FaceRec3*>(ctx->frec.p);
       m.face_gid = ctx->multi ? static_cast<const uint32_t*>(ctx->face_gid.p) : nullptr;
       m.cb = face_key_bits(ctx);
-      m.skip_fin = P.fin_at[L] && P.adjacency;  // the walk below does the blocks that end here
       // faces per work fetch: enough warps to fill the GPU (24 resident per SM)
       const int64_t warps = (int64_t)ctx->num_sms * 24;
       m.batch = (int)std::max<int64_t>(1, std::min<int64_t>(kFaceBatch, ctx->nf / (2 * warps)));
@@ -766,8 +809,8 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
       }
       if (a.blockcnt) CK(cudaMemsetAsync(a.blockcnt, 0, sizeof(uint64_t) * (size_t)(lb.cap > 0 ? lb.cap : 1), st));
       timed(ctx, st, "mark_faces", [&] { return launch_mark_faces(m, ctx->num_sms, st); });
-      if (m.skip_fin) {
-        // blocks whose geometry ends here: the walk, which also records their faces
+      if (P.walk_at[L]) {
+        // the other geometries' blocks: the walk (it also records the faces of those that end here)
         a.skip_mark_only = 1;
         CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), st));
         timed(ctx, st, "refine_level", [&] { return launch_refine(a, ctx->num_sms, st); });
@@ -960,6 +1003,8 @@ amr_status collect(amr_ctx* ctx, const Plan& P, cudaStream_t st, amr_refine_resu
   TRY(device_error(ctx, e));
   const uint64_t* sc = reinterpret_cast<const uint64_t*>(h + 512);
   const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(h);
+  // finest blocks whose records did not fit shared memory: keep their records from now on
+  if (cnt[CNT_BIG_BLOCKS] > 0 && !ctx->want_spill && P.adjacency) ctx->want_spill = true;
   amr_refine_result r{};
   r.n_levels = P.NL;
   for (int L = 0; L < P.NL; ++L) {
@@ -1009,7 +1054,11 @@ amr_status collect(amr_ctx* ctx, const Plan& P, cudaStream_t st, amr_refine_resu
 // Eager pass (or graph replay when the inputs match the captured graph), then
 // capture when graph mode is asked for.
 amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine_result* out) {
-  const Plan P = make_plan(ctx, prm);
+  Plan P = make_plan(ctx, prm);
+  const uint64_t face_sig = assign_face_levels(ctx, P, prm);
+  if (ctx->multi)  // the rows now carry the face_levels bits
+    CK(cudaMemcpyAsync(ctx->table.p, ctx->geoms.data(), sizeof(GeomParams) * ctx->geoms.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
   GraphKey key;
   key.layout_gen = ctx->layout_gen;
   key.nf = ctx->nf;
@@ -1025,8 +1074,7 @@ amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine
   key.pred = prm->predicate;
   key.search = prm->search;
   key.prop = prm->propagate;
-  for (int L = 0; L < P.NL; ++L)
-    if (P.face_at[L]) key.face_levels |= 1u << L;
+  key.face_levels = face_sig;
   const bool want_graph = prm->use_graph != 0;
   if (want_graph && ctx->gexec && ctx->gkey == key) {
     // replay on the graph stream, ordered after the caller's stream
@@ -1041,7 +1089,8 @@ amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine
     if (s == AMR_OK) {
       r.graph_replay = 1;
       *out = r;
-      if (ctx->want_recs > ctx->cap_recs) drop_graph(ctx);  // next call: eager pass with more staging
+      // next call: an eager pass with more record staging or the spill area
+      if (ctx->want_recs > ctx->cap_recs || (ctx->want_spill && !ctx->spill.p)) drop_graph(ctx);
       return AMR_OK;
     }
     if (s != AMR_EOVERFLOW) return s;

@@ -35,7 +35,8 @@ enum : int {
   CNT_CLASS_FALLBACK = 7,
   CNT_FACE_SETUPS = 8,  // faces set up by the face-centric marking
   CNT_FACE_TESTS = 9,   // (face, cell) tests run by it
-  CNT_N = 10,
+  CNT_BIG_BLOCKS = 10,  // finest blocks with more survivor records than shared memory stages
+  CNT_N = 11,
 };
 
 // Per-geometry parameters.  A launch may cover the blocks (faces) of many
@@ -53,7 +54,7 @@ struct GeomParams {
   int B;
   int n_levels;
   int root[3];
-  int pad;
+  uint32_t face_levels;  // bit L: this geometry's mask-only blocks of level L are marked face by face
   int64_t bin_base;
   int64_t root_base;   // first level-0 block of this geometry in the concatenated list
   int64_t face_base;   // first face of this geometry in the concatenated face arrays
@@ -387,9 +388,9 @@ struct FaceBinArgs {
   uint32_t* count;
   int sampled;                 // 1: the paper's sampled-point membership (single geometry)
   double sample_s;             // sample spacing (half a bin length)
-  unsigned long long* fstat;   // nullable: [0] max over faces of the largest AABB side / h0 of the face's
-                               // geometry (FP32 bits), [1] the sum of that ratio, fixed point 2^-16
-                               // (zeroed before)
+  unsigned long long* fstat;   // nullable, per geometry g: [2g] max over its faces of the largest AABB
+                               // side / h0 (FP32 bits), [2g + 1] the sum of that ratio, fixed point
+                               // 2^-16 (zeroed before)
 };
 int launch_face_bins(const FaceBinArgs& a, cudaStream_t st);
 int launch_face_bins(int dim, const float* X, int64_t nf, const BinGrid& g, uint32_t* frange, uint32_t* count,
@@ -420,7 +421,9 @@ struct __align__(16) SurvRec {
   uint32_t pad;
   uint64_t cells;
 };
-constexpr int kRecCap = 64;  // records kept per block; more send the block to a full re-walk
+constexpr int kRecCap = 64;     // records of a block staged in shared memory
+constexpr int kSpillCap = 960;  // more, up to this many, go to the warp's spill area (when given);
+                                // a block with still more records is walked again for its lists
 
 struct RefineLevel {
   int dim;
@@ -443,7 +446,8 @@ struct RefineLevel {
   SurvRec* recs;               // survivor records (nullable), capacity cap_recs
   int64_t cap_recs;
   uint64_t* rec_count;         // device: records handed out on this level
-  uint64_t* rec_desc;          // per block: offset << 8 | count, or ~0 (records incomplete)
+  uint64_t* rec_desc;          // per block: offset << 16 | count, or ~0 (records incomplete)
+  SurvRec* spill;              // nullable: kSpillCap records per warp of the launch (records past kRecCap)
   unsigned long long* counters;
   unsigned* work;              // dynamic work counter (zeroed before launch)
   unsigned* err;
@@ -451,8 +455,8 @@ struct RefineLevel {
   int pred;                    // adjacency predicate: 0 box (SAT of the inflated cell), 1 point (Alg. 1)
   int search;                  // candidates: 0 the bins of the inflated query box, 1 the cell's own bin (point only)
   int batch;                   // consecutive blocks a warp takes per work fetch (1..kMaxBatch)
-  int skip_mark_only;          // 1: blocks whose geometry continues below this level were marked face
-                               // by face; only the blocks whose geometry ends here are walked
+  int skip_mark_only;          // 1: blocks of geometries with this level's face_levels bit were marked
+                               // face by face; the walk takes only the others
 };
 constexpr int kMaxBatch = 8;
 int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st);
@@ -462,8 +466,7 @@ int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st);
 // lv.work zeroed before the launch; blocks found through the level-0 root
 // order or, deeper, the block hash (keys / vals, hmask = slots - 1, key bits cb).
 // With a geometry table (lv.table) every face reads its row through face_gid;
-// faces of geometries that ended above this level are skipped, and so are
-// those whose geometry ends here when skip_fin is set (the walk does those).
+// only faces whose geometry has this level's face_levels bit are marked.
 struct MarkArgs {
   RefineLevel lv;
   const FaceRec3* rec;  // 3D face records (2D reads lv.X)
@@ -472,7 +475,6 @@ struct MarkArgs {
   const uint32_t* vals;
   uint32_t hmask;
   int cb;
-  int skip_fin;
   int batch;            // faces a warp takes per work fetch (1..kFaceBatch)
 };
 constexpr int kFaceBatch = 8;  // most faces a warp takes per work fetch

@@ -206,50 +206,55 @@ __device__ void sampled_bins(const float* X, int64_t nf, int64_t f, const GeomPa
 // its own geometry) and one count per (face, bin) incidence.
 template <int D>
 __global__ void k_face_bins(FaceBinArgs a) {
-  float ext_max = 0.f;             // face-size statistics (the refine plans its marking from them)
-  unsigned long long ext_sum = 0;
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.nf; f += (int64_t)gridDim.x * blockDim.x) {
-    const GeomParams P = geom_row(a.g0, a.table, a.face_gid, f);
-    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    float ext = 0.f;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform trip count: lane i takes face f0 + i (the face-size statistics are reduced per warp)
+  for (int64_t f0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); f0 < a.nf; f0 += stride) {
+    const int64_t f = f0 + lane;
+    uint32_t gid = 0xffffffffu;  // no face: a group of its own
+    float rel = 0.f;
+    if (f < a.nf) {
+      gid = a.face_gid ? a.face_gid[f] : 0u;
+      const GeomParams P = geom_row(a.g0, a.table, a.face_gid, f);
+      int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+      float ext = 0.f;
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      float mn = a.X[(int64_t)c * a.nf + f], mx = mn;
+      for (int c = 0; c < D; ++c) {
+        float mn = a.X[(int64_t)c * a.nf + f], mx = mn;
 #pragma unroll
-      for (int k = 1; k < D; ++k) {
-        const float x = a.X[(int64_t)(k * D + c) * a.nf + f];
-        mn = fminf(mn, x);
-        mx = fmaxf(mx, x);
+        for (int k = 1; k < D; ++k) {
+          const float x = a.X[(int64_t)(k * D + c) * a.nf + f];
+          mn = fminf(mn, x);
+          mx = fmaxf(mx, x);
+        }
+        ext = fmaxf(ext, mx - mn);
+        lo[c] = bin_coord_fast(mn, P, c);
+        hi[c] = bin_coord_fast(mx, P, c);
+        a.frange[(int64_t)c * a.nf + f] = (uint32_t)lo[c] | ((uint32_t)hi[c] << 16);
       }
-      ext = fmaxf(ext, mx - mn);
-      lo[c] = bin_coord_fast(mn, P, c);
-      hi[c] = bin_coord_fast(mx, P, c);
-      a.frange[(int64_t)c * a.nf + f] = (uint32_t)lo[c] | ((uint32_t)hi[c] << 16);
+      if (!(ext <= 3.0e38f)) ext = INFINITY;  // a non-finite coordinate
+      rel = ext / P.h0_hi;                     // in root cells of the face's own geometry
+      const int64_t B = P.B;
+      if (a.sampled) {
+        sampled_bins<D>(a.X, a.nf, f, P, a.sample_s, lo, hi, [&](int x, int y, int z) {
+          atomicAdd(&a.count[P.bin_base + x + B * (y + B * (int64_t)z)], 1u);
+        });
+      } else {
+        for (int z = lo[2]; z <= hi[2]; ++z)
+          for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&a.count[P.bin_base + x + B * (y + B * (int64_t)z)], 1u);
+      }
     }
-    if (!(ext <= 3.0e38f)) ext = INFINITY;  // a non-finite coordinate
-    const float rel = ext / P.h0_hi;        // in root cells of the face's own geometry
-    ext_max = fmaxf(ext_max, rel);
-    ext_sum += rel < 1.0e7f ? (unsigned long long)(rel * 65536.0f) : 655360000000ull;
-    const int64_t B = P.B;
-    if (a.sampled) {
-      sampled_bins<D>(a.X, a.nf, f, P, a.sample_s, lo, hi, [&](int x, int y, int z) {
-        atomicAdd(&a.count[P.bin_base + x + B * (y + B * (int64_t)z)], 1u);
-      });
-      continue;
-    }
-    for (int z = lo[2]; z <= hi[2]; ++z)
-      for (int y = lo[1]; y <= hi[1]; ++y)
-        for (int x = lo[0]; x <= hi[0]; ++x) atomicAdd(&a.count[P.bin_base + x + B * (y + B * (int64_t)z)], 1u);
-  }
-  if (a.fstat) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ext_max = fmaxf(ext_max, __shfl_xor_sync(0xffffffffu, ext_max, o));
-      ext_sum += __shfl_xor_sync(0xffffffffu, ext_sum, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      if (ext_max > 0.f) atomicMax(a.fstat, (unsigned long long)__float_as_uint(ext_max));  // >= 0: bits order
-      if (ext_sum) atomicAdd(a.fstat + 1, ext_sum);
+    if (a.fstat) {
+      // per geometry: the largest ratio (non-negative FP32 bits order like the values) and the sum of
+      // the ratios in fixed point 2^-16 (each clamped to 2^10 root cells, so 32 of them fit 32 bits)
+      const unsigned grp = __match_any_sync(0xffffffffu, gid);
+      const uint32_t mx = __reduce_max_sync(grp, __float_as_uint(rel));
+      const uint32_t sm = __reduce_add_sync(grp, rel < 1024.0f ? (uint32_t)(rel * 65536.0f) : (1u << 26));
+      if (gid != 0xffffffffu && lane == __ffs(grp) - 1) {
+        if (mx) atomicMax(a.fstat + 2 * (int64_t)gid, (unsigned long long)mx);
+        if (sm) atomicAdd(a.fstat + 2 * (int64_t)gid + 1, (unsigned long long)sm);
+      }
     }
   }
 }

@@ -424,7 +424,7 @@ __device__ __forceinline__ int point_test(const Surv<D>& S, const float* o, floa
 }
 
 struct WarpCounters {
-  unsigned long long fb = 0, band = 0, cand = 0, surv = 0;
+  unsigned long long fb = 0, band = 0, cand = 0, surv = 0, big = 0;
 };
 
 template <int D>
@@ -705,6 +705,29 @@ __device__ __forceinline__ void walk_block(const RefineLevel& a, const GeomParam
   }
 }
 
+// One survivor record past the shared-memory stage, into the warp's spill area
+// (out of line: it is rare, and the walk's registers stay with the common case).
+// The area of the calling warp: kSpillCap records per warp of the launch.
+__device__ __forceinline__ SurvRec* warp_spill(SurvRec* spill) {
+  return spill + ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kSpillCap;
+}
+
+__device__ __noinline__ void spill_record(SurvRec* spill, uint32_t i, uint32_t face, uint64_t cells) {
+  SurvRec r;
+  r.face = face;
+  r.pad = 0u;
+  r.cells = cells;
+  warp_spill(spill)[i] = r;
+}
+
+// The block's K survivor records (staged in shared memory, past kRecCap in the
+// warp's spill area) into a contiguous range of the level's record array, and
+// its descriptor: offset << 16 | K, 0 for none, ~0 when they are incomplete (the
+// adjacency pass then walks the block again).  Whole warp.
+template <int D>
+__device__ __forceinline__ void store_records(const RefineLevel& a, WarpSmem<D>& sm, uint32_t K, unsigned blk,
+                                              int lane);
+
 // Block count of a launch: from device memory when given (bounded by the
 // capacity; an overflow is reported), else the host count.
 __device__ __forceinline__ int64_t launch_count(int64_t n, const uint64_t* n_dev, unsigned* err) {
@@ -715,6 +738,34 @@ __device__ __forceinline__ int64_t launch_count(int64_t n, const uint64_t* n_dev
     return n;
   }
   return (int64_t)nd;
+}
+
+template <int D>
+__device__ __forceinline__ void store_records(const RefineLevel& a, WarpSmem<D>& sm, uint32_t K, unsigned blk,
+                                              int lane) {
+  __syncwarp();  // the staged and spilled records are visible to the whole warp
+  const uint32_t kmax = (uint32_t)kRecCap + (a.spill ? (uint32_t)kSpillCap : 0u);
+  uint64_t base = ~0ull;
+  if (K > 0 && K <= kmax) {
+    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(a.rec_count), (unsigned long long)K);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((int64_t)(base + K) > a.cap_recs) base = ~0ull;
+  }
+  if (base != ~0ull) {
+    for (uint32_t i = lane; i < K; i += 32) {
+      SurvRec r;
+      if (i < (uint32_t)kRecCap) {
+        r.face = sm.rf[i];
+        r.pad = 0u;
+        r.cells = sm.rm[i];
+      } else {
+        r = warp_spill(a.spill)[i - kRecCap];
+      }
+      a.recs[base + i] = r;
+    }
+  }
+  if (lane == 0) a.rec_desc[blk] = K == 0 ? 0ull : (base == ~0ull ? ~0ull : (base << 16) | K);
+  __syncwarp();
 }
 
 template <int D, int PRED>
@@ -749,11 +800,11 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
     const GeomParams& P = a.table ? a.table[gid] : a.g0;
     // per-cell face counts and survivor records only where the block's geometry ends here
     const bool fin = a.blockcnt && a.level == P.n_levels - 1;
-    if (a.skip_mark_only && !fin) continue;  // marked face by face
+    if (a.skip_mark_only && ((P.face_levels >> a.level) & 1u)) continue;  // marked face by face
     uint32_t cnt0 = 0, cnt1 = 0;
     bool h0 = false, h1 = false;
     if (fin) {
-      uint32_t K = 0;  // records of this block (warp-uniform)
+      uint32_t K = 0;  // records of this block (warp-uniform); past kRecCap into the warp's spill area
       walk_block<D, PRED, false>(a, P, gid, b, sm, phase, lane, wc, h0, h1, [&](uint32_t f, bool r0, bool r1) {
         cnt0 += r0 ? 1u : 0u;
         cnt1 += r1 ? 1u : 0u;
@@ -761,33 +812,21 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
           const uint64_t cm = (uint64_t)__ballot_sync(0xffffffffu, r0) |
                               ((uint64_t)__ballot_sync(0xffffffffu, r1) << 32);
           if (cm) {
-            if (K < (uint32_t)kRecCap && lane == 0) {
-              sm.rf[K] = f;
-              sm.rm[K] = cm;
+            if (lane == 0) {
+              if (K < (uint32_t)kRecCap) {
+                sm.rf[K] = f;
+                sm.rm[K] = cm;
+              } else if (a.spill && K < (uint32_t)(kRecCap + kSpillCap)) {
+                spill_record(a.spill, K - kRecCap, f, cm);
+              }
             }
             ++K;
           }
         }
       });
       if (a.recs) {
-        __syncwarp();
-        uint64_t base = ~0ull;
-        if (K > 0 && K <= (uint32_t)kRecCap) {
-          if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(a.rec_count), (unsigned long long)K);
-          base = __shfl_sync(0xffffffffu, base, 0);
-          if ((int64_t)(base + K) > a.cap_recs) base = ~0ull;
-        }
-        if (base != ~0ull) {
-          for (uint32_t i = lane; i < K; i += 32) {
-            SurvRec r;
-            r.face = sm.rf[i];
-            r.pad = 0u;
-            r.cells = sm.rm[i];
-            a.recs[base + i] = r;
-          }
-        }
-        if (lane == 0) a.rec_desc[blk] = K == 0 ? 0ull : (base == ~0ull ? ~0ull : (base << 8) | K);
-        __syncwarp();
+        if (K > (uint32_t)kRecCap) wc.big += 1;
+        store_records<D>(a, sm, K, blk, lane);
       }
     } else {
       walk_block<D, PRED, true>(a, P, gid, b, sm, phase, lane, wc, h0, h1, [](uint32_t, bool, bool) {});
@@ -815,9 +854,9 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
   }
   }
   // flush warp counters
-  unsigned long long v[4] = {wc.fb, wc.band, wc.cand, wc.surv};
+  unsigned long long v[5] = {wc.fb, wc.band, wc.cand, wc.surv, wc.big};
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 5; ++i) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
   }
@@ -826,7 +865,102 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
     if (v[1]) atomicAdd(&a.counters[CNT_BAND], v[1]);
     atomicAdd(&a.counters[CNT_CANDIDATES], v[2]);       // per-lane counts
     atomicAdd(&a.counters[CNT_SURVIVORS], v[3] / 32);   // every lane counted the same survivors
+    if (v[4]) atomicAdd(&a.counters[CNT_BIG_BLOCKS], v[4] / 32);
   }
+}
+
+// Ascending sort of P keys in shared memory (P a power of two; pad the tail
+// with ~0), with a 64-bit payload per key when pay is given, by the whole warp:
+// the bitonic network, one compare-exchange per lane and pair of each stage.
+__device__ __noinline__ void warp_bitonic(uint32_t* k, uint64_t* pay, uint32_t P, int lane) {
+  for (uint32_t s = 2; s <= P; s <<= 1)
+    for (uint32_t j = s >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = (uint32_t)lane; i < P; i += 32) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const bool up = (i & s) == 0;
+          const uint32_t x = k[i], y = k[l];
+          if (up ? x > y : x < y) {
+            k[i] = y;
+            k[l] = x;
+            if (pay) {
+              const uint64_t t = pay[i];
+              pay[i] = pay[l];
+              pay[l] = t;
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+}
+
+// Ascending face ids in each of a block's cell lists (cell c's count and offset
+// held by lane c, or lane c - 32 in n1 / off1): the warp sorts one list at a time
+// in the shared memory at sf (room for cap keys); a longer list is sorted in
+// place by one lane.  Out of line: only blocks walked again need it.
+__device__ __noinline__ void sort_cell_lists(uint32_t* adj_ids, int NC, uint32_t n0, uint32_t n1, uint64_t off0,
+                                             uint64_t off1, uint32_t* sf, uint32_t cap, int lane) {
+  for (int c = 0; c < NC; ++c) {
+    const uint32_t cnt = c < 32 ? __shfl_sync(0xffffffffu, n0, c) : __shfl_sync(0xffffffffu, n1, c - 32);
+    const uint64_t off = c < 32 ? __shfl_sync(0xffffffffu, off0, c) : __shfl_sync(0xffffffffu, off1, c - 32);
+    if (cnt <= 1) continue;
+    uint32_t* L = adj_ids + off;
+    if (cnt <= cap) {
+      uint32_t P = 32;
+      while (P < cnt) P <<= 1;
+      for (uint32_t i = lane; i < P; i += 32) sf[i] = i < cnt ? L[i] : 0xffffffffu;
+      __syncwarp();
+      warp_bitonic(sf, nullptr, P, lane);
+      for (uint32_t i = lane; i < cnt; i += 32) L[i] = sf[i];
+      __syncwarp();
+    } else if (lane == 0) {
+      for (uint32_t i = 1; i < cnt; ++i) {
+        const uint32_t v = L[i];
+        uint32_t k = i;
+        while (k > 0 && L[k - 1] > v) {
+          L[k] = L[k - 1];
+          --k;
+        }
+        L[k] = v;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// A block's K survivor records sorted by face id into shared memory at sf (the
+// face ids; the cell masks follow them, returned), by the whole warp.
+__device__ __noinline__ const uint64_t* sort_records(const SurvRec* recs, uint32_t K, uint32_t* sf, int lane) {
+  uint32_t P = 64;
+  while (P < K) P <<= 1;
+  uint64_t* sk = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(sf) + 4 * P);
+  for (uint32_t i = lane; i < P; i += 32) {
+    if (i < K) {
+      const SurvRec r = recs[i];
+      sf[i] = r.face;
+      sk[i] = r.cells;
+    } else {
+      sf[i] = 0xffffffffu;
+      sk[i] = 0ull;
+    }
+  }
+  __syncwarp();
+  warp_bitonic(sf, sk, P, lane);
+  return sk;
+}
+
+// Shared memory of a warp that a sort may use: the survivor data and the entry
+// buffers (not the mbarriers that follow them).
+template <int D>
+__host__ __device__ constexpr uint32_t sort_region_bytes() {
+  return (uint32_t)(sizeof(Surv<D>) * 32 + sizeof(typename EntryT<D>::type) * 64);
+}
+// Largest power of two P with P keys (and P payloads of 8 bytes) in the region.
+__host__ __device__ constexpr uint32_t pow2_floor(uint32_t x) {
+  uint32_t p = 1;
+  while (p * 2 <= x) p *= 2;
+  return p;
 }
 
 // Emit the adjacent-face lists of the blocks whose geometry ends at this
@@ -921,11 +1055,28 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
       }
     };
     const uint64_t desc = a.lv.recs ? a.lv.rec_desc[blk] : ~0ull;
-    if (desc != ~0ull) {
+    constexpr uint32_t kSortRecs = pow2_floor(sort_region_bytes<D>() / 12);  // key + payload per record
+    constexpr uint32_t kSortKeys = pow2_floor(sort_region_bytes<D>() / 4);
+    if (desc != ~0ull && (uint32_t)(desc & 0xffffu) > (uint32_t)kRecCap &&
+        (uint32_t)(desc & 0xffffu) <= kSortRecs) {
+      // many records: sort them by face id in shared memory, then list the cells' faces in that order
+      const uint32_t K = (uint32_t)(desc & 0xffffu);
+      const uint64_t r0 = desc >> 16;
+      uint32_t* sf = reinterpret_cast<uint32_t*>(&sm);
+      const uint64_t* sk = sort_records(a.lv.recs + r0, K, sf, lane);
+      for (uint32_t j = 0; j < K; ++j) {
+        const uint64_t mj = sk[j];
+        put(lane < NC && ((mj >> lane) & 1ull), D == 3 && ((mj >> (lane + 32)) & 1ull), sf[j]);
+      }
+      __syncwarp();
+      if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
+      continue;
+    }
+    if (desc != ~0ull && (uint32_t)(desc & 0xffffu) <= (uint32_t)kRecCap) {
       // the refine pass left this block's surviving faces with their cell masks:
       // rank them by face id, then every lane lists its cells' faces in that order
-      const uint32_t K = (uint32_t)(desc & 0xffu);
-      const uint64_t r0 = desc >> 8;
+      const uint32_t K = (uint32_t)(desc & 0xffffu);
+      const uint64_t r0 = desc >> 16;
       uint32_t f[2] = {0xffffffffu, 0xffffffffu};
       uint64_t cm[2] = {0ull, 0ull};
 #pragma unroll
@@ -967,21 +1118,9 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
     walk_block<D, PRED, false>(a.lv, P, gid, b, sm, phase, lane, wc, h0, h1,
                          [&](uint32_t fc, bool r0, bool r1) { put(r0, r1, fc); });
     if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
-    if (!can0 || !can1) continue;
-    // ascending face ids per cell (lists are short: insertion sort in place)
-    for (int s = 0; s < 2; ++s) {
-      const uint32_t cnt = s == 0 ? n0 : n1;
-      uint32_t* L = a.adj_ids + (s == 0 ? off0 : off1);
-      for (uint32_t i = 1; i < cnt; ++i) {
-        const uint32_t v = L[i];
-        uint32_t k = i;
-        while (k > 0 && L[k - 1] > v) {
-          L[k] = L[k - 1];
-          --k;
-        }
-        L[k] = v;
-      }
-    }
+    if (!__all_sync(0xffffffffu, can0 && can1)) continue;  // lists beyond the capacity (reported)
+    // ascending face ids per cell
+    sort_cell_lists(a.adj_ids, NC, n0, n1, off0, off1, reinterpret_cast<uint32_t*>(&sm), kSortKeys, lane);
   }
   }
 }
@@ -1237,11 +1376,11 @@ __global__ void __launch_bounds__(kMarkWarps * 32, 6) k_mark_faces(MarkArgs m) {
     for (int q = 0; q < batch; ++q) {
       const int64_t f = (int64_t)base + q;
       if (f >= a.nf) break;
-      // the face's geometry: faces of geometries that ended above this level have nothing to mark;
-      // where the geometry ends here and the walk records this level, the walk marks its blocks
+      // the face's geometry: only geometries marked face by face on this level (their blocks of the
+      // level have the mask as the only output; the walk does the others)
       const uint32_t gid = a.table ? __ldg(m.face_gid + f) : 0u;
       const GeomParams& P = a.table ? a.table[gid] : a.g0;
-      if (a.level > P.n_levels - 1 || (m.skip_fin && a.level == P.n_levels - 1)) continue;
+      if (!((P.face_levels >> a.level) & 1u)) continue;
       const FastGeom g = fast_geom(P, a.level);
       const float hf = g.h_hi;
       const float inv_h = 1.0f / hf;
