@@ -327,6 +327,36 @@ class _DevArray:
                                          "data": (int(ptr or 0), False), "version": 3, "strides": None}
 
 
+class _Deferred:
+    """A value built on first access (see _LazyDict)."""
+
+    __slots__ = ("make",)
+
+    def __init__(self, make):
+        self.make = make
+
+
+class _LazyDict(dict):
+    """dict whose _Deferred entries are built on first access: the result views of a refinement
+    cost nothing until they are read (a step that only needs the device state skips them)."""
+
+    def __getitem__(self, k):
+        v = dict.__getitem__(self, k)
+        if isinstance(v, _Deferred):
+            v = v.make()
+            dict.__setitem__(self, k, v)
+        return v
+
+    def get(self, k, default=None):
+        return self[k] if k in self else default
+
+    def values(self):
+        return [self[k] for k in self]
+
+    def items(self):
+        return [(k, self[k]) for k in self]
+
+
 def _view(ptr, shape, dtype):
     import torch
 
@@ -402,9 +432,13 @@ class AmrGeom:
     def bin(self, B: int, sampled: bool = False):
         """Step 2: CSR bins; returns dict(offsets, ids) as borrowed int32 CUDA tensors (uint32 bits).
         sampled: the paper's sampled-point membership instead of the exact AABB overlap."""
+        import torch
+
         v = amr_bin_faces_sampled(self.ctx, B) if sampled else amr_bin_faces(self.ctx, B)
-        self.bins = {"B": v.B, "n_bins": v.n_bins, "nnz": v.nnz,
-                     "offsets": _u32(v.offsets, v.n_bins + 1), "ids": _u32(v.ids, v.nnz)}
+        off, ids, nb, nnz = v.offsets, v.ids, int(v.n_bins), int(v.nnz)
+        self.bins = _LazyDict(B=v.B, n_bins=nb, nnz=nnz,
+                              offsets=_Deferred(lambda: _view(off, (nb + 1,), torch.int32)),
+                              ids=_Deferred(lambda: _view(ids, (nnz,), torch.int32)))
         return self.bins
 
     def refine(self, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=None,
@@ -426,30 +460,34 @@ class AmrGeom:
         import torch
 
         D = self.dim
+
+        def lazy(ptr, shape, dtype):
+            return _Deferred(lambda: _view(ptr, shape, dtype))
+
         levels = []
         for L in range(r.n_levels):
             n = int(r.n_blocks[L])
-            levels.append({
-                "blocks": _view(r.block_coords[L], (n, D), torch.int32),
-                "parent": _view(r.block_parent[L], (n,), torch.int32) if L > 0 else None,
-                "mask": _view(r.cell_mask[L], (n,), torch.int64),
-                "flag": _view(r.block_flag[L], (n,), torch.uint8),
-            })
-        out = {"levels": levels, "n_fallback": int(r.n_fallback), "n_band": int(r.n_band),
-               "n_candidates": int(r.n_candidates), "n_survivors": int(r.n_survivors),
-               "n_link_candidates": int(r.n_link_candidates), "n_face_setups": int(r.n_face_setups),
-               "n_face_tests": int(r.n_face_tests), "graph_replay": bool(r.graph_replay)}
+            levels.append(_LazyDict(
+                blocks=lazy(r.block_coords[L], (n, D), torch.int32),
+                parent=lazy(r.block_parent[L], (n,), torch.int32) if L > 0 else None,
+                mask=lazy(r.cell_mask[L], (n,), torch.int64),
+                flag=lazy(r.block_flag[L], (n,), torch.uint8),
+            ))
+        out = _LazyDict(levels=levels, n_fallback=int(r.n_fallback), n_band=int(r.n_band),
+                        n_candidates=int(r.n_candidates), n_survivors=int(r.n_survivors),
+                        n_link_candidates=int(r.n_link_candidates), n_face_setups=int(r.n_face_setups),
+                        n_face_tests=int(r.n_face_tests), graph_replay=bool(r.graph_replay))
         if want_adjacency or want_links:
             na, npairs = int(r.n_adj_cells), int(r.n_adj_pairs)
-            out["adj_cell"] = _u32(r.adj_cell, na)
-            out["adj_off"] = _u32(r.adj_off, na + 1)
-            out["adj_ids"] = _u32(r.adj_ids, npairs)
+            out["adj_cell"] = lazy(r.adj_cell, (na,), torch.int32)
+            out["adj_off"] = lazy(r.adj_off, (na + 1,), torch.int32)
+            out["adj_ids"] = lazy(r.adj_ids, (npairs,), torch.int32)
         if want_links:
             nl = int(r.n_links)
-            out["link_cell"] = _u32(r.link_cell, nl)
-            out["link_dir"] = _view(r.link_dir, (nl,), torch.uint8)
-            out["link_q"] = _view(r.link_q, (nl,), torch.float32)
-            out["link_face"] = _u32(r.link_face, nl)
+            out["link_cell"] = lazy(r.link_cell, (nl,), torch.int32)
+            out["link_dir"] = lazy(r.link_dir, (nl,), torch.uint8)
+            out["link_q"] = lazy(r.link_q, (nl,), torch.float32)
+            out["link_face"] = lazy(r.link_face, (nl,), torch.int32)
         self.result = out
         return out
 
