@@ -38,6 +38,9 @@ L2_FLUSH_BYTES = 512 << 20
 OPS_BLOCK_CANDIDATE = 120.0   # face setup up to the AABB cull (vertex offsets, edges, three box axes)
 OPS_BLOCK_SURVIVOR = 280.0    # the remaining ten axes of the block-level test for a survivor
 OPS_CELL_TEST = 80.0          # one cell against one survivor: 13 axes x (projection + interval test)
+# DRAM bytes (read + write) per launch of the current kernels, from one ncu capture each
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the c2 workload; other workloads report null
+MEASURED_TRAFFIC = {("c2", "links"): 133.0e6, ("c2", "refine_level"): 8.95e6}
 OPS_FACE_SETUP = 400.0        # face-by-face marking, per (face, level): cell range, frame, 13 axis intervals
 OPS_LINK_FACE = 150.0         # per (adjacent cell, face): double-float offsets, plane offset, cross products
 OPS_LINK_DIR = 40.0           # per (adjacent cell, face, direction): den, three edge signs, t
@@ -231,6 +234,7 @@ def run_ours(args, rank, world, local):
     t_mark = sum(kern[k]["ms_per_step"] for k in ("mark_faces", "block_hash") if k in kern)
     dom = max(kern.items(), key=lambda kv: kv[1]["ms_per_step"])
     roof = roofline(dom[0], dom[1], w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks, n_fsetup, n_ftest)
+    roof["traffic"] = MEASURED_TRAFFIC.get((args.workload, dom[0]))
     NCe = 64 if w.dim == 3 else 16
     n_tests = n_surv * NCe + n_ftest  # block-walk cell tests + face-by-face (face, cell) tests
     binning = bin_roofline(w, nnz, t_bin)
@@ -502,7 +506,8 @@ def run_paper_setups(args, dev, flush, bins=(1, 2, 4, 8, 16), reps=3):
                 tk = g.timings()
                 g.timing(False)
                 t_bin = sum(tk[k][0] for k in ("bin_count", "bin_scan", "bin_scatter") if k in tk) / reps
-                t_det = sum(tk[k][0] for k in ("refine_level", "propagate") if k in tk) / reps
+                t_det = sum(tk[k][0] for k in ("refine_level", "propagate", "mark_faces", "block_hash")
+                            if k in tk) / reps
                 r["bin_ms"].append(round(t_bin, 4))
                 r["detect_ms"].append(round(t_det, 4))
                 r["blocks_per_level"].append([int(lv["blocks"].shape[0]) for lv in res["levels"]])
