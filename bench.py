@@ -62,6 +62,23 @@ def parse_args(argv=None):
     return p.parse_args(argv)
 
 
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest x over the ranks (one all-reduce over the job's process group; x for one rank)."""
+    if world <= 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, world: int, ms_step: float) -> float:
+    """Units all ranks processed per second: every rank runs the same workload (replicas, weak
+    scaling), timed by the slowest rank's step."""
+    return units_per_rank * world / (ms_step * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -211,11 +228,8 @@ def run_ours(args, rank, world, local):
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
     ms_step = sum(ms) / len(ms)
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = cells * world / (ms_step * 1e-3)
+    ms_step = max_over_ranks(ms_step, world, dev)
+    value = whole_job_value(cells, world, ms_step)
 
     # per-kernel timing pass (CUDA events around each launch, on the context stream)
     g.timing(True)
@@ -228,6 +242,9 @@ def run_ours(args, rank, world, local):
         g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=False)
     tk = g.timings()
     g.timing(False)
+    # the algorithmic cell-face test count of the step (per cell, the distinct faces in the bins its
+    # inflated box overlaps; fixed by the geometry and the bins), outside every timed region
+    c_alg_levels, c_alg = g.candidate_count()
     kern = {name: {"ms_per_step": v[0] / n_t, "launches_per_step": v[1] / n_t} for name, v in tk.items()}
     t_bin = sum(kern[k]["ms_per_step"] for k in ("bin_count", "bin_scan", "bin_scatter") if k in kern)
     t_refine = kern.get("refine_level", {}).get("ms_per_step", 0.0)
@@ -250,9 +267,13 @@ def run_ours(args, rank, world, local):
                    "level_loop": "CUDA graph replay" if use_graph else "eager",
                    "fp64_fallbacks_per_step": n_fb, "band_cases_per_step": n_band,
                    "block_face_candidates": n_cand, "block_survivors": n_surv, "link_candidates": n_lcand,
-                   "face_pass_setups": n_fsetup, "face_pass_tests": n_ftest},
+                   "face_pass_setups": n_fsetup, "face_pass_tests": n_ftest,
+                   "c_alg_per_step": c_alg, "c_alg_per_level": c_alg_levels},
         "faces_binned_per_s": w.n_faces / (t_bin * 1e-3) if t_bin > 0 else None,
-        "cell_face_tests_per_s": n_tests / ((t_refine + t_mark) * 1e-3) if t_refine + t_mark > 0 else None,
+        # algorithmic cell-face tests (C_alg) over the time of all marking kernels of the step
+        "cell_face_tests_per_s": c_alg / ((t_refine + t_mark) * 1e-3) if t_refine + t_mark > 0 else None,
+        # the tests the kernels ran: block-walk survivors x cells, plus the face-by-face (face, cell) tests
+        "executed_cell_face_tests_per_s": n_tests / ((t_refine + t_mark) * 1e-3) if t_refine + t_mark > 0 else None,
         "binning": binning,
         "kernels_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in kern.items()},
         "wall_s": wall,

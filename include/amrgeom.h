@@ -268,6 +268,15 @@ typedef struct {
 } amr_adapt_diff;
 AMR_API amr_status amr_adapt_diff_get(amr_ctx* ctx, amr_adapt_diff* out);
 
+/* Algorithmic cell-face test count of the last refinement (a measurement; Sec. "Spatial Binning
+ * Algorithm": every cell checks the faces of the bins around it).  Per level L, per_level[L] =
+ * sum over the cells of its blocks of the number of distinct faces stored in the bins that the
+ * cell's inflated box (centre +- (h_L / 2 + d_L)) overlaps; the bin range is formed in FP64, so
+ * the count is exact and fixed by the geometry and the bin density, whatever the kernels execute.
+ * per_level: host array of AMR_MAX_LEVELS (levels past n_levels get 0); total: nullable host.
+ * Single-geometry contexts after amr_refine_near_wall (else AMR_ESTATE). */
+AMR_API amr_status amr_candidate_count(amr_ctx* ctx, int64_t* per_level, int64_t* total);
+
 /* Wait for all work of the context; report device-side check failures. */
 AMR_API amr_status amr_sync(amr_ctx* ctx);
 

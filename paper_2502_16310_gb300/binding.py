@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ECUDA", 4
 EXPORTED = ["amr_create", "amr_destroy", "amr_status_str", "amr_last_error", "amr_set_stream", "amr_geom_load",
             "amr_bin_faces", "amr_bin_faces_sampled", "amr_refine_near_wall", "amr_sync", "amr_timing_enable",
             "amr_timing_reset", "amr_timing_get", "amr_launch_count", "amr_bin_faces_static", "amr_q_backward",
-            "amr_classify_nodes", "amr_fluid_links", "amr_adapt_diff_get", "amr_autotune",
+            "amr_classify_nodes", "amr_fluid_links", "amr_adapt_diff_get", "amr_candidate_count", "amr_autotune",
             "amr_batch_create", "amr_batch_destroy", "amr_batch_add", "amr_batch_set_bins", "amr_batch_run",
             "amr_batch_get_view", "amr_batch_q_backward", "amr_batch_last_error", "amr_batch_launch_count"]
 
@@ -142,6 +142,8 @@ def lib(build_if_missing: bool = True):
         L.amr_fluid_links.argtypes = [P, C.POINTER(amr_refine_result)]
         L.amr_adapt_diff_get.restype = C.c_int
         L.amr_adapt_diff_get.argtypes = [P, C.POINTER(amr_adapt_diff)]
+        L.amr_candidate_count.restype = C.c_int
+        L.amr_candidate_count.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.amr_autotune.restype = C.c_int
         L.amr_autotune.argtypes = [P, C.POINTER(amr_refine_params), P, C.c_int, P, C.c_int, C.POINTER(C.c_int),
                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -502,6 +504,15 @@ class AmrGeom:
         _check(self.ctx, lib().amr_classify_nodes(self.ctx, C.byref(ptr), C.byref(nfb)))
         n = int(self.last_result.n_adj_cells) if self.last_result is not None else 0
         return _view(ptr.value, (n,), torch.uint8), int(nfb.value)
+
+    def candidate_count(self):
+        """Algorithmic cell-face test count of the last refine: (per-level list, total); per cell, the
+        distinct faces in the bins its inflated box overlaps (exact, fixed by geometry and bins)."""
+        per = (C.c_int64 * MAX_LEVELS)()
+        tot = C.c_int64()
+        _check(self.ctx, lib().amr_candidate_count(self.ctx, per, C.byref(tot)))
+        n = int(self.last_result.n_levels) if self.last_result is not None else 0
+        return [int(per[L]) for L in range(n)], int(tot.value)
 
     def adapt_diff(self):
         """Per level (after a refine with keep_previous): new_to_old / old_to_new index maps (borrowed int32

@@ -120,6 +120,7 @@ struct amr_ctx {
   uint64_t* d_tot = nullptr;
   DevBuf fstat;                           // per geometry: face-size statistics (see FaceBinArgs)
   DevBuf spill;                           // per-warp spill of survivor records (once a call needed it)
+  DevBuf calg;                            // per-level algorithmic test counts (amr_candidate_count)
   bool want_spill = false;
   void* h_stat = nullptr;                 // their mapped pinned copy (h_stat_dev as the device sees it)
   char* h_stat_dev = nullptr;
@@ -478,6 +479,7 @@ void amr_ctx_free(amr_ctx* ctx) {
   if (ctx->h_stat) cudaFreeHost(ctx->h_stat);
   release(ctx, ctx->fstat);
   release(ctx, ctx->spill);
+  release(ctx, ctx->calg);
 }
 
 // Binning of every geometry of the table in one pass (count, scan, scatter).
@@ -1591,6 +1593,42 @@ amr_status amr_adapt_diff_get(amr_ctx* ctx, amr_adapt_diff* out) {
     d.n_removed[L] = (int64_t)h[2 * L + 1];
   }
   *out = d;
+  return AMR_OK;
+}
+
+amr_status amr_candidate_count(amr_ctx* ctx, int64_t* per_level, int64_t* total) {
+  if (!ctx || !per_level) return AMR_EINVAL;
+  if (ctx->multi) return fail(ctx, AMR_ESTATE, "amr_candidate_count on a batch context");
+  if (!ctx->refined) return fail(ctx, AMR_ESTATE, "amr_candidate_count before amr_refine_near_wall");
+  cudaStream_t st = ctx->stream;
+  const amr_refine_result& r = ctx->last;
+  TRY(ensure_aux(ctx, ctx->calg, sizeof(unsigned long long) * AMR_MAX_LEVELS));
+  CK(cudaMemsetAsync(ctx->calg.p, 0, sizeof(unsigned long long) * AMR_MAX_LEVELS, st));
+  unsigned long long* out = static_cast<unsigned long long*>(ctx->calg.p);
+  for (int L = 0; L < r.n_levels; ++L) {
+    if (r.n_blocks[L] <= 0) continue;
+    CountArgs a{};
+    a.dim = ctx->dom.dim;
+    a.level = L;
+    a.g0 = ctx->geoms[0];
+    a.blocks = r.block_coords[L];
+    a.n = r.n_blocks[L];
+    a.offsets = static_cast<const uint32_t*>(ctx->offsets.p);
+    a.payload = ctx->payload.p;
+    a.out = out + L;
+    timed(ctx, st, "candidate_count", [&] { return launch_count_candidates(a, ctx->num_sms, st); });
+  }
+  CK(cudaGetLastError());
+  // counts at 1280 of the pinned block (16 levels at most)
+  TRY(small_copy(ctx, st, {{ctx->h_dev + 1280, out, sizeof(unsigned long long) * AMR_MAX_LEVELS}}));
+  TRY(sync_check(ctx, st));
+  const unsigned long long* h = reinterpret_cast<const unsigned long long*>(static_cast<char*>(ctx->h_pinned) + 1280);
+  int64_t tot = 0;
+  for (int L = 0; L < AMR_MAX_LEVELS; ++L) {
+    per_level[L] = L < r.n_levels ? (int64_t)h[L] : 0;
+    tot += per_level[L];
+  }
+  if (total) *total = tot;
   return AMR_OK;
 }
 

@@ -480,6 +480,21 @@ struct MarkArgs {
 constexpr int kFaceBatch = 8;  // most faces a warp takes per work fetch
 int launch_mark_faces(const MarkArgs& m, int num_sms, cudaStream_t st);
 
+// The algorithmic cell-face test count of one level (single geometry): per cell
+// of its blocks, the distinct faces in the bins its inflated box overlaps,
+// summed into *out.
+struct CountArgs {
+  int dim;
+  int level;
+  GeomParams g0;
+  const int32_t* blocks;
+  int64_t n;                 // blocks of the level
+  const uint32_t* offsets;
+  const void* payload;
+  unsigned long long* out;
+};
+int launch_count_candidates(const CountArgs& a, int num_sms, cudaStream_t st);
+
 struct EmitArgs {
   RefineLevel lv;
   const uint64_t* block_base;  // exclusive scan of blockcnt over this level
