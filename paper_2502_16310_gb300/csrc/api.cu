@@ -121,6 +121,7 @@ struct amr_ctx {
   DevBuf fstat;                           // per geometry: face-size statistics (see FaceBinArgs)
   DevBuf spill;                           // per-warp spill of survivor records (once a call needed it)
   DevBuf calg;                            // per-level algorithmic test counts (amr_candidate_count)
+  DevBuf defer;                           // the adjacency's second-pass block list
   bool want_spill = false;
   void* h_stat = nullptr;                 // their mapped pinned copy (h_stat_dev as the device sees it)
   char* h_stat_dev = nullptr;
@@ -480,6 +481,7 @@ void amr_ctx_free(amr_ctx* ctx) {
   release(ctx, ctx->fstat);
   release(ctx, ctx->spill);
   release(ctx, ctx->calg);
+  release(ctx, ctx->defer);
 }
 
 // Binning of every geometry of the table in one pass (count, scan, scatter).
@@ -915,6 +917,12 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
       ea.adj_ids = static_cast<uint32_t*>(ctx->adj_ids.p);
       ea.cap_cells = ctx->cap_cells;
       ea.cap_pairs = ctx->cap_pairs;
+      // the second pass's block list: [0] its count, then the blocks (one slot per block of the level)
+      if (eager) TRY(ensure(ctx, ctx->defer, sizeof(uint32_t) * (size_t)(lb.cap + 1)));
+      ea.defer_n = static_cast<unsigned*>(ctx->defer.p);
+      ea.defer = static_cast<uint32_t*>(ctx->defer.p) + 1;
+      ea.defer_cap = lb.cap;
+      CK(cudaMemsetAsync(ea.defer_n, 0, sizeof(unsigned), st));
       CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), st));
       timed(ctx, st, "adjacency", [&] { return launch_adjacency(ea, ctx->num_sms, st); });
       timed(ctx, st, "advance", [&] {

@@ -503,7 +503,11 @@ struct EmitArgs {
   uint32_t* adj_off;
   uint32_t* adj_ids;
   int64_t cap_cells, cap_pairs;
+  uint32_t* defer;             // blocks for the second pass (capacity defer_cap) ...
+  unsigned* defer_n;           // ... and their count (zeroed before the launch)
+  int64_t defer_cap;
 };
+// Both passes (the work counter zeroed before the launch; it is reused by the second).
 int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st);
 
 struct ChildrenArgs {

@@ -964,39 +964,22 @@ __host__ __device__ constexpr uint32_t pow2_floor(uint32_t x) {
 }
 
 // Emit the adjacent-face lists of the blocks whose geometry ends at this
-// level: same walk as k_refine (so the same decisions), each lane appends the
-// faces of its cells at offsets given by the block-level scan and the per-cell
-// counts, then sorts each list.  Rows and pairs continue after the running
-// totals of earlier levels.
-template <int D, int PRED>
-__global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
-  extern __shared__ __align__(16) unsigned char s_raw[];
-  WarpSmem<D>& sm = reinterpret_cast<WarpSmem<D>*>(s_raw)[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
-  warp_smem_init<D>(sm, lane);
-  uint32_t phase = 0;
+// level, in two passes.  MODE 0 takes every block: it writes the block's rows
+// (adjacent cells and their list offsets, from the block-level scan and the
+// per-cell counts) and, when the refine pass kept at most kRecCap survivor
+// records, ranks them by face id and lists each cell's faces in that order; it
+// needs only a little shared memory, so many warps stay resident.  Other blocks
+// go to a list that MODE 1 takes, with the walk's shared memory: more records
+// are sorted there, and blocks without records are walked again (the same
+// decisions as k_refine) and their lists sorted.  Rows and pairs continue after
+// the running totals of earlier levels.
+template <int D, int PRED, int MODE>
+__device__ __forceinline__ void emit_block(const EmitArgs& a, unsigned blk, uint32_t gid, WarpSmem<D>& sm,
+                                           uint32_t& phase, WarpCounters& wc, uint64_t* rm, uint32_t* rf,
+                                           int lane, uint64_t run_cells, uint64_t run_pairs) {
   constexpr int NC = D == 3 ? 64 : 16;
-  const int64_t n = launch_count(a.lv.n_blocks, a.lv.n_dev, a.lv.err);
-  const uint64_t run_cells = a.run ? a.run[0] : 0ull, run_pairs = a.run ? a.run[1] : 0ull;
-  WarpCounters wc;
-  // 32 blocks per atomic: each lane reads one block's mask, the warp then takes
-  // the marked blocks of the group one after another
-  for (;;) {
-    unsigned base = 0;
-    if (lane == 0) base = atomicAdd(a.lv.work, 32u);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= n) break;
-    const bool in_range = (int64_t)base + lane < n;
-    const uint64_t my_mask = in_range ? a.lv.mask[base + lane] : 0ull;
-    const uint32_t my_gid = in_range && a.lv.gid ? a.lv.gid[base + lane] : 0u;
-    unsigned todo = __ballot_sync(0xffffffffu, my_mask != 0);
-  while (todo) {
-    const int q = __ffs(todo) - 1;
-    todo &= todo - 1;
-    const unsigned blk = base + (unsigned)q;
-    const uint32_t gid = __shfl_sync(0xffffffffu, my_gid, q);
     const GeomParams& P = a.lv.table ? a.lv.table[gid] : a.lv.g0;
-    if (a.lv.level != P.n_levels - 1) continue;
+    if (a.lv.level != P.n_levels - 1) return;
     int b[3] = {0, 0, 0};
 #pragma unroll
     for (int c = 0; c < D; ++c) b[c] = a.lv.blocks[(int64_t)blk * D + c];
@@ -1016,7 +999,7 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
     const uint32_t atot0 = __shfl_sync(0xffffffffu, j0, 31);
     const uint32_t j1 = warp_inclusive_scan<uint32_t>(a1);
     bool bad = (int64_t)(off1 + n1) > a.cap_pairs || (int64_t)(off0 + n0) > a.cap_pairs;
-    if (a0) {
+    if (MODE == 0 && a0) {
       const uint64_t row = cell_base + j0 - 1;
       if ((int64_t)row < a.cap_cells) {
         a.adj_cell[row] = blk * (uint32_t)NC + lane;
@@ -1025,7 +1008,7 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
         bad = true;
       }
     }
-    if (a1) {
+    if (MODE == 0 && a1) {
       const uint64_t row = cell_base + atot0 + j1 - 1;
       if ((int64_t)row < a.cap_cells) {
         a.adj_cell[row] = blk * (uint32_t)NC + 32 + lane;
@@ -1057,21 +1040,7 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
     const uint64_t desc = a.lv.recs ? a.lv.rec_desc[blk] : ~0ull;
     constexpr uint32_t kSortRecs = pow2_floor(sort_region_bytes<D>() / 12);  // key + payload per record
     constexpr uint32_t kSortKeys = pow2_floor(sort_region_bytes<D>() / 4);
-    if (desc != ~0ull && (uint32_t)(desc & 0xffffu) > (uint32_t)kRecCap &&
-        (uint32_t)(desc & 0xffffu) <= kSortRecs) {
-      // many records: sort them by face id in shared memory, then list the cells' faces in that order
-      const uint32_t K = (uint32_t)(desc & 0xffffu);
-      const uint64_t r0 = desc >> 16;
-      uint32_t* sf = reinterpret_cast<uint32_t*>(&sm);
-      const uint64_t* sk = sort_records(a.lv.recs + r0, K, sf, lane);
-      for (uint32_t j = 0; j < K; ++j) {
-        const uint64_t mj = sk[j];
-        put(lane < NC && ((mj >> lane) & 1ull), D == 3 && ((mj >> (lane + 32)) & 1ull), sf[j]);
-      }
-      __syncwarp();
-      if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
-      continue;
-    }
+    if constexpr (MODE == 0) {
     if (desc != ~0ull && (uint32_t)(desc & 0xffffu) <= (uint32_t)kRecCap) {
       // the refine pass left this block's surviving faces with their cell masks:
       // rank them by face id, then every lane lists its cells' faces in that order
@@ -1101,27 +1070,100 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
       for (int h = 0; h < 2; ++h) {
         const uint32_t i = (uint32_t)lane + 32u * h;
         if (i < K) {
-          sm.rf[rank[h]] = f[h];
-          sm.rm[rank[h]] = cm[h];
+          rf[rank[h]] = f[h];
+          rm[rank[h]] = cm[h];
         }
       }
       __syncwarp();
       for (uint32_t j = 0; j < K; ++j) {
-        const uint64_t mj = sm.rm[j];
-        put(lane < NC && ((mj >> lane) & 1ull), D == 3 && ((mj >> (lane + 32)) & 1ull), sm.rf[j]);
+        const uint64_t mj = rm[j];
+        put(lane < NC && ((mj >> lane) & 1ull), D == 3 && ((mj >> (lane + 32)) & 1ull), rf[j]);
       }
       __syncwarp();
       if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
-      continue;
+      return;
+    }
+      // more records than staged in shared memory, or none kept: the second pass takes the block
+      if (lane == 0) {
+        const unsigned pos = atomicAdd(a.defer_n, 1u);
+        if ((int64_t)pos < a.defer_cap)
+          a.defer[pos] = blk;
+        else
+          atomicOr(a.lv.err, ERR_OVERFLOW);
+      }
+      return;
+    } else {
+    if (desc != ~0ull && (uint32_t)(desc & 0xffffu) > (uint32_t)kRecCap &&
+        (uint32_t)(desc & 0xffffu) <= kSortRecs) {
+      // many records: sort them by face id in shared memory, then list the cells' faces in that order
+      const uint32_t K = (uint32_t)(desc & 0xffffu);
+      const uint64_t r0 = desc >> 16;
+      uint32_t* sf = reinterpret_cast<uint32_t*>(&sm);
+      const uint64_t* sk = sort_records(a.lv.recs + r0, K, sf, lane);
+      for (uint32_t j = 0; j < K; ++j) {
+        const uint64_t mj = sk[j];
+        put(lane < NC && ((mj >> lane) & 1ull), D == 3 && ((mj >> (lane + 32)) & 1ull), sf[j]);
+      }
+      __syncwarp();
+      if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
+      return;
     }
     bool h0 = false, h1 = false;
     walk_block<D, PRED, false>(a.lv, P, gid, b, sm, phase, lane, wc, h0, h1,
                          [&](uint32_t fc, bool r0, bool r1) { put(r0, r1, fc); });
     if (bad || c0 != n0 || c1 != n1) atomicOr(a.lv.err, ERR_OVERFLOW);
-    if (!__all_sync(0xffffffffu, can0 && can1)) continue;  // lists beyond the capacity (reported)
+    if (!__all_sync(0xffffffffu, can0 && can1)) return;  // lists beyond the capacity (reported)
     // ascending face ids per cell
     sort_cell_lists(a.adj_ids, NC, n0, n1, off0, off1, reinterpret_cast<uint32_t*>(&sm), kSortKeys, lane);
-  }
+    }
+}
+
+template <int D, int PRED, int MODE>
+__global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
+  constexpr int kW = 8;  // warps per CTA at most
+  __shared__ uint64_t s_rm[MODE == 0 ? kW : 1][kRecCap];
+  __shared__ uint32_t s_rf[MODE == 0 ? kW : 1][kRecCap];
+  extern __shared__ __align__(16) unsigned char s_raw[];  // MODE 1: the walk's per-warp memory
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  WarpSmem<D>& sm = reinterpret_cast<WarpSmem<D>*>(s_raw)[MODE == 0 ? 0 : wid];
+  uint32_t phase = 0;
+  if constexpr (MODE == 1) warp_smem_init<D>(sm, lane);
+  uint64_t* rm = s_rm[MODE == 0 ? wid : 0];
+  uint32_t* rf = s_rf[MODE == 0 ? wid : 0];
+  const uint64_t run_cells = a.run ? a.run[0] : 0ull, run_pairs = a.run ? a.run[1] : 0ull;
+  WarpCounters wc;
+  if constexpr (MODE == 0) {
+    const int64_t n = launch_count(a.lv.n_blocks, a.lv.n_dev, a.lv.err);
+    // 32 blocks per atomic: each lane reads one block's mask, the warp then takes
+    // the marked blocks of the group one after another
+    for (;;) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(a.lv.work, 32u);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= n) break;
+      const bool in_range = (int64_t)base + lane < n;
+      const uint64_t my_mask = in_range ? a.lv.mask[base + lane] : 0ull;
+      const uint32_t my_gid = in_range && a.lv.gid ? a.lv.gid[base + lane] : 0u;
+      unsigned todo = __ballot_sync(0xffffffffu, my_mask != 0);
+      while (todo) {
+        const int q = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t gid = __shfl_sync(0xffffffffu, my_gid, q);
+        emit_block<D, PRED, MODE>(a, base + (unsigned)q, gid, sm, phase, wc, rm, rf, lane, run_cells, run_pairs);
+      }
+    }
+  } else {
+    const int64_t nd = (int64_t)*a.defer_n;
+    const int64_t n = nd < a.defer_cap ? nd : a.defer_cap;
+    for (;;) {
+      unsigned i = 0;
+      if (lane == 0) i = atomicAdd(a.lv.work, 1u);
+      i = __shfl_sync(0xffffffffu, i, 0);
+      if ((int64_t)i >= n) break;
+      const unsigned blk = a.defer[i];
+      const uint32_t gid = a.lv.gid ? a.lv.gid[blk] : 0u;
+      emit_block<D, PRED, MODE>(a, blk, gid, sm, phase, wc, rm, rf, lane, run_cells, run_pairs);
+    }
   }
 }
 
@@ -1569,18 +1611,34 @@ int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st) {
 int launch_adjacency(const EmitArgs& a, int num_sms, cudaStream_t st) {
   if (!a.lv.n_dev && a.lv.n_blocks <= 0) return 0;
   const int warps = a.lv.warps > 0 ? a.lv.warps : 4;
-  const int g = grid_warps(num_sms, a.lv.n_blocks, warps, a.lv.n_dev != nullptr);
-  const size_t smem = (size_t)warps * (a.lv.dim == 3 ? sizeof(WarpSmem<3>) : sizeof(WarpSmem<2>));
-  auto go = [&](auto kernel) {
-    allow_smem(kernel, smem);
-    kernel<<<g, warps * 32, smem, st>>>(a);
-  };
   const int mode = a.lv.search == 1 ? 2 : (a.lv.pred == 1 ? 1 : 0);
-  if (a.lv.dim == 3)
-    mode == 2 ? go(k_adjacency<3, 2>) : (mode == 1 ? go(k_adjacency<3, 1>) : go(k_adjacency<3, 0>));
-  else
-    mode == 2 ? go(k_adjacency<2, 2>) : (mode == 1 ? go(k_adjacency<2, 1>) : go(k_adjacency<2, 0>));
-  return 1;
+  // first pass: little shared memory, so up to 64 warps per SM
+  {
+    const int64_t cap = (int64_t)num_sms * (64 / warps > 0 ? 64 / warps : 1);
+    int64_t g = a.lv.n_dev ? cap : (a.lv.n_blocks / 32 + warps) / warps;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    auto go = [&](auto kernel) { kernel<<<(unsigned)g, warps * 32, 0, st>>>(a); };
+    if (a.lv.dim == 3)
+      mode == 2 ? go(k_adjacency<3, 2, 0>) : (mode == 1 ? go(k_adjacency<3, 1, 0>) : go(k_adjacency<3, 0, 0>));
+    else
+      mode == 2 ? go(k_adjacency<2, 2, 0>) : (mode == 1 ? go(k_adjacency<2, 1, 0>) : go(k_adjacency<2, 0, 0>));
+  }
+  // second pass over the listed blocks (its count on the device): the walk's shared memory
+  cudaMemsetAsync(a.lv.work, 0, sizeof(unsigned), st);
+  {
+    const int g = grid_warps(num_sms, 0, warps, true);
+    const size_t smem = (size_t)warps * (a.lv.dim == 3 ? sizeof(WarpSmem<3>) : sizeof(WarpSmem<2>));
+    auto go = [&](auto kernel) {
+      allow_smem(kernel, smem);
+      kernel<<<g, warps * 32, smem, st>>>(a);
+    };
+    if (a.lv.dim == 3)
+      mode == 2 ? go(k_adjacency<3, 2, 1>) : (mode == 1 ? go(k_adjacency<3, 1, 1>) : go(k_adjacency<3, 0, 1>));
+    else
+      mode == 2 ? go(k_adjacency<2, 2, 1>) : (mode == 1 ? go(k_adjacency<2, 1, 1>) : go(k_adjacency<2, 0, 1>));
+  }
+  return 2;
 }
 
 int launch_mark_faces(const MarkArgs& m, int num_sms, cudaStream_t st) {
