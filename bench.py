@@ -60,8 +60,8 @@ def parse_args(argv=None):
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     p.add_argument("--batch-geoms", type=int, default=48)
     p.add_argument("--e2e-threads", type=int, default=0,
-                   help="host threads (one context each) of the e2e leg; 0 = 3 for steps that copy back less "
-                        "than 2 GB, else 1")
+                   help="host threads (one context each) of the e2e leg; 0 = three threads for steps that "
+                        "copy back less than 2 GB, else one thread alternating two contexts")
     return p.parse_args(argv)
 
 
@@ -598,11 +598,14 @@ def bin_roofline(w, nnz, t_bin_ms):
 
 def run_e2e(w, args, dev):
     """Same metric through the public API with host buffers: every step uploads its inputs from pinned
-    host memory (inside amr_geom_load) and copies every output back to pinned host memory.  A few host
-    threads, each with its own context and stream, take the steps in turn, as a user streaming results
-    to the host would run it: one thread's uploads, host-side calls and copies overlap the others' GPU
-    work, and their kernels share the GPU.  Host wall clock from the start of the timed steps to the end
-    of the last step's copies."""
+    host memory (inside amr_geom_load) and copies every output back to pinned host memory, as a user
+    streaming results to the host would run it.  Steps that copy back less than 2 GB: a few host
+    threads, each with its own context and stream, take the steps in turn; one thread's uploads,
+    host-side calls and copies overlap the others' GPU work, and their kernels share the GPU.  Steps
+    that copy back more are long and bound by the copies: one host thread alternates two contexts, so
+    a step's copies overlap the next step's compute without a third step's kernels and pinned output
+    competing for the GPU and the host link.  Host wall clock from the start of the timed steps to the
+    end of the last step's copies."""
     import threading
 
     import torch
@@ -613,16 +616,14 @@ def run_e2e(w, args, dev):
     hi = torch.from_numpy(w.idx).pin_memory()
     bi = hv.numel() * 4 + hi.numel() * 4
     use_graph = not args.no_graph
-    NT = max(1, args.e2e_threads) if args.e2e_threads > 0 else 3
-    ctxs, bufs = [], [{} for _ in range(NT)]
-    out = [None] * NT
+    out = {}
 
-    def new_ctx():
+    def new_slot():
         with torch.cuda.stream(torch.cuda.Stream(device=dev)):
-            ctxs.append(AmrGeom(w.dim, (w.root,) * w.dim))
+            return [AmrGeom(w.dim, (w.root,) * w.dim), {}]
 
-    def step(i):
-        g, out_bufs = ctxs[i], bufs[i]
+    def step(slot, i):
+        g, out_bufs = slot
         g.load(hv, hi)
         g.bin(w.bins)
         res = g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=use_graph)
@@ -642,14 +643,25 @@ def run_e2e(w, args, dev):
                 nbytes += t.numel() * t.element_size()
         out[i] = (res, nbytes)
 
+    # one untimed step gives the bytes a step copies back
+    first = new_slot()
+    step(first, 0)
+    torch.cuda.synchronize()
+    if args.e2e_threads > 0:
+        NT, NC = args.e2e_threads, 1
+    elif out[0][1] >= 2e9:
+        NT, NC = 1, 2
+    else:
+        NT, NC = 3, 1
+    slots = [[first if i == 0 and c == 0 else new_slot() for c in range(NC)] for i in range(NT)]
     errors = []
 
     def worker(i, n, go):
         try:
             torch.cuda.set_device(dev)
             go.wait()
-            for _ in range(n):
-                step(i)
+            for k in range(n):
+                step(slots[i][k % NC], i)
         except Exception as e:  # surfaced by the main thread
             errors.append(e)
 
@@ -668,30 +680,20 @@ def run_e2e(w, args, dev):
             raise errors[0]
         return time.perf_counter() - t0
 
-    # One untimed step on one context gives the bytes a step copies back.  Steps that copy back
-    # gigabytes are long and bound by the copies: there one thread already leaves the GPU no host
-    # gap, while several contexts each pinning a copy of the output contend for the host link.
-    new_ctx()
-    step(0)
-    torch.cuda.synchronize()
-    if args.e2e_threads <= 0 and out[0][1] >= 2e9:
-        NT = 1
-    del bufs[NT:], out[NT:]
-    while len(ctxs) < NT:
-        new_ctx()
-    run_threads(max(2, args.warmup))  # warm-up: allocations, graph captures, pinned buffers
-    K = NT * max(2, args.steps // NT)
+    run_threads(NC * max(2, args.warmup))  # warm-up: allocations, graph captures, pinned buffers
+    K = NT * NC * max(2, args.steps // (NT * NC))
     dt = run_threads(K // NT) / K
     res, bo = out[0]
     cells = near_wall_cells(res)
-    for g in ctxs:
-        g.close()
+    for per_thread in slots:
+        for g, _ in per_thread:
+            g.close()
     return {"value": cells / dt, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
             "ms_per_step": dt * 1e3, "level_loop": "CUDA graph replay" if use_graph else "eager",
-            "threads": NT, "steps": K,
+            "threads": NT, "contexts_per_thread": NC, "steps": K,
             "note": f"host wall clock over K steps: load(pinned host) -> bin -> refine -> D2H of every output to "
-                    f"pinned host; {NT} host threads with a context and stream each take the steps in turn, "
-                    f"so steps overlap on the GPU (the device-side value times one stream)"}
+                    f"pinned host; {NT} host thread(s), each taking its steps in turn on {NC} context(s) with "
+                    f"a stream each, so steps overlap on the GPU (the device-side value times one stream)"}
 
 
 # ---------------------------------------------------------------------------
