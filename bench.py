@@ -34,16 +34,16 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 512 << 20
 
-# Algorithmic work per unit (FP32-pipe operations counted from the kernel source; see DESIGN.md):
+# Algorithmic work per unit (FP32-pipe operations counted from the kernel source):
 OPS_BLOCK_CANDIDATE = 120.0   # face setup up to the AABB cull (vertex offsets, edges, three box axes)
 OPS_BLOCK_SURVIVOR = 280.0    # the remaining ten axes of the block-level test for a survivor
 OPS_CELL_TEST = 80.0          # one cell against one survivor: 13 axes x (projection + interval test)
-# DRAM bytes (read + write) per launch of the current kernels, from one ncu capture each
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the c2 workload; other workloads report null
-MEASURED_TRAFFIC = {("c2", "links"): 133.0e6, ("c2", "refine_level"): 8.95e6}
 OPS_FACE_SETUP = 400.0        # face-by-face marking, per (face, level): cell range, frame, 13 axis intervals
 OPS_LINK_FACE = 150.0         # per (adjacent cell, face): double-float offsets, plane offset, cross products
 OPS_LINK_DIR = 40.0           # per (adjacent cell, face, direction): den, three edge signs, t
+# DRAM bytes (read + write) per launch of the current kernels, from one ncu capture each
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the c2 workload; other workloads report null
+MEASURED_TRAFFIC = {("c2", "links"): 133.0e6, ("c2", "refine_level"): 8.95e6}
 
 
 def parse_args(argv=None):
