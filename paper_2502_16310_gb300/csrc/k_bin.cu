@@ -204,10 +204,22 @@ __device__ void sampled_bins(const float* X, int64_t nf, int64_t f, const GeomPa
 
 // Per face: bin range of its AABB along each axis (packed lo | hi << 16, bins of
 // its own geometry) and one count per (face, bin) incidence.
-template <int D>
-__global__ void k_face_bins(FaceBinArgs a) {
+template <int D, bool SAMPLED>
+__global__ void __launch_bounds__(kThreads) k_face_bins(FaceBinArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // The face-size statistics of the geometry of the block's first face collect in shared memory
+  // and reach global memory once per block: one global address per geometry would otherwise take
+  // an atomic from every warp of the launch.
+  __shared__ unsigned long long s_stat[2];
+  __shared__ uint32_t s_gid;
+  if (threadIdx.x == 0) {
+    const int64_t f1 = blockIdx.x * (int64_t)blockDim.x;
+    s_gid = f1 < a.nf ? (a.face_gid ? a.face_gid[f1] : 0u) : 0xffffffffu;
+    s_stat[0] = 0ull;
+    s_stat[1] = 0ull;
+  }
+  __syncthreads();
   // warp-uniform trip count: lane i takes face f0 + i (the face-size statistics are reduced per warp)
   for (int64_t f0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); f0 < a.nf; f0 += stride) {
     const int64_t f = f0 + lane;
@@ -215,7 +227,7 @@ __global__ void k_face_bins(FaceBinArgs a) {
     float rel = 0.f;
     if (f < a.nf) {
       gid = a.face_gid ? a.face_gid[f] : 0u;
-      const GeomParams P = geom_row(a.g0, a.table, a.face_gid, f);
+      const GeomParams& P = a.table ? a.table[a.face_gid ? a.face_gid[f] : 0u] : a.g0;
       int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
       float ext = 0.f;
 #pragma unroll
@@ -235,7 +247,7 @@ __global__ void k_face_bins(FaceBinArgs a) {
       if (!(ext <= 3.0e38f)) ext = INFINITY;  // a non-finite coordinate
       rel = ext / P.h0_hi;                     // in root cells of the face's own geometry
       const int64_t B = P.B;
-      if (a.sampled) {
+      if constexpr (SAMPLED) {
         sampled_bins<D>(a.X, a.nf, f, P, a.sample_s, lo, hi, [&](int x, int y, int z) {
           atomicAdd(&a.count[P.bin_base + x + B * (y + B * (int64_t)z)], 1u);
         });
@@ -252,9 +264,17 @@ __global__ void k_face_bins(FaceBinArgs a) {
       const uint32_t mx = __reduce_max_sync(grp, __float_as_uint(rel));
       const uint32_t sm = __reduce_add_sync(grp, rel < 1024.0f ? (uint32_t)(rel * 65536.0f) : (1u << 26));
       if (gid != 0xffffffffu && lane == __ffs(grp) - 1) {
-        if (mx) atomicMax(a.fstat + 2 * (int64_t)gid, (unsigned long long)mx);
-        if (sm) atomicAdd(a.fstat + 2 * (int64_t)gid + 1, (unsigned long long)sm);
+        unsigned long long* dst = gid == s_gid ? s_stat : a.fstat + 2 * (int64_t)gid;
+        if (mx) atomicMax(dst, (unsigned long long)mx);
+        if (sm) atomicAdd(dst + 1, (unsigned long long)sm);
       }
+    }
+  }
+  if (a.fstat) {
+    __syncthreads();
+    if (threadIdx.x == 0 && s_gid != 0xffffffffu) {
+      if (s_stat[0]) atomicMax(a.fstat + 2 * (int64_t)s_gid, s_stat[0]);
+      if (s_stat[1]) atomicAdd(a.fstat + 2 * (int64_t)s_gid + 1, s_stat[1]);
     }
   }
 }
@@ -263,8 +283,8 @@ __global__ void k_face_bins(FaceBinArgs a) {
 // the bin's count (which leaves the counts zeroed for the next call) and writes
 // the face id and its payload entry (coordinates, normal, id | first-bin
 // flags, bin coordinates) there.
-template <int D>
-__global__ void k_scatter(ScatterArgs a) {
+template <int D, bool SAMPLED>
+__global__ void __launch_bounds__(kThreads, SAMPLED ? 1 : 4) k_scatter(ScatterArgs a) {
   using E = typename EntryT<D>::type;
   E* payload = static_cast<E*>(a.payload);
   const int64_t nf = a.f.nf;
@@ -306,7 +326,7 @@ __global__ void k_scatter(ScatterArgs a) {
 #pragma unroll
       for (int q = 0; q < (int)(sizeof(E) / 16); ++q) dst[q] = src[q];
     };
-    if (a.f.sampled) {
+    if constexpr (SAMPLED) {
       sampled_bins<D>(a.f.X, nf, f, P, a.f.sample_s, lo, hi, put);
       continue;
     }
@@ -321,7 +341,7 @@ __global__ void k_scatter(ScatterArgs a) {
 // smaller than the tile count and the element count may come from device
 // memory (n_dev, bounded by the capacity n_cap).
 template <typename T, int ITEMS>
-__global__ void __launch_bounds__(kThreads) k_scan(const T* __restrict__ in, T* __restrict__ out, int64_t n_cap,
+__global__ void __launch_bounds__(kThreads, 5) k_scan(const T* __restrict__ in, T* __restrict__ out, int64_t n_cap,
                                                     const uint64_t* n_dev, uint64_t* total, uint64_t* state,
                                                     unsigned* ticket, unsigned* err) {
   __shared__ unsigned s_tile;
@@ -350,26 +370,23 @@ __global__ void __launch_bounds__(kThreads) k_scan(const T* __restrict__ in, T* 
     const long long tile = s_tile;
     if (tile >= ntiles) break;
     const int64_t base = tile * (int64_t)kThreads * ITEMS + (int64_t)threadIdx.x * ITEMS;
-    uint64_t v[ITEMS];
+    T v[ITEMS];  // the items stay in their own width; sums and prefixes are 64-bit
     uint64_t sum = 0;
     const bool full = vec && base + ITEMS <= n;
     if (full) {
       // ITEMS * sizeof(T) bytes as 16-byte loads
-      T t[ITEMS];
       const uint4* src = reinterpret_cast<const uint4*>(in + base);
 #pragma unroll
-      for (int q = 0; q < (int)(ITEMS * sizeof(T) / 16); ++q) reinterpret_cast<uint4*>(t)[q] = src[q];
-#pragma unroll
-      for (int i = 0; i < ITEMS; ++i) v[i] = (uint64_t)t[i];
+      for (int q = 0; q < (int)(ITEMS * sizeof(T) / 16); ++q) reinterpret_cast<uint4*>(v)[q] = src[q];
     } else {
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
         const int64_t j = base + i;
-        v[i] = j < n ? (uint64_t)in[j] : 0ull;
+        v[i] = j < n ? in[j] : (T)0;
       }
     }
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) sum += v[i];
+    for (int i = 0; i < ITEMS; ++i) sum += (uint64_t)v[i];
     const uint64_t incl = warp_inclusive_scan<unsigned long long>(sum);
     if (lane == 31) s_warp[wid] = incl;
     __syncthreads();
@@ -380,26 +397,25 @@ __global__ void __launch_bounds__(kThreads) k_scan(const T* __restrict__ in, T* 
     }
     __syncthreads();
     const uint64_t warp_excl = wid > 0 ? s_warp[wid - 1] : 0ull;
+    const uint64_t agg = s_warp[kThreads / 32 - 1];
     if (wid == 0) {
-      const uint64_t agg = s_warp[kThreads / 32 - 1];
-      const uint64_t pre = lookback_warp(state, tile, agg, err);
-      if (lane == 0) {
-        s_prefix = pre;
-        if (tile == ntiles - 1) *total = pre + agg;
-      }
+      const uint64_t p = lookback_warp(state, tile, agg, err);
+      if (lane == 0) s_prefix = p;
     }
     __syncthreads();
-    uint64_t run = s_prefix + warp_excl + incl - sum;
+    const uint64_t pre = s_prefix;
+    if (threadIdx.x == 0 && tile == ntiles - 1) *total = pre + agg;
+    uint64_t run = pre + warp_excl + incl - sum;
     if (full) {
-      T t[ITEMS];
 #pragma unroll
-      for (int i = 0; i < ITEMS; ++i) {
-        t[i] = (T)run;
-        run += v[i];
+      for (int i = 0; i < ITEMS; ++i) {  // exclusive prefixes in place
+        const T x = v[i];
+        v[i] = (T)run;
+        run += x;
       }
       uint4* dst = reinterpret_cast<uint4*>(out + base);
 #pragma unroll
-      for (int q = 0; q < (int)(ITEMS * sizeof(T) / 16); ++q) dst[q] = reinterpret_cast<const uint4*>(t)[q];
+      for (int q = 0; q < (int)(ITEMS * sizeof(T) / 16); ++q) dst[q] = reinterpret_cast<const uint4*>(v)[q];
     } else {
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
@@ -509,10 +525,17 @@ int launch_face_normals(const float* X, int64_t nf, float* nrm, FaceRec3* rec, c
 int launch_face_bins(const FaceBinArgs& a, cudaStream_t st) {
   if (a.nf <= 0) return 0;
   const int gr = grid_for(a.nf, kThreads);
-  if (a.dim == 3)
-    k_face_bins<3><<<gr, kThreads, 0, st>>>(a);
-  else
-    k_face_bins<2><<<gr, kThreads, 0, st>>>(a);
+  if (a.dim == 3) {
+    if (a.sampled)
+      k_face_bins<3, true><<<gr, kThreads, 0, st>>>(a);
+    else
+      k_face_bins<3, false><<<gr, kThreads, 0, st>>>(a);
+  } else {
+    if (a.sampled)
+      k_face_bins<2, true><<<gr, kThreads, 0, st>>>(a);
+    else
+      k_face_bins<2, false><<<gr, kThreads, 0, st>>>(a);
+  }
   return 1;
 }
 
@@ -567,10 +590,17 @@ int launch_scan_u64(const uint64_t* in, uint64_t* out, int64_t n, const uint64_t
 int launch_scatter(const ScatterArgs& a, cudaStream_t st) {
   if (a.f.nf <= 0) return 0;
   const int g = grid_for(a.f.nf, kThreads);
-  if (a.f.dim == 3)
-    k_scatter<3><<<g, kThreads, 0, st>>>(a);
-  else
-    k_scatter<2><<<g, kThreads, 0, st>>>(a);
+  if (a.f.dim == 3) {
+    if (a.f.sampled)
+      k_scatter<3, true><<<g, kThreads, 0, st>>>(a);
+    else
+      k_scatter<3, false><<<g, kThreads, 0, st>>>(a);
+  } else {
+    if (a.f.sampled)
+      k_scatter<2, true><<<g, kThreads, 0, st>>>(a);
+    else
+      k_scatter<2, false><<<g, kThreads, 0, st>>>(a);
+  }
   return 1;
 }
 
