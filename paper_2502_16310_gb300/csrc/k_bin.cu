@@ -286,53 +286,114 @@ __global__ void __launch_bounds__(kThreads) k_face_bins(FaceBinArgs a) {
 template <int D, bool SAMPLED>
 __global__ void __launch_bounds__(kThreads, SAMPLED ? 1 : 4) k_scatter(ScatterArgs a) {
   using E = typename EntryT<D>::type;
+  constexpr int QE = (int)(sizeof(E) / 16);  // 16-byte quarters of an entry
   E* payload = static_cast<E*>(a.payload);
   const int64_t nf = a.f.nf;
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
-    const GeomParams& P = a.f.table ? a.f.table[a.f.face_gid ? a.f.face_gid[f] : 0u] : a.f.g0;
-    const int64_t B = P.B, bin_base = P.bin_base;
-    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  if constexpr (SAMPLED) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+      const GeomParams& P = a.f.table ? a.f.table[a.f.face_gid ? a.f.face_gid[f] : 0u] : a.f.g0;
+      const int64_t B = P.B, bin_base = P.bin_base;
+      int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const uint32_t r = a.f.frange[(int64_t)c * nf + f];
-      lo[c] = (int)(r & 0xffffu);
-      hi[c] = (int)(r >> 16);
-    }
-    E e{};
-    if constexpr (D == 3) {
-      // the face record's first 48 bytes are the entry's vertices and normal
-      const float4* R = reinterpret_cast<const float4*>(a.rec + f);
-      float4* q = reinterpret_cast<float4*>(&e);
-      q[0] = __ldg(R);
-      q[1] = __ldg(R + 1);
-      q[2] = __ldg(R + 2);
-    } else {
+      for (int c = 0; c < D; ++c) {
+        const uint32_t r = a.f.frange[(int64_t)c * nf + f];
+        lo[c] = (int)(r & 0xffffu);
+        hi[c] = (int)(r >> 16);
+      }
+      E e{};
+      if constexpr (D == 3) {
+        // the face record's first 48 bytes are the entry's vertices and normal
+        const float4* R = reinterpret_cast<const float4*>(a.rec + f);
+        float4* q = reinterpret_cast<float4*>(&e);
+        q[0] = __ldg(R);
+        q[1] = __ldg(R + 1);
+        q[2] = __ldg(R + 2);
+      } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) e.v[j] = a.f.X[(int64_t)j * nf + f];
-    }
-    auto put = [&](int x, int y, int z) {
-      const int64_t b = bin_base + x + B * (y + B * (int64_t)z);
-      const uint32_t old = atomicSub(&a.f.count[b], 1u);
-      const int64_t pos = (int64_t)a.offsets[b] + old - 1;
-      a.ids[pos] = (uint32_t)f;
-      uint32_t flags = (x == lo[0] ? (1u << 29) : 0u) | (y == lo[1] ? (1u << 30) : 0u);
-      if (D == 3) flags |= (z == lo[2] ? (1u << 31) : 0u);
-      e.id = (uint32_t)f | flags;
-      e.bin[0] = (uint32_t)x;
-      e.bin[1] = (uint32_t)y;
-      e.bin[2] = (uint32_t)z;
-      const float4* src = reinterpret_cast<const float4*>(&e);
-      float4* dst = reinterpret_cast<float4*>(payload + pos);
+        for (int j = 0; j < 4; ++j) e.v[j] = a.f.X[(int64_t)j * nf + f];
+      }
+      sampled_bins<D>(a.f.X, nf, f, P, a.f.sample_s, lo, hi, [&](int x, int y, int z) {
+        const int64_t b = bin_base + x + B * (y + B * (int64_t)z);
+        const uint32_t old = atomicSub(&a.f.count[b], 1u);
+        const int64_t pos = (int64_t)a.offsets[b] + old - 1;
+        a.ids[pos] = (uint32_t)f;
+        uint32_t flags = (x == lo[0] ? (1u << 29) : 0u) | (y == lo[1] ? (1u << 30) : 0u);
+        if (D == 3) flags |= (z == lo[2] ? (1u << 31) : 0u);
+        e.id = (uint32_t)f | flags;
+        e.bin[0] = (uint32_t)x;
+        e.bin[1] = (uint32_t)y;
+        e.bin[2] = (uint32_t)z;
+        const float4* src = reinterpret_cast<const float4*>(&e);
+        float4* dst = reinterpret_cast<float4*>(payload + pos);
 #pragma unroll
-      for (int q = 0; q < (int)(sizeof(E) / 16); ++q) dst[q] = src[q];
-    };
-    if constexpr (SAMPLED) {
-      sampled_bins<D>(a.f.X, nf, f, P, a.f.sample_s, lo, hi, put);
-      continue;
+        for (int q = 0; q < QE; ++q) dst[q] = src[q];
+      });
     }
-    for (int z = lo[2]; z <= hi[2]; ++z)
-      for (int y = lo[1]; y <= hi[1]; ++y)
-        for (int x = lo[0]; x <= hi[0]; ++x) put(x, y, z);
+  } else {
+    // Lane = face; the warp steps through the incidences of its 32 faces together.  Each
+    // incidence's entry is staged in shared memory and the warp writes 32 / QE whole entries
+    // per store instruction (QE lanes per entry), so every entry leaves as full 32-byte
+    // sectors instead of QE scattered 16-byte pieces.
+    __shared__ float4 s_ent[kThreads / 32][32 * QE];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t f0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); f0 < nf; f0 += stride) {
+      const int64_t f = f0 + lane;
+      int n = 0, nx = 1, ny = 1;
+      int lo[3] = {0, 0, 0};
+      int64_t B = 0, bin_base = 0;
+      float4 head[QE - 1];  // the entry's coordinates (and normal), the same for all its bins
+      if (f < nf) {
+        const GeomParams& P = a.f.table ? a.f.table[a.f.face_gid ? a.f.face_gid[f] : 0u] : a.f.g0;
+        B = P.B;
+        bin_base = P.bin_base;
+        int ext[3] = {1, 1, 1};
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const uint32_t r = a.f.frange[(int64_t)c * nf + f];
+          lo[c] = (int)(r & 0xffffu);
+          ext[c] = (int)(r >> 16) - lo[c] + 1;
+        }
+        nx = ext[0];
+        ny = ext[1];
+        n = ext[0] * ext[1] * ext[2];
+        if constexpr (D == 3) {
+          // the face record's first 48 bytes are the entry's vertices and normal
+          const float4* R = reinterpret_cast<const float4*>(a.rec + f);
+          head[0] = __ldg(R);
+          head[1] = __ldg(R + 1);
+          head[2] = __ldg(R + 2);
+        } else {
+          head[0] = make_float4(a.f.X[f], a.f.X[nf + f], a.f.X[2 * nf + f], a.f.X[3 * nf + f]);
+        }
+      }
+      const int m = __reduce_max_sync(0xffffffffu, n);
+      for (int k = 0; k < m; ++k) {
+        int64_t pos = -1;
+        if (k < n) {
+          const int x = lo[0] + k % nx, y = lo[1] + (k / nx) % ny, z = lo[2] + k / (nx * ny);
+          const int64_t b = bin_base + x + B * (y + B * (int64_t)z);
+          const uint32_t old = atomicSub(&a.f.count[b], 1u);
+          pos = (int64_t)a.offsets[b] + old - 1;
+          a.ids[pos] = (uint32_t)f;
+          uint32_t flags = (x == lo[0] ? (1u << 29) : 0u) | (y == lo[1] ? (1u << 30) : 0u);
+          if (D == 3) flags |= (z == lo[2] ? (1u << 31) : 0u);
+#pragma unroll
+          for (int q = 0; q < QE - 1; ++q) s_ent[wid][lane * QE + q] = head[q];
+          s_ent[wid][lane * QE + QE - 1] =
+              make_float4(__uint_as_float((uint32_t)f | flags), __uint_as_float((uint32_t)x),
+                          __uint_as_float((uint32_t)y), __uint_as_float((uint32_t)z));
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < QE; ++r) {
+          const int j = r * (32 / QE) + lane / QE;  // entry written by this lane in round r
+          const int64_t pj = __shfl_sync(0xffffffffu, pos, j);
+          if (pj >= 0) reinterpret_cast<float4*>(payload + pj)[lane % QE] = s_ent[wid][j * QE + lane % QE];
+        }
+        __syncwarp();  // the next incidence reuses the staging area
+      }
+    }
   }
 }
 
