@@ -97,6 +97,21 @@ def test_bin_density_independence(B):
     assert np.array_equal(ref["link_q"], out["link_q"])
 
 
+@pytest.mark.parametrize("B", [200, 256])
+def test_fine_bin_grid(B):
+    """Grids of 8.0 M and 16.8 M bins: thousands of scan tiles chained by the look-back (at B = 200
+    the last tile is partial).  Bins exact against the oracle; every result equal to that of B = 1."""
+    w = small_workload("sphere3")
+    ref = U.run_gpu(w, B=1)
+    out = U.run_gpu(w, B=B)
+    geo, off, ids = _oracle(w, B)
+    U.compare_bins(out["offsets"], out["ids"], off, ids)
+    for L in range(len(ref["levels"])):
+        assert np.array_equal(ref["levels"][L]["mask"], out["levels"][L]["mask"])
+    assert np.array_equal(ref["adj_ids"], out["adj_ids"])
+    assert np.array_equal(ref["link_q"], out["link_q"])
+
+
 def test_deterministic_repeat():
     w = small_workload("bumpy3")
     a = U.run_gpu(w)
