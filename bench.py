@@ -58,6 +58,8 @@ def parse_args(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-graph", action="store_true", help="time the eager path instead of graph replays")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
+    p.add_argument("--bin-only", action="store_true",
+                   help="time the binning alone (load once, then count, scan and scatter per step)")
     p.add_argument("--batch-geoms", type=int, default=48)
     p.add_argument("--e2e-threads", type=int, default=0,
                    help="host threads (one context each) of the e2e leg; 0 = three threads for steps that "
@@ -596,6 +598,54 @@ def bin_roofline(w, nnz, t_bin_ms):
             "peak_source": src}
 
 
+def run_bin_only(args, local):
+    """Binning alone on the workload's geometry: per step the three binning kernels (count, scan,
+    scatter), each timed by the library with CUDA events on its stream, L2 flushed between steps.  The
+    device holds only the geometry and the bins, so this is also the small case for kernel captures of
+    the binning."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+    from paper_2502_16310_gb300 import binding as Bd
+    from synth import workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    g = AmrGeom(w.dim, (w.root,) * w.dim)
+    g.load(torch.from_numpy(w.verts).to(dev), torch.from_numpy(w.idx).to(dev))
+    for _ in range(max(args.warmup, 1)):
+        nnz = int(g.bin(w.bins)["nnz"])
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    g.timing(True)
+    g.timing_reset()
+    sampler.start()
+    l0 = Bd.amr_launch_count(g.ctx)
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        g.bin(w.bins)
+    torch.cuda.synchronize()
+    launches = Bd.amr_launch_count(g.ctx) - l0
+    clocks = sampler.stop()
+    tk = g.timings()
+    g.timing(False)
+    names = ("bin_count", "bin_scan", "bin_scatter")
+    kern = {k: tk[k][0] / args.steps for k in names if k in tk}
+    t_bin = sum(kern.values())
+    g.close()
+    binning = bin_roofline(w, nnz, t_bin)
+    return {"metric": "faces binned/s", "value": w.n_faces / (t_bin * 1e-3), "unit": "faces/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_bin, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {w.description}",
+                       "faces": w.n_faces, "bins_per_axis": w.bins, "incidences": nnz,
+                       "l2": "flushed between steps (512 MB write)"},
+            "kernels_ms_per_step": {k: round(v, 5) for k, v in kern.items()},
+            "roofline": binning, "clocks": clocks, "gpu_launches": int(launches)}
+
+
 def run_e2e(w, args, dev):
     """Same metric through the public API with host buffers: every step uploads its inputs from pinned
     host memory (inside amr_geom_load) and copies every output back to pinned host memory, as a user
@@ -820,6 +870,10 @@ def main(argv=None):
         torch.cuda.set_device(local)
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.bin_only:
+        if rank == 0:
+            print(json.dumps(run_bin_only(args, local)), flush=True)
+        return 0
     line = run_ours(args, rank, world, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from synth import workload
