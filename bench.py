@@ -646,6 +646,15 @@ def run_bin_only(args, local):
             "roofline": binning, "clocks": clocks, "gpu_launches": int(launches)}
 
 
+def e2e_layout(d2h_bytes, threads_arg):
+    """(host threads, contexts per thread) of the e2e leg: as asked, else three threads with one
+    context each for steps that copy back less than 2 GB, one thread alternating two contexts for
+    larger ones."""
+    if threads_arg > 0:
+        return threads_arg, 1
+    return (1, 2) if d2h_bytes >= 2e9 else (3, 1)
+
+
 def run_e2e(w, args, dev):
     """Same metric through the public API with host buffers: every step uploads its inputs from pinned
     host memory (inside amr_geom_load) and copies every output back to pinned host memory, as a user
@@ -697,12 +706,7 @@ def run_e2e(w, args, dev):
     first = new_slot()
     step(first, 0)
     torch.cuda.synchronize()
-    if args.e2e_threads > 0:
-        NT, NC = args.e2e_threads, 1
-    elif out[0][1] >= 2e9:
-        NT, NC = 1, 2
-    else:
-        NT, NC = 3, 1
+    NT, NC = e2e_layout(out[0][1], args.e2e_threads)
     slots = [[first if i == 0 and c == 0 else new_slot() for c in range(NC)] for i in range(NT)]
     errors = []
 
