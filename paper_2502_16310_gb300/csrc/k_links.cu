@@ -17,6 +17,8 @@
 // with a forward error bound; t = num / (h c_i.n) is accurate to a few ulps.
 // Undecided signs go to an FP64 evaluation.  Links leave in (cell, direction)
 // order through a single-pass ticketed look-back over thread blocks.
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace amr {
@@ -577,14 +579,16 @@ size_t links_scratch_bytes(int64_t n_adj) {
 int launch_links(const LinkArgs& a, void* scratch, int num_sms, cudaStream_t st) {
   cudaMemsetAsync(scratch, 0, links_scratch_bytes(a.cap_rows), st);
   // persistent: as many blocks as fit on the GPU at once, tiles handed out by ticket
-  static int occ[2] = {0, 0};
-  int& o = occ[a.dim == 3 ? 1 : 0];
+  // blocks per SM, asked once per dimension (contexts on several host threads may ask together)
+  static std::atomic<int> occ[2] = {0, 0};
+  int o = occ[a.dim == 3 ? 1 : 0].load(std::memory_order_relaxed);
   if (o == 0) {
     if (a.dim == 3)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_links<3>, kLThreads, 0);
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_links<2>, kLThreads, 0);
     if (o < 1) o = 1;
+    occ[a.dim == 3 ? 1 : 0].store(o, std::memory_order_relaxed);
   }
   int64_t tiles = (a.cap_rows + kLRows - 1) / kLRows;
   if (tiles < 1) tiles = 1;
