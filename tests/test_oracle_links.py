@@ -209,3 +209,28 @@ def test_q_grad_matches_finite_differences(oracle_lib, kind):
                 assert an == pytest.approx(num, rel=1e-5, abs=1e-6 * (abs(an) + 1.0)), (f, k, c, an, num)
                 n_cmp += 1
     assert n_cmp > 50
+
+
+@pytest.mark.parametrize("lattice", [9, 19])
+def test_velocity_sets(oracle_lib, lattice):
+    """The oracle's velocity sets are DdQq (rest vector first): the 2D set is the 8 neighbours of the
+    square, the 3D set the 6 face and 12 edge neighbours of the cube; each closed under negation, with
+    zero sum, and isotropic second moments (sum c_a c_b proportional to the identity)."""
+    from oracle.oracle import lattice_dirs
+
+    c = lattice_dirs(lattice).astype(np.int64)
+    D = 2 if lattice == 9 else 3
+    assert c.shape == (lattice, 3) and np.all(c[0] == 0)
+    if D == 2:
+        assert np.all(c[:, 2] == 0)
+    m = c[1:, :D]
+    assert len({tuple(r) for r in m.tolist()}) == lattice - 1
+    n2 = (m * m).sum(axis=1)
+    want = [(1, 4), (2, 4)] if D == 2 else [(1, 6), (2, 12)]
+    assert sorted(np.unique(n2, return_counts=True)[0].tolist()) == [w[0] for w in want]
+    assert [int((n2 == k).sum()) for k, _ in want] == [n for _, n in want]
+    assert np.all(np.abs(m) <= 1)
+    assert {tuple(r) for r in m.tolist()} == {tuple(r) for r in (-m).tolist()}
+    assert np.all(m.sum(axis=0) == 0)
+    second = m.T @ m
+    assert np.array_equal(second, second[0, 0] * np.eye(D, dtype=np.int64))
