@@ -358,6 +358,14 @@ class _LazyDict(dict):
     def items(self):
         return [(k, self[k]) for k in self]
 
+    def __iter__(self):
+        # defined here so that dict(d) and {**d} go through keys() and __getitem__ (CPython copies a
+        # dict subclass's raw entries when it keeps dict's own iterator)
+        return dict.__iter__(self)
+
+    def copy(self):
+        return {k: self[k] for k in self}
+
 
 def _view(ptr, shape, dtype):
     import torch
