@@ -52,3 +52,19 @@ def test_oracle_does_not_link_cuda_library():
         if fn.endswith(".py"):
             assert "oracle" not in open(os.path.join(ROOT, "paper_2502_16310_gb300", fn)).read().replace(
                 "no oracle", "")
+
+
+def test_product_path_never_reaches_the_oracle():
+    """The package, its kernels and the public header name nothing of oracle/ (the checker is test
+    infrastructure only), and the package fails loudly instead of falling back when the CUDA library
+    cannot be loaded."""
+    pkg = os.path.join(ROOT, "paper_2502_16310_gb300")
+    files = [os.path.join(pkg, f) for f in os.listdir(pkg) if f.endswith(".py")]
+    files += [os.path.join(pkg, "csrc", f) for f in os.listdir(os.path.join(pkg, "csrc"))
+              if f.endswith((".cu", ".cuh", ".h"))]
+    files += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
+    for fn in files:
+        text = open(fn).read()
+        assert not re.search(r"\boracle\b|amr_oracle|orc_", text), fn
+    binding = open(os.path.join(pkg, "binding.py")).read()
+    assert "raise ImportError" in binding
