@@ -75,6 +75,19 @@ typedef struct {
   double origin[3];      /* domain origin */
   double h0;             /* level-0 cell size, > 0 */
   void* stream;          /* cudaStream_t to order all work on; NULL = a stream the context creates */
+  /* Optional device allocator (give both or neither; NULL = cudaMallocAsync /
+   * cudaFreeAsync on the context's stream).  Every device buffer the context owns
+   * is taken from dev_alloc(bytes, user), which returns device memory of the
+   * current device usable on the context's stream (NULL = out of memory: the
+   * call fails with ENOMEM), and is handed back with dev_free(ptr, user) once the
+   * context's stream has finished every use of it (the library synchronises the
+   * stream first).  Both are called on the host thread that calls the library;
+   * buffers grow only in eager calls, never while a graph is replayed.  Pinned
+   * host staging (a few KB) is not taken from it.  amr_bin_faces_static ignores
+   * these fields. */
+  void* (*dev_alloc)(size_t bytes, void* user);
+  void (*dev_free)(void* ptr, void* user);
+  void* user;
 } amr_domain;
 
 /* Create a context on the current CUDA device.  *out receives the handle.
@@ -108,13 +121,23 @@ AMR_API amr_status amr_geom_load(amr_ctx* ctx, const float* coords, int64_t n_ve
  * (B = 1 is the paper's naive scheme), B^dim <= 2^30.  Bin b = bx + B*by (+ B^2*bz).
  * offsets[b]..offsets[b+1] index the face ids of bin b in `ids`; the order
  * within a bin is unspecified (atomic scatter).  EOVERFLOW: more than 2^32 - 1
- * (face, bin) entries. */
+ * (face, bin) entries.
+ * payload: one entry per (face, bin) entry, in the order of `ids` (entry k
+ * belongs to ids[k]), so that a bin's faces with their coordinates are one
+ * contiguous run of memory; payload_bytes per entry, 16-byte aligned:
+ *   3D (64 B): f32 v[9] (vertex-major coordinates), f32 n[3] (the normal
+ *              (v1-v0)x(v2-v0) formed in FP64, rounded to FP32), u32 id, u32 bin[3];
+ *   2D (32 B): f32 v[4], u32 id, u32 bin[3] (bin[2] = 0);
+ * id = face id in bits 0..28, bit 29 / 30 / 31 set when this bin is the first
+ * of the face's bin range along x / y / z; bin = this entry's bin coordinates. */
 typedef struct {
   int B;
   int64_t n_bins;             /* B^dim */
   int64_t nnz;                /* total (face, bin) entries */
   const uint32_t* offsets;    /* device [n_bins + 1] */
   const uint32_t* ids;        /* device [nnz] */
+  const void* payload;        /* device [nnz] entries of payload_bytes (see above) */
+  int64_t payload_bytes;      /* 64 (3D) or 32 (2D) */
 } amr_bins_view;
 AMR_API amr_status amr_bin_faces(amr_ctx* ctx, int bin_density, amr_bins_view* out);
 
@@ -358,13 +381,18 @@ AMR_API int64_t amr_launch_count(const amr_ctx* ctx);
  *   ids        DEVICE u32 [ids_capacity], written (face ids grouped by bin; order
  *              within a bin unspecified).
  *   nnz        HOST, receives the number of (face, bin) entries.
- * Returns EINVAL for sizes beyond the maxima or non-device pointers (nothing is
- * launched), EOVERFLOW when nnz > ids_capacity (offsets and *nnz are still valid,
- * ids is untouched).  The call waits for the count and the scan; the ids are
- * written asynchronously on the stream.  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call shares the one array per device, so calls
- * whose work overlaps on the GPU (other streams or threads) race: serialise them. */
+ * Returns EINVAL for sizes beyond the maxima or pointers that are not device
+ * (or managed) memory of the current device (nothing is launched), EINVAL too
+ * when a coordinate is NaN or infinite (checked on the device; offsets, ids and
+ * *nnz are then not valid), EOVERFLOW when nnz > ids_capacity (offsets and *nnz
+ * are still valid, ids is untouched).  The call waits on its stream for the
+ * count and the scan before it returns; the ids are written asynchronously on
+ * the stream after that.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not use this
+ * entry point after a cudaDeviceReset of that device.  Every call shares the one
+ * array per device, so calls whose work overlaps on the GPU (other streams or
+ * threads) race: serialise them. */
 #define AMR_STATIC_MAX_BINS (1 << 18)
 #define AMR_STATIC_MAX_FACES (1 << 17)
 AMR_API amr_status amr_bin_faces_static(const amr_domain* dom, const float* faces, int64_t n_faces, int bin_density,

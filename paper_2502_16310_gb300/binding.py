@@ -42,14 +42,18 @@ class AmrError(RuntimeError):
         self.status = status
 
 
+DEV_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+DEV_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class amr_domain(C.Structure):
     _fields_ = [("dim", C.c_int), ("root_blocks", C.c_int * 3), ("origin", C.c_double * 3), ("h0", C.c_double),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("dev_alloc", DEV_ALLOC), ("dev_free", DEV_FREE), ("user", C.c_void_p)]
 
 
 class amr_bins_view(C.Structure):
     _fields_ = [("B", C.c_int), ("n_bins", C.c_int64), ("nnz", C.c_int64), ("offsets", C.c_void_p),
-                ("ids", C.c_void_p)]
+                ("ids", C.c_void_p), ("payload", C.c_void_p), ("payload_bytes", C.c_int64)]
 
 
 class amr_refine_params(C.Structure):
@@ -181,9 +185,17 @@ def _check(ctx, st: int):
 
 # -- C-named entry points ------------------------------------------------------
 
-def amr_create(dim: int, root_blocks, origin=(0.0, 0.0, 0.0), h0: float | None = None, stream: int | None = None):
+def amr_create(dim: int, root_blocks, origin=(0.0, 0.0, 0.0), h0: float | None = None, stream: int | None = None,
+               dev_alloc=None, dev_free=None, user=None):
+    """dev_alloc / dev_free: optional DEV_ALLOC / DEV_FREE callbacks (both or neither) that every device buffer
+    of the context is taken from and returned to; the caller keeps them alive until amr_destroy."""
     L = lib()
     d = amr_domain()
+    if dev_alloc is not None:
+        d.dev_alloc = dev_alloc
+    if dev_free is not None:
+        d.dev_free = dev_free
+    d.user = user
     d.dim = dim
     rb = list(root_blocks) + [1] * (3 - len(root_blocks))
     for a in range(3):
@@ -391,7 +403,10 @@ class AmrGeom:
     The context's work is ordered on the current torch CUDA stream at creation.
     """
 
-    def __init__(self, dim: int, root_blocks, origin=(0.0, 0.0, 0.0), h0: float | None = None):
+    def __init__(self, dim: int, root_blocks, origin=(0.0, 0.0, 0.0), h0: float | None = None, dev_alloc=None,
+                 dev_free=None):
+        """dev_alloc / dev_free: optional DEV_ALLOC / DEV_FREE callbacks (both or neither) from which the
+        context takes every device buffer (kept alive with the context)."""
         import torch
 
         if not torch.cuda.is_available():
@@ -402,7 +417,8 @@ class AmrGeom:
         # torch's default stream has handle 0; pass the legacy default stream (handle 1) so the
         # context's work stays ordered with torch's own kernels and copies
         handle = self.stream.cuda_stream or 1
-        self.ctx = amr_create(dim, self.root, origin, h0, handle)
+        self._hooks = (dev_alloc, dev_free)
+        self.ctx = amr_create(dim, self.root, origin, h0, handle, dev_alloc=dev_alloc, dev_free=dev_free)
         self._keep = []
         self.bins = None
         self.last_result = None
@@ -446,9 +462,13 @@ class AmrGeom:
 
         v = amr_bin_faces_sampled(self.ctx, B) if sampled else amr_bin_faces(self.ctx, B)
         off, ids, nb, nnz = v.offsets, v.ids, int(v.n_bins), int(v.nnz)
+        pay, pw = v.payload, int(v.payload_bytes) // 4
+        # payload: [nnz, 16] (3D) or [nnz, 8] (2D) 32-bit words per entry (coordinates and normal as
+        # float bits, then id with flags, then bin coordinates)
         self.bins = _LazyDict(B=v.B, n_bins=nb, nnz=nnz,
                               offsets=_Deferred(lambda: _view(off, (nb + 1,), torch.int32)),
-                              ids=_Deferred(lambda: _view(ids, (nnz,), torch.int32)))
+                              ids=_Deferred(lambda: _view(ids, (nnz,), torch.int32)),
+                              payload=_Deferred(lambda: _view(pay, (nnz, pw), torch.int32)))
         return self.bins
 
     def refine(self, n_levels: int, d_abs=0.0, d_rel=1.0, lattice=0, want_adjacency=True, want_links=None,

@@ -172,15 +172,33 @@ amr_status fail(amr_ctx* c, amr_status s, const char* fmt, ...) {
   } while (0)
 
 // Grow a buffer that no captured graph reads (the layout generation stays).
+// Hand a device buffer back: in stream order (cudaFreeAsync), or to the caller's
+// allocator once the context's stream has finished every use of it.
+cudaError_t dev_release(amr_ctx* ctx, void* p) {
+  if (!p) return cudaSuccess;
+  if (ctx->dom.dev_free) {
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    ctx->dom.dev_free(p, ctx->dom.user);
+    return e;
+  }
+  return cudaFreeAsync(p, ctx->stream);
+}
+
 amr_status ensure_aux(amr_ctx* ctx, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.cap >= bytes) return AMR_OK;
   if (b.p) {
-    CK(cudaFreeAsync(b.p, ctx->stream));
+    CK(dev_release(ctx, b.p));
     b.p = nullptr;
     b.cap = 0;
   }
   size_t want = bytes + bytes / 4 + 256;
+  if (ctx->dom.dev_alloc) {
+    b.p = ctx->dom.dev_alloc(want, ctx->dom.user);
+    if (!b.p) return fail(ctx, AMR_ENOMEM, "device allocation of %zu bytes failed (caller's allocator)", want);
+    b.cap = want;
+    return AMR_OK;
+  }
   cudaError_t e = cudaMallocAsync(&b.p, want, ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -204,13 +222,13 @@ amr_status ensure_keep(amr_ctx* ctx, DevBuf& b, size_t bytes, size_t keep) {
   DevBuf nb;
   TRY(ensure(ctx, nb, bytes));
   if (b.p && keep) CK(cudaMemcpyAsync(nb.p, b.p, keep < b.cap ? keep : b.cap, cudaMemcpyDeviceToDevice, ctx->stream));
-  if (b.p) CK(cudaFreeAsync(b.p, ctx->stream));
+  if (b.p) CK(dev_release(ctx, b.p));
   b = nb;
   return AMR_OK;
 }
 
 void release(amr_ctx* ctx, DevBuf& b) {
-  if (b.p) cudaFreeAsync(b.p, ctx->stream);
+  if (b.p) dev_release(ctx, b.p);
   b.p = nullptr;
   b.cap = 0;
 }
@@ -458,7 +476,7 @@ void amr_ctx_free(amr_ctx* ctx) {
                    &ctx->link_cell, &ctx->link_dir,     &ctx->link_q,     &ctx->link_face,  &ctx->idx,
                    &ctx->vert_off,  &ctx->vert_corners, &ctx->face_off,   &ctx->face_links, &ctx->sort_keys,
                    &ctx->grad_face, &ctx->sort_scratch, &ctx->group_cnt,  &ctx->lvl_ptrs,   &ctx->table,
-                   &ctx->face_gid};
+                   &ctx->face_gid,  &ctx->fstat,        &ctx->spill,      &ctx->calg,       &ctx->defer};
   for (DevBuf* b : all) release(ctx, *b);
   for (int L = 0; L < AMR_MAX_LEVELS; ++L) {
     LevelBufs& l = ctx->lv[L];
@@ -478,10 +496,6 @@ void amr_ctx_free(amr_ctx* ctx) {
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   if (ctx->h_stat) cudaFreeHost(ctx->h_stat);
-  release(ctx, ctx->fstat);
-  release(ctx, ctx->spill);
-  release(ctx, ctx->calg);
-  release(ctx, ctx->defer);
 }
 
 // Binning of every geometry of the table in one pass (count, scan, scatter).
@@ -708,7 +722,8 @@ RefineLevel level_args(amr_ctx* ctx, const Plan& P, int L) {
     a.cap_recs = ctx->cap_recs;
     a.rec_count = ctx->d_scal + SC_REC + L;
     a.rec_desc = static_cast<uint64_t*>(ctx->lv[L].desc.p);
-    a.spill = ctx->want_spill ? static_cast<SurvRec*>(ctx->spill.p) : nullptr;
+    a.spill = ctx->want_spill || refine_by_groups(a.dim, L, P.pred, P.search) ? static_cast<SurvRec*>(ctx->spill.p)
+                                                                                : nullptr;
   }
   a.counters = ctx->counters;
   a.work = ctx->d_work;
@@ -778,7 +793,8 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
         }
         // blocks with more survivor records than shared memory stages were seen: a spill area for
         // every warp the refine launch can hold (32 per SM)
-        if (ctx->want_spill)
+        // (a level marked by parent groups always stages a group's records past shared memory there)
+        if (ctx->want_spill || refine_by_groups(D, L, P.pred, P.search))
           TRY(ensure(ctx, ctx->spill, sizeof(SurvRec) * (size_t)kSpillCap * 32 * (size_t)ctx->num_sms));
       }
     }
@@ -1161,6 +1177,7 @@ amr_status amr_create(const amr_domain* dom, amr_ctx** out) {
   if (!dom || (dom->dim != 2 && dom->dim != 3) || !(dom->h0 > 0.0)) return AMR_EINVAL;
   for (int a = 0; a < dom->dim; ++a)
     if (dom->root_blocks[a] < 1 || dom->root_blocks[a] > (1 << 20)) return AMR_EINVAL;
+  if (!dom->dev_alloc != !dom->dev_free) return AMR_EINVAL;  // both allocator hooks or neither
   amr_ctx* ctx = new amr_ctx();
   ctx->dom = *dom;
   for (int a = dom->dim; a < 3; ++a) ctx->dom.root_blocks[a] = 1;
@@ -1273,6 +1290,8 @@ static amr_status bin_faces_impl(amr_ctx* ctx, int B, amr_bins_view* out, bool s
   out->nnz = ctx->nnz;
   out->offsets = static_cast<const uint32_t*>(ctx->offsets.p);
   out->ids = static_cast<const uint32_t*>(ctx->ids.p);
+  out->payload = ctx->payload.p;
+  out->payload_bytes = D == 3 ? (int64_t)sizeof(Entry3) : (int64_t)sizeof(Entry2);
   return AMR_OK;
 }
 

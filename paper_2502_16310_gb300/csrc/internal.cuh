@@ -358,6 +358,9 @@ __device__ __forceinline__ T warp_inclusive_scan(T v) {
 // from device memory (so that launches can be captured in a CUDA graph before
 // the sizes are known); the host passes a capacity instead.
 // ---------------------------------------------------------------------------
+// Streaming multiprocessors of the current device (queried once per device);
+// grids of the grid-stride kernels are capped at a multiple of it.
+int current_sm_count();
 // Gather nf faces into the SoA array X (row stride ld, default nf) starting at face f0.
 int launch_load_indexed(int dim, const float* verts, int64_t nv, const int32_t* idx, int64_t nf, float* X,
                         unsigned* err, cudaStream_t st, int64_t ld = -1, int64_t f0 = 0);
@@ -460,6 +463,13 @@ struct RefineLevel {
 };
 constexpr int kMaxBatch = 8;
 int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st);
+// Levels that launch_refine marks by parent groups (one warp per marked parent's 8
+// children): 3D box predicate, whole-query-box search, below the roots.  The
+// finest such level then always stages survivor records past shared memory in
+// the spill area.
+inline bool refine_by_groups(int dim, int level, int pred, int search) {
+  return dim == 3 && level > 0 && pred == 0 && search == 0;
+}
 
 // Face-by-face marking of the blocks of a level whose only output is the mask
 // (box or point predicate, whole-domain search): lv.mask / lv.flag zeroed and

@@ -869,6 +869,408 @@ __global__ void __launch_bounds__(256) k_refine(RefineLevel a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Refinement by parent groups (3D box predicate, levels below the roots).
+//
+// Every block of such a level is one of the 8 children of a marked parent,
+// and the children of a parent are consecutive (slot order).  One warp takes a
+// parent's 8 children together: it walks the bins of the parent box inflated
+// by d_L once (the union of the children's query boxes), deduplicates, and
+// culls each candidate against the whole inflated parent box; every survivor
+// is then culled against each child's box (lane-parallel, certified, all 13
+// axes), and only the remaining (face, child) pairs run the cell tests.  The
+// bins are walked once per 8 children instead of once per child.
+//
+// The frame is the parent's corner (= child 0's corner); the cell thresholds
+// of a survivor hold for all 512 cells of the group (its error bound takes
+// the group's extent, 8 cells, as the bound on the cell-centre offsets).  The
+// decisions are the per-block walk's (certified FP32 or the same FP64
+// resolution), so the masks, counts and records are identical.
+// ---------------------------------------------------------------------------
+constexpr int kGroupPool = 24;  // survivor records of a group staged in shared memory (more: spill area)
+
+struct GroupSmem {
+  Surv<3> surv[32];
+  Entry3 buf[2][32];
+  uint64_t bar[2];
+  SurvRec pool[kGroupPool];  // face, child (pad), cell mask
+  uint16_t cnt[8][64];       // per child and cell: faces that meet the cell (finest level)
+  uint8_t sidx[32];          // lanes of the chunk's survivors, in lane order
+};
+
+// Child j of the group may meet the face: no axis certifiably separates the
+// projections of its cell centres (a box of half-width 1.5 h around the child
+// centre cj) from the face's cell-level interval.  The widening by
+// (t.z - t.x) = 2 eps absorbs the rounding of the child-centre projection and
+// of the additions, so a culled child has no cell that meets the face.
+__device__ __forceinline__ bool child_may_meet(const Surv<3>& S, const float* cj, float h15) {
+  const float4 q0 = S.en[0], q1 = S.en[1], q2 = S.en[2];
+  auto sep = [&](float x, float A1, const float4& t) {
+    const float w = fmaf(h15, A1, t.z - t.x);
+    return (x + w < t.x) | (x - w > t.y);
+  };
+  bool out = sep(cj[0], 1.f, S.t[0]) | sep(cj[1], 1.f, S.t[1]) | sep(cj[2], 1.f, S.t[2]);
+  out |= sep(fmaf(cj[2], q2.w, fmaf(cj[1], q2.z, cj[0] * q2.y)), fabsf(q2.y) + fabsf(q2.z) + fabsf(q2.w), S.t[3]);
+  const float e[3][3] = {{q0.x, q0.y, q0.z}, {q0.w, q1.x, q1.y}, {q1.z, q1.w, q2.x}};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float ex = e[k][0], ey = e[k][1], ez = e[k][2];
+    out |= sep(fmaf(cj[2], ey, -cj[1] * ez), fabsf(ey) + fabsf(ez), S.t[4 + 3 * k]);
+    out |= sep(fmaf(cj[0], ez, -cj[2] * ex), fabsf(ex) + fabsf(ez), S.t[5 + 3 * k]);
+    out |= sep(fmaf(cj[1], ex, -cj[0] * ey), fabsf(ex) + fabsf(ey), S.t[6 + 3 * k]);
+  }
+  return !out;
+}
+
+// Per-warp counters of the group kernel (32-bit: a warp's counts stay far below 2^32).
+struct GroupCounters {
+  uint32_t fb = 0, band = 0, cand = 0, surv = 0, big = 0;
+};
+
+// FP64 decision of one (cell, face) pair of a group (the per-block walk's resolution).
+__device__ __noinline__ bool resolve_group(const RefineLevel& a, uint32_t gid, uint32_t face, const int* b,
+                                           int cell_local, GroupCounters& wc) {
+  unsigned long long fb = 0, band = 0;
+  const bool r = resolve_fp64<3>(a, gid, face, b, cell_local, &fb, &band);
+  wc.fb += (uint32_t)fb;
+  wc.band += (uint32_t)band;
+  return r;
+}
+
+// One parent group: walk, culls and cell tests.  kMark: only the masks are
+// wanted (the walk ends once every cell of the 8 children is marked); else the
+// per-cell counts and the survivor records of the finest level are kept.
+// hb0 / hb1: bit j = the lane's cell `lane` / `lane + 32` of child j is adjacent.
+template <bool kMark>
+__device__ __forceinline__ void walk_group(const RefineLevel& a, const GeomParams& P, uint32_t gid, const int* c0,
+                                           GroupSmem& sm, uint32_t& phase, int lane, GroupCounters& wc,
+                                           uint32_t& hb0, uint32_t& hb1, uint32_t& K, SurvRec* spill) {
+  const FastGeom g = fast_geom(P, a.level);
+  const float hf = g.h_hi;
+  BlockFrame<3> F;
+  int qlo[3], qhi[3];
+  float O = 8.0f * hf;
+  float shift[3];
+  const int Bn = P.B;
+  const float margin = 1e-6f * (float)Bn + 1e-3f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float lo;
+    df_position(P.org_hi[c], P.org_lo[c], (float)(4 * c0[c]), g.h_hi, g.h_lo, F.Xb[c], lo);
+    shift[c] = lo;
+    F.cB[c] = fmaf(4.0f, g.h_hi, lo);
+    O = fmaxf(O, 8.0f * hf + 2.0f * fabsf(lo));
+    const float k0 = (float)(4 * c0[c]);
+    const float xlo = fmaf(k0, g.h_hi, fmaf(k0, g.h_lo, -g.d));
+    const float xhi = fmaf(k0 + 8.0f, g.h_hi, fmaf(k0 + 8.0f, g.h_lo, g.d));
+    const float tlo = floorf(xlo * P.scale32[c] - margin);
+    const float thi = floorf(xhi * P.scale32[c] + margin);
+    qlo[c] = tlo < 0.f ? 0 : (tlo > (float)(Bn - 1) ? Bn - 1 : (int)tlo);
+    qhi[c] = thi < 0.f ? 0 : (thi > (float)(Bn - 1) ? Bn - 1 : (int)thi);
+  }
+  F.h = hf;
+  F.r = fmaf(0.5f, hf, g.d);
+  F.rb = fmaf(4.0f, hf, g.d);  // the union of the 512 inflated cells: the parent box inflated by d
+  F.O = O;
+  const float h15 = 1.5f * hf;
+  uint32_t full = 0;  // children whose 64 cells are all marked (kMark)
+  const int64_t B = Bn;
+  const Entry3* payload = static_cast<const Entry3*>(a.payload);
+  const int nx = qhi[0] - qlo[0] + 1, ny = qhi[1] - qlo[1] + 1;
+  const int nrows = ny * (qhi[2] - qlo[2] + 1);
+  for (int rg = 0; rg < nrows; rg += 32) {
+    uint32_t rs = 0, rn = 0;
+    const int ri = rg + lane;
+    if (ri < nrows) {
+      const int y = qlo[1] + ri % ny, z = qlo[2] + ri / ny;
+      const int64_t b0 = P.bin_base + qlo[0] + B * (y + B * (int64_t)z);
+      rs = a.offsets[b0];
+      rn = a.offsets[b0 + nx] - rs;
+    }
+    const uint32_t incl = warp_inclusive_scan<uint32_t>(rn);
+    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t rv = incl - rn;
+    const uint32_t nch = (T + 31u) / 32u;
+    if (nch == 0) continue;
+    int cb = 0;
+    issue_chunk<Entry3>(payload, rs, rn, rv, 0u, T, sm.buf[0], &sm.bar[0], lane);
+    for (uint32_t c = 0; c < nch; ++c) {
+      const int nb = cb ^ 1;
+      const bool more = c + 1 < nch;
+      if (more) issue_chunk<Entry3>(payload, rs, rn, rv, c + 1, T, sm.buf[nb], &sm.bar[nb], lane);
+      mbar_wait_bounded(&sm.bar[cb], (phase >> cb) & 1u, a.err);
+      phase ^= 1u << cb;
+      const uint32_t n = T - 32u * c < 32u ? T - 32u * c : 32u;
+      bool surv = false;
+      if ((uint32_t)lane < n) {
+        const Entry3& ent = sm.buf[cb][lane];
+        const uint32_t id = ent.id;
+        // visit a face only in the first bin of its range inside the query box
+        const bool canon = (((id >> 29) & 1u) || (int)ent.bin[0] == qlo[0]) &&
+                           (((id >> 30) & 1u) || (int)ent.bin[1] == qlo[1]) &&
+                           (((id >> 31) & 1u) || (int)ent.bin[2] == qlo[2]);
+        if (canon) {
+          wc.cand++;
+          const float nh[3] = {ent.n[0], ent.n[1], ent.n[2]};
+          float V[9];
+#pragma unroll
+          for (int j = 0; j < 9; ++j) V[j] = ent.v[j];
+          surv = setup_face<3>(V, nh, F, sm.surv[lane]);
+          sm.surv[lane].face = id & kIdMask;
+        }
+      }
+      unsigned m = __ballot_sync(0xffffffffu, surv);
+      if (surv) sm.sidx[__popc(m & ((1u << lane) - 1u))] = (uint8_t)lane;
+      __syncwarp();
+      // child culls: lane = (survivor, child) pair
+      const int ns = __popc(m);
+      for (int base = 0; base < 8 * ns; base += 32) {
+        const int p = base + lane;
+        bool keep = false;
+        int s = 0;
+        if (p < 8 * ns) {
+          s = sm.sidx[p >> 3];
+          const int j = p & 7;
+          float cj[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float l = (float)(4 * ((j >> q) & 1) + 2);
+            cj[q] = fmaf(l, g.h_hi, fmaf(l, g.h_lo, shift[q]));
+          }
+          keep = child_may_meet(sm.surv[s], cj, h15);
+        }
+        const unsigned kb = __ballot_sync(0xffffffffu, keep);
+        if ((lane & 7) == 0 && p < 8 * ns) sm.surv[s].pad[0] = (kb >> (lane & 24)) & 0xffu;
+      }
+      __syncwarp();
+      while (m) {
+        const int s = __ffs(m) - 1;
+        m &= m - 1;
+        const Surv<3>& S = sm.surv[s];
+        uint32_t cm = S.pad[0];
+        if (kMark) cm &= ~full;
+        wc.surv += __popc(cm);
+        while (cm) {
+          const int j = __ffs(cm) - 1;
+          cm &= cm - 1;
+          // read the survivor's thresholds from shared memory per child (not held in registers
+          // across the children, which spills)
+          asm volatile("" ::: "memory");
+          const int cx = j & 1, cy = (j >> 1) & 1, cz = (j >> 2) & 1;
+          // the lane's cells `lane` and `lane + 32` of child j, centres in the frame
+          float o0[3], o1[3];
+          {
+            const int d0[3] = {4 * cx, 4 * cy, 4 * cz};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              const float a0 = (float)(d0[q] + ((lane >> (2 * q)) & 3)) + 0.5f;
+              const float a1 = (float)(d0[q] + (((lane + 32) >> (2 * q)) & 3)) + 0.5f;
+              o0[q] = fmaf(a0, g.h_hi, fmaf(a0, g.h_lo, shift[q]));
+              o1[q] = fmaf(a1, g.h_hi, fmaf(a1, g.h_lo, shift[q]));
+            }
+          }
+          const bool m0 = kMark && ((hb0 >> j) & 1u), m1 = kMark && ((hb1 >> j) & 1u);
+          int t0 = 0, t1 = 0;
+          cell_test2<3>(S, o0, o1, t0, t1);
+          const int bj[3] = {c0[0] + cx, c0[1] + cy, c0[2] + cz};  // child j's block coordinates
+          bool r0 = false, r1 = false;
+          if (!m0) {
+            if (t0 == 2) t0 = resolve_group(a, gid, S.face, bj, lane, wc) ? 1 : 0;
+            r0 = t0 != 0;
+          }
+          if (!m1) {
+            if (t1 == 2) t1 = resolve_group(a, gid, S.face, bj, lane + 32, wc) ? 1 : 0;
+            r1 = t1 != 0;
+          }
+          hb0 |= (uint32_t)r0 << j;
+          hb1 |= (uint32_t)r1 << j;
+          if constexpr (kMark) {
+            if (__all_sync(0xffffffffu, ((hb0 & hb1) >> j) & 1u)) full |= 1u << j;
+          } else {
+            const uint32_t n0 = sm.cnt[j][lane], n1 = sm.cnt[j][lane + 32];
+            if ((r0 && n0 == 0xffffu) || (r1 && n1 == 0xffffu)) atomicOr(a.err, ERR_OVERFLOW);
+            sm.cnt[j][lane] = (uint16_t)min(n0 + (uint32_t)r0, 0xffffu);
+            sm.cnt[j][lane + 32] = (uint16_t)min(n1 + (uint32_t)r1, 0xffffu);
+            if (a.recs) {
+              const uint64_t cells = (uint64_t)__ballot_sync(0xffffffffu, r0) |
+                                     ((uint64_t)__ballot_sync(0xffffffffu, r1) << 32);
+              if (cells) {
+                if (lane == 0) {
+                  SurvRec r;
+                  r.face = S.face;
+                  r.pad = (uint32_t)j;
+                  r.cells = cells;
+                  if (K < (uint32_t)kGroupPool)
+                    sm.pool[K] = r;
+                  else if (spill && K < (uint32_t)(kGroupPool + kSpillCap))
+                    spill[K - kGroupPool] = r;
+                }
+                ++K;
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (kMark && full == 0xffu) {
+        if (more) {
+          mbar_wait_bounded(&sm.bar[nb], (phase >> nb) & 1u, a.err);  // the copy already in flight
+          phase ^= 1u << nb;
+          __syncwarp();
+        }
+        return;
+      }
+      cb = nb;
+    }
+  }
+}
+
+// The group's K records into a contiguous range of the level's record array,
+// grouped by child (each child's records in the order they were found), and
+// every child's descriptor: offset << 16 | count, 0 for none, ~0 when the
+// records are incomplete (the adjacency pass then walks the block again).
+__device__ __noinline__ void store_group_records(const RefineLevel& a, GroupSmem& sm, const SurvRec* spill,
+                                                  uint32_t K, unsigned blk0, int lane) {
+  __syncwarp();  // the staged and spilled records are visible to the whole warp
+  const uint32_t kmax = (uint32_t)kGroupPool + (spill ? (uint32_t)kSpillCap : 0u);
+  uint64_t base = ~0ull;
+  if (K > 0 && K <= kmax) {
+    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(a.rec_count), (unsigned long long)K);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((int64_t)(base + K) > a.cap_recs) base = ~0ull;
+  }
+  if (K == 0 || base == ~0ull) {
+    if (lane < 8) a.rec_desc[blk0 + lane] = K == 0 ? 0ull : ~0ull;
+    __syncwarp();
+    return;
+  }
+  auto rec = [&](uint32_t i) { return i < (uint32_t)kGroupPool ? sm.pool[i] : spill[i - kGroupPool]; };
+  // records per child, then the child's first position
+  uint32_t cntj = 0;  // lane j < 8: records of child j
+  for (uint32_t i0 = 0; i0 < K; i0 += 32) {
+    const uint32_t i = i0 + (uint32_t)lane;
+    const uint32_t j = i < K ? rec(i).pad : 8u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t n = __popc(__ballot_sync(0xffffffffu, j == (uint32_t)q));
+      if (lane == q) cntj += n;
+    }
+  }
+  const uint32_t incl = warp_inclusive_scan<uint32_t>(lane < 8 ? cntj : 0u);
+  const uint32_t first = incl - (lane < 8 ? cntj : 0u);
+  if (lane < 8) a.rec_desc[blk0 + lane] = cntj == 0 ? 0ull : ((base + first) << 16) | cntj;
+  uint32_t run = first;  // lane j < 8: next position of child j
+  for (uint32_t i0 = 0; i0 < K; i0 += 32) {
+    const uint32_t i = i0 + (uint32_t)lane;
+    SurvRec r;
+    r.pad = 8u;
+    if (i < K) r = rec(i);
+    uint32_t pos = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const unsigned bq = __ballot_sync(0xffffffffu, r.pad == (uint32_t)q);
+      const uint32_t rq = __shfl_sync(0xffffffffu, run, q);
+      if (r.pad == (uint32_t)q) pos = rq + __popc(bq & ((1u << lane) - 1u));
+      if (lane == q) run += __popc(bq);
+    }
+    if (i < K) {
+      SurvRec o;
+      o.face = r.face;
+      o.pad = 0u;
+      o.cells = r.cells;
+      a.recs[base + pos] = o;
+    }
+  }
+  __syncwarp();
+}
+
+constexpr int kGroupWarps = 4;  // warps per CTA of k_refine_groups (4 CTAs per SM by registers and shared memory)
+
+__global__ void __launch_bounds__(kGroupWarps * 32, 4) k_refine_groups(RefineLevel a) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  GroupSmem& sm = reinterpret_cast<GroupSmem*>(s_raw)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  uint32_t phase = 0;
+  const int64_t n = launch_count(a.n_blocks, a.n_dev, a.err);
+  if ((n & 7) != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.err, ERR_BADINDEX);  // children in eights
+  const int64_t ng = n >> 3;
+  SurvRec* spill = a.spill ? warp_spill(a.spill) : nullptr;
+  GroupCounters wc;
+  for (;;) {
+    unsigned gi = 0;
+    if (lane == 0) gi = atomicAdd(a.work, 1u);
+    gi = __shfl_sync(0xffffffffu, gi, 0);
+    if ((int64_t)gi >= ng) break;
+    const unsigned blk0 = gi * 8u;
+    int cv = lane < 3 ? a.blocks[(int64_t)blk0 * 3 + lane] : 0;
+    int c0[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) c0[c] = __shfl_sync(0xffffffffu, cv, c);
+    const uint32_t gid = a.gid ? a.gid[blk0] : 0u;
+    const GeomParams& P = a.table ? a.table[gid] : a.g0;
+    if (a.skip_mark_only && ((P.face_levels >> a.level) & 1u)) continue;  // marked face by face
+    const bool fin = a.blockcnt && a.level == P.n_levels - 1;
+    uint32_t hb0 = 0, hb1 = 0, K = 0;
+    if (fin) {
+      reinterpret_cast<uint4*>(sm.cnt)[lane] = make_uint4(0u, 0u, 0u, 0u);
+      reinterpret_cast<uint4*>(sm.cnt)[lane + 32] = make_uint4(0u, 0u, 0u, 0u);
+      __syncwarp();
+      walk_group<false>(a, P, gid, c0, sm, phase, lane, wc, hb0, hb1, K, spill);
+      if (a.recs) {
+        if (K > (uint32_t)kGroupPool) wc.big += 1;
+        store_group_records(a, sm, spill, K, blk0, lane);
+      }
+    } else {
+      walk_group<true>(a, P, gid, c0, sm, phase, lane, wc, hb0, hb1, K, spill);
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+      const unsigned blk = blk0 + (unsigned)j;
+      const uint64_t m = (uint64_t)__ballot_sync(0xffffffffu, (hb0 >> j) & 1u) |
+                         ((uint64_t)__ballot_sync(0xffffffffu, (hb1 >> j) & 1u) << 32);
+      if (lane == 0) {
+        a.mask[blk] = m;
+        a.flag[blk] = m != 0 ? 1 : 0;
+      }
+      if (a.blockcnt) {
+        uint32_t pairs = 0;
+        if (fin) {
+          const uint32_t n0 = sm.cnt[j][lane], n1 = sm.cnt[j][lane + 32];
+          if (a.cellcnt) {
+            a.cellcnt[(int64_t)blk * 64 + lane] = (uint16_t)n0;
+            a.cellcnt[(int64_t)blk * 64 + 32 + lane] = (uint16_t)n1;
+          }
+          pairs = n0 + n1;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        }
+        if (lane == 0) a.blockcnt[blk] = fin ? ((uint64_t)pairs | ((uint64_t)__popcll(m) << 32)) : 0ull;
+      }
+    }
+  }
+  // fb, band and cand are per-lane counts; surv and big, warp-uniform ones
+  unsigned long long v[5] = {wc.fb, wc.band, wc.cand, wc.surv, wc.big};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  }
+  if (lane == 0) {
+    if (v[0]) atomicAdd(&a.counters[CNT_FALLBACK], v[0]);
+    if (v[1]) atomicAdd(&a.counters[CNT_BAND], v[1]);
+    atomicAdd(&a.counters[CNT_CANDIDATES], v[2]);
+    atomicAdd(&a.counters[CNT_SURVIVORS], v[3]);  // (face, child) pairs that ran the cell tests
+    if (v[4]) atomicAdd(&a.counters[CNT_BIG_BLOCKS], v[4]);
+  }
+}
+
 // Ascending sort of P keys in shared memory (P a power of two; pad the tail
 // with ~0), with a 64-bit payload per key when pay is given, by the whole warp:
 // the bitonic network, one compare-exchange per lane and pair of each stage.
@@ -1601,6 +2003,14 @@ int launch_refine(const RefineLevel& a, int num_sms, cudaStream_t st) {
     kernel<<<g, warps * 32, smem, st>>>(a);
   };
   const int mode = a.search == 1 ? 2 : (a.pred == 1 ? 1 : 0);
+  if (refine_by_groups(a.dim, a.level, a.pred, a.search)) {
+    // one warp per parent group of 8 children
+    const int gg = grid_warps(num_sms, a.n_blocks / 8, kGroupWarps, a.n_dev != nullptr);
+    const size_t gsm = (size_t)kGroupWarps * sizeof(GroupSmem);
+    allow_smem(k_refine_groups, gsm);
+    k_refine_groups<<<gg, kGroupWarps * 32, gsm, st>>>(a);
+    return 1;
+  }
   if (a.dim == 3)
     mode == 2 ? go(k_refine<3, 2>) : (mode == 1 ? go(k_refine<3, 1>) : go(k_refine<3, 0>));
   else
