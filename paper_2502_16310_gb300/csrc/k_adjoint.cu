@@ -222,7 +222,8 @@ __global__ void k_vertex_grad(const float* __restrict__ grad_face, const uint32_
 inline int grid_1d(int64_t n, int threads = 256) {
   int64_t g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
-  if (g > 152 * 32) g = 152 * 32;
+  const int64_t cap = (int64_t)current_sm_count() * 32;
+  if (g > cap) g = cap;
   return (int)g;
 }
 

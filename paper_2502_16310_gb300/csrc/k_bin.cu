@@ -10,15 +10,37 @@
 // (face, bin) incidences with atomics, a single-pass decoupled look-back scan
 // turns counts into the CSR start indices (binned_face_ids_N), and a scatter
 // writes face ids plus a contiguous per-bin copy of the face coordinates.
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace amr {
+
+int current_sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return 1;
+  }
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      return 1;
+    }
+    cache[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
 
 namespace {
 
 constexpr int kThreads = 256;
 
-inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
+inline int grid_for(int64_t n, int threads, int cap = 0) {
+  if (cap <= 0) cap = current_sm_count() * 16;
   int64_t g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
   if (g > cap) g = cap;
@@ -766,13 +788,23 @@ __global__ void k_scatter_ids(int64_t nf, const uint32_t* __restrict__ frange, c
   }
 }
 
-bool on_device(const void* p) {
+// Every coordinate finite, else ERR_NONFINITE in the error word (the regular
+// path rejects such faces at load; here the caller's array is binned as given).
+__global__ void k_check_finite(const float* __restrict__ X, int64_t n, unsigned* err) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(X[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_NONFINITE);
+}
+
+// Device memory of device dev (or managed memory, which every device can reach).
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
 }
 
 }  // namespace
@@ -792,10 +824,10 @@ extern "C" AMR_API amr_status amr_bin_faces_static(const amr_domain* dom, const 
     nb *= B;
     if (nb > kStaticMaxBins) return AMR_EINVAL;
   }
-  if (n_faces > 0 && (!faces || !on_device(faces))) return AMR_EINVAL;
-  if (!on_device(offsets) || (ids_capacity > 0 && (!ids || !on_device(ids)))) return AMR_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AMR_ECUDA;
+  if (n_faces > 0 && (!faces || !on_device(faces, dev))) return AMR_EINVAL;
+  if (!on_device(offsets, dev) || (ids_capacity > 0 && (!ids || !on_device(ids, dev)))) return AMR_EINVAL;
   unsigned char* s = nullptr;
   if (static_scratch(dev, &s) != cudaSuccess) return AMR_ECUDA;
   cudaStream_t st = dom->stream ? static_cast<cudaStream_t>(dom->stream) : cudaStreamLegacy;
@@ -813,6 +845,10 @@ extern "C" AMR_API amr_status amr_bin_faces_static(const amr_domain* dom, const 
   // the array keeps the previous call's contents: zero the counts, the total and the error word
   if (cudaMemsetAsync(count, 0, 4 * (size_t)nb, st) != cudaSuccess) return AMR_ECUDA;
   if (cudaMemsetAsync(s + kStTotal, 0, 16, st) != cudaSuccess) return AMR_ECUDA;
+  if (n_faces > 0) {
+    const int64_t nx = (int64_t)D * D * n_faces;
+    k_check_finite<<<grid_for(nx, kThreads), kThreads, 0, st>>>(faces, nx, err);
+  }
   launch_face_bins(D, faces, n_faces, g, frange, count, st);
   launch_scan_u32(count, offsets, nb, total, s + kStScan, err, st);
   uint64_t h_total = 0;
@@ -820,6 +856,7 @@ extern "C" AMR_API amr_status amr_bin_faces_static(const amr_domain* dom, const 
   if (cudaMemcpyAsync(&h_total, total, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return AMR_ECUDA;
   if (cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return AMR_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return AMR_ECUDA;
+  if (h_err & ERR_NONFINITE) return AMR_EINVAL;
   if (h_err & ERR_TIMEOUT) return AMR_ETIMEOUT;
   if (h_err || h_total > 0xffffffffull) return AMR_EOVERFLOW;
   *nnz = (int64_t)h_total;

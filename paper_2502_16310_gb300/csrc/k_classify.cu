@@ -208,7 +208,8 @@ __global__ void k_fluid_move(const uint32_t* link_cell, const uint8_t* link_dir,
 int launch_classify(const ClassifyArgs& a, cudaStream_t st) {
   if (a.n_rows <= 0) return 0;
   int64_t g = (a.n_rows + kCThreads - 1) / kCThreads;
-  if (g > 152 * 16) g = 152 * 16;
+  const int64_t cap = (int64_t)current_sm_count() * 16;
+  if (g > cap) g = cap;
   if (a.dim == 3)
     k_classify<3><<<(unsigned)g, kCThreads, 0, st>>>(a);
   else

@@ -76,7 +76,8 @@ __global__ void k_prop_commit(int64_t cap, const uint64_t* n_dev, uint8_t* flags
 int grid_of(int64_t n) {
   int64_t g = (n + kPThreads - 1) / kPThreads;
   if (g < 1) g = 1;
-  if (g > 152 * 8) g = 152 * 8;
+  const int64_t cap = (int64_t)current_sm_count() * 8;
+  if (g > cap) g = cap;
   return (int)g;
 }
 

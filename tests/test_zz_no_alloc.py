@@ -101,3 +101,26 @@ def test_static_limits_and_capacity():
         _static(w, 32, cap=10)
     assert e.value.status == Bd.AMR_EOVERFLOW
     _same_bins(_static(w, 32), _regular(w, 32))
+
+
+def test_static_rejects_non_finite_then_recovers():
+    """A NaN or infinite coordinate is an error (EINVAL), as it is for amr_geom_load, and the next call on
+    valid faces still matches the regular binning."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrError, amr_bin_faces_static
+    from paper_2502_16310_gb300 import binding as Bd
+
+    w = small_workload("sphere3")
+    B = 16
+    for bad in (float("nan"), float("inf")):
+        fv = torch.from_numpy(w.verts[w.idx]).cuda()
+        soa = fv.permute(1, 2, 0).contiguous()
+        soa[1, 2, w.n_faces // 2] = bad
+        off = torch.zeros(B ** 3 + 1, dtype=torch.int32, device="cuda")
+        ids = torch.zeros(64 * w.n_faces, dtype=torch.int32, device="cuda")
+        with pytest.raises(AmrError) as e:
+            amr_bin_faces_static(3, (w.root,) * 3, soa.data_ptr(), w.n_faces, B, off.data_ptr(), ids.data_ptr(),
+                                 ids.numel(), stream=1)
+        assert e.value.status == Bd.AMR_EINVAL
+    _same_bins(_static(w, B), _regular(w, B))
