@@ -25,8 +25,10 @@ def to_np(t, dtype=None):
 
 
 def run_gpu(w, *, B=None, n_levels=None, want_links=True, facelist=False, d_abs=None, d_rel=None, predicate=0,
-            face_pass=0, want_adjacency=True, root=None):
-    """Whole CUDA pass for a workload; returns the AmrGeom and host copies of every output."""
+            face_pass=0, want_adjacency=True, root=None, use_graph=False):
+    """Whole CUDA pass for a workload; returns host copies of every output.  use_graph: refine twice with
+    the level loop captured as a CUDA graph, so the outputs are those of a graph replay (as the bench
+    runs it)."""
     import torch
 
     from paper_2502_16310_gb300 import AmrGeom
@@ -40,9 +42,10 @@ def run_gpu(w, *, B=None, n_levels=None, want_links=True, facelist=False, d_abs=
     else:
         g.load(v, torch.from_numpy(w.idx).cuda())
     bins = g.bin(B)
-    res = g.refine(n_levels, w.d_abs if d_abs is None else d_abs, w.d_rel if d_rel is None else d_rel,
-                   w.lattice if want_links else 0, want_adjacency or want_links, want_links, predicate=predicate,
-                   face_pass=face_pass)
+    for _ in range(2 if use_graph else 1):
+        res = g.refine(n_levels, w.d_abs if d_abs is None else d_abs, w.d_rel if d_rel is None else d_rel,
+                       w.lattice if want_links else 0, want_adjacency or want_links, want_links,
+                       predicate=predicate, face_pass=face_pass, use_graph=use_graph)
     torch.cuda.synchronize()
     out = {"offsets": to_np(bins["offsets"], np.uint32), "ids": to_np(bins["ids"], np.uint32), "levels": []}
     for lv in res["levels"]:
@@ -151,17 +154,21 @@ def compare_links(geo, dim, level, lattice, fin_blocks, adj_cell, link_cell, lin
     assert np.all(np.diff(key) > 0), "links not strictly sorted by (cell, direction)"
     assert np.all((link_dir >= 1) & (link_dir <= Q1))
     assert np.all((link_q >= 0) & (link_q <= 1))
-    dense_q = np.full((n_adj, Q1), np.nan)
-    dense_f = np.full((n_adj, Q1), -1, np.int64)
-    dense_q[link_cell, link_dir - 1] = link_q
-    dense_f[link_cell, link_dir - 1] = link_face
     rows = np.arange(n_adj)
     if sample is not None and n_adj > sample:
         rng = rng or np.random.default_rng(2)
         rows = np.sort(rng.choice(n_adj, size=sample, replace=False))
+    # the GPU's links of the checked rows as [rows, Q1] tables (links are sorted by cell)
+    lo = np.searchsorted(link_cell, rows, "left")
+    cnt = np.searchsorted(link_cell, rows, "right") - lo
+    row_of = np.repeat(np.arange(rows.size), cnt)
+    pos = np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt) + np.repeat(lo, cnt)
+    gq = np.full((rows.size, Q1), np.nan)
+    gf = np.full((rows.size, Q1), -1, np.int64)
+    gq[row_of, link_dir[pos].astype(np.int64) - 1] = link_q[pos]
+    gf[row_of, link_dir[pos].astype(np.int64) - 1] = link_face[pos]
     cells = cells_of(dim, fin_blocks, (adj_cell[rows] // nc).astype(np.int64), (adj_cell[rows] % nc).astype(np.int64))
     q_o, f_o, b_o = geo.cell_links(level, lattice, cells)
-    gq, gf = dense_q[rows], dense_f[rows]
     # a link inherits the band of its face's adjacency decision: links are formed against the
     # cell's adjacency list, and a face in the adjacency band may be listed or not
     a_off, a_ids, a_band = geo.cell_faces(level, cells, d_abs, d_rel, pred=pred)

@@ -124,3 +124,76 @@ def test_graph_replays_follow_a_moving_wall():
     assert replays[0] is False and all(replays[1:]), replays
     g.close()
     e.close()
+
+
+def test_moved_steps_against_oracle():
+    """Each moved step's hierarchy is the oracle's hierarchy of the moved vertices (re-adaptation rebuilds
+    from the roots, so the marks depend only on the geometry), and the new <-> old maps equal the maps
+    between the oracle's own block lists of the two steps.  The shifts put no decision in the margin band
+    (checked), so the block lists must agree exactly."""
+    import torch
+
+    from oracle.oracle import run_pipeline
+    from paper_2502_16310_gb300 import AmrGeom
+
+    w = small_workload("sphere3")
+    g = AmrGeom(3, (w.root,) * 3)
+    shift = np.array([0.011, -0.004, 0.007], np.float32)
+    prev = None
+    for step in range(3):
+        v = w.verts + step * shift
+        g.load(torch.from_numpy(v).cuda(), torch.from_numpy(w.idx).cuda())
+        g.bin(w.bins)
+        res = g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, keep_previous=step > 0,
+                       use_graph=step > 1)
+        torch.cuda.synchronize()
+        blocks = [U.to_np(lv["blocks"]).copy() for lv in res["levels"]]
+        masks = [U.to_np(lv["mask"], np.uint64).copy() for lv in res["levels"]]
+        orc = run_pipeline(3, v, w.idx, root=w.root, n_levels=w.n_levels, B=w.bins, lattice=w.lattice, links=False)
+        assert all(int(np.count_nonzero(lv["band"])) == 0 for lv in orc["levels"]), "shift puts cells in the band"
+        for L, lv in enumerate(orc["levels"]):
+            assert np.array_equal(blocks[L], lv["blocks"]), (step, L)
+            assert np.array_equal(masks[L], lv["mask"]), (step, L)
+        if prev is not None:
+            d = g.adapt_diff()
+            for L, lv in enumerate(orc["levels"]):
+                n2o, o2n = _maps(prev[L], lv["blocks"]), _maps(lv["blocks"], prev[L])
+                assert np.array_equal(U.to_np(d[L]["new_to_old"]).astype(np.int64), n2o), (step, L)
+                assert np.array_equal(U.to_np(d[L]["old_to_new"]).astype(np.int64), o2n), (step, L)
+            assert d[-1]["created"] > 0 and d[-1]["removed"] > 0
+        prev = [lv["blocks"] for lv in orc["levels"]]
+    g.close()
+
+
+def test_moving_c2_step_sampled():
+    """The bench's moving wall (the c2 sphere, a quarter of a finest cell per step, graph replays): after
+    several moves, every level of the current hierarchy is checked against the oracle on sampled blocks
+    (lockstep: the oracle takes the GPU's blocks of each level), children exactly."""
+    import torch
+
+    from oracle.oracle import Domain, OracleGeometry
+    from paper_2502_16310_gb300 import AmrGeom
+    from synth import workload
+
+    w = workload("c2")
+    g = AmrGeom(3, (w.root,) * 3)
+    h_fin = 1.0 / (4 * w.root * 2 ** (w.n_levels - 1))
+    delta = np.array([0.25 * h_fin, 0.1 * h_fin, 0.05 * h_fin], np.float32)
+    idx = torch.from_numpy(w.idx).cuda()
+    for k in range(4):
+        v = (w.verts + np.float32(k) * delta).astype(np.float32)
+        g.load(torch.from_numpy(v).cuda(), idx)
+        g.bin(w.bins)
+        res = g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=True, keep_previous=k > 0)
+    torch.cuda.synchronize()
+    geo = OracleGeometry(3, v, w.idx)
+    geo.bin(Domain.unit(3, w.root), w.bins)
+    rng = np.random.default_rng(12)
+    lv = res["levels"]
+    for L in range(len(lv)):
+        b = U.to_np(lv[L]["blocks"]).copy()
+        m = U.to_np(lv[L]["mask"], np.uint64).copy()
+        U.compare_level(geo, 3, L, b, m, sample=200, rng=rng)
+        if L + 1 < len(lv):
+            U.check_children(3, b, m, U.to_np(lv[L + 1]["blocks"]).copy(), U.to_np(lv[L + 1]["parent"]).copy())
+    g.close()

@@ -123,7 +123,7 @@ def test_deterministic_repeat():
 @pytest.mark.parametrize("name", ["c2", "c3"])
 def test_full_size_sampled(name):
     w = workload(name)
-    out = U.run_gpu(w)
+    out = U.run_gpu(w, use_graph=True)
     geo, off, ids = _oracle(w)
     U.compare_bins(out["offsets"], out["ids"], off, ids)
     _full_check(w, out, geo, sample=300)
@@ -132,7 +132,7 @@ def test_full_size_sampled(name):
 @pytest.mark.slow
 def test_c4_full_size_sampled():
     w = workload("c4")
-    out = U.run_gpu(w)
+    out = U.run_gpu(w, use_graph=True)
     geo, off, ids = _oracle(w)
     U.compare_bins(out["offsets"], out["ids"], off, ids)
-    _full_check(w, out, geo, sample=60)
+    _full_check(w, out, geo, sample=200)
