@@ -7,7 +7,10 @@ every level with child compaction, the finest level's adjacent-face lists and
 its D3Q19 wall links.  Headline value: near-wall cells identified per second
 (adjacent cells summed over all levels), whole job over all ranks.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c4] [--impl reference]
+
+The default workload is the largest single-geometry one (c4: 1,310,720 triangles,
+64^3 roots, 6 levels, 256^3 bins); c1-c3 are timed beside it (`per_workload`).
 
 Multi-GPU: the path has no exchange step, so N ranks run N independent
 replicas of the workload (weak scaling, no collective on the data path).
@@ -36,14 +39,14 @@ L2_FLUSH_BYTES = 512 << 20
 
 # Algorithmic work per unit (FP32-pipe operations counted from the kernel source):
 OPS_BLOCK_CANDIDATE = 120.0   # face setup up to the AABB cull (vertex offsets, edges, three box axes)
-OPS_BLOCK_SURVIVOR = 280.0    # the remaining ten axes of the block-level test for a survivor
-OPS_CELL_TEST = 80.0          # one cell against one survivor: 13 axes x (projection + interval test)
+OPS_CELL_TEST = 80.0          # one cell against one (face, block) survivor: 13 axes x (projection + interval test)
 OPS_FACE_SETUP = 400.0        # face-by-face marking, per (face, level): cell range, frame, 13 axis intervals
 OPS_LINK_FACE = 150.0         # per (adjacent cell, face): double-float offsets, plane offset, cross products
 OPS_LINK_DIR = 40.0           # per (adjacent cell, face, direction): den, three edge signs, t
 # DRAM bytes (read + write) per launch of the current kernels, from one ncu capture each
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the c2 workload; other workloads report null
-MEASURED_TRAFFIC = {("c2", "links"): 133.0e6, ("c2", "refine_level"): 8.95e6}
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the named workload; others report null
+MEASURED_TRAFFIC = {("c4", "links"): 3794712832 + 6534081536, ("c4", "refine_level"): 393028096 + 2277046272,
+                    ("c2", "links"): 133.0e6}
 
 
 def parse_args(argv=None):
@@ -51,11 +54,12 @@ def parse_args(argv=None):
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
-    p.add_argument("--workload", default="c2")
+    p.add_argument("--workload", default="c4")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    p.add_argument("--no-all-cores", action="store_true", help="skip the oracle timing on all host cores")
     p.add_argument("--no-graph", action="store_true", help="time the eager path instead of graph replays")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     p.add_argument("--bin-only", action="store_true",
@@ -288,22 +292,61 @@ def run_ours(args, rank, world, local):
     }
     if not args.no_e2e:
         line["e2e"] = run_e2e(w, args, dev)
-    if not args.no_extras and world == 1:
-        line["classify"] = run_classify(g, w, verts, idx, flush)
+        line["e2e"]["single_stream"] = run_e2e_single_stream(w, args, dev)
     g.close()
     if not args.no_extras and world == 1:
-        line["adjoint"] = run_adjoint(args, dev, flush)
+        line["classify"] = run_classify("c2", dev, flush)
+    if not args.no_extras and world == 1:
+        names = [n for n in ("c3", args.workload) if workload(n).adjoint]
+        line["adjoint"] = {n: run_adjoint(n, dev, flush) for n in dict.fromkeys(names)}
+        line["per_workload"] = {n: run_device_steps(n, dev, flush, use_graph)
+                                for n in ("c1", "c2", "c3", "c4") if n != args.workload}
         line["batched"] = run_batched(args, dev, flush)
         line["paper_setups"] = run_paper_setups(args, dev, flush)
         line["moving"] = run_moving(args, dev, flush)
     return line
 
 
-def run_classify(g, w, verts, idx, flush, reps=5):
-    """Node classification of the finest adjacent cells (fluid / solid) and the restriction of the
-    links to fluid cells, on the bench workload: CUDA-event times on the context stream."""
+def run_device_steps(name, dev, flush, use_graph, steps=10, warmup=3):
+    """Device time of the whole step (load, bin, refine with adjacency and links) on another workload:
+    CUDA events on the context's stream, L2 flushed between steps (outside the events)."""
     import torch
 
+    from paper_2502_16310_gb300 import AmrGeom
+    from synth import workload
+
+    w = workload(name)
+    g = AmrGeom(w.dim, (w.root,) * w.dim)
+    v = torch.from_numpy(w.verts).to(dev)
+    ix = torch.from_numpy(w.idx).to(dev)
+
+    def step():
+        g.load(v, ix)
+        g.bin(w.bins)
+        return g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=use_graph)
+
+    for _ in range(warmup):
+        res = step()
+    torch.cuda.synchronize()
+    cells = near_wall_cells(res)
+    ms = _timed_steps(step, steps, flush, g.stream)
+    g.close()
+    return {"workload": f"{name}: {w.description}", "ms_per_step": ms, "near_wall_cells_per_step": cells,
+            "cells_per_s": cells / (ms * 1e-3), "steps": steps}
+
+
+def run_classify(name, dev, flush, reps=5):
+    """Node classification of the finest adjacent cells (fluid / solid) and the restriction of the
+    links to fluid cells, on the 20,480-triangle sphere: CUDA-event times on the context stream."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+    from synth import workload
+
+    w = workload(name)
+    g = AmrGeom(w.dim, (w.root,) * w.dim)
+    verts = torch.from_numpy(w.verts).to(dev)
+    idx = torch.from_numpy(w.idx).to(dev)
     g.load(verts, idx)
     g.bin(w.bins)
     res = g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True)
@@ -324,7 +367,9 @@ def run_classify(g, w, verts, idx, flush, reps=5):
     out = g.fluid_links()
     b.record(st)
     torch.cuda.synchronize()
-    return {"cells": int(cls.numel()), "classify_ms": sum(ms) / len(ms), "solid_fraction": solid,
+    g.close()
+    return {"workload": f"{name}: {w.description}", "cells": int(cls.numel()), "classify_ms": sum(ms) / len(ms),
+            "solid_fraction": solid,
             "winding_fallbacks": nfb, "links": n_links, "fluid_links": int(out["link_q"].shape[0]),
             "fluid_links_ms": a.elapsed_time(b),
             "note": "classify/fluid_links times include their host round trip (one read-back each)"}
@@ -389,15 +434,16 @@ def _timed_steps(fn, n, flush, stream):
     return total / n
 
 
-def run_adjoint(args, dev, flush):
-    """Adjoint vs forward on the workload with q adjoint (c3): forward = load + bin + refine with links;
-    backward = amr_q_backward for random upstream weights (includes regrouping the links by face)."""
+def run_adjoint(name, dev, flush):
+    """Adjoint vs forward on a workload with the q adjoint (c3, c4): forward = load + bin + refine with
+    links (graph replay); backward = amr_q_backward for seeded random upstream weights (it includes
+    regrouping the links by face).  CUDA-event times on the context's stream."""
     import torch
 
     from paper_2502_16310_gb300 import AmrGeom
     from synth import workload
 
-    w = workload("c3")
+    w = workload(name)
     g = AmrGeom(3, (w.root,) * 3)
     v = torch.from_numpy(w.verts).to(dev)
     ix = torch.from_numpy(w.idx).to(dev)
@@ -417,17 +463,19 @@ def run_adjoint(args, dev, flush):
         fwd()
         g.q_backward(wts)
 
-    t_f = _timed_steps(fwd, 10, flush, st)
-    t_fb = _timed_steps(both, 10, flush, st)
+    n = 10 if w.n_faces < 500_000 else 6
+    t_f = _timed_steps(fwd, n, flush, st)
+    t_fb = _timed_steps(both, n, flush, st)
     g.close()
     t_b = t_fb - t_f
-    return {"workload": "c3: " + w.description, "links": nl, "forward_ms": t_f, "backward_ms": t_b,
-            "adjoint_over_forward": t_b / t_f}
+    return {"workload": f"{name}: " + w.description, "links": nl, "forward_ms": t_f, "backward_ms": t_b,
+            "adjoint_over_forward": t_b / t_f, "steps": n}
 
 
 def run_batched(args, dev, flush):
     """The 48-geometry workload: one batched launch per level (graph replay) vs one geometry at a time
-    (each with its own context and graph), bin densities and warps per block from the autotuner."""
+    (each with its own context and graph), bin densities and warps per block from the autotuner; forward
+    alone, and forward plus the q adjoint (seeded random upstream weights) in both legs."""
     import torch
 
     from paper_2502_16310_gb300 import AmrBatch, AmrGeom
@@ -451,12 +499,12 @@ def run_batched(args, dev, flush):
     tune_s = time.perf_counter() - t0
 
     def single():
-        cells = 0
+        out = []
         for w, (v, ix), g in zip(ws, data, ctxs):
             g.load(v, ix)
             g.bin(w.bins)
-            g.refine(w.n_levels, w.d_abs, w.d_rel, 19, True, True, use_graph=True)
-        return cells
+            out.append(g.refine(w.n_levels, w.d_abs, w.d_rel, 19, True, True, use_graph=True))
+        return out
 
     b = AmrBatch(3)
     for w, (v, ix) in zip(ws, data):
@@ -466,8 +514,22 @@ def run_batched(args, dev, flush):
         b.run(19, True, True, use_graph=True)
 
     for _ in range(3):
-        single()
+        res = single()
         batched()
+    gen = torch.Generator(dev).manual_seed(1)
+    wts = [torch.randn(int(r["link_q"].shape[0]), device=dev, generator=gen) for r in res]
+    wts_all = torch.cat(wts)
+    assert wts_all.numel() == int(b.result.n_links), "batched and single runs differ in their link counts"
+
+    def single_adj():
+        single()
+        for g, wt in zip(ctxs, wts):
+            g.q_backward(wt)
+
+    def batched_adj():
+        batched()
+        b.q_backward(wts_all)
+
     # near-wall cells of the whole set (from the batch's masks)
     r = b.result
     cells = 0
@@ -480,18 +542,31 @@ def run_batched(args, dev, flush):
             cells += int(lut[m.view(torch.uint8).long()].sum().item())
     t_single = _timed_steps(single, 5, flush, st)
     t_batch = _timed_steps(batched, 5, flush, st)
-    launches_batch = b.launch_count()
+    single_adj()  # warm-up: every context's adjoint buffers
+    t_single_adj = _timed_steps(single_adj, 5, flush, st)
+    # the 48 single contexts hold their outputs and adjoint buffers: free them before the batch's adjoint
+    # allocates its own (the set has about 2.5e9 links)
     for g in ctxs:
         g.close()
+    del res
+    torch.cuda.synchronize()
+    batched_adj()  # warm-up: the batch's adjoint buffers
+    l0 = b.launch_count()
+    t_batch_adj = _timed_steps(batched_adj, 5, flush, st)
+    launches_batch = (b.launch_count() - l0) / 5
     b.close()
     return {"workload": f"{len(ws)} SH-perturbed geodesic spheres, {sum(w.n_faces for w in ws)} triangles, "
                         f"roots 16^3..48^3, 2..6 levels, bin density tuned per geometry",
-            "near_wall_cells": cells, "single_ms": t_single, "batched_ms": t_batch,
+            "near_wall_cells": cells, "links": int(wts_all.numel()),
+            "single_ms": t_single, "batched_ms": t_batch,
             "single_cells_per_s": cells / (t_single * 1e-3), "batched_cells_per_s": cells / (t_batch * 1e-3),
-            "batched_over_single": t_single / t_batch, "generate_s": gen_s, "tune_s": tune_s}
+            "batched_over_single": t_single / t_batch,
+            "single_fwd_adj_ms": t_single_adj, "batched_fwd_adj_ms": t_batch_adj,
+            "batched_over_single_fwd_adj": t_single_adj / t_batch_adj,
+            "batched_launches_per_fwd_adj": launches_batch, "generate_s": gen_s, "tune_s": tune_s}
 
 
-def run_paper_setups(args, dev, flush, bins=(1, 2, 4, 8, 16), reps=3):
+def run_paper_setups(args, dev, flush, bins=(1, 2, 4, 6, 7, 8, 9, 10, 12, 14, 16), reps=3):
     """The paper's two speed-up setups (point predicate, absolute d_spec, refined twice) at its bin
     densities, each in two modes: `exact` (AABB bins, every bin the test region overlaps: the marks do
     not depend on B) and `paper` (the paper's sampled bins, face detection in the cell's own bin, then
@@ -552,7 +627,10 @@ def roofline(name, k, w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks, n
     NC = 64 if w.dim == 3 else 16
     alu_peak = N_SM * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12  # FP32-pipe Tops/s at the max SM clock
     if name == "refine_level":
-        ops = (n_cand * OPS_BLOCK_CANDIDATE + n_surv * OPS_BLOCK_SURVIVOR + n_surv * NC * OPS_CELL_TEST) / launches
+        # deduplicated candidates set up against the walked box (a parent group's on the levels below the
+        # roots) and the cell tests of every (face, block) pair that passed the culls; the rest of the
+        # survivors' setups and the child culls are left out (a lower bound)
+        ops = (n_cand * OPS_BLOCK_CANDIDATE + n_surv * NC * OPS_CELL_TEST) / launches
         a = ops / t / 1e12
         return {"kernel": name, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s (FP32 pipe)",
                 "frac": a / alu_peak, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2070 MHz"}
@@ -581,21 +659,36 @@ def roofline(name, k, w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks, n
             "traffic": None, "peak_source": src}
 
 
+def bin_method_bytes(D, n_faces, n_bins, nnz):
+    """Algorithmic bytes of the binning as the method defines them: the face coordinates read by the
+    count and scatter passes (2 x 4 D^2 per face), the bin counters zeroed, counted, scanned and read as
+    offsets (16 bytes per bin), and per (face, bin) incidence its 4-byte id and its coordinates (4 D^2)."""
+    return 2 * 4 * D * D * n_faces + 16 * n_bins + (4 + 4 * D * D) * nnz
+
+
+def bin_impl_bytes(D, n_faces, n_bins, nnz):
+    """Bytes the implementation moves on purpose: the method's bytes with the per-face bin range written and
+    read back (2 x 4 D) and the full payload entry (64 bytes in 3D, 32 in 2D: coordinates, FP32 normal, id
+    with flags, bin coordinates) in place of the bare coordinates."""
+    entry = 64 if D == 3 else 32
+    return 2 * 4 * D * D * n_faces + 2 * 4 * D * n_faces + 16 * n_bins + (4 + entry) * nnz
+
+
 def bin_roofline(w, nnz, t_bin_ms):
-    """HBM roofline of the binning kernels (count, scan, scatter) together: algorithmic bytes =
-    face coordinates read by the count and scatter passes (2 x 4 D^2 per face), the per-face bin range
-    written and read back (2 x 4 D), the counter array zeroed, counted, scanned and read as offsets
-    (16 bytes per bin) and, per (face, bin) incidence, its 4-byte id and its payload entry."""
+    """HBM roofline of the binning kernels (count, scan, scatter) together.  `frac` counts the method's
+    algorithmic bytes (bin_method_bytes); the implementation's larger figure is reported beside it."""
     hbm, src = measured_peaks()
     D = w.dim
-    entry = 64 if D == 3 else 32
     nb = w.bins ** D
-    byts = 2 * 4 * D * D * w.n_faces + 2 * 4 * D * w.n_faces + 16 * nb + (4 + entry) * nnz
+    byts = bin_method_bytes(D, w.n_faces, nb, nnz)
+    impl = bin_impl_bytes(D, w.n_faces, nb, nnz)
     t = t_bin_ms * 1e-3
     a = byts / t / 1e9 if t > 0 else 0.0
+    ai = impl / t / 1e9 if t > 0 else 0.0
     return {"kernels": ["bin_count", "bin_scan", "bin_scatter"], "bound": "hbm", "faces_per_s": w.n_faces / t,
             "incidences": nnz, "bytes": byts, "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-            "peak_source": src}
+            "peak_source": src, "ms": t_bin_ms,
+            "impl_bytes": impl, "impl_achieved": ai, "impl_frac": ai / hbm}
 
 
 def run_bin_only(args, local):
@@ -750,6 +843,58 @@ def run_e2e(w, args, dev):
                     f"a stream each, so steps overlap on the GPU (the device-side value times one stream)"}
 
 
+def run_e2e_single_stream(w, args, dev):
+    """End-to-end latency of one step at a time through the public API: one context, one stream, one host
+    thread; each step uploads its inputs from pinned host memory (inside amr_geom_load), bins, refines and
+    copies every output back to pinned host memory, and the host waits for the copies before the next step
+    starts.  Host wall clock per step (median and mean)."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrGeom
+
+    hv = torch.from_numpy(w.verts).pin_memory()
+    hi = torch.from_numpy(w.idx).pin_memory()
+    use_graph = not args.no_graph
+    with torch.cuda.stream(torch.cuda.Stream(device=dev)):
+        g = AmrGeom(w.dim, (w.root,) * w.dim)
+    bufs = {}
+
+    def step():
+        g.load(hv, hi)
+        g.bin(w.bins)
+        res = g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True, use_graph=use_graph)
+        tensors = []
+        for lv in res["levels"]:
+            tensors += [lv["blocks"], lv["mask"]]
+        tensors += [res["adj_cell"], res["adj_off"], res["adj_ids"], res["link_cell"], res["link_dir"],
+                    res["link_q"], res["link_face"]]
+        nbytes = 0
+        with torch.cuda.stream(g.stream):
+            for j, t in enumerate(tensors):
+                buf = bufs.get(j)
+                if buf is None or buf.numel() < t.numel() or buf.dtype != t.dtype:
+                    buf = torch.empty(t.numel() + t.numel() // 8 + 1024, dtype=t.dtype).pin_memory()
+                    bufs[j] = buf
+                buf[:t.numel()].copy_(t.reshape(-1), non_blocking=True)
+                nbytes += t.numel() * t.element_size()
+        g.stream.synchronize()
+        return nbytes
+
+    for _ in range(max(2, min(args.warmup, 3))):
+        step()
+    ts = []
+    n = max(3, min(args.steps, 10))
+    for _ in range(n):
+        t0 = time.perf_counter()
+        bo = step()
+        ts.append(time.perf_counter() - t0)
+    g.close()
+    ts.sort()
+    return {"ms_median": ts[len(ts) // 2] * 1e3, "ms_mean": sum(ts) / len(ts) * 1e3, "steps": n,
+            "d2h_bytes_per_step": bo,
+            "note": "one context, one stream, one host thread: each step's copies end before the next step starts"}
+
+
 # ---------------------------------------------------------------------------
 # the oracle on the host (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
@@ -801,6 +946,75 @@ def oracle_sampled_step(w, frac0, rng, max_blocks=400, max_cells=400):
     return est_t, est_cells, time.process_time() - t_start
 
 
+def host_cpu():
+    """(CPU model, logical cores) of this host."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return model or "unknown", os.cpu_count() or 1
+
+
+def _oracle_worker(job):
+    """One host process of the all-cores oracle run: seeded subtree samples until `seconds` of CPU time."""
+    w, seed, seconds = job
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    frac, spent, ts, cs = 1.0 / 64, 0.0, [], []
+    while spent < seconds:
+        et, ec, cpu = oracle_sampled_step(w, frac, rng)
+        spent += cpu
+        ts.append(et)
+        cs.append(ec)
+    return ts, cs, spent
+
+
+def run_cpu_baseline_all_cores(w, seconds):
+    """The oracle as it stands on every host core at once: one process per core (spawned), each timing its
+    own seeded subtree samples of the workload while all the others run.  The whole workload splits over
+    blocks with no exchange, so the all-cores throughput is the sum of the per-process throughputs measured
+    under that load."""
+    import multiprocessing as mp
+
+    model, ncpu = host_cpu()
+    oracle_build()
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(ncpu) as pool:
+        res = pool.map(_oracle_worker, [(w, 1000 + i, seconds) for i in range(ncpu)])
+    wall = time.perf_counter() - t0
+    value = sum((sum(cs) / len(cs)) / (sum(ts) / len(ts)) for ts, cs, _ in res)
+    n = sum(len(ts) for ts, _, _ in res)
+    return {"value": value, "unit": UNIT, "cores": ncpu, "cpu_model": model, "kind": "oracle",
+            "sample": (f"{ncpu} spawned processes, {n} seeded subtree samples of {w.name} in all (1/64 of the "
+                       f"roots, <=400 blocks per level, <=400 finest adjacent cells each), times and counts scaled "
+                       f"to the full workload; value = sum of the per-process throughputs under full load; "
+                       f"{wall:.1f} s wall")}
+
+
+def oracle_build():
+    import oracle
+
+    oracle.build()
+
+
 def run_cpu_baseline(w, seconds):
     import numpy as np
 
@@ -818,7 +1032,8 @@ def run_cpu_baseline(w, seconds):
         if cpu < 1.0 and frac < 1.0 / 8:
             frac *= 2
     et, ec = float(np.mean(est_ts)), float(np.mean(est_cs))
-    return {"value": ec / et, "unit": UNIT, "cores": 1, "kind": "oracle",
+    model, ncpu = host_cpu()
+    return {"value": ec / et, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": model, "nproc": ncpu,
             "sample": (f"{len(est_ts)} seeded subtree samples of {w.name} (roots sampled at up to 1/8, <=400 "
                        f"blocks per level, <=400 finest adjacent cells for faces+links), times and counts scaled "
                        f"by inverse inclusion probability; {spent:.1f} s CPU"),
@@ -855,7 +1070,8 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": float(np.mean(ts)) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {w.description}"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": host_cpu()[0], "nproc": host_cpu()[1]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
 
@@ -882,7 +1098,10 @@ def main(argv=None):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from synth import workload
 
-        line["cpu_baseline"] = run_cpu_baseline(workload(args.workload), args.cpu_seconds)
+        wl = workload(args.workload)
+        line["cpu_baseline"] = run_cpu_baseline(wl, args.cpu_seconds)
+        if not args.no_all_cores:
+            line["cpu_baseline"]["all_cores"] = run_cpu_baseline_all_cores(wl, args.cpu_seconds)
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:

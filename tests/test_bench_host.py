@@ -13,7 +13,7 @@ import bench  # noqa: E402
 def test_defaults_meet_the_timing_rules():
     a = bench.parse_args([])
     assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1
-    assert a.workload == "c2" and a.impl == "ours"
+    assert a.workload == "c4" and a.impl == "ours"
     assert a.e2e_threads == 0 and not a.bin_only
     assert bench.parse_args(["--bin-only", "--workload", "c4"]).bin_only
 
@@ -30,14 +30,20 @@ def test_e2e_layout():
 
 
 def test_bin_roofline_bytes():
-    # 3D: coordinates twice (2 x 36 B per face), bin ranges written and read (2 x 12 B per face),
-    # 16 B per bin, 4 + 64 B per incidence
+    # the method's bytes: coordinates read twice (2 x 36 B per face), 16 B per bin, and per incidence
+    # the 4-byte id plus the face's 36 B of coordinates
     w = SimpleNamespace(dim=3, bins=4, n_faces=10)
     r = bench.bin_roofline(w, 15, 1e-3)
-    assert r["bytes"] == 720 + 240 + 16 * 64 + 68 * 15
+    assert r["bytes"] == 720 + 16 * 64 + 40 * 15
     assert abs(r["achieved"] - r["bytes"] / 1e-6 / 1e9) < 1e-9
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
-    # 2D: 32-byte entries
+    # the implementation's bytes beside it: bin ranges written and read (2 x 12 B per face), 4 + 64 B per
+    # incidence
+    assert r["impl_bytes"] == 720 + 240 + 16 * 64 + 68 * 15
+    assert r["impl_frac"] > r["frac"]
+    # 2D: 16 B of coordinates per face and incidence (32-byte entries in the implementation)
     w2 = SimpleNamespace(dim=2, bins=8, n_faces=5)
-    assert bench.bin_roofline(w2, 7, 1e-3)["bytes"] == 2 * 16 * 5 + 2 * 8 * 5 + 16 * 64 + 36 * 7
+    r2 = bench.bin_roofline(w2, 7, 1e-3)
+    assert r2["bytes"] == 2 * 16 * 5 + 16 * 64 + 20 * 7
+    assert r2["impl_bytes"] == 2 * 16 * 5 + 2 * 8 * 5 + 16 * 64 + 36 * 7
