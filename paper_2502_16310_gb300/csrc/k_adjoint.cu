@@ -11,8 +11,9 @@
 //
 // Determinism without float atomics: links are grouped by face with a stable
 // LSD radix sort (keys = face ids, values = link indices, so each face's links
-// stay in ascending link order); one thread per face accumulates its links'
-// contributions in that order (double-float sums).  For indexed input the face
+// stay in ascending link order); one warp per face accumulates its links'
+// contributions, lane j the links j, j + 32, ... of that order (double-float
+// sums), then a fixed shuffle tree adds the lanes.  For indexed input the face
 // corners are grouped by vertex the same way (once per load) and one thread
 // per vertex sums its corners in ascending (face, corner) order.
 #include "internal.cuh"
@@ -119,12 +120,18 @@ __constant__ int c_dirs19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0},  {0, 1,
                                     {0, 1, 1},  {0, -1, -1}, {0, 1, -1},  {0, -1, 1}};
 __constant__ int c_dirs9[9][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}, {1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
 
-// One thread per face: sum over its links (ascending link order) of
-// grad_q * dt/dv_k, written as grad_face[f][k][c].
+// One warp per face: lane j sums grad_q * dt/dv_k over the face's links j,
+// j + 32, ... of its ascending link list (double-float), then a fixed shuffle
+// tree adds the lanes' sums into lane 0, which writes grad_face[f][k][c].  The
+// order of every addition is fixed by the face's link list, so the result is
+// the same bit for bit on every run.
 template <int D>
-__global__ void k_face_grad(AdjointArgs a) {
+__global__ void __launch_bounds__(256) k_face_grad(AdjointArgs a) {
   constexpr int NC = D == 3 ? 64 : 16;
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.nf; f += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t f = w0; f < a.nf; f += nw) {
     float hi[D * D], lo[D * D];
 #pragma unroll
     for (int j = 0; j < D * D; ++j) hi[j] = lo[j] = 0.f;
@@ -133,8 +140,7 @@ __global__ void k_face_grad(AdjointArgs a) {
     for (int j = 0; j < D * D; ++j) V[j] = a.X[(int64_t)j * a.nf + f];
     const uint32_t b0 = a.face_off[f], b1 = a.face_off[f + 1];
     if (b1 == b0) {
-#pragma unroll
-      for (int j = 0; j < D * D; ++j) a.grad_face[(int64_t)f * D * D + j] = 0.f;
+      if (lane < D * D) a.grad_face[(int64_t)f * D * D + lane] = 0.f;
       continue;
     }
     // links of this face live on the finest level of its geometry
@@ -142,7 +148,7 @@ __global__ void k_face_grad(AdjointArgs a) {
     const int Lf = P.n_levels - 1;
     const FastGeom fg = fast_geom(P, Lf);
     const int32_t* blocks = a.level_blocks[Lf];
-    for (uint32_t s = b0; s < b1; ++s) {
+    for (uint32_t s = b0 + (uint32_t)lane; s < b1; s += 32u) {
       const uint32_t l = a.face_links[s];
       const float gq = a.grad_q[l];
       const uint32_t cellrow = a.link_cell[l];
@@ -196,8 +202,24 @@ __global__ void k_face_grad(AdjointArgs a) {
         acc2(hi[3], lo[3], gq * g1[1]);
       }
     }
+    // lanes' double-float sums into lane 0 (fixed tree)
 #pragma unroll
-    for (int j = 0; j < D * D; ++j) a.grad_face[(int64_t)f * D * D + j] = hi[j] + lo[j];
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int j = 0; j < D * D; ++j) {
+        const float ph = __shfl_down_sync(0xffffffffu, hi[j], o);
+        const float pl = __shfl_down_sync(0xffffffffu, lo[j], o);
+        acc2(hi[j], lo[j], ph);
+        lo[j] += pl;
+      }
+    }
+    float out = 0.f;
+#pragma unroll
+    for (int j = 0; j < D * D; ++j) {
+      const float v = __shfl_sync(0xffffffffu, hi[j] + lo[j], 0);
+      if (lane == j) out = v;
+    }
+    if (lane < D * D) a.grad_face[(int64_t)f * D * D + lane] = out;
   }
 }
 
@@ -286,10 +308,11 @@ int launch_count_keys(const uint32_t* keys, int64_t n, uint32_t* cnt, cudaStream
 
 int launch_face_grad(const AdjointArgs& a, cudaStream_t st) {
   if (a.nf <= 0) return 0;
+  // one warp per face, 8 warps per block
   if (a.dim == 3)
-    k_face_grad<3><<<grid_1d(a.nf, 128), 128, 0, st>>>(a);
+    k_face_grad<3><<<grid_1d(a.nf, 8), 256, 0, st>>>(a);
   else
-    k_face_grad<2><<<grid_1d(a.nf, 128), 128, 0, st>>>(a);
+    k_face_grad<2><<<grid_1d(a.nf, 8), 256, 0, st>>>(a);
   return 1;
 }
 
