@@ -41,8 +41,9 @@ L2_FLUSH_BYTES = 512 << 20
 OPS_BLOCK_CANDIDATE = 120.0   # face setup up to the AABB cull (vertex offsets, edges, three box axes)
 OPS_CELL_TEST = 80.0          # one cell against one (face, block) survivor: 13 axes x (projection + interval test)
 OPS_FACE_SETUP = 400.0        # face-by-face marking, per (face, level): cell range, frame, 13 axis intervals
-OPS_LINK_FACE = 150.0         # per (adjacent cell, face): double-float offsets, plane offset, cross products
-OPS_LINK_DIR = 40.0           # per (adjacent cell, face, direction): den, three edge signs, t
+OPS_LINK_DIR = 40.0           # per (adjacent cell, face, lattice direction): one watertight segment-triangle test
+OPS_LINK_FACE = 150.0         # per (adjacent cell, face), executed on top: double-float offsets, plane offset,
+                              # cross products and the line filters (reported beside the roofline, not in it)
 # DRAM bytes (read + write) per launch of the current kernels, from one ncu capture each
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the named workload; others report null
 MEASURED_TRAFFIC = {("c4", "links"): 3794712832 + 6534081536, ("c4", "refine_level"): 393028096 + 2277046272,
@@ -367,10 +368,11 @@ def run_classify(name, dev, flush, reps=5):
     out = g.fluid_links()
     b.record(st)
     torch.cuda.synchronize()
+    n_fluid = int(out["link_q"].shape[0])
     g.close()
     return {"workload": f"{name}: {w.description}", "cells": int(cls.numel()), "classify_ms": sum(ms) / len(ms),
             "solid_fraction": solid,
-            "winding_fallbacks": nfb, "links": n_links, "fluid_links": int(out["link_q"].shape[0]),
+            "winding_fallbacks": nfb, "links": n_links, "fluid_links": n_fluid,
             "fluid_links_ms": a.elapsed_time(b),
             "note": "classify/fluid_links times include their host round trip (one read-back each)"}
 
@@ -639,12 +641,17 @@ def roofline(name, k, w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks, n
         a = ops / t / 1e12
         return {"kernel": name, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s (FP32 pipe)",
                 "frac": a / alu_peak, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2070 MHz"}
-    if name in ("links", "adjacency"):
+    if name == "links":
+        # algorithmic work: one ~40-op watertight test per (adjacent cell, adjacent face, lattice direction)
         Q1 = 18 if w.dim == 3 else 8
-        if name == "links":
-            ops = n_pairs * (OPS_LINK_FACE + Q1 * OPS_LINK_DIR) / launches
-        else:
-            ops = (n_pairs * OPS_CELL_TEST * 0 + n_surv * NC * OPS_CELL_TEST) / launches
+        ops = n_pairs * Q1 * OPS_LINK_DIR / launches
+        a = ops / t / 1e12
+        ex = n_pairs * (OPS_LINK_FACE + Q1 * OPS_LINK_DIR) / launches / t / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s (FP32 pipe)",
+                "frac": a / alu_peak, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2070 MHz",
+                "ops_per_launch": ops, "with_per_pair_setup_tops": ex}
+    if name == "adjacency":
+        ops = n_surv * NC * OPS_CELL_TEST / launches
         a = ops / t / 1e12
         return {"kernel": name, "bound": "alu", "achieved": a, "peak": alu_peak, "unit": "Tops/s (FP32 pipe)",
                 "frac": a / alu_peak, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2070 MHz"}

@@ -48,6 +48,7 @@ struct TimingSlot {
 
 struct LevelBufs {
   DevBuf blocks, gid, parent, mask, flag, cellcnt, blockcnt, base, desc;
+  DevBuf first;           // per block: index of its first child in the next level, -1 without children
   DevBuf prev, n2o, o2n;  // previous call's blocks (kept on request) and the re-adaptation maps
   int64_t n_prev = 0;
   int64_t cap = 0;  // capacity in blocks
@@ -68,9 +69,11 @@ struct GraphKey {
   int64_t nf = 0, n_geom = 0;
   int n_levels = 0, lattice = 0, adjacency = 0, links = 0, warps = 0, B = 0, pred = 0, search = 0, prop = 0;
   uint64_t face_levels = 0;  // signature of the per-geometry choice of face by face
+  uint64_t bins = 0;         // signature of the bin grids (every geometry's density, sampled or exact)
   double d_abs = 0, d_rel = 0;
   bool operator==(const GraphKey& o) const {
     return layout_gen == o.layout_gen && nf == o.nf && n_geom == o.n_geom && n_levels == o.n_levels &&
+           bins == o.bins &&
            lattice == o.lattice && adjacency == o.adjacency && links == o.links && warps == o.warps && B == o.B &&
            pred == o.pred && search == o.search && prop == o.prop && face_levels == o.face_levels &&
            d_abs == o.d_abs && d_rel == o.d_rel;
@@ -481,7 +484,7 @@ void amr_ctx_free(amr_ctx* ctx) {
   for (int L = 0; L < AMR_MAX_LEVELS; ++L) {
     LevelBufs& l = ctx->lv[L];
     DevBuf* lb[] = {&l.blocks, &l.gid,  &l.parent, &l.mask, &l.flag, &l.cellcnt,
-                    &l.blockcnt, &l.base, &l.desc,   &l.prev, &l.n2o,  &l.o2n};
+                    &l.blockcnt, &l.base, &l.desc,   &l.prev, &l.n2o,  &l.o2n, &l.first};
     for (DevBuf* b : lb) release(ctx, *b);
   }
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
@@ -635,15 +638,6 @@ double face_cells(const amr_ctx* ctx, const GeomParams& g, int L, double ext, do
   return std::pow(ext * std::ldexp(1.0, L) + 2.0 * dh + pad, (double)ctx->dom.dim);
 }
 
-// Coordinate bits per axis of the block hash key: 21 for one geometry, else
-// what the geometry id leaves of 63 bits.
-int face_key_bits(const amr_ctx* ctx) {
-  if (!ctx->multi) return 21;
-  int gb = 1;
-  while (gb < 32 && ((size_t)1 << gb) < ctx->geoms.size()) ++gb;
-  return std::min(21, (63 - gb) / ctx->dom.dim);
-}
-
 Plan make_plan(const amr_ctx* ctx, const amr_refine_params* p) {
   Plan P{};
   for (const auto& g : ctx->geoms) P.NL = g.n_levels > P.NL ? g.n_levels : P.NL;
@@ -666,7 +660,6 @@ Plan make_plan(const amr_ctx* ctx, const amr_refine_params* p) {
 // the geometry rows, uploaded with the table); the plan's face_at / walk_at say
 // which of the two launches a level needs.  Returns a signature of the choice.
 uint64_t assign_face_levels(amr_ctx* ctx, Plan& P, const amr_refine_params* p) {
-  const int cb = face_key_bits(ctx);
   uint64_t sig = 1469598103934665603ull;
   for (size_t gi = 0; gi < ctx->geoms.size(); ++gi) {
     GeomParams& g = ctx->geoms[gi];
@@ -675,8 +668,6 @@ uint64_t assign_face_levels(amr_ctx* ctx, Plan& P, const amr_refine_params* p) {
     const double emean = gi < ctx->face_ext_mean.size() ? ctx->face_ext_mean[gi] : INFINITY;
     for (int L = 0; L < g.n_levels && p->face_pass != AMR_FACE_PASS_OFF; ++L) {
       bool ok = P.search == AMR_SEARCH_QUERY_BOX && (L < g.n_levels - 1 || !P.adjacency);
-      for (int c = 0; c < ctx->dom.dim && ok; ++c)
-        if (((int64_t)g.root[c] << L) >= (1ll << cb)) ok = false;
       ok = ok && face_cells(ctx, g, L, emax, 4.0) <= kMaxFaceCells;
       if (ok && p->face_pass == AMR_FACE_PASS_AUTO) ok = face_cells(ctx, g, L, emean, 1.0) <= kAutoFaceCells;
       if (ok) bits |= 1u << L;
@@ -801,32 +792,18 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
     RefineLevel a = level_args(ctx, P, L);
     CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), st));
     if (P.face_at[L]) {
-      // face by face: masks and flags start clear; deeper levels find their blocks through the hash
+      // face by face: masks and flags start clear; deeper levels find their blocks by descending
+      // from the roots through the upper levels' first-child arrays
       CK(cudaMemsetAsync(a.mask, 0, sizeof(uint64_t) * (size_t)(lb.cap > 0 ? lb.cap : 1), st));
       CK(cudaMemsetAsync(a.flag, 0, (size_t)(lb.cap > 0 ? lb.cap : 1), st));
       MarkArgs m{};
       m.lv = a;
       m.rec = static_cast<const FaceRec3*>(ctx->frec.p);
       m.face_gid = ctx->multi ? static_cast<const uint32_t*>(ctx->face_gid.p) : nullptr;
-      m.cb = face_key_bits(ctx);
+      for (int l = 0; l < L; ++l) m.first_child[l] = static_cast<const int32_t*>(ctx->lv[l].first.p);
       // faces per work fetch: enough warps to fill the GPU (24 resident per SM)
       const int64_t warps = (int64_t)ctx->num_sms * 24;
       m.batch = (int)std::max<int64_t>(1, std::min<int64_t>(kFaceBatch, ctx->nf / (2 * warps)));
-      if (L > 0) {
-        const uint32_t slots = propagate_hash_slots(lb.cap);
-        if (eager) {
-          TRY(ensure(ctx, ctx->hkeys, sizeof(unsigned long long) * slots));
-          TRY(ensure(ctx, ctx->hvals, sizeof(uint32_t) * slots));
-        }
-        m.keys = static_cast<const unsigned long long*>(ctx->hkeys.p);
-        m.vals = static_cast<const uint32_t*>(ctx->hvals.p);
-        m.hmask = slots - 1;
-        timed(ctx, st, "block_hash", [&] {
-          return launch_hash_build(D, a.blocks, a.gid, m.cb, lb.cap, a.n_dev,
-                                   static_cast<unsigned long long*>(ctx->hkeys.p), static_cast<uint32_t*>(ctx->hvals.p),
-                                   slots, ctx->d_err, st);
-        });
-      }
       if (a.blockcnt) CK(cudaMemsetAsync(a.blockcnt, 0, sizeof(uint64_t) * (size_t)(lb.cap > 0 ? lb.cap : 1), st));
       timed(ctx, st, "mark_faces", [&] { return launch_mark_faces(m, ctx->num_sms, st); });
       if (P.walk_at[L]) {
@@ -863,6 +840,7 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
         const size_t c1 = (size_t)(cap > 0 ? cap : 1);
         TRY(ensure(ctx, nx.blocks, sizeof(int32_t) * D * c1));
         TRY(ensure(ctx, nx.parent, sizeof(int32_t) * c1));
+        TRY(ensure(ctx, lb.first, sizeof(int32_t) * (size_t)(lb.cap > 0 ? lb.cap : 1)));
         if (ctx->multi) TRY(ensure(ctx, nx.gid, sizeof(uint32_t) * c1));
         TRY(ensure(ctx, ctx->scratch, children_scratch_bytes(lb.cap)));
       }
@@ -880,6 +858,7 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
       ca.child_blocks = static_cast<int32_t*>(nx.blocks.p);
       ca.child_gid = ctx->multi ? static_cast<uint32_t*>(nx.gid.p) : nullptr;
       ca.child_parent = static_cast<int32_t*>(nx.parent.p);
+      ca.first_child = static_cast<int32_t*>(lb.first.p);
       ca.cap_out = nx.cap;
       ca.total = ctx->d_scal + SC_N + L + 1;
       ca.err = ctx->d_err;
@@ -1021,6 +1000,7 @@ amr_status collect(amr_ctx* ctx, const Plan& P, cudaStream_t st, amr_refine_resu
   char* h = static_cast<char*>(ctx->h_pinned);
   // pinned layout: [0, 8 CNT_N) counters, 128 error word, 256 level pointers, 512 scalars
   static_assert(sizeof(unsigned long long) * CNT_N <= 128, "counters overlap the error word");
+  static_assert(kMaxLevels == AMR_MAX_LEVELS, "level arrays of the kernels and of the ABI agree");
   TRY(small_copy(ctx, st, {{ctx->h_dev, ctx->counters, sizeof(unsigned long long) * CNT_N},
                       {ctx->h_dev + 128, ctx->d_err, sizeof(unsigned)},
                       {ctx->h_dev + 512, ctx->d_scal, sizeof(uint64_t) * SC_WORDS}}));
@@ -1101,6 +1081,8 @@ amr_status amr_run_refine(amr_ctx* ctx, const amr_refine_params* prm, amr_refine
   key.search = prm->search;
   key.prop = prm->propagate;
   key.face_levels = face_sig;
+  key.bins = ctx->sampled_bins ? 1ull : 0ull;
+  for (const auto& g : ctx->geoms) key.bins = (key.bins ^ (uint64_t)g.B) * 1099511628211ull;
   const bool want_graph = prm->use_graph != 0;
   if (want_graph && ctx->gexec && ctx->gkey == key) {
     // replay on the graph stream, ordered after the caller's stream
@@ -1391,7 +1373,6 @@ amr_status group_by_key(amr_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n
   cudaStream_t st = ctx->stream;
   TRY(ensure(ctx, off, sizeof(uint32_t) * (size_t)(n_keys + 1)));
   TRY(ensure(ctx, grouped, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)));
-  TRY(ensure(ctx, ctx->sort_keys, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)));
   TRY(ensure(ctx, ctx->sort_scratch, radix_sort_scratch_bytes(n)));
   TRY(ensure(ctx, ctx->scratch, scan_u32_scratch_bytes(n_keys)));
   TRY(ensure(ctx, ctx->group_cnt, sizeof(uint32_t) * (size_t)(n_keys > 0 ? n_keys : 1)));
@@ -1400,7 +1381,7 @@ amr_status group_by_key(amr_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n
     int k = launch_count_keys(keys, n, static_cast<uint32_t*>(ctx->group_cnt.p), st);
     k += launch_scan_u32(static_cast<const uint32_t*>(ctx->group_cnt.p), static_cast<uint32_t*>(off.p), n_keys,
                          ctx->d_tot, ctx->scratch.p, ctx->d_err, st);
-    k += launch_stable_sort(keys, n, key_bits(n_keys), static_cast<uint32_t*>(ctx->sort_keys.p),
+    k += launch_stable_sort(keys, n, key_bits(n_keys), nullptr,
                             static_cast<uint32_t*>(grouped.p), nullptr, ctx->sort_scratch.p, ctx->d_tot, ctx->d_err,
                             st);
     return k;

@@ -14,6 +14,7 @@ constexpr double kBandRel = 1e-6;               // margin band of the adjacency 
 constexpr int kMaxFaces = 1 << 29;              // face ids keep 3 flag bits in the bin payload
 constexpr uint32_t kIdMask = (1u << 29) - 1u;
 constexpr long long kSpinLimit = 1ll << 24;     // bounded waits: iterations before giving up
+constexpr int kMaxLevels = 16;                  // grid levels at most (the C ABI's AMR_MAX_LEVELS)
 
 // device error word bits
 enum : unsigned {
@@ -474,17 +475,16 @@ inline bool refine_by_groups(int dim, int level, int pred, int search) {
 // Face-by-face marking of the blocks of a level whose only output is the mask
 // (box or point predicate, whole-domain search): lv.mask / lv.flag zeroed and
 // lv.work zeroed before the launch; blocks found through the level-0 root
-// order or, deeper, the block hash (keys / vals, hmask = slots - 1, key bits cb).
+// order or, deeper, by descending from the root through the first-child arrays.
 // With a geometry table (lv.table) every face reads its row through face_gid;
 // only faces whose geometry has this level's face_levels bit are marked.
 struct MarkArgs {
   RefineLevel lv;
   const FaceRec3* rec;  // 3D face records (2D reads lv.X)
   const uint32_t* face_gid;
-  const unsigned long long* keys;
-  const uint32_t* vals;
-  uint32_t hmask;
-  int cb;
+  // per level l < lv.level: the first-child index of each block (-1: none), so that a
+  // block of this level is found from its root by one step per level
+  const int32_t* first_child[kMaxLevels];
   int batch;            // faces a warp takes per work fetch (1..kFaceBatch)
 };
 constexpr int kFaceBatch = 8;  // most faces a warp takes per work fetch
@@ -534,6 +534,8 @@ struct ChildrenArgs {
   int32_t* child_blocks;
   uint32_t* child_gid;         // nullable
   int32_t* child_parent;
+  int32_t* first_child;        // nullable: per block of this level, the index of its first child in the
+                               // next level (its children follow in slot order), -1 without children
   int64_t cap_out;
   uint64_t* total;             // device: number of children (next level's count)
   unsigned* err;
@@ -643,7 +645,8 @@ struct AdjointArgs {
   float* grad_face;            // [nf][D][D]
 };
 size_t radix_sort_scratch_bytes(int64_t n);
-// Stable sort of n u32 keys (low key_bits significant); values default to 0..n-1.
+// Stable sort of n u32 keys (low key_bits significant); values default to 0..n-1
+// (vals_in null); sorted_keys may be null when only the values are wanted.
 int launch_stable_sort(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys, uint32_t* sorted_vals,
                        const uint32_t* vals_in, void* scratch, uint64_t* total, unsigned* err, cudaStream_t st);
 int launch_count_keys(const uint32_t* keys, int64_t n, uint32_t* cnt, cudaStream_t st);

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kRThreads) k_radix_hist(const uint32_t* __rest
 // Stable scatter of one tile: warp w owns keys [w*512, (w+1)*512) of the tile;
 // per-warp digit counts are prefixed across warps, then each warp walks its
 // keys 32 at a time in order, ranking equal digits with __match_any_sync.
+// vals_in null: the values are the keys' indices; keys_out null: keys not kept.
 __global__ void __launch_bounds__(kRThreads) k_radix_scatter(const uint32_t* __restrict__ keys_in,
                                                              const uint32_t* __restrict__ vals_in, int64_t n, int shift,
                                                              const uint32_t* __restrict__ offs, int64_t n_tiles,
@@ -82,13 +83,13 @@ __global__ void __launch_bounds__(kRThreads) k_radix_scatter(const uint32_t* __r
     uint32_t k = 0, v = 0, d = 0;
     if (ok) {
       k = keys_in[j];
-      v = vals_in[j];
+      v = vals_in ? vals_in[j] : (uint32_t)j;  // no input values: the key's own index
       d = (k >> shift) & (kRDigits - 1);
     }
     const unsigned peers = __match_any_sync(0xffffffffu, ok ? d : 0xffffffffu) & active;
     if (ok) {
       const uint32_t pos = cnt[wid][d] + __popc(peers & lt);
-      keys_out[pos] = k;
+      if (keys_out) keys_out[pos] = k;
       vals_out[pos] = v;
     }
     __syncwarp();
@@ -273,30 +274,24 @@ int launch_stable_sort(const uint32_t* keys, int64_t n, int key_bits, uint32_t* 
   uint32_t* vb = kb + n;
   void* scan_scr = reinterpret_cast<void*>(((uintptr_t)(vb + n) + 255) & ~(uintptr_t)255);
   int launches = 0;
-  cudaMemcpyAsync(ka, keys, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
-  if (vals_in) {
-    cudaMemcpyAsync(va, vals_in, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
-  } else {
-    k_iota<<<grid_1d(n), 256, 0, st>>>(va, n);
-    ++launches;
-  }
   int passes = (key_bits + kRBits - 1) / kRBits;
   if (passes < 1) passes = 1;
+  // the first pass reads the caller's keys (and values, or the indices), the last writes the
+  // caller's outputs; the passes between ping-pong through the scratch
+  const uint32_t* kin = keys;
+  const uint32_t* vin = vals_in;
   for (int p = 0; p < passes; ++p) {
     const int shift = p * kRBits;
-    k_radix_hist<<<(unsigned)tiles, kRThreads, 0, st>>>(ka, n, shift, hist, tiles);
+    const bool last = p == passes - 1;
+    uint32_t* kout = last ? sorted_keys : (p % 2 == 0 ? kb : ka);
+    uint32_t* vout = last ? sorted_vals : (p % 2 == 0 ? vb : va);
+    k_radix_hist<<<(unsigned)tiles, kRThreads, 0, st>>>(kin, n, shift, hist, tiles);
     launches += 1 + launch_scan_u32(hist, offs, nh, total, scan_scr, err, st);
-    k_radix_scatter<<<(unsigned)tiles, kRThreads, 0, st>>>(ka, va, n, shift, offs, tiles, kb, vb);
+    k_radix_scatter<<<(unsigned)tiles, kRThreads, 0, st>>>(kin, vin, n, shift, offs, tiles, kout, vout);
     ++launches;
-    uint32_t* t = ka;
-    ka = kb;
-    kb = t;
-    t = va;
-    va = vb;
-    vb = t;
+    kin = kout;
+    vin = vout;
   }
-  cudaMemcpyAsync(sorted_keys, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(sorted_vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
   return launches;
 }
 

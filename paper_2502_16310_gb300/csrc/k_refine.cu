@@ -1630,6 +1630,19 @@ __global__ void __launch_bounds__(kChThreads) k_children(ChildrenArgs a, uint64_
     }
     __syncthreads();
     uint64_t k = s_prefix + wex + incl - sum;
+    if (a.first_child) {
+      uint64_t kk = k;
+#pragma unroll
+      for (int i = 0; i < kChItems; ++i) {
+        const int64_t j = base + i;
+        if (j < n) {
+          const uint64_t o = kk * NCH;
+          if (fl[i] && o >= 0x7fffffffull) atomicOr(a.err, ERR_OVERFLOW);
+          a.first_child[j] = fl[i] ? (int32_t)o : -1;
+        }
+        kk += fl[i];
+      }
+    }
 #pragma unroll
     for (int i = 0; i < kChItems; ++i) {
       if (fl[i]) {
@@ -1894,13 +1907,19 @@ __global__ void __launch_bounds__(kMarkWarps * 32, 6) k_mark_faces(MarkArgs m) {
         if (lane == 0) atomicOr(a.err, ERR_OVERFLOW);
         continue;
       }
-      // index of the level's block with coordinates b, or -1 when the level does not have it
+      // index of the level's block with coordinates b, or -1 when the level does not have it: its
+      // root by the root order, then per level the ancestor's first child plus the slot (the
+      // coordinates' bit of that level per axis); the upper levels' arrays stay in cache
       auto find = [&](const int* b) -> int64_t {
-        if (a.level == 0) {
-          const int64_t i = P.root_base + b[0] + (int64_t)P.root[0] * (b[1] + (int64_t)P.root[1] * b[2]);
-          return i < nblk ? i : -1;
+        const int L = a.level;
+        int64_t i = P.root_base + (b[0] >> L) + (int64_t)P.root[0] * ((b[1] >> L) + (int64_t)P.root[1] * (b[2] >> L));
+        for (int l = 1; l <= L && i >= 0; ++l) {
+          const int sh = L - l;
+          const int slot = ((b[0] >> sh) & 1) | (((b[1] >> sh) & 1) << 1) | (D == 3 ? ((b[2] >> sh) & 1) << 2 : 0);
+          const int32_t c = __ldg(m.first_child[l - 1] + i);
+          i = c >= 0 ? (int64_t)c + slot : -1;
         }
-        return hash_find(m.keys, m.vals, m.hmask, block_key_g(gid, b, D, m.cb));
+        return i < nblk ? i : -1;
       };
       // the range's blocks: looked up once, one lane per block, when they fit the slots
       int blo[3] = {0, 0, 0}, nbk[3] = {1, 1, 1};

@@ -47,3 +47,13 @@ def test_bin_roofline_bytes():
     r2 = bench.bin_roofline(w2, 7, 1e-3)
     assert r2["bytes"] == 2 * 16 * 5 + 16 * 64 + 20 * 7
     assert r2["impl_bytes"] == 2 * 16 * 5 + 2 * 8 * 5 + 16 * 64 + 36 * 7
+
+
+def test_links_roofline_counts_the_survey_ops():
+    # 40 ops per (adjacent cell, face, lattice direction); the per-pair setup is reported beside it
+    w = SimpleNamespace(dim=3, bins=4, n_faces=10)
+    k = {"ms_per_step": 2.0, "launches_per_step": 1.0}
+    r = bench.roofline("links", k, w, {}, 0, 0, 0, 1000, [], {})
+    assert abs(r["achieved"] - 1000 * 18 * 40 / 2e-3 / 1e12) < 1e-12
+    assert r["with_per_pair_setup_tops"] > r["achieved"]
+    assert r["bound"] == "alu" and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
