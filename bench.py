@@ -258,7 +258,7 @@ def run_ours(args, rank, world, local):
     kern = {name: {"ms_per_step": v[0] / n_t, "launches_per_step": v[1] / n_t} for name, v in tk.items()}
     t_bin = sum(kern[k]["ms_per_step"] for k in ("bin_count", "bin_scan", "bin_scatter") if k in kern)
     t_refine = kern.get("refine_level", {}).get("ms_per_step", 0.0)
-    t_mark = sum(kern[k]["ms_per_step"] for k in ("mark_faces", "block_hash") if k in kern)
+    t_mark = kern.get("mark_faces", {}).get("ms_per_step", 0.0)
     dom = max(kern.items(), key=lambda kv: kv[1]["ms_per_step"])
     roof = roofline(dom[0], dom[1], w, kern, n_cand, n_surv, n_adj, n_pairs, blocks, clocks, n_fsetup, n_ftest)
     roof["traffic"] = MEASURED_TRAFFIC.get((args.workload, dom[0]))
@@ -609,7 +609,7 @@ def run_paper_setups(args, dev, flush, bins=(1, 2, 4, 6, 7, 8, 9, 10, 12, 14, 16
                 tk = g.timings()
                 g.timing(False)
                 t_bin = sum(tk[k][0] for k in ("bin_count", "bin_scan", "bin_scatter") if k in tk) / reps
-                t_det = sum(tk[k][0] for k in ("refine_level", "propagate", "mark_faces", "block_hash")
+                t_det = sum(tk[k][0] for k in ("refine_level", "propagate", "mark_faces")
                             if k in tk) / reps
                 r["bin_ms"].append(round(t_bin, 4))
                 r["detect_ms"].append(round(t_det, 4))

@@ -621,9 +621,9 @@ struct Plan {
 };
 
 // Face-by-face marking applies to a geometry's blocks of a level whose only
-// output is the mask, with the whole-domain search, block coordinates that fit
-// the hash key and faces whose cell ranges stay small (the geometry's largest
-// face of the last binning, widened by d, covers at most kMaxFaceCells cells).
+// output is the mask, with the whole-domain search, and faces whose cell ranges
+// stay small (the geometry's largest face of the last binning, widened by d,
+// covers at most kMaxFaceCells cells).
 constexpr double kMaxFaceCells = 32768.0;
 // Automatic choice: face by face where the geometry's mean face covers at most
 // this many cells of the level (the block walk is cheaper once faces span many cells).

@@ -113,3 +113,44 @@ def test_bin_payload_matches_ids_and_faces(kind):
         first = np.full(w.n_faces, np.iinfo(np.int64).max)
         np.minimum.at(first, ids.astype(np.int64), bc[:, a])
         assert np.array_equal(flag.astype(bool), bc[:, a] == first[ids]), a
+
+
+def test_caller_allocator_failure_is_enomem():
+    """An allocator that runs out (returns NULL) makes the call fail with AMR_ENOMEM; the context still
+    closes and hands back every buffer it got, and a later context works."""
+    import torch
+
+    from paper_2502_16310_gb300 import AmrError, AmrGeom
+    from paper_2502_16310_gb300 import binding as Bd
+
+    live, budget = {}, {"left": 6}
+
+    @Bd.DEV_ALLOC
+    def alloc(n, user):
+        if budget["left"] <= 0:
+            return None
+        budget["left"] -= 1
+        t = torch.empty(int(n), dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    @Bd.DEV_FREE
+    def free(p, user):
+        del live[p]
+
+    w = small_workload("bumpy3")
+    g, err = None, None
+    try:  # the budget runs out in the context's set-up or in one of the steps
+        g = AmrGeom(3, (w.root,) * 3, dev_alloc=alloc, dev_free=free)
+        g.load(torch.from_numpy(w.verts).cuda(), torch.from_numpy(w.idx).cuda())
+        g.bin(w.bins)
+        g.refine(w.n_levels, w.d_abs, w.d_rel, w.lattice, True, True)
+    except AmrError as ex:
+        err = ex
+    assert err is not None and err.status == Bd.AMR_ENOMEM
+    if g is not None:
+        g.close()
+    assert not live, "every buffer the context got went back"
+    ref = AmrGeom(3, (w.root,) * 3)
+    assert _refine_all(ref, w)["link_q"].size > 0
+    ref.close()
