@@ -46,8 +46,7 @@ OPS_LINK_FACE = 150.0         # per (adjacent cell, face), executed on top: doub
                               # cross products and the line filters (reported beside the roofline, not in it)
 # DRAM bytes (read + write) per launch of the current kernels, from one ncu capture each
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the named workload; others report null
-MEASURED_TRAFFIC = {("c4", "links"): 3794712832 + 6534081536, ("c4", "refine_level"): 393028096 + 2277046272,
-                    ("c2", "links"): 133.0e6}
+MEASURED_TRAFFIC = {("c4", "refine_level"): 393028096 + 2277046272}
 
 
 def parse_args(argv=None):

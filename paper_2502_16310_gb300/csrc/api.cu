@@ -106,7 +106,7 @@ struct amr_ctx {
   // buffers
   DevBuf X, nrm, frec, recs, hkeys, hvals, mkeys, mvals, cls, flbase, tl_cell, tl_dir, tl_q, tl_face, stage_a, stage_b, frange, count, offsets, ids, payload, scratch, misc, scal;
   LevelBufs lv[AMR_MAX_LEVELS];
-  DevBuf adj_cell, adj_off, adj_ids, link_cell, link_dir, link_q, link_face;
+  DevBuf adj_cell, adj_off, adj_ids, link_cell, link_dir, link_q, link_face, link_stage;
   int64_t cap_cells = 0, cap_pairs = 0, cap_links = 0;
   int64_t cap_recs = 0, want_recs = 0;  // survivor record staging (entries)
   bool sampled_bins = false;             // the last binning used the paper's sampled membership
@@ -476,7 +476,7 @@ void amr_ctx_free(amr_ctx* ctx) {
                    &ctx->tl_cell, &ctx->tl_dir, &ctx->tl_q, &ctx->tl_face, &ctx->nrm,          &ctx->stage_a,    &ctx->stage_b,    &ctx->frange,
                    &ctx->count,     &ctx->offsets,      &ctx->ids,        &ctx->payload,    &ctx->scratch,
                    &ctx->misc,      &ctx->scal,         &ctx->adj_cell,   &ctx->adj_off,    &ctx->adj_ids,
-                   &ctx->link_cell, &ctx->link_dir,     &ctx->link_q,     &ctx->link_face,  &ctx->idx,
+                   &ctx->link_cell, &ctx->link_dir,     &ctx->link_q,     &ctx->link_face,  &ctx->link_stage, &ctx->idx,
                    &ctx->vert_off,  &ctx->vert_corners, &ctx->face_off,   &ctx->face_links, &ctx->sort_keys,
                    &ctx->grad_face, &ctx->sort_scratch, &ctx->group_cnt,  &ctx->lvl_ptrs,   &ctx->table,
                    &ctx->face_gid,  &ctx->fstat,        &ctx->spill,      &ctx->calg,       &ctx->defer};
@@ -959,12 +959,14 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
               ctx->cap_links = nc;
             }
             TRY(ensure(ctx, ctx->scratch, links_scratch_bytes(ctx->cap_cells)));
+            TRY(ensure(ctx, ctx->link_stage, links_stage_bytes(ctx->cap_links)));
           }
           la.link_cell = static_cast<uint32_t*>(ctx->link_cell.p);
           la.link_dir = static_cast<uint8_t*>(ctx->link_dir.p);
           la.link_q = static_cast<float*>(ctx->link_q.p);
           la.link_face = static_cast<uint32_t*>(ctx->link_face.p);
           la.link_cap = ctx->cap_links;
+          la.stage = ctx->link_stage.p;
           timed(ctx, st, "links", [&] { return launch_links(la, ctx->scratch.p, ctx->num_sms, st); });
           if (!eager) break;
           CK(cudaGetLastError());

@@ -615,11 +615,14 @@ struct LinkArgs {
   float* link_q;
   uint32_t* link_face;
   int64_t link_cap;
+  void* stage;                 // staging area of links_stage_bytes(link_cap) bytes
   uint64_t* n_links;           // device: this level's link count
   unsigned long long* counters;
   unsigned* err;
 };
 size_t links_scratch_bytes(int64_t n_adj);
+size_t links_stage_bytes(int64_t cap_links);
+// Three kernels (links, the scan of the tiles' counts, placement); returns the launch count.
 int launch_links(const LinkArgs& a, void* scratch, int num_sms, cudaStream_t st);
 // close: adj_off[run[0] + cells] = run[1] + pairs (end marker of the level's rows);
 // else: run[0] += cells, run[1] += pairs, run[2] += links (n_links nullable).

@@ -15,8 +15,11 @@
 // in double-float from the face's double-float normal.  Per direction the
 // inside test is the sign of three sums of cross-product components, each
 // with a forward error bound; t = num / (h c_i.n) is accurate to a few ulps.
-// Undecided signs go to an FP64 evaluation.  Links leave in (cell, direction)
-// order through a single-pass ticketed look-back over thread blocks.
+// Undecided signs go to an FP64 evaluation.  Each tile of cells appends its
+// links, in (cell, direction) order, to a staging area at a position taken
+// from one counter; a scan of the per-tile counts in tile order then gives
+// every tile its place in the output, and a second kernel moves the links
+// there.  No tile waits for the tiles before it.
 #include <atomic>
 
 #include "internal.cuh"
@@ -148,6 +151,30 @@ __device__ __forceinline__ unsigned long long hit_key(float t, uint32_t f) {
   return ((unsigned long long)__float_as_uint(t) << 32) | f;
 }
 
+// A staged link in 64 bits: the FP32 bits of q (q <= 1, so below 2^30), the
+// direction (5 bits) and the face id (29 bits; face counts stay below 2^29).
+constexpr uint32_t kOneBits = 0x3f800000u;
+static_assert(kOneBits < (1u << 30), "q in [0, 1] fits 30 bits");
+static_assert(kMaxFaces <= (1 << 29), "face ids fit 29 bits");
+__device__ __forceinline__ unsigned long long stage_key(unsigned long long k, int dir) {
+  const uint32_t tb = (uint32_t)(k >> 32);
+  return ((unsigned long long)(tb < kOneBits ? tb : kOneBits) << 34) | ((unsigned long long)dir << 29) |
+         (k & ((1ull << 29) - 1));
+}
+
+// Per-launch bookkeeping of the tiles (all in the scratch buffer but the staging area).
+struct LinkTiles {
+  unsigned* ticket;              // next tile to take
+  unsigned long long* bump;      // staging entries claimed so far
+  uint64_t* n_tiles;             // tiles of this launch (written by block 0)
+  uint64_t* count;               // per tile: its links
+  uint64_t* start;               // per tile: its first staging entry
+  uint64_t* place;               // per tile: its first output entry past the level's start (scan of count)
+  unsigned long long* stage_key; // staged links (stage_key)
+  uint8_t* stage_row;            // their row within the tile
+  int64_t stage_cap;
+};
+
 // D3Q19 components packed two bits per direction (value + 1), for lanes that
 // each hold a different direction.
 __host__ __device__ constexpr uint64_t pack_dir_axis(int a) {
@@ -198,15 +225,18 @@ __device__ __forceinline__ uint32_t line_candidates(const float (&nh)[3], float 
 // queued in shared memory, are tested densely, each by the certified
 // per-direction test (FP64 when a sign is not certified); hits keep the
 // per-(cell, direction) minimum of (t, face) in shared memory.  Phase 2: one
-// thread per row counts its links; a block scan plus the ticketed look-back
-// give the output position, in (cell, direction) order.
+// thread per row counts its links; a block scan gives each row its place in
+// the tile's run of the staging area, claimed with one atomic per tile.
 template <int D>
-__global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state, unsigned* ticket) {
+__global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, LinkTiles lt) {
   constexpr int Q1 = D == 3 ? 18 : 8;
   constexpr int NC = D == 3 ? 64 : 16;
   constexpr int NW = kLThreads / 32;
   constexpr int NPR = D == 3 ? 32 : 1;
+  // per (direction, row) the least hit key, and per row the directions hit; both are back to
+  // empty (~0, 0) at the end of every tile, since phase 2 resets what it reads
   __shared__ unsigned long long s_key[Q1][kLRows];
+  __shared__ uint32_t s_mask[kLRows];
   __shared__ uint32_t s_off[kLRows + 1];
   constexpr uint32_t kRowCap = 1024;    // pairs of a tile whose row is tabulated (more: binary search)
   __shared__ uint8_t s_row[kRowCap];    // row of the tile's pair p0 + k
@@ -216,25 +246,28 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
   __shared__ uint16_t s_q[NW][D == 3 ? 32 * 18 : 1];
   __shared__ uint32_t s_warp[NW];
   __shared__ uint64_t s_prefix;
+  // a tile's links gathered for the store: keys in the pair records, rows in the queue
+  constexpr uint32_t kCompact = D == 3 ? (uint32_t)(sizeof(s_pr) / 8) : 0u;
+  static_assert(D == 2 || sizeof(s_q) >= sizeof(s_pr) / 8, "a row byte per gathered key");
   __shared__ unsigned s_tile, s_chunk;
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   const uint64_t row0 = a.run ? a.run[0] : 0ull;
-  const uint64_t link0 = a.run ? a.run[2] : 0ull;
   int64_t nrows = a.level_tot ? (int64_t)(*a.level_tot >> 32) : a.cap_rows;
   if ((int64_t)row0 + nrows > a.cap_rows) {
     if (blockIdx.x == 0 && tid == 0) atomicOr(a.err, ERR_OVERFLOW);
     nrows = a.cap_rows - (int64_t)row0 > 0 ? a.cap_rows - (int64_t)row0 : 0;
   }
   const int64_t ntiles = (nrows + kLRows - 1) / kLRows;
-  if (ntiles == 0) {
-    if (blockIdx.x == 0 && tid == 0) *a.n_links = 0;
-    return;
-  }
+  if (blockIdx.x == 0 && tid == 0) *lt.n_tiles = (uint64_t)ntiles;  // for the scan of the tile counts
+  if (ntiles == 0) return;
   unsigned long long n_fb = 0, n_band = 0, n_cand = 0;  // n_cand: warp-uniform
+#pragma unroll
+  for (int q = 0; q < Q1; ++q) s_key[q][tid] = ~0ull;
+  s_mask[tid] = 0u;
   for (;;) {
     if (tid == 0) {
-      s_tile = atomicAdd(ticket, 1u);
+      s_tile = atomicAdd(lt.ticket, 1u);
       s_chunk = 0u;
     }
     __syncthreads();
@@ -252,8 +285,6 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
         const uint32_t t0 = a.adj_off[first], e0 = a.adj_off[first + i], e1 = a.adj_off[first + i + 1];
         for (uint32_t e = e0; e < e1 && e - t0 < kRowCap; ++e) s_row[e - t0] = (uint8_t)i;
       }
-#pragma unroll
-      for (int q = 0; q < Q1; ++q) s_key[q][i] = ~0ull;
       if (i < nr) {
         const uint32_t id = a.adj_cell[first + i];
         const uint32_t blk = id / NC, bit = id % NC;
@@ -320,7 +351,10 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
             const int ci[2] = {c_d2q9[di][0], c_d2q9[di][1]};
             const LinkHit h = link_fp64_2(V, xc, ci, hL);
             if (h.band) ++n_band;
-            if (h.hit) atomicMin(&s_key[di - 1][r], hit_key((float)h.t, f));
+            if (h.hit) {
+              atomicMin(&s_key[di - 1][r], hit_key((float)h.t, f));
+              atomicOr(&s_mask[r], 1u << (di - 1));
+            }
           }
         } else {
           // stage 1
@@ -469,6 +503,7 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
               if (!(out && !unc)) {
                 if (!unc && all_in && sn > eps_num && sn + eps_num < hd * (1.0f - 8.0f * kU32)) {
                   atomicMin(&s_key[di - 1][rq], hit_key(num / (h32 * den), fq));
+                  atomicOr(&s_mask[rq], 1u << (di - 1));
                 } else {
                   // undecided signs: FP64 evaluation from the FP64 cell centre
                   const uint32_t id = a.adj_cell[first + rq];
@@ -482,7 +517,10 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
                   const LinkHit h = link_fallback_3(V, a.blocks + (int64_t)blk * 3, bit, o3, hL, di);
                   ++n_fb;
                   if (h.band) ++n_band;
-                  if (h.hit) atomicMin(&s_key[di - 1][rq], hit_key((float)h.t, fq));
+                  if (h.hit) {
+                    atomicMin(&s_key[di - 1][rq], hit_key((float)h.t, fq));
+                    atomicOr(&s_mask[rq], 1u << (di - 1));
+                  }
                 }
               }
             }
@@ -492,51 +530,58 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
       }
     }
     __syncthreads();
-    // phase 2: compaction in (cell, direction) order
-    uint32_t hits = 0;
-    if (tid < nr) {
-#pragma unroll
-      for (int q = 0; q < Q1; ++q) hits += s_key[q][tid] != ~0ull ? 1u : 0u;
-    }
+    // phase 2: the tile's links in (cell, direction) order
+    const uint32_t mask = s_mask[tid];  // rows past the tile's end have none
+    s_mask[tid] = 0u;
+    const uint32_t hits = __popc(mask);
     const uint32_t incl = warp_inclusive_scan<uint32_t>(hits);
     if (lane == 31) s_warp[wid] = incl;
     __syncthreads();
-    if (wid == 0) {
-      uint32_t w = lane < NW ? s_warp[lane] : 0u;
-      w = warp_inclusive_scan<uint32_t>(w);
-      if (lane < NW) s_warp[lane] = w;
-    }
-    __syncthreads();
-    const uint32_t wex = wid > 0 ? s_warp[wid - 1] : 0u;
-    if (wid == 0) {
-      const uint64_t agg = s_warp[NW - 1];
-      const uint64_t pre = lookback_warp(state, tile, agg, a.err);
-      if (lane == 0) {
-        s_prefix = pre;
-        if (tile == ntiles - 1) {
-          *a.n_links = pre + agg;
-          if ((int64_t)(link0 + pre + agg) > a.link_cap) atomicOr(a.err, ERR_OVERFLOW);
-        }
-      }
-    }
-    __syncthreads();
-    uint64_t pos = link0 + s_prefix + wex + incl - hits;
-    if (hits) {
+    uint32_t n = 0, loc = incl - hits;
 #pragma unroll
-      for (int q = 0; q < Q1; ++q) {
-        const unsigned long long k = s_key[q][tid];
-        if (k != ~0ull) {
-          if ((int64_t)pos < a.link_cap) {
-            a.link_cell[pos] = (uint32_t)(first + tid);
-            a.link_dir[pos] = (uint8_t)(q + 1);
-            a.link_q[pos] = __uint_as_float((uint32_t)(k >> 32));
-            a.link_face[pos] = (uint32_t)k;
-          }
-          ++pos;
+    for (int w = 0; w < NW; ++w) {
+      const uint32_t x = s_warp[w];
+      loc += w < wid ? x : 0u;
+      n += x;
+    }
+    if (tid == 0) {  // claim the tile's run of the staging area (read after the next barrier)
+      const unsigned long long off = n ? atomicAdd(lt.bump, (unsigned long long)n) : 0ull;
+      lt.count[tile] = n;
+      lt.start[tile] = off;
+      s_prefix = off;
+    }
+    if (n <= kCompact) {
+      // gather the run in shared memory (the pair records are free now), then store it
+      // with consecutive threads on consecutive entries
+      unsigned long long* ck = reinterpret_cast<unsigned long long*>(&s_pr[0][0]);
+      uint8_t* cr = reinterpret_cast<uint8_t*>(&s_q[0][0]);
+      for (uint32_t m = mask; m; m &= m - 1, ++loc) {
+        const int q = __ffs(m) - 1;
+        ck[loc] = stage_key(s_key[q][tid], q + 1);
+        cr[loc] = (uint8_t)tid;
+        s_key[q][tid] = ~0ull;
+      }
+      __syncthreads();
+      const uint64_t off = s_prefix;
+      for (uint32_t i = tid; i < n; i += kLThreads) {
+        if ((int64_t)(off + i) < lt.stage_cap) {
+          lt.stage_key[off + i] = ck[i];
+          lt.stage_row[off + i] = cr[i];
         }
       }
+    } else {
+      __syncthreads();
+      const uint64_t off = s_prefix;
+      for (uint32_t m = mask; m; m &= m - 1, ++loc) {
+        const int q = __ffs(m) - 1;
+        if ((int64_t)(off + loc) < lt.stage_cap) {
+          lt.stage_key[off + loc] = stage_key(s_key[q][tid], q + 1);
+          lt.stage_row[off + loc] = (uint8_t)tid;
+        }
+        s_key[q][tid] = ~0ull;
+      }
     }
-    __syncthreads();
+    __syncthreads();  // the gathered run, s_warp and s_prefix are reused by the next tile
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -547,6 +592,43 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, uint64_t* state
     if (n_fb) atomicAdd(&a.counters[CNT_LINK_FALLBACK], n_fb);
     if (n_band) atomicAdd(&a.counters[CNT_LINK_BAND], n_band);
     if (n_cand) atomicAdd(&a.counters[CNT_LINK_CAND], n_cand);
+  }
+}
+
+// Move each tile's staged links to its place in the output: a warp per tile,
+// lanes over its links, so reads and writes are both contiguous runs.
+__global__ void __launch_bounds__(256, 4) k_links_place(LinkArgs a, LinkTiles lt) {
+  const uint64_t row0 = a.run ? a.run[0] : 0ull;
+  const uint64_t link0 = a.run ? a.run[2] : 0ull;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)(link0 + *a.n_links) > a.link_cap) atomicOr(a.err, ERR_OVERFLOW);
+  const int64_t nt = (int64_t)*lt.n_tiles;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nt; t += nw) {
+    const uint64_t n = lt.count[t], src = lt.start[t], dst = link0 + lt.place[t];
+    const uint32_t first = (uint32_t)(row0 + (uint64_t)t * kLRows);
+    for (uint64_t j0 = 0; j0 < n; j0 += 4 * 32) {  // four loads in flight per lane
+      unsigned long long k[4];
+      uint32_t rw[4];
+      bool ok[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint64_t j = j0 + 32u * u + (uint64_t)lane;
+        ok[u] = j < n && (int64_t)(src + j) < lt.stage_cap && (int64_t)(dst + j) < a.link_cap;
+        k[u] = ok[u] ? lt.stage_key[src + j] : 0ull;
+        rw[u] = ok[u] ? lt.stage_row[src + j] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint64_t d = dst + j0 + 32u * u + (uint64_t)lane;
+        if (ok[u]) {
+          a.link_cell[d] = first + rw[u];
+          a.link_dir[d] = (uint8_t)((k[u] >> 29) & 31u);
+          a.link_q[d] = __uint_as_float((uint32_t)(k[u] >> 34));
+          a.link_face[d] = (uint32_t)(k[u] & ((1ull << 29) - 1));
+        }
+      }
+    }
   }
 }
 
@@ -571,13 +653,41 @@ __global__ void k_advance(const uint64_t* level_tot, const uint64_t* n_links, ui
 
 }  // namespace
 
-size_t links_scratch_bytes(int64_t n_adj) {
+namespace {
+constexpr size_t kLinkHead = 32;  // ticket, bump, tile count
+int64_t link_tiles(int64_t n_adj) {
   const int64_t tiles = (n_adj + kLRows - 1) / kLRows;
-  return 16 + (size_t)(tiles > 0 ? tiles : 1) * 8;
+  return tiles > 0 ? tiles : 1;
+}
+size_t align16(size_t n) { return (n + 15) & ~(size_t)15; }
+}  // namespace
+
+size_t links_scratch_bytes(int64_t n_adj) {
+  const int64_t tiles = link_tiles(n_adj);
+  return kLinkHead + align16(3 * sizeof(uint64_t) * (size_t)tiles) + scan_u64_scratch_bytes(tiles);
+}
+
+size_t links_stage_bytes(int64_t cap_links) {
+  const int64_t n = cap_links > 0 ? cap_links : 1;
+  return align16(sizeof(unsigned long long) * (size_t)n) + (size_t)n;
 }
 
 int launch_links(const LinkArgs& a, void* scratch, int num_sms, cudaStream_t st) {
-  cudaMemsetAsync(scratch, 0, links_scratch_bytes(a.cap_rows), st);
+  const int64_t cap_tiles = link_tiles(a.cap_rows);
+  char* base = static_cast<char*>(scratch);
+  LinkTiles lt{};
+  lt.ticket = reinterpret_cast<unsigned*>(base);
+  lt.bump = reinterpret_cast<unsigned long long*>(base + 8);
+  lt.n_tiles = reinterpret_cast<uint64_t*>(base + 16);
+  lt.count = reinterpret_cast<uint64_t*>(base + kLinkHead);
+  lt.start = lt.count + cap_tiles;
+  lt.place = lt.start + cap_tiles;
+  void* scan_scratch = base + kLinkHead + align16(3 * sizeof(uint64_t) * (size_t)cap_tiles);
+  const int64_t stage_cap = a.link_cap > 0 ? a.link_cap : 1;
+  lt.stage_key = static_cast<unsigned long long*>(a.stage);
+  lt.stage_row = static_cast<uint8_t*>(a.stage) + align16(sizeof(unsigned long long) * (size_t)stage_cap);
+  lt.stage_cap = a.link_cap;
+  cudaMemsetAsync(scratch, 0, kLinkHead, st);
   // persistent: as many blocks as fit on the GPU at once, tiles handed out by ticket
   // blocks per SM, asked once per dimension (contexts on several host threads may ask together)
   static std::atomic<int> occ[2] = {0, 0};
@@ -590,16 +700,19 @@ int launch_links(const LinkArgs& a, void* scratch, int num_sms, cudaStream_t st)
     if (o < 1) o = 1;
     occ[a.dim == 3 ? 1 : 0].store(o, std::memory_order_relaxed);
   }
-  int64_t tiles = (a.cap_rows + kLRows - 1) / kLRows;
-  if (tiles < 1) tiles = 1;
-  if (tiles > (int64_t)num_sms * o) tiles = (int64_t)num_sms * o;
-  unsigned* ticket = reinterpret_cast<unsigned*>(scratch);
-  uint64_t* state = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 16);
+  int64_t grid = cap_tiles;
+  if (grid > (int64_t)num_sms * o) grid = (int64_t)num_sms * o;
   if (a.dim == 3)
-    k_links<3><<<(unsigned)tiles, kLThreads, 0, st>>>(a, state, ticket);
+    k_links<3><<<(unsigned)grid, kLThreads, 0, st>>>(a, lt);
   else
-    k_links<2><<<(unsigned)tiles, kLThreads, 0, st>>>(a, state, ticket);
-  return 1;
+    k_links<2><<<(unsigned)grid, kLThreads, 0, st>>>(a, lt);
+  // the tiles' places (exclusive scan in tile order) and the level's link count
+  const int n_scan = launch_scan_u64(lt.count, lt.place, cap_tiles, lt.n_tiles, a.n_links, scan_scratch, a.err,
+                                     num_sms, st);
+  int64_t pg = (cap_tiles + 7) / 8;  // 8 warps per block, a warp per tile
+  if (pg > (int64_t)num_sms * 4) pg = (int64_t)num_sms * 4;  // resident at once
+  k_links_place<<<(unsigned)pg, 256, 0, st>>>(a, lt);
+  return 2 + n_scan;
 }
 
 int launch_advance(const uint64_t* level_tot, const uint64_t* n_links, uint64_t* run, uint32_t* adj_off,
