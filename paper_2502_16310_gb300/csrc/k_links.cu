@@ -265,14 +265,13 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, LinkTiles lt) {
 #pragma unroll
   for (int q = 0; q < Q1; ++q) s_key[q][tid] = ~0ull;
   s_mask[tid] = 0u;
+  // tiles by ticket; phase 2 of each tile takes the next ticket, so its latency is hidden
+  if (tid == 0) s_tile = atomicAdd(lt.ticket, 1u);
+  __syncthreads();
   for (;;) {
-    if (tid == 0) {
-      s_tile = atomicAdd(lt.ticket, 1u);
-      s_chunk = 0u;
-    }
-    __syncthreads();
     const long long tile = s_tile;
     if (tile >= ntiles) break;
+    if (tid == 0) s_chunk = 0u;
     const int64_t first = (int64_t)row0 + tile * (int64_t)kLRows;
     const int nr = (int)(nrows - tile * (int64_t)kLRows < kLRows ? nrows - tile * (int64_t)kLRows : kLRows);
     // phase 0 (kLThreads == kLRows: thread i owns row i)
@@ -531,6 +530,8 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, LinkTiles lt) {
     }
     __syncthreads();
     // phase 2: the tile's links in (cell, direction) order
+    unsigned next = 0u;
+    if (tid == 0) next = atomicAdd(lt.ticket, 1u);  // stored at the end of the phase
     const uint32_t mask = s_mask[tid];  // rows past the tile's end have none
     s_mask[tid] = 0u;
     const uint32_t hits = __popc(mask);
@@ -581,6 +582,7 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, LinkTiles lt) {
         s_key[q][tid] = ~0ull;
       }
     }
+    if (tid == 0) s_tile = next;
     __syncthreads();  // the gathered run, s_warp and s_prefix are reused by the next tile
   }
 #pragma unroll
