@@ -948,7 +948,10 @@ amr_status engine_pass(amr_ctx* ctx, const Plan& P, bool eager, bool slack, cuda
         la.err = ctx->d_err;
         for (int attempt = 0; attempt < 2; ++attempt) {
           if (eager) {
-            const int64_t want = run_links + (cells * 4 > 16 ? cells * 4 : 16);
+            // first guess: a quarter more links than (cell, face) pairs (the synthetic spheres have
+            // 1.1 per pair); a level with more re-runs once at its exact count
+            const int64_t guess = pairs + pairs / 4 + 1024;
+            const int64_t want = run_links + (guess > cells ? guess : cells);
             if (want > ctx->cap_links || attempt > 0) {
               const int64_t nc = attempt > 0 ? ctx->cap_links : want;
               const size_t keep = (size_t)run_links;

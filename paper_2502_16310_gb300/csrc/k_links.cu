@@ -424,7 +424,9 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, LinkTiles lt) {
             {
               const float Dl[9] = {nh[0], nh[1], nh[2], nh[0] + nh[1], nh[0] - nh[1], nh[0] + nh[2], nh[0] - nh[2],
                                    nh[1] + nh[2], nh[1] - nh[2]};
-              uint32_t drop = 0;
+              // s U < -e  <=>  fma(U, s, e) < 0 exactly (s = +-1, one rounding keeps the sign),
+              // so the least of the three edges' values decides the line
+              float lo[9];
 #pragma unroll
               for (int k = 0; k < 3; ++k) {
                 const float e1 = 8.0f * kU32 * 1.0f * M[k], e2 = 8.0f * kU32 * 2.0f * M[k];
@@ -432,13 +434,13 @@ __global__ void __launch_bounds__(kLThreads) k_links(LinkArgs a, LinkTiles lt) {
                                     C[k][0] + C[k][2], C[k][0] - C[k][2], C[k][1] + C[k][2], C[k][1] - C[k][2]};
 #pragma unroll
                 for (int l = 0; l < 9; ++l) {
-                  const float u = Dl[l] > 0.f ? U[l] : -U[l];
-                  if (u < -(l < 3 ? e1 : e2)) drop |= 1u << l;
+                  const float v = fmaf(U[l], Dl[l] > 0.f ? 1.0f : -1.0f, l < 3 ? e1 : e2);
+                  lo[l] = k == 0 ? v : fminf(lo[l], v);
                 }
               }
 #pragma unroll
               for (int l = 0; l < 9; ++l)
-                if (((drop >> l) & 1u) && fabsf(Dl[l]) > 4.0e-5f * nn2) cand &= ~(3u << (2 * l));
+                if (lo[l] < 0.0f && fabsf(Dl[l]) > 4.0e-5f * nn2) cand &= ~(3u << (2 * l));
             }
             if (cand) {
               float4* W = s_pr[wid][lane].q;
