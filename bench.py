@@ -46,7 +46,9 @@ OPS_LINK_FACE = 150.0         # per (adjacent cell, face), executed on top: doub
                               # cross products and the line filters (reported beside the roofline, not in it)
 # DRAM bytes (read + write) per launch of the current kernels, from one ncu capture each
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the named workload; others report null
-MEASURED_TRAFFIC = {("c4", "refine_level"): 393028096 + 2277046272}
+MEASURED_TRAFFIC = {("c4", "refine_level"): 393028096 + 2277046272,
+                    # the link step: k_links, the scan of its tile counts, k_links_place
+                    ("c4", "links"): 3767884032 + 4520228096 + 12329216 + 5006110976 + 6612879872}
 
 
 def parse_args(argv=None):
@@ -507,6 +509,26 @@ def run_batched(args, dev, flush):
             out.append(g.refine(w.n_levels, w.d_abs, w.d_rel, 19, True, True, use_graph=True))
         return out
 
+    # one geometry at a time first, then the batch: the two never hold their buffers together
+    for _ in range(3):
+        res = single()
+    gen = torch.Generator(dev).manual_seed(1)
+    wts = [torch.randn(int(r["link_q"].shape[0]), device=dev, generator=gen) for r in res]
+    wts_all = torch.cat(wts)
+
+    def single_adj():
+        single()
+        for g, wt in zip(ctxs, wts):
+            g.q_backward(wt)
+
+    t_single = _timed_steps(single, 5, flush, st)
+    single_adj()  # warm-up: every context's adjoint buffers
+    t_single_adj = _timed_steps(single_adj, 5, flush, st)
+    for g in ctxs:
+        g.close()
+    del res
+    torch.cuda.synchronize()
+
     b = AmrBatch(3)
     for w, (v, ix) in zip(ws, data):
         b.add(v, ix, w.root, w.n_levels, w.d_abs, w.d_rel, w.bins)
@@ -514,23 +536,13 @@ def run_batched(args, dev, flush):
     def batched():
         b.run(19, True, True, use_graph=True)
 
-    for _ in range(3):
-        res = single()
-        batched()
-    gen = torch.Generator(dev).manual_seed(1)
-    wts = [torch.randn(int(r["link_q"].shape[0]), device=dev, generator=gen) for r in res]
-    wts_all = torch.cat(wts)
-    assert wts_all.numel() == int(b.result.n_links), "batched and single runs differ in their link counts"
-
-    def single_adj():
-        single()
-        for g, wt in zip(ctxs, wts):
-            g.q_backward(wt)
-
     def batched_adj():
         batched()
         b.q_backward(wts_all)
 
+    for _ in range(3):
+        batched()
+    assert wts_all.numel() == int(b.result.n_links), "batched and single runs differ in their link counts"
     # near-wall cells of the whole set (from the batch's masks)
     r = b.result
     cells = 0
@@ -541,16 +553,7 @@ def run_batched(args, dev, flush):
         if n:
             m = _view(r.cell_mask[L], (n,), torch.int64)
             cells += int(lut[m.view(torch.uint8).long()].sum().item())
-    t_single = _timed_steps(single, 5, flush, st)
     t_batch = _timed_steps(batched, 5, flush, st)
-    single_adj()  # warm-up: every context's adjoint buffers
-    t_single_adj = _timed_steps(single_adj, 5, flush, st)
-    # the 48 single contexts hold their outputs and adjoint buffers: free them before the batch's adjoint
-    # allocates its own (the set has about 2.5e9 links)
-    for g in ctxs:
-        g.close()
-    del res
-    torch.cuda.synchronize()
     batched_adj()  # warm-up: the batch's adjoint buffers
     l0 = b.launch_count()
     t_batch_adj = _timed_steps(batched_adj, 5, flush, st)
