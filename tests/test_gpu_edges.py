@@ -64,6 +64,35 @@ def test_faces_outside_domain_and_degenerate():
     _oracle_check(w, out)
 
 
+def test_links_beyond_the_first_capacity_guess():
+    """A flat square just off the cell centres: about 5 links per cell next to it and 3 per (cell, face)
+    pair, so the first eager pass's link capacity (a quarter above the pair count) is too small and the
+    level's links are run again at their exact count; eager and graph-replay outputs agree with each
+    other and, on sampled rows, with the oracle."""
+    h = 1.0 / 128.0
+    z0 = 0.5 + 0.37 * h
+    v = np.array([[0.1, 0.1, z0], [0.9, 0.1, z0], [0.9, 0.9, z0], [0.1, 0.9, z0]], np.float32)
+    f = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    w = Workload("flat", 3, v, f, root=16, n_levels=2, bins=16, lattice=19)
+    out = U.run_gpu(w)
+    n_pairs, n_links = out["adj_ids"].shape[0], out["link_q"].shape[0]
+    assert n_links > n_pairs + n_pairs // 4 + 1024, (n_links, n_pairs)  # the re-run path ran
+    again = U.run_gpu(w, use_graph=True)
+    for k in ("adj_cell", "adj_off", "adj_ids", "link_cell", "link_dir", "link_face"):
+        assert np.array_equal(out[k], again[k]), k
+    assert np.array_equal(out["link_q"].view(np.uint32), again["link_q"].view(np.uint32))
+    from oracle.oracle import Domain, OracleGeometry
+
+    geo = OracleGeometry(3, w.verts, w.idx)
+    geo.bin(Domain.unit(3, w.root), w.bins)
+    lv = out["levels"]
+    rng = np.random.default_rng(5)
+    U.compare_adjacency(geo, 3, 1, lv[1]["blocks"], lv[1]["mask"], out["adj_cell"], out["adj_off"], out["adj_ids"],
+                        sample=300, rng=rng, d_abs=w.d_abs, d_rel=w.d_rel)
+    U.compare_links(geo, 3, 1, 19, lv[1]["blocks"], out["adj_cell"], out["link_cell"], out["link_dir"],
+                    out["link_q"], out["link_face"], sample=400, rng=rng, d_abs=w.d_abs, d_rel=w.d_rel)
+
+
 def test_2d_naive_bins_and_half_cell_distance():
     w = small_workload("circle")
     w.d_rel = 0.5  # the smallest near-wall distance links allow
