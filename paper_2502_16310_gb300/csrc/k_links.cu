@@ -9,13 +9,14 @@
 // box, so no other face can be met).  Coplanar segments miss; ties keep the
 // smallest face id.
 //
-// One thread per adjacent cell.  Per face the thread forms the vertex offsets
-// from the cell centre as exact double-float pairs, the three edge cross
-// products (shared by all directions) and the plane offset num = n.(v0 - x)
-// in double-float from the face's double-float normal.  Per direction the
-// inside test is the sign of three sums of cross-product components, each
-// with a forward error bound; t = num / (h c_i.n) is accurate to a few ulps.
-// Undecided signs go to an FP64 evaluation.  Each tile of cells appends its
+// Blocks take tiles of adjacent cells, and a lane one (cell, face) pair of a
+// tile at a time.  Per pair the lane forms the vertex offsets from the cell
+// centre as exact double-float pairs, the three edge cross products (shared by
+// all directions) and the plane offset num = n.(v0 - x) in double-float from
+// the face's double-float normal.  Per direction the inside test is the sign
+// of three sums of cross-product components, each with a forward error bound;
+// t = num / (h c_i.n) is accurate to a few ulps.  Undecided signs go to an
+// FP64 evaluation.  Each tile of cells appends its
 // links, in (cell, direction) order, to a staging area at a position taken
 // from one counter; a scan of the per-tile counts in tile order then gives
 // every tile its place in the output, and a second kernel moves the links
