@@ -93,6 +93,45 @@ def test_links_beyond_the_first_capacity_guess():
                     out["link_q"], out["link_face"], sample=400, rng=rng, d_abs=w.d_abs, d_rel=w.d_rel)
 
 
+def _wall_grid(lo, hi, h, n_walls, off):
+    """Axis-aligned square walls, each two triangles spanning [lo, hi]^2 in the other two axes, at
+    coordinates (i + off) h for the given wall indices, in all three axes."""
+    tris = []
+    for axis in range(3):
+        u, v = [(axis + 1) % 3, (axis + 2) % 3]
+        for i in n_walls:
+            c = (i + off) * h
+            corners = []
+            for a, b in ((lo, lo), (hi, lo), (hi, hi), (lo, hi)):
+                p = [0.0, 0.0, 0.0]
+                p[axis], p[u], p[v] = c, a, b
+                corners.append(p)
+            tris += [[corners[0], corners[1], corners[2]], [corners[0], corners[2], corners[3]]]
+    t = np.array(tris, np.float32)
+    return t.reshape(-1, 3), np.arange(t.shape[0] * 3, dtype=np.int32).reshape(-1, 3)
+
+
+def test_links_dense_tile():
+    """Walls between every pair of neighbouring cell centres in all three axes: every inner cell has all
+    18 links, so a tile of 128 cells holds more links than the link kernel gathers in shared memory
+    (1,792) and stores them directly; the outputs agree with the oracle on sampled rows."""
+    h = 1.0 / 64.0
+    v, f = _wall_grid(0.36, 0.64, h, range(23, 40), 0.87)
+    w = Workload("walls", 3, v, f, root=8, n_levels=2, bins=16, lattice=19)
+    out = U.run_gpu(w)
+    per_tile = np.bincount(out["link_cell"].astype(np.int64) // 128)
+    assert per_tile.max() > 1792, per_tile.max()
+    assert np.all(np.diff(out["link_cell"].astype(np.int64) * 32 + out["link_dir"]) > 0)
+    from oracle.oracle import Domain, OracleGeometry
+
+    geo = OracleGeometry(3, w.verts, w.idx)
+    geo.bin(Domain.unit(3, w.root), w.bins)
+    lv = out["levels"]
+    rng = np.random.default_rng(6)
+    U.compare_links(geo, 3, 1, 19, lv[1]["blocks"], out["adj_cell"], out["link_cell"], out["link_dir"],
+                    out["link_q"], out["link_face"], sample=300, rng=rng, d_abs=w.d_abs, d_rel=w.d_rel)
+
+
 def test_2d_naive_bins_and_half_cell_distance():
     w = small_workload("circle")
     w.d_rel = 0.5  # the smallest near-wall distance links allow
