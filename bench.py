@@ -295,6 +295,7 @@ def run_ours(args, rank, world, local):
     if not args.no_e2e:
         line["e2e"] = run_e2e(w, args, dev)
         line["e2e"]["single_stream"] = run_e2e_single_stream(w, args, dev)
+        line["e2e"]["host_link"] = host_link_rates(dev)
     g.close()
     if not args.no_extras and world == 1:
         line["classify"] = run_classify("c2", dev, flush)
@@ -850,6 +851,27 @@ def run_e2e(w, args, dev):
             "note": f"host wall clock over K steps: load(pinned host) -> bin -> refine -> D2H of every output to "
                     f"pinned host; {NT} host thread(s), each taking its steps in turn on {NC} context(s) with "
                     f"a stream each, so steps overlap on the GPU (the device-side value times one stream)"}
+
+
+def host_link_rates(dev, nbytes=1 << 30, reps=3):
+    """Device-to-pinned-host and pinned-host-to-device copy rates of this machine (one stream, best of a few
+    1 GiB copies): the host link the e2e copies run over, which varies between boxes."""
+    import torch
+
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    out = {}
+    for name, dst, src in (("d2h_gbps", h, d), ("h2d_gbps", d, h)):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        out[name] = nbytes / best / 1e9
+    del d, h
+    return out
 
 
 def run_e2e_single_stream(w, args, dev):
