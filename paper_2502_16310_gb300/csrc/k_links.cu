@@ -609,22 +609,34 @@ __global__ void __launch_bounds__(256, 4) k_links_place(LinkArgs a, LinkTiles lt
   const int64_t nt = (int64_t)*lt.n_tiles;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nt; t += nw) {
-    const uint64_t n = lt.count[t], src = lt.start[t], dst = link0 + lt.place[t];
+  int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint64_t nn = 0, ns = 0, np = 0;  // the next tile's count, start and place, loaded a tile ahead
+  if (t < nt) {
+    nn = lt.count[t];
+    ns = lt.start[t];
+    np = lt.place[t];
+  }
+  for (; t < nt; t += nw) {
+    const uint64_t n = nn, src = ns, dst = link0 + np;
+    if (t + nw < nt) {
+      nn = lt.count[t + nw];
+      ns = lt.start[t + nw];
+      np = lt.place[t + nw];
+    }
     const uint32_t first = (uint32_t)(row0 + (uint64_t)t * kLRows);
-    for (uint64_t j0 = 0; j0 < n; j0 += 4 * 32) {  // four loads in flight per lane
-      unsigned long long k[4];
-      uint32_t rw[4];
-      bool ok[4];
+    for (uint64_t j0 = 0; j0 < n; j0 += 8 * 32) {  // eight loads in flight per lane
+      unsigned long long k[8];
+      uint32_t rw[8];
+      bool ok[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const uint64_t j = j0 + 32u * u + (uint64_t)lane;
         ok[u] = j < n && (int64_t)(src + j) < lt.stage_cap && (int64_t)(dst + j) < a.link_cap;
         k[u] = ok[u] ? lt.stage_key[src + j] : 0ull;
         rw[u] = ok[u] ? lt.stage_row[src + j] : 0u;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const uint64_t d = dst + j0 + 32u * u + (uint64_t)lane;
         if (ok[u]) {
           a.link_cell[d] = first + rw[u];
