@@ -48,7 +48,7 @@ OPS_LINK_FACE = 150.0         # per (adjacent cell, face), executed on top: doub
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the named workload; others report null
 MEASURED_TRAFFIC = {("c4", "refine_level"): 393028096 + 2277046272,
                     # the link step: k_links, the scan of its tile counts, k_links_place
-                    ("c4", "links"): 3767884032 + 4520228096 + 12329216 + 5006110976 + 6612879872}
+                    ("c4", "links"): 3768263936 + 4520397312 + 12329216 + 5083136000 + 6614900736}
 
 
 def parse_args(argv=None):
