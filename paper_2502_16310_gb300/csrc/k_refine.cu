@@ -1378,14 +1378,16 @@ __host__ __device__ constexpr uint32_t pow2_floor(uint32_t x) {
 template <int D, int PRED, int MODE>
 __device__ __forceinline__ void emit_block(const EmitArgs& a, unsigned blk, uint32_t gid, WarpSmem<D>& sm,
                                            uint32_t& phase, WarpCounters& wc, uint64_t* rm, uint32_t* rf,
-                                           int lane, uint64_t run_cells, uint64_t run_pairs) {
+                                           int lane, uint64_t run_cells, uint64_t run_pairs,
+                                           const uint64_t* pre = nullptr) {
+  // pre (MODE 0): the block's base and record descriptor, loaded with its batch
   constexpr int NC = D == 3 ? 64 : 16;
     const GeomParams& P = a.lv.table ? a.lv.table[gid] : a.lv.g0;
     if (a.lv.level != P.n_levels - 1) return;
     int b[3] = {0, 0, 0};
 #pragma unroll
     for (int c = 0; c < D; ++c) b[c] = a.lv.blocks[(int64_t)blk * D + c];
-    const uint64_t base = a.block_base[blk];
+    const uint64_t base = pre ? pre[0] : a.block_base[blk];
     const uint64_t pair_base = run_pairs + (base & 0xffffffffull);
     const uint64_t cell_base = run_cells + (base >> 32);
     const uint32_t n0 = lane < NC ? a.lv.cellcnt[(int64_t)blk * NC + lane] : 0u;
@@ -1439,7 +1441,7 @@ __device__ __forceinline__ void emit_block(const EmitArgs& a, unsigned blk, uint
         }
       }
     };
-    const uint64_t desc = a.lv.recs ? a.lv.rec_desc[blk] : ~0ull;
+    const uint64_t desc = pre ? pre[1] : (a.lv.recs ? a.lv.rec_desc[blk] : ~0ull);
     constexpr uint32_t kSortRecs = pow2_floor(sort_region_bytes<D>() / 12);  // key + payload per record
     constexpr uint32_t kSortKeys = pow2_floor(sort_region_bytes<D>() / 4);
     if constexpr (MODE == 0) {
@@ -1546,12 +1548,18 @@ __global__ void __launch_bounds__(256) k_adjacency(EmitArgs a) {
       const bool in_range = (int64_t)base + lane < n;
       const uint64_t my_mask = in_range ? a.lv.mask[base + lane] : 0ull;
       const uint32_t my_gid = in_range && a.lv.gid ? a.lv.gid[base + lane] : 0u;
-      unsigned todo = __ballot_sync(0xffffffffu, my_mask != 0);
+      // the marked blocks' row bases and record descriptors, one coalesced load for the batch
+      const bool marked = my_mask != 0;
+      const uint64_t my_base = marked ? a.block_base[base + lane] : 0ull;
+      const uint64_t my_desc = marked && a.lv.recs ? a.lv.rec_desc[base + lane] : ~0ull;
+      unsigned todo = __ballot_sync(0xffffffffu, marked);
       while (todo) {
         const int q = __ffs(todo) - 1;
         todo &= todo - 1;
         const uint32_t gid = __shfl_sync(0xffffffffu, my_gid, q);
-        emit_block<D, PRED, MODE>(a, base + (unsigned)q, gid, sm, phase, wc, rm, rf, lane, run_cells, run_pairs);
+        const uint64_t pre[2] = {__shfl_sync(0xffffffffu, my_base, q), __shfl_sync(0xffffffffu, my_desc, q)};
+        emit_block<D, PRED, MODE>(a, base + (unsigned)q, gid, sm, phase, wc, rm, rf, lane, run_cells, run_pairs,
+                                  pre);
       }
     }
   } else {
